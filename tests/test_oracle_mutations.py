@@ -1,0 +1,97 @@
+"""Planted mistakes in the oracle must be caught by its pins (CPU only).
+
+Each case patches one plausible error into the oracle (a flipped sign, a dropped
+factor, a transposed link, a wrong recurrence sign) and checks that at least
+one pin of ``test_oracle_pins`` then fails.
+"""
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import wilson as W
+import test_oracle_pins as P
+
+
+def _medium():
+    p = P._params(4, 8, kappa_s=0.075, xi=3.5)
+    return p, S.random_gauge(4, 8, 0.3, 21), S.gaussian_source(4, 8, 22)
+
+
+def _small():
+    p = P._params(2, 4)
+    return p, S.random_gauge(2, 4, 0.3, 11), S.gaussian_source(2, 4, 12)
+
+
+def test_flipped_wrap_sign_is_caught(monkeypatch):
+    orig = W._vw
+
+    def bad(U, p):
+        V, Wm = orig(U, p)
+        return -V, Wm
+
+    monkeypatch.setattr(W, "_vw", bad)
+    with pytest.raises(AssertionError):
+        P.test_Tinv_matches_dense_inverse(-1)
+    with pytest.raises(AssertionError):
+        P.test_temporal_factorisation(_medium())
+
+
+def test_backsub_sign_of_app_b_is_caught(monkeypatch):
+    """The recurrence as printed in App. B (chi - U psi) is not T_0's inverse."""
+
+    def bad(U0, rhs, mu):
+        T = rhs.shape[W.AX_T]
+        chi = np.zeros_like(rhs)
+        chi[W._t_index(chi, T - 1)] = rhs[W._t_index(rhs, T - 1)] / mu
+        for t in range(T - 2, -1, -1):
+            chi[W._t_index(chi, t)] = (rhs[W._t_index(rhs, t)] - W.colour(U0[t], chi[W._t_index(chi, t + 1)])) / mu
+        return chi
+
+    monkeypatch.setattr(W, "T0_backsub", bad)
+    with pytest.raises(AssertionError):
+        P.test_Tinv_matches_dense_inverse(1)
+
+
+def test_dropped_projector_half_is_caught(monkeypatch):
+    def bad(U, psi, mu, bc):
+        Umu = W.link(U, mu)
+        fwd = W.colour(Umu, W.shift(psi, mu, +1, bc))
+        bwd = W.colour(W.dag(W.shift(Umu, mu, -1, 1.0)), W.shift(psi, mu, -1, bc))
+        return W.spin(W.I4 - W.GAMMA[mu], fwd) + W.spin(W.I4 + W.GAMMA[mu], bwd)
+
+    monkeypatch.setattr(W, "hop", bad)
+    with pytest.raises(AssertionError):
+        P.test_free_field_momentum_space()
+
+
+def test_untransposed_backward_link_is_caught(monkeypatch):
+    def bad(U, psi, mu, bc):
+        Umu = W.link(U, mu)
+        fwd = W.colour(Umu, W.shift(psi, mu, +1, bc))
+        bwd = W.colour(W.shift(Umu, mu, -1, 1.0), W.shift(psi, mu, -1, bc))
+        return W.spin(0.5 * (W.I4 - W.GAMMA[mu]), fwd) + W.spin(0.5 * (W.I4 + W.GAMMA[mu]), bwd)
+
+    monkeypatch.setattr(W, "hop", bad)
+    with pytest.raises(AssertionError):
+        P.test_gamma5_hermiticity(_medium())
+
+
+def test_wrong_schur_sign_is_caught(monkeypatch):
+    def bad(U, psi_o, p, par3=None):
+        if par3 is None:
+            par3 = W.parity3(p.L, p.T)
+        x = W.restrict(psi_o, par3 == 1)
+        return x + W.Dbar_s(U, W.Dbar_s(U, x, p, 0, par3), p, 1, par3) / p.gamma_f ** 2
+
+    monkeypatch.setattr(W, "M_hat", bad)
+    with pytest.raises(AssertionError):
+        P.test_Mhat_is_dense_schur_complement(_small())
+    with pytest.raises(AssertionError):
+        P.test_tprec_full_block_form(_medium())
+
+
+def test_swapped_projectors_in_CL_is_caught(monkeypatch):
+    monkeypatch.setattr(W, "C_L", lambda U, psi, p: W.spin(W.P_MINUS, psi) + W.spin(W.P_PLUS, W.Tinv(U, psi, p)))
+    with pytest.raises(AssertionError):
+        P.test_temporal_factorisation(_medium())
