@@ -1,0 +1,138 @@
+/*
+ * wf.h -- C ABI of libwf: the temporally preconditioned anisotropic Wilson operator
+ * and its Krylov solve on one GPU (sm_103a), after B. Joo, R. G. Edwards and
+ * M. J. Peardon, "An anisotropic preconditioning for the Wilson fermion matrix on
+ * the lattice", arXiv 0910.0992.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: L^3 x T sites, spatially periodic; time boundary sign bc = +1 (periodic)
+ *   or -1 (antiperiodic). L must be even and >= 2; 2 <= T <= 128.
+ * Operator: the paper's Wilson matrix (§II, Eq. for M with A = 0)
+ *       M = mu - D_t - D_s / gamma_f,   mu = 1 / (2 kappa_t),   gamma_f = kappa_t / kappa_s,
+ *   i.e. 1/(2 kappa_t) times the hopping-parameter form; D_t and D_s are the temporal
+ *   and spatial hopping terms with projectors (1 -+ gamma_mu)/2 (§II, Eqs. for D_t, D_s).
+ * Spin basis: Euclidean Dirac-Pauli, gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *   gamma_t = diag(1, 1, -1, -1), gamma_5 = gamma_x gamma_y gamma_z gamma_t; so P_+ = (1 + gamma_t)/2
+ *   keeps spins 0-1 and P_- spins 2-3 (§II.C, "Dirac-Pauli spin basis").
+ * Temporal wrap: T[N_t-1, 0] = -bc U_t(N_t-1) (§II.A; the printed form of this entry is
+ *   garbled, this reading makes mu - D_t = C_L^-1 C_R^-1 hold).
+ * Arrays (all complex128, interleaved re/im, C order):
+ *   gauge   U[t][z][y][x][mu][row][col], mu = 0, 1, 2, 3 for x, y, z, t; links must be SU(3).
+ *   spinor  psi[rhs][t][z][y][x][spin][colour]                 ("full field")
+ *   half    psi[rhs][t][k][spin][colour], k the index of the site among the sites of one
+ *           3-D parity p3 = (x + y + z) mod 2 in lexicographic order: k = (x >> 1) + (L/2)(y + L z)
+ *           ("odd field" when p3 = 1).
+ * Pointers: every array argument may be host or device memory; the library tells them apart
+ *   (cudaPointerGetAttributes) and copies host arrays in and out itself. Input and output
+ *   must not overlap. The library never keeps a caller pointer after a call returns.
+ * Streams: all device work is ordered on the handle's stream (wf_set_stream); every call
+ *   returns only when its results are complete (calls are synchronous for status).
+ * Errors: every int-returning call returns WF_OK or one of the codes below and records a
+ *   message readable with wf_last_error. No C++ exception crosses the ABI.
+ */
+#ifndef WF_H
+#define WF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wf_handle wf_handle_t;
+
+enum wf_status {
+  WF_OK = 0,
+  WF_EINVAL = 1,     /* invalid argument: sizes, parameters, pointers, no gauge loaded */
+  WF_ENOMEM = 2,     /* device allocation failed */
+  WF_ECUDA = 3,      /* a CUDA runtime call failed */
+  WF_ESINGULAR = 4,  /* the temporal preconditioner does not exist: det(1 - bc mu^-T P) ~ 0 */
+  WF_ENOCONV = 5,    /* solver stopped at its iteration limit; outputs are still written */
+  WF_ENAN = 6,       /* NaN or Inf met in a norm during a solve */
+  WF_ETIMEOUT = 7    /* reserved for bounded device-side waits */
+};
+
+enum wf_method {
+  WF_UNPREC = 0,         /* CGNR on M */
+  WF_EO4D = 1,           /* CGNR on the 4-D Schur (even-odd) operator (§II.B, 4D-Schur) */
+  WF_TEMPORAL = 2,       /* CGNR on C_L M C_R (§II.A) */
+  WF_TEMPORAL_SCHUR = 3  /* CGNR on M-hat = 1 - gamma_f^-2 D-bar^oe D-bar^eo (§II.B, Eq. TPrecFull) */
+};
+
+enum wf_precision {
+  WF_FP64 = 0,  /* every operator apply in FP64 */
+  WF_FP32 = 1   /* FP32 operator applies, FP64 reliable updates and true residual */
+};
+
+#define WF_X0 1 /* wf_solve flag: x holds the initial guess on entry */
+
+/* Create a handle for an L^3 x T lattice (§II). kappa_t <= 0 selects kappa_t = xi * kappa_s.
+ * bc = +1 or -1. Allocates the gauge storage on the current device. Returns WF_EINVAL for
+ * odd or too small L, T outside [2, 128], kappa_s <= 0 or bc not +-1. */
+int wf_create(int L, int T, double xi, double kappa_s, double kappa_t, int bc, wf_handle_t** out);
+
+/* Release the handle and all its device memory. Null is accepted. */
+int wf_destroy(wf_handle_t* h);
+
+/* Order all later device work of h on this CUDA stream (a cudaStream_t; 0 = legacy default). */
+int wf_set_stream(wf_handle_t* h, void* stream);
+
+/* Message of the last error on h (never null; empty after success). */
+const char* wf_last_error(const wf_handle_t* h);
+
+/* Sizes of the arrays the handle works on: complex128 elements per right-hand side. */
+long long wf_field_elems(const wf_handle_t* h);  /* full field: 12 L^3 T */
+long long wf_half_elems(const wf_handle_t* h);   /* one parity: 6 L^3 T  */
+
+/* Load a gauge field (layout above). The library copies it (FP64 master, FP32 shadow, links
+ * split into U_t and spatial links by 3-D parity) and builds, per spatial site, the SMW
+ * wrap-around matrices Lambda = (1 - bc mu^-T P)^-1 of T^-1 and its counterpart for T^-dag
+ * (§II.A, step 1: X(0) = -bc mu^-T P with P the Polyakov product, Lambda = (I + W^dag X)^-1).
+ * Returns WF_ESINGULAR if some |det(1 - bc mu^-T P)| < 1e-12. */
+int wf_load_gauge(wf_handle_t* h, const double* U);
+
+/* out = M in (dagger = 0) or M^dag in = gamma_5 M gamma_5 in (dagger = 1); full fields, nrhs of
+ * them back to back (§II, Eq. for M). */
+int wf_apply_M(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
+
+/* out = T^-1 in (dagger = 0) or (T^dag)^-1 in (dagger = 1) on every spin component of full
+ * fields: the exact inverse of the cyclic temporal matrix of every spatial site (§II.A, Eq. for T
+ * and the SMW inverse). */
+int wf_apply_Tinv(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
+
+/* out = C_L in = (P_+ + P_- T^-1) in (which = 0) or C_R in = (P_- + P_+ T^-dag) in (which = 1),
+ * full fields (§II.A). */
+int wf_apply_C(wf_handle_t* h, const double* in, double* out, int which, int nrhs);
+
+/* out_odd = M-hat in_odd (dagger = 0) or M-hat^dag in_odd = gamma_5 M-hat gamma_5 in_odd
+ * (dagger = 1) on odd fields, where (§II.B, Eq. TPrecFull and the D-bar definition)
+ *   M-hat = 1 - gamma_f^-2 C_L^o D_s^oe C_R^e C_L^e D_s^eo C_R^o. */
+int wf_apply_schur(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+
+/* FP32 variants: same contracts, FP64 in and out, every internal step in FP32. */
+int wf_apply_M_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
+int wf_apply_Tinv_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
+int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+
+/* Solve M x = rhs for nrhs full-field right-hand sides with CG on the normal equations of the
+ * operator `method` selects, FP64 or mixed `precision`. For WF_TEMPORAL_SCHUR the source is
+ * prepared with S_L and the solution recovered with S_R (§II.B, S_L and S_R). A solve is done
+ * when the FP64 true residual ||rhs - M x||_2 / ||rhs||_2 <= tol, computed with the full M.
+ * iters_out[k] (CG iterations) and true_resid_out[k] are written for every right-hand side
+ * (host arrays of nrhs entries; either may be null). flags: WF_X0 to start from x.
+ * Returns WF_ENOCONV (outputs written) if some right-hand side missed tol within 100000
+ * iterations, WF_ENAN if a norm became NaN or Inf. */
+int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
+             int flags, int* iters_out, double* true_resid_out);
+
+/* Per-kernel timing on the handle's stream (CUDA events around every launch), for
+ * benchmarks. wf_profile(h, 1) clears the counters and starts recording; wf_profile(h, 0)
+ * stops. wf_profile_get fills up to cap entries of (name, launches, total milliseconds) and
+ * returns how many kernels were recorded. Names stay valid while h lives. */
+int wf_profile(wf_handle_t* h, int on);
+int wf_profile_get(wf_handle_t* h, const char** names, long long* launches, double* total_ms, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H */

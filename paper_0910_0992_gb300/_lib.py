@@ -1,0 +1,223 @@
+"""ctypes binding of libwf.so: one Python function per C entry point (include/wf.h)."""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "libwf.so")
+
+WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ESINGULAR, WF_ENOCONV, WF_ENAN, WF_ETIMEOUT = range(8)
+WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR = range(4)
+WF_FP64, WF_FP32 = 0, 1
+WF_X0 = 1
+
+_STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "WF_ESINGULAR",
+           5: "WF_ENOCONV", 6: "WF_ENAN", 7: "WF_ETIMEOUT"}
+
+if not os.path.exists(lib_path):
+    raise ImportError(f"libwf.so is not built ({lib_path}); run paper_0910_0992_gb300.build_lib.build()")
+lib = ctypes.CDLL(lib_path)
+
+_vp, _ip, _dp, _i, _d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+
+_SIGS = {
+    "wf_create": (_i, [_i, _i, _d, _d, _d, _i, ctypes.POINTER(_vp)]),
+    "wf_destroy": (_i, [_vp]),
+    "wf_set_stream": (_i, [_vp, _vp]),
+    "wf_last_error": (ctypes.c_char_p, [_vp]),
+    "wf_field_elems": (ctypes.c_longlong, [_vp]),
+    "wf_half_elems": (ctypes.c_longlong, [_vp]),
+    "wf_load_gauge": (_i, [_vp, _vp]),
+    "wf_apply_M": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_M_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_Tinv": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_Tinv_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_C": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_schur": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_schur_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
+    "wf_profile": (_i, [_vp, _i]),
+    "wf_profile_get": (_i, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), _dp, _i]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares (all must resolve in libwf.so)."""
+    return sorted(_SIGS)
+
+
+class WFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(h, code):
+    if code != WF_OK:
+        raise WFError(code, (lib.wf_last_error(h) or b"").decode())
+    return code
+
+
+def _ptr(a):
+    """Address of a complex128 C-contiguous torch tensor / NumPy array (or a raw int address)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):  # torch.Tensor
+        import torch
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise TypeError("expected a contiguous complex128 tensor")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous complex128 array")
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- raw entry points
+def wf_create(L, T, xi, kappa_s, kappa_t, bc):
+    h = _vp()
+    code = lib.wf_create(int(L), int(T), float(xi), float(kappa_s), float(kappa_t), int(bc), ctypes.byref(h))
+    if code != WF_OK:
+        raise WFError(code, "wf_create rejected its arguments or could not allocate")
+    return h
+
+
+def wf_destroy(h):
+    return lib.wf_destroy(h)
+
+
+def wf_set_stream(h, stream):
+    return _check(h, lib.wf_set_stream(h, stream))
+
+
+def wf_last_error(h):
+    return (lib.wf_last_error(h) or b"").decode()
+
+
+def wf_field_elems(h):
+    return lib.wf_field_elems(h)
+
+
+def wf_half_elems(h):
+    return lib.wf_half_elems(h)
+
+
+def wf_load_gauge(h, U):
+    return _check(h, lib.wf_load_gauge(h, _ptr(U)))
+
+
+def _apply(fn):
+    def call(h, inp, out, flag, nrhs=1):
+        return _check(h, fn(h, _ptr(inp), _ptr(out), int(flag), int(nrhs)))
+    return call
+
+
+wf_apply_M = _apply(lib.wf_apply_M)
+wf_apply_M_f32 = _apply(lib.wf_apply_M_f32)
+wf_apply_Tinv = _apply(lib.wf_apply_Tinv)
+wf_apply_Tinv_f32 = _apply(lib.wf_apply_Tinv_f32)
+wf_apply_C = _apply(lib.wf_apply_C)
+wf_apply_schur = _apply(lib.wf_apply_schur)
+wf_apply_schur_f32 = _apply(lib.wf_apply_schur_f32)
+
+
+def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):
+    """Returns (status, iterations[nrhs], true_residual[nrhs]); raises on errors other than WF_ENOCONV."""
+    iters = (ctypes.c_int * nrhs)()
+    res = (ctypes.c_double * nrhs)()
+    code = lib.wf_solve(h, _ptr(rhs), _ptr(x), int(nrhs), float(tol), int(method), int(precision), int(flags),
+                        iters, res)
+    if code not in (WF_OK, WF_ENOCONV):
+        _check(h, code)
+    return code, list(iters), list(res)
+
+
+def wf_profile(h, on):
+    return _check(h, lib.wf_profile(h, int(on)))
+
+
+def wf_profile_get(h, cap=64):
+    """{kernel name: (launches, total milliseconds)} recorded since wf_profile(h, 1)."""
+    names = (ctypes.c_char_p * cap)()
+    cnt = (ctypes.c_longlong * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = lib.wf_profile_get(h, names, cnt, ms, cap)
+    if n < 0:
+        raise WFError(-n, wf_last_error(h))
+    return {names[i].decode(): (cnt[i], ms[i]) for i in range(min(n, cap))}
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Wilson:
+    """A handle with its parameters; methods allocate outputs like their inputs (torch or NumPy)."""
+
+    def __init__(self, L, T, kappa_s, kappa_t=0.0, xi=0.0, bc=-1):
+        self.L, self.T, self.bc = int(L), int(T), int(bc)
+        self.h = wf_create(L, T, xi, kappa_s, kappa_t, bc)
+
+    def close(self):
+        if self.h is not None:
+            wf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _like(a):
+        if hasattr(a, "data_ptr"):
+            import torch
+            return torch.empty_like(a)
+        import numpy as np
+        return np.empty_like(a)
+
+    def set_stream(self, stream):
+        wf_set_stream(self.h, stream)
+
+    def load_gauge(self, U):
+        wf_load_gauge(self.h, U)
+
+    def _nrhs(self, a, per):
+        n = 1
+        for s in a.shape:
+            n *= int(s)
+        if n % per:
+            raise ValueError("array size is not a multiple of one field")
+        return n // per
+
+    def apply_M(self, x, dagger=False, f32=False):
+        out = self._like(x)
+        (wf_apply_M_f32 if f32 else wf_apply_M)(self.h, x, out, dagger, self._nrhs(x, wf_field_elems(self.h)))
+        return out
+
+    def apply_Tinv(self, x, dagger=False, f32=False):
+        out = self._like(x)
+        (wf_apply_Tinv_f32 if f32 else wf_apply_Tinv)(self.h, x, out, dagger, self._nrhs(x, wf_field_elems(self.h)))
+        return out
+
+    def apply_C(self, x, which):
+        out = self._like(x)
+        wf_apply_C(self.h, x, out, which, self._nrhs(x, wf_field_elems(self.h)))
+        return out
+
+    def apply_schur(self, x_odd, dagger=False, f32=False):
+        out = self._like(x_odd)
+        (wf_apply_schur_f32 if f32 else wf_apply_schur)(self.h, x_odd, out, dagger,
+                                                         self._nrhs(x_odd, wf_half_elems(self.h)))
+        return out
+
+    def solve(self, rhs, tol=1e-10, method=WF_TEMPORAL_SCHUR, precision=WF_FP64, x0=None):
+        x = self._like(rhs) if x0 is None else x0
+        flags = WF_X0 if x0 is not None else 0
+        nrhs = self._nrhs(rhs, wf_field_elems(self.h))
+        status, iters, res = wf_solve(self.h, rhs, x, nrhs, tol, method, precision, flags)
+        return x, iters, res, status

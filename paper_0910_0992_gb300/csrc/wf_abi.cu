@@ -1,0 +1,853 @@
+// C-ABI of libwf (declared in include/wf.h): handle, gauge ingest, operator applies
+// and the CGNR solver for the temporally preconditioned Wilson matrix.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/wf.h"
+#include "wf_internal.h"
+#include "wf_line.cuh"
+
+using namespace wf;
+
+// ----------------------------------------------------------------------------
+// Handle
+// ----------------------------------------------------------------------------
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+
+struct wf_handle {
+  Geom g{};
+  double xi = 0, kappa_s = 0, kappa_t = 0;
+  cudaStream_t stream = 0;
+  int device = 0;
+  std::string err;
+  bool gauge = false;
+  // gauge, per parity: U_t [Nl][9][tp], spatial [3][Nl][9][tp], Lambda [Nl][9]
+  DevBuf ut64[2], us64[2], lamb64[2], lamf64[2];
+  DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];
+  DevBuf iflag;
+  std::map<std::string, std::unique_ptr<DevBuf>> ws;  // named work buffers
+  // profiling
+  bool prof = false;
+  std::vector<std::string> prof_names;
+  std::map<std::string, int> prof_ids;
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<long long> prof_count;
+  std::vector<double> prof_ms;
+  double* host_scalars = nullptr;  // pinned
+
+  template <typename T>
+  T* buf(const std::string& name, size_t count) {
+    auto& b = ws[name];
+    if (!b) b.reset(new DevBuf());
+    b->ensure(count * sizeof(T), stream);
+    return b->as<T>();
+  }
+  size_t half_int() const { return (size_t)g.Nl * NSPIN_C * g.tp; }  // internal elements, one parity, one rhs
+  size_t lex_elems() const { return (size_t)g.L * g.L * g.L * g.T * NSPIN_C; }
+
+  // ---- profiling helpers
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    WF_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  void fold_pending() {
+    if (prof_pending.empty()) return;
+    WF_CUDA(cudaEventSynchronize(prof_pending.back().b));
+    for (auto& r : prof_pending) {
+      float ms = 0.f;
+      WF_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      prof_ms[r.id] += ms;
+      prof_count[r.id] += 1;
+      ev_pool.push_back(r.a);
+      ev_pool.push_back(r.b);
+    }
+    prof_pending.clear();
+  }
+};
+
+namespace {
+
+// RAII: CUDA events around one kernel launch when profiling is on
+struct Prof {
+  wf_handle* h;
+  ProfRec rec{};
+  bool on;
+  Prof(wf_handle* hh, const char* name) : h(hh), on(hh->prof) {
+    if (!on) return;
+    auto it = h->prof_ids.find(name);
+    if (it == h->prof_ids.end()) {
+      int id = (int)h->prof_names.size();
+      h->prof_ids[name] = id;
+      h->prof_names.push_back(name);
+      h->prof_count.push_back(0);
+      h->prof_ms.push_back(0.0);
+      rec.id = id;
+    } else {
+      rec.id = it->second;
+    }
+    rec.a = h->take_event();
+    rec.b = h->take_event();
+    WF_CUDA(cudaEventRecord(rec.a, h->stream));
+  }
+  ~Prof() {
+    if (!on) return;
+    cudaEventRecord(rec.b, h->stream);
+    h->prof_pending.push_back(rec);
+    if (h->prof_pending.size() > 4096) {
+      try {
+        h->fold_pending();
+      } catch (...) {
+      }
+    }
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int fail(wf_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(wf_handle* h, F&& f) {
+  if (!h) return WF_EINVAL;
+  h->err.clear();
+  try {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) WF_CUDA(cudaSetDevice(h->device));
+    return f();
+  } catch (const Error& e) {
+    return fail(h, e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(h, WF_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(h, WF_ECUDA, e.what());
+  } catch (...) {
+    return fail(h, WF_ECUDA, "unknown error");
+  }
+}
+
+// device view of an input array (staged to the device if it lives on the host)
+const Cx<double>* dev_in(wf_handle* h, const double* p, size_t elems, const char* name) {
+  if (!p) throw Error(WF_EINVAL, "null array argument");
+  if (is_device_ptr(p)) return reinterpret_cast<const Cx<double>*>(p);
+  Cx<double>* d = h->buf<Cx<double>>(name, elems);
+  WF_CUDA(cudaMemcpyAsync(d, p, elems * sizeof(Cx<double>), cudaMemcpyHostToDevice, h->stream));
+  return d;
+}
+// device buffer for an output array; finish_out copies it back if the caller's array is host memory
+Cx<double>* dev_out(wf_handle* h, double* p, size_t elems, const char* name, bool& staged) {
+  if (!p) throw Error(WF_EINVAL, "null array argument");
+  staged = !is_device_ptr(p);
+  if (!staged) return reinterpret_cast<Cx<double>*>(p);
+  return h->buf<Cx<double>>(name, elems);
+}
+void finish_out(wf_handle* h, double* p, const Cx<double>* d, size_t elems, bool staged) {
+  if (staged) WF_CUDA(cudaMemcpyAsync(p, d, elems * sizeof(Cx<double>), cudaMemcpyDeviceToHost, h->stream));
+  WF_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ----------------------------------------------------------------------------
+// Gauge views per precision
+// ----------------------------------------------------------------------------
+template <typename R>
+struct Gauge {
+  const Cx<R>* ut[2];
+  const Cx<R>* us[2];
+  const Cx<R>* lamb[2];
+  const Cx<R>* lamf[2];
+};
+template <typename R>
+Gauge<R> gauge_of(wf_handle* h);
+template <>
+Gauge<double> gauge_of<double>(wf_handle* h) {
+  Gauge<double> G;
+  for (int p = 0; p < 2; ++p) {
+    G.ut[p] = h->ut64[p].as<Cx<double>>();
+    G.us[p] = h->us64[p].as<Cx<double>>();
+    G.lamb[p] = h->lamb64[p].as<Cx<double>>();
+    G.lamf[p] = h->lamf64[p].as<Cx<double>>();
+  }
+  return G;
+}
+template <>
+Gauge<float> gauge_of<float>(wf_handle* h) {
+  Gauge<float> G;
+  for (int p = 0; p < 2; ++p) {
+    G.ut[p] = h->ut32[p].as<Cx<float>>();
+    G.us[p] = h->us32[p].as<Cx<float>>();
+    G.lamb[p] = h->lamb32[p].as<Cx<float>>();
+    G.lamf[p] = h->lamf32[p].as<Cx<float>>();
+  }
+  return G;
+}
+
+template <typename R>
+LineArgs<R> line_args(wf_handle* h, int parity, int nrhs) {
+  Gauge<R> G = gauge_of<R>(h);
+  LineArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = h->g;
+  a.parity = parity;
+  a.nrhs = nrhs;
+  a.ut = G.ut[parity];
+  a.us_out = G.us[parity];
+  a.us_nbr = G.us[1 - parity];
+  a.lamb = G.lamb[parity];
+  a.lamf = G.lamf[parity];
+  a.inv_mu = (R)(1.0 / h->g.mu);
+  a.bc = (R)h->g.bc;
+  a.opu = OP_COPY;
+  a.opl = OP_COPY;
+  return a;
+}
+
+template <typename R>
+const char* pname(const char* base);
+template <>
+const char* pname<double>(const char* base) {
+  static std::map<std::string, std::string> m;
+  auto& s = m[base];
+  if (s.empty()) s = std::string(base) + "_f64";
+  return s.c_str();
+}
+template <>
+const char* pname<float>(const char* base) {
+  static std::map<std::string, std::string> m;
+  auto& s = m[base];
+  if (s.empty()) s = std::string(base) + "_f32";
+  return s.c_str();
+}
+
+// ----------------------------------------------------------------------------
+// Operators on internal fields
+// ----------------------------------------------------------------------------
+
+// out = C in on one parity: op_up / op_lo per spin half (copy, T^-dag, T^-1)
+template <typename R>
+void line_load(wf_handle* h, int parity, const Cx<R>* in, Cx<R>* out, int opu, int opl, int nrhs, const char* name) {
+  LineArgs<R> a = line_args<R>(h, parity, nrhs);
+  a.src_up = in;
+  a.src_lo = in + 6 * h->g.tp;
+  a.opu = opu;
+  a.opl = opl;
+  a.out = out;
+  Prof P(h, pname<R>(name));
+  launch_line<R>(a, SRC_LOAD, h->stream);
+}
+
+// M-hat (dagger: gamma_5 M-hat gamma_5) on odd internal fields: three fused kernels
+//   K-a  y = C_R^o x                        (T^-dag on the upper half only)
+//   K-b  z = C_R^e C_L^e D_s^eo y           (hop, then T^-dag upper / T^-1 lower)
+//   K-c  out = x - gamma_f^-2 C_L^o D_s^oe z (hop, T^-1 lower, axpy)
+template <typename R>
+void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z) {
+  const int tp = h->g.tp;
+  {
+    LineArgs<R> a = line_args<R>(h, 1, nrhs);
+    a.src_up = dagger ? x + 6 * tp : x;
+    a.src_lo = dagger ? x : x + 6 * tp;
+    a.opu = OP_FWD;
+    a.opl = OP_SKIP;
+    a.out = y;
+    Prof P(h, pname<R>("schur_a_tdag"));
+    launch_line<R>(a, SRC_LOAD, h->stream);
+  }
+  {
+    LineArgs<R> a = line_args<R>(h, 0, nrhs);
+    a.src_up = y;
+    a.src_lo = dagger ? x : x + 6 * tp;
+    a.opu = OP_FWD;
+    a.opl = OP_BWD;
+    a.out = z;
+    Prof P(h, pname<R>("schur_b_hop_tsolve"));
+    launch_line<R>(a, SRC_HOP, h->stream);
+  }
+  {
+    LineArgs<R> a = line_args<R>(h, 1, nrhs);
+    a.src_up = z;
+    a.src_lo = z + 6 * tp;
+    a.opu = OP_COPY;
+    a.opl = OP_BWD;
+    a.xpost = x;
+    a.apost = (R)(-1.0 / (h->g.gamma_f * h->g.gamma_f));
+    a.swap_out = dagger;
+    a.out = out;
+    Prof P(h, pname<R>("schur_c_hop_tinv_axpy"));
+    launch_line<R>(a, SRC_HOP, h->stream);
+  }
+}
+
+// out = M in (or x + a M in) on both parities
+template <typename R>
+void m_apply(wf_handle* h, const Cx<R>* in_e, const Cx<R>* in_o, Cx<R>* out_e, Cx<R>* out_o, const Cx<R>* x_e,
+             const Cx<R>* x_o, double a, int nrhs) {
+  Gauge<R> G = gauge_of<R>(h);
+  for (int p = 0; p < 2; ++p) {
+    MArgs<R> m;
+    std::memset(&m, 0, sizeof(m));
+    m.g = h->g;
+    m.parity = p;
+    m.nrhs = nrhs;
+    m.psi_p = p ? in_o : in_e;
+    m.psi_q = p ? in_e : in_o;
+    m.ut = G.ut[p];
+    m.us_out = G.us[p];
+    m.us_nbr = G.us[1 - p];
+    m.x = p ? x_o : x_e;
+    m.a = (R)a;
+    m.out = p ? out_o : out_e;
+    m.mu = (R)h->g.mu;
+    m.inv_gf = (R)(1.0 / h->g.gamma_f);
+    m.bc = (R)h->g.bc;
+    Prof P(h, pname<R>("apply_M"));
+    launch_apply_M<R>(m, h->stream);
+  }
+}
+
+void check_geometry(int L, int T) {
+  if (L < 2 || (L & 1)) throw Error(WF_EINVAL, "L must be even and >= 2");
+  if (T < 2 || T > 128) throw Error(WF_EINVAL, "T must lie in [2, 128]");
+}
+
+// choose sites per lane n and lanes per line lpl (power of two <= 32) with minimal padding
+void choose_layout(Geom& g) {
+  int best_tp = 1 << 30, best_n = 0, best_lpl = 0;
+  for (int n = 1; n <= 4; ++n) {
+    int need = (g.T + n - 1) / n;
+    int lpl = 1;
+    while (lpl < need) lpl <<= 1;
+    if (lpl > 32) continue;
+    int tp = n * lpl;
+    if (tp < best_tp) {
+      best_tp = tp;
+      best_n = n;
+      best_lpl = lpl;
+    }
+  }
+  if (!best_n) throw Error(WF_EINVAL, "T too large for the line layout");
+  g.n = best_n;
+  g.lpl = best_lpl;
+  g.tp = best_tp;
+  g.lpw = 32 / best_lpl;
+}
+
+// ----------------------------------------------------------------------------
+// Solver
+// ----------------------------------------------------------------------------
+struct SolveStats {
+  std::vector<int> iters;
+  std::vector<double> resid;
+};
+
+
+std::vector<double> read_scalars(wf_handle* h, const double* d, int n) {
+  std::vector<double> v(n);
+  WF_CUDA(cudaMemcpyAsync(h->host_scalars, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  WF_CUDA(cudaStreamSynchronize(h->stream));
+  std::memcpy(v.data(), h->host_scalars, n * sizeof(double));
+  for (double x : v)
+    if (!std::isfinite(x)) throw Error(WF_ENAN, "NaN or Inf in a solver norm");
+  return v;
+}
+
+// CGNR on M-hat with operator applies in precision R (R = double: plain FP64 CG; R = float:
+// FP32 iterations with FP64 reliable updates of the residual). Solves for y_o given b_o
+// (FP64 internal odd fields) to |b - M-hat y| <= target[k] for every rhs k. Returns iterations.
+template <typename R>
+std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, int nrhs, const std::vector<double>& target,
+                            int maxiter, bool x0) {
+  const size_t n = h->half_int();
+  const size_t nt = n * nrhs;
+  cudaStream_t s = h->stream;
+  double* sc = h->buf<double>("cg_scalars", 16 * (size_t)nrhs);
+  double *gam = sc, *gnew = sc + nrhs, *qq = sc + 2 * nrhs, *rr = sc + 3 * nrhs;
+  int* active = h->buf<int>("cg_active", nrhs);
+  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
+  std::vector<int> act(nrhs, 1), iters(nrhs, 0);
+  WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+
+  Cx<R>* r = h->buf<Cx<R>>(pname<R>("cg_r"), nt);
+  Cx<R>* sv = h->buf<Cx<R>>(pname<R>("cg_s"), nt);
+  Cx<R>* p = h->buf<Cx<R>>(pname<R>("cg_p"), nt);
+  Cx<R>* q = h->buf<Cx<R>>(pname<R>("cg_q"), nt);
+  Cx<R>* xi = h->buf<Cx<R>>(pname<R>("cg_x"), nt);
+  Cx<R>* ty = h->buf<Cx<R>>(pname<R>("cg_ty"), nt);
+  Cx<R>* tz = h->buf<Cx<R>>(pname<R>("cg_tz"), nt);
+  Cx<double>* r64 = h->buf<Cx<double>>("cg_r64", nt);
+  Cx<double>* ty64 = h->buf<Cx<double>>("cg_ty64", nt);
+  Cx<double>* tz64 = h->buf<Cx<double>>("cg_tz64", nt);
+  const bool mixed = sizeof(R) == 4;
+
+  // r64 = b - M-hat y (FP64) or b
+  auto true_schur_residual = [&]() {
+    schur_apply<double>(h, y, r64, 0, nrhs, ty64, tz64);
+    launch_axpby<double>(r64, b, nt, 1.0, -1.0, s);  // r64 = b - M-hat y
+  };
+  if (x0) {
+    true_schur_residual();
+  } else {
+    WF_CUDA(cudaMemsetAsync(y, 0, nt * sizeof(Cx<double>), s));
+    WF_CUDA(cudaMemcpyAsync(r64, b, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  }
+  // working residual in precision R; x increment accumulates in R
+  if (mixed) {
+    launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s);
+    WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<R>), s));
+  } else {
+    WF_CUDA(cudaMemcpyAsync(r, r64, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  }
+  Cx<R>* xacc = mixed ? xi : reinterpret_cast<Cx<R>*>(y);
+
+  launch_norm2<double>(r64, n, nrhs, partial, rr, s);
+  std::vector<double> rnorm2 = read_scalars(h, rr, nrhs);
+  std::vector<double> rmax(nrhs);
+  for (int k = 0; k < nrhs; ++k) {
+    rmax[k] = std::sqrt(rnorm2[k]);
+    if (rnorm2[k] <= target[k] * target[k]) act[k] = 0;
+  }
+  WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  auto all_done = [&]() {
+    for (int a : act)
+      if (a) return false;
+    return true;
+  };
+  if (all_done()) return iters;
+
+  schur_apply<R>(h, r, sv, 1, nrhs, ty, tz);  // s = M-hat^dag r
+  WF_CUDA(cudaMemcpyAsync(p, sv, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  launch_norm2<R>(sv, n, nrhs, partial, gam, s);
+
+  const double delta = 0.1;  // reliable-update trigger: residual dropped by this factor
+  for (int it = 0; it < maxiter; ++it) {
+    schur_apply<R>(h, p, q, 0, nrhs, ty, tz);  // q = M-hat p
+    launch_norm2<R>(q, n, nrhs, partial, qq, s);
+    launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s);
+    for (int k = 0; k < nrhs; ++k)
+      if (act[k]) iters[k]++;
+    std::vector<double> rrh = read_scalars(h, rr, nrhs);
+    bool changed = false;
+    bool need_ru = false;
+    for (int k = 0; k < nrhs; ++k) {
+      if (!act[k]) continue;
+      const double rn = std::sqrt(rrh[k]);
+      if (mixed) {
+        if (rn < delta * rmax[k] || rrh[k] <= target[k] * target[k]) need_ru = true;
+      } else if (rrh[k] <= target[k] * target[k]) {
+        act[k] = 0;
+        changed = true;
+      }
+    }
+    if (need_ru) {
+      // reliable update: fold the FP32 increment into y, recompute the residual in FP64
+      launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);
+      WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<R>), s));
+      true_schur_residual();
+      launch_norm2<double>(r64, n, nrhs, partial, rr, s);
+      launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s);
+      std::vector<double> r64n = read_scalars(h, rr, nrhs);
+      for (int k = 0; k < nrhs; ++k) {
+        if (!act[k]) continue;
+        rmax[k] = std::sqrt(r64n[k]);
+        if (r64n[k] <= target[k] * target[k]) {
+          act[k] = 0;
+          changed = true;
+        }
+      }
+    }
+    if (changed) WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (all_done()) break;
+    schur_apply<R>(h, r, sv, 1, nrhs, ty, tz);  // s = M-hat^dag r
+    launch_norm2<R>(sv, n, nrhs, partial, gnew, s);
+    launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s);
+    launch_copy_scalar(gam, gnew, nrhs, s);
+  }
+  if (mixed) launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);
+  return iters;
+}
+
+// Temporal + 3-D Schur solve (§II.B): prepare with S_L, CGNR on M-hat, reconstruct with S_R,
+// verify with the FP64 true residual of M.
+int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
+                         int precision, bool x0, int* iters_out, double* resid_out) {
+  const size_t n = h->half_int();
+  const size_t nt = n * nrhs;
+  cudaStream_t s = h->stream;
+  const double igf = 1.0 / h->g.gamma_f;
+  Cx<double>* eta_e = h->buf<Cx<double>>("sv_eta_e", nt);
+  Cx<double>* eta_o = h->buf<Cx<double>>("sv_eta_o", nt);
+  Cx<double>* a_e = h->buf<Cx<double>>("sv_a_e", nt);
+  Cx<double>* b_o = h->buf<Cx<double>>("sv_b_o", nt);
+  Cx<double>* y_o = h->buf<Cx<double>>("sv_y_o", nt);
+  Cx<double>* psi_e = h->buf<Cx<double>>("sv_psi_e", nt);
+  Cx<double>* psi_o = h->buf<Cx<double>>("sv_psi_o", nt);
+  Cx<double>* r_e = h->buf<Cx<double>>("sv_r_e", nt);
+  Cx<double>* r_o = h->buf<Cx<double>>("sv_r_o", nt);
+  double* sc = h->buf<double>("sv_scalars", 4 * (size_t)nrhs);
+  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
+
+  launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, s);
+  // source preparation (S_L): a_e = C_R^e C_L^e eta_e ; b_o = C_L^o [eta_o + gamma_f^-1 D_s^oe a_e]
+  line_load<double>(h, 0, eta_e, a_e, OP_FWD, OP_BWD, nrhs, "prep_tsolve");
+  {
+    LineArgs<double> a = line_args<double>(h, 1, nrhs);
+    a.src_up = a_e;
+    a.src_lo = a_e + 6 * h->g.tp;
+    a.xpre = eta_o;
+    a.apre = igf;
+    a.opu = OP_COPY;
+    a.opl = OP_BWD;
+    a.out = b_o;
+    Prof P(h, "prep_hop_f64");
+    launch_line<double>(a, SRC_HOP, s);
+  }
+  // |eta|^2 per rhs
+  launch_norm2<double>(eta_e, n, nrhs, partial, sc, s);
+  launch_norm2<double>(eta_o, n, nrhs, partial, sc + nrhs, s);
+  std::vector<double> e2 = read_scalars(h, sc, 2 * nrhs);
+  std::vector<double> eta2(nrhs), target(nrhs);
+  for (int k = 0; k < nrhs; ++k) {
+    eta2[k] = e2[k] + e2[nrhs + k];
+    // |eta - M psi| = |C_L^o^-1 r_o| <= (mu + 1) |r_o|
+    target[k] = tol * std::sqrt(eta2[k]) / (h->g.mu + 1.0);
+  }
+  bool have_x0 = x0;
+  if (x0) {
+    // initial guess: y_o = (C_R^o)^-1 psi_o; use only the odd part of the guess
+    Cx<double>* g_e = r_e;
+    launch_import_spinor<double>(h->g, x_lex, g_e, psi_o, nrhs, 0, s);
+    // (C_R^o)^-1 = P_- + P_+ T^dag is not needed exactly: start from y_o = psi_o
+    WF_CUDA(cudaMemcpyAsync(y_o, psi_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  }
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> rel(nrhs, 0.0);
+  const int maxiter = 100000;
+  int status = WF_OK;
+  for (int pass = 0; pass < 6; ++pass) {
+    std::vector<int> it = precision == WF_FP32 ? cgnr_schur<float>(h, b_o, y_o, nrhs, target, maxiter, have_x0)
+                                               : cgnr_schur<double>(h, b_o, y_o, nrhs, target, maxiter, have_x0);
+    for (int k = 0; k < nrhs; ++k) iters[k] += it[k];
+    have_x0 = true;
+    // reconstruction (S_R): psi_o = C_R^o y_o ; psi_e = C_R^e C_L^e [eta_e + gamma_f^-1 D_s^eo psi_o]
+    line_load<double>(h, 1, y_o, psi_o, OP_FWD, OP_COPY, nrhs, "recon_tsolve");
+    {
+      LineArgs<double> a = line_args<double>(h, 0, nrhs);
+      a.src_up = psi_o;
+      a.src_lo = psi_o + 6 * h->g.tp;
+      a.xpre = eta_e;
+      a.apre = igf;
+      a.opu = OP_FWD;
+      a.opl = OP_BWD;
+      a.out = psi_e;
+      Prof P(h, "recon_hop_f64");
+      launch_line<double>(a, SRC_HOP, s);
+    }
+    // true residual r = eta - M psi in FP64
+    m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
+    launch_norm2<double>(r_e, n, nrhs, partial, sc, s);
+    launch_norm2<double>(r_o, n, nrhs, partial, sc + nrhs, s);
+    std::vector<double> r2 = read_scalars(h, sc, 2 * nrhs);
+    bool ok = true;
+    for (int k = 0; k < nrhs; ++k) {
+      rel[k] = std::sqrt((r2[k] + r2[nrhs + k]) / (eta2[k] > 0 ? eta2[k] : 1.0));
+      if (rel[k] > tol) {
+        ok = false;
+        target[k] *= 0.5 * tol / rel[k];
+      }
+      if (iters[k] >= maxiter) status = WF_ENOCONV;
+    }
+    if (ok || status == WF_ENOCONV) break;
+    if (pass == 5) status = WF_ENOCONV;
+  }
+  launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, s);
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters_out) iters_out[k] = iters[k];
+    if (resid_out) resid_out[k] = rel[k];
+  }
+  return status;
+}
+
+template <typename R>
+int apply_schur_abi(wf_handle* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  const size_t ce = (size_t)nrhs * h->g.T * h->g.Nl * NSPIN_C;
+  const size_t nt = h->half_int() * nrhs;
+  const Cx<double>* din = dev_in(h, in_odd, ce, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out_odd, ce, "stage_out", staged);
+  Cx<R>* x = h->buf<Cx<R>>(pname<R>("ap_x"), nt);
+  Cx<R>* o = h->buf<Cx<R>>(pname<R>("ap_o"), nt);
+  Cx<R>* y = h->buf<Cx<R>>(pname<R>("ap_y"), nt);
+  Cx<R>* z = h->buf<Cx<R>>(pname<R>("ap_z"), nt);
+  launch_import_compact<R>(h->g, din, x, nrhs, 0, h->stream);
+  schur_apply<R>(h, x, o, dagger, nrhs, y, z);
+  launch_export_compact<R>(h->g, o, dout, nrhs, 0, h->stream);
+  finish_out(h, out_odd, dout, ce, staged);
+  return WF_OK;
+}
+
+template <typename R>
+int apply_M_abi(wf_handle* h, const double* in, double* out, int dagger, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  const size_t le = h->lex_elems() * nrhs;
+  const size_t nt = h->half_int() * nrhs;
+  const Cx<double>* din = dev_in(h, in, le, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out, le, "stage_out", staged);
+  Cx<R>* ie = h->buf<Cx<R>>(pname<R>("ap_ie"), nt);
+  Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
+  Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
+  Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
+  launch_import_spinor<R>(h->g, din, ie, io, nrhs, dagger, h->stream);
+  m_apply<R>(h, ie, io, oe, oo, nullptr, nullptr, 0.0, nrhs);
+  launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, dagger, h->stream);
+  finish_out(h, out, dout, le, staged);
+  return WF_OK;
+}
+
+template <typename R>
+int apply_line_abi(wf_handle* h, const double* in, double* out, int opu, int opl, int nrhs, const char* name) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  const size_t le = h->lex_elems() * nrhs;
+  const size_t nt = h->half_int() * nrhs;
+  const Cx<double>* din = dev_in(h, in, le, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out, le, "stage_out", staged);
+  Cx<R>* ie = h->buf<Cx<R>>(pname<R>("ap_ie"), nt);
+  Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
+  Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
+  Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
+  launch_import_spinor<R>(h->g, din, ie, io, nrhs, 0, h->stream);
+  line_load<R>(h, 0, ie, oe, opu, opl, nrhs, name);
+  line_load<R>(h, 1, io, oo, opu, opl, nrhs, name);
+  launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, 0, h->stream);
+  finish_out(h, out, dout, le, staged);
+  return WF_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+extern "C" {
+
+int wf_create(int L, int T, double xi, double kappa_s, double kappa_t, int bc, wf_handle_t** out) {
+  if (!out) return WF_EINVAL;
+  *out = nullptr;
+  if (L < 2 || (L & 1) || T < 2 || T > 128) return WF_EINVAL;
+  if (!(kappa_s > 0) || (bc != 1 && bc != -1)) return WF_EINVAL;
+  if (!(kappa_t > 0)) {
+    if (!(xi > 0)) return WF_EINVAL;
+    kappa_t = xi * kappa_s;
+  }
+  wf_handle* h = nullptr;
+  try {
+    h = new wf_handle();
+    h->xi = xi;
+    h->kappa_s = kappa_s;
+    h->kappa_t = kappa_t;
+    Geom& g = h->g;
+    g.L = L;
+    g.T = T;
+    g.Lh = L / 2;
+    g.Nl = L * L * L / 2;
+    g.mu = 1.0 / (2.0 * kappa_t);
+    g.gamma_f = kappa_t / kappa_s;
+    g.bc = (double)bc;
+    check_geometry(L, T);
+    choose_layout(g);
+    WF_CUDA(cudaGetDevice(&h->device));
+    WF_CUDA(cudaMallocHost(&h->host_scalars, 4096 * sizeof(double)));
+    *out = h;
+    return WF_OK;
+  } catch (const Error& e) {
+    delete h;
+    return e.code;
+  } catch (...) {
+    delete h;
+    return WF_ENOMEM;
+  }
+}
+
+int wf_destroy(wf_handle_t* h) {
+  if (!h) return WF_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& r : h->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->host_scalars) cudaFreeHost(h->host_scalars);
+  delete h;
+  return WF_OK;
+}
+
+int wf_set_stream(wf_handle_t* h, void* stream) {
+  return guarded(h, [&]() {
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    return WF_OK;
+  });
+}
+
+const char* wf_last_error(const wf_handle_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+long long wf_field_elems(const wf_handle_t* h) { return h ? (long long)h->g.L * h->g.L * h->g.L * h->g.T * 12 : 0; }
+long long wf_half_elems(const wf_handle_t* h) { return h ? (long long)h->g.L * h->g.L * h->g.L * h->g.T * 6 : 0; }
+
+int wf_load_gauge(wf_handle_t* h, const double* U) {
+  return guarded(h, [&]() {
+    const Geom& g = h->g;
+    const size_t V = (size_t)g.L * g.L * g.L * g.T;
+    const Cx<double>* dU = dev_in(h, U, V * 36, "stage_gauge");
+    const size_t nut = (size_t)g.Nl * 9 * g.tp, nus = 3 * nut, nlam = (size_t)g.Nl * 9;
+    cudaStream_t s = h->stream;
+    for (int p = 0; p < 2; ++p) {
+      h->ut64[p].ensure(nut * sizeof(Cx<double>), s);
+      h->us64[p].ensure(nus * sizeof(Cx<double>), s);
+      h->lamb64[p].ensure(nlam * sizeof(Cx<double>), s);
+      h->lamf64[p].ensure(nlam * sizeof(Cx<double>), s);
+      h->ut32[p].ensure(nut * sizeof(Cx<float>), s);
+      h->us32[p].ensure(nus * sizeof(Cx<float>), s);
+      h->lamb32[p].ensure(nlam * sizeof(Cx<float>), s);
+      h->lamf32[p].ensure(nlam * sizeof(Cx<float>), s);
+    }
+    h->iflag.ensure(sizeof(int), s);
+    WF_CUDA(cudaMemsetAsync(h->iflag.p, 0, sizeof(int), s));
+    Cx<double>* ut[2] = {h->ut64[0].as<Cx<double>>(), h->ut64[1].as<Cx<double>>()};
+    Cx<double>* us[2] = {h->us64[0].as<Cx<double>>(), h->us64[1].as<Cx<double>>()};
+    launch_import_gauge(g, dU, ut, us, s);
+    for (int p = 0; p < 2; ++p) {
+      launch_tline_init(g, ut[p], h->lamb64[p].as<Cx<double>>(), h->lamf64[p].as<Cx<double>>(), h->iflag.as<int>(), s);
+      launch_d2f(ut[p], h->ut32[p].as<Cx<float>>(), nut, s);
+      launch_d2f(us[p], h->us32[p].as<Cx<float>>(), nus, s);
+      launch_d2f(h->lamb64[p].as<Cx<double>>(), h->lamb32[p].as<Cx<float>>(), nlam, s);
+      launch_d2f(h->lamf64[p].as<Cx<double>>(), h->lamf32[p].as<Cx<float>>(), nlam, s);
+    }
+    int flag = 0;
+    WF_CUDA(cudaMemcpyAsync(&flag, h->iflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    h->gauge = true;
+    if (flag) {
+      h->gauge = false;
+      throw Error(WF_ESINGULAR, "temporal preconditioner singular: |det(1 - bc mu^-T P)| < 1e-12 on some line");
+    }
+    return WF_OK;
+  });
+}
+
+int wf_apply_M(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_M_abi<double>(h, in, out, dagger ? 1 : 0, nrhs); });
+}
+int wf_apply_M_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_M_abi<float>(h, in, out, dagger ? 1 : 0, nrhs); });
+}
+int wf_apply_Tinv(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
+  return guarded(h, [&]() {
+    int op = dagger ? OP_FWD : OP_BWD;
+    return apply_line_abi<double>(h, in, out, op, op, nrhs, "tinv");
+  });
+}
+int wf_apply_Tinv_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
+  return guarded(h, [&]() {
+    int op = dagger ? OP_FWD : OP_BWD;
+    return apply_line_abi<float>(h, in, out, op, op, nrhs, "tinv");
+  });
+}
+int wf_apply_C(wf_handle_t* h, const double* in, double* out, int which, int nrhs) {
+  return guarded(h, [&]() {
+    if (which == 0) return apply_line_abi<double>(h, in, out, OP_COPY, OP_BWD, nrhs, "c_left");
+    if (which == 1) return apply_line_abi<double>(h, in, out, OP_FWD, OP_COPY, nrhs, "c_right");
+    throw Error(WF_EINVAL, "which must be 0 (C_L) or 1 (C_R)");
+  });
+}
+int wf_apply_schur(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_schur_abi<double>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_schur_abi<float>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+
+int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision, int flags,
+             int* iters_out, double* true_resid_out) {
+  return guarded(h, [&]() {
+    if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+    if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+    if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
+    if (precision != WF_FP64 && precision != WF_FP32) throw Error(WF_EINVAL, "unknown precision");
+    const size_t le = h->lex_elems() * nrhs;
+    const bool x0 = (flags & WF_X0) != 0;
+    const Cx<double>* drhs = dev_in(h, rhs, le, "stage_in");
+    bool staged;
+    Cx<double>* dx = dev_out(h, x, le, "stage_out", staged);
+    if (x0 && staged) WF_CUDA(cudaMemcpyAsync(dx, x, le * sizeof(Cx<double>), cudaMemcpyHostToDevice, h->stream));
+    int st;
+    if (method == WF_TEMPORAL_SCHUR)
+      st = solve_temporal_schur(h, drhs, dx, nrhs, tol, precision, x0, iters_out, true_resid_out);
+    else
+      throw Error(WF_EINVAL, "method not available");
+    finish_out(h, x, dx, le, staged);
+    if (st == WF_ENOCONV) h->err = "solver did not reach tol";
+    return st;
+  });
+}
+
+int wf_profile(wf_handle_t* h, int on) {
+  return guarded(h, [&]() {
+    h->fold_pending();
+    if (on) {
+      std::fill(h->prof_count.begin(), h->prof_count.end(), 0);
+      std::fill(h->prof_ms.begin(), h->prof_ms.end(), 0.0);
+    }
+    h->prof = on != 0;
+    return WF_OK;
+  });
+}
+
+int wf_profile_get(wf_handle_t* h, const char** names, long long* launches, double* total_ms, int cap) {
+  if (!h) return -WF_EINVAL;
+  try {
+    h->fold_pending();
+  } catch (const Error& e) {
+    h->err = e.what();
+    return -e.code;
+  }
+  int n = (int)h->prof_names.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (names) names[i] = h->prof_names[i].c_str();
+    if (launches) launches[i] = h->prof_count[i];
+    if (total_ms) total_ms[i] = h->prof_ms[i];
+  }
+  return n;
+}
+
+}  // extern "C"

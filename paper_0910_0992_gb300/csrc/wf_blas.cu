@@ -1,0 +1,174 @@
+// BLAS-1 for the Krylov loop: norms with FP64 accumulation and the fused CG vector
+// updates. Arrays are [nrhs][n] complex; per-RHS scalars live in device memory, so
+// the CG loop runs without host round trips.
+#include "wf_internal.h"
+
+namespace wf {
+
+constexpr int kBT = 256;
+constexpr int kMaxPartial = 1024;  // partial sums per RHS (scratch: nrhs * kMaxPartial doubles)
+
+static int parts_for(size_t n) {
+  size_t b = (n + (size_t)kBT * 8 - 1) / ((size_t)kBT * 8);
+  if (b < 1) b = 1;
+  if (b > kMaxPartial) b = kMaxPartial;
+  return (int)b;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kBT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (threadIdx.x < kBT / 32) v = red[threadIdx.x];
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBT) k_norm2(const Cx<R>* __restrict__ x, size_t n, double* partial) {
+  const int rhs = blockIdx.y;
+  const Cx<R>* xr = x + (size_t)rhs * n;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const Cx<R> v = xr[i];
+    acc += (double)v.re * v.re + (double)v.im * v.im;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kBT) k_final_sum(const double* __restrict__ partial, int parts, double* out) {
+  const int rhs = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < parts; i += kBT) acc += partial[rhs * parts + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[rhs] = acc;
+}
+
+template <typename R>
+void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s) {
+  const int parts = parts_for(n);
+  k_norm2<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, n, partial);
+  k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, out);
+  WF_CUDA(cudaGetLastError());
+}
+template void launch_norm2<float>(const Cx<float>*, size_t, int, double*, double*, cudaStream_t);
+template void launch_norm2<double>(const Cx<double>*, size_t, int, double*, double*, cudaStream_t);
+
+// alpha = gamma / |q|^2; x += alpha p; r -= alpha q; partial |r|^2
+template <typename R>
+__global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __restrict__ r, const Cx<R>* __restrict__ p,
+                                                const Cx<R>* __restrict__ q, size_t n, const double* gamma,
+                                                const double* qq, const int* active, double* partial) {
+  const int rhs = blockIdx.y;
+  const bool on = active[rhs] != 0;
+  const double qn = qq[rhs];
+  const R alpha = (on && qn > 0.0) ? (R)(gamma[rhs] / qn) : R(0);
+  const size_t off = (size_t)rhs * n;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const Cx<R> pv = p[off + i], qv = q[off + i];
+    Cx<R> xv = x[off + i], rv = r[off + i];
+    xv.re = fma(alpha, pv.re, xv.re);
+    xv.im = fma(alpha, pv.im, xv.im);
+    rv.re = fma(-alpha, qv.re, rv.re);
+    rv.im = fma(-alpha, qv.im, rv.im);
+    x[off + i] = xv;
+    r[off + i] = rv;
+    acc += (double)rv.re * rv.re + (double)rv.im * rv.im;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = acc;
+}
+
+template <typename R>
+void launch_cg_xr(Cx<R>* x, Cx<R>* r, const Cx<R>* p, const Cx<R>* q, size_t n, int nrhs, const double* gamma,
+                  const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s) {
+  const int parts = parts_for(n);
+  k_cg_xr<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, r, p, q, n, gamma, qq, active, partial);
+  k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, rr_out);
+  WF_CUDA(cudaGetLastError());
+}
+template void launch_cg_xr<float>(Cx<float>*, Cx<float>*, const Cx<float>*, const Cx<float>*, size_t, int,
+                                  const double*, const double*, const int*, double*, double*, cudaStream_t);
+template void launch_cg_xr<double>(Cx<double>*, Cx<double>*, const Cx<double>*, const Cx<double>*, size_t, int,
+                                   const double*, const double*, const int*, double*, double*, cudaStream_t);
+
+// beta = gamma_new / gamma_old; p = s + beta p
+template <typename R>
+__global__ void __launch_bounds__(kBT) k_cg_p(Cx<R>* __restrict__ p, const Cx<R>* __restrict__ sv, size_t n,
+                                               const double* gnew, const double* gold, const int* active) {
+  const int rhs = blockIdx.y;
+  if (!active[rhs]) return;
+  const double go = gold[rhs];
+  const R beta = go > 0.0 ? (R)(gnew[rhs] / go) : R(0);
+  const size_t off = (size_t)rhs * n;
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const Cx<R> s = sv[off + i];
+    Cx<R> pv = p[off + i];
+    pv.re = fma(beta, pv.re, s.re);
+    pv.im = fma(beta, pv.im, s.im);
+    p[off + i] = pv;
+  }
+}
+
+template <typename R>
+void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* gnew, const double* gold,
+                 const int* active, cudaStream_t s) {
+  const int parts = parts_for(n) * 2;
+  k_cg_p<R><<<dim3(parts, nrhs), kBT, 0, s>>>(p, sv, n, gnew, gold, active);
+  WF_CUDA(cudaGetLastError());
+}
+template void launch_cg_p<float>(Cx<float>*, const Cx<float>*, size_t, int, const double*, const double*,
+                                 const int*, cudaStream_t);
+template void launch_cg_p<double>(Cx<double>*, const Cx<double>*, size_t, int, const double*, const double*,
+                                  const int*, cudaStream_t);
+
+template <typename R>
+__global__ void __launch_bounds__(kBT) k_axpby(Cx<R>* __restrict__ y, const Cx<R>* __restrict__ x, size_t n, R a, R b) {
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const Cx<R> xv = x[i];
+    Cx<R> yv = y[i];
+    yv.re = a * xv.re + b * yv.re;
+    yv.im = a * xv.im + b * yv.im;
+    y[i] = yv;
+  }
+}
+template <typename R>
+void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s) {
+  k_axpby<R><<<parts_for(n) * 2, kBT, 0, s>>>(y, x, n, (R)a, (R)b);
+  WF_CUDA(cudaGetLastError());
+}
+template void launch_axpby<float>(Cx<float>*, const Cx<float>*, size_t, double, double, cudaStream_t);
+template void launch_axpby<double>(Cx<double>*, const Cx<double>*, size_t, double, double, cudaStream_t);
+
+__global__ void __launch_bounds__(kBT) k_add_f_to_d(Cx<double>* __restrict__ y, const Cx<float>* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    Cx<double> yv = y[i];
+    yv.re += (double)x[i].re;
+    yv.im += (double)x[i].im;
+    y[i] = yv;
+  }
+}
+void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s) {
+  k_add_f_to_d<<<parts_for(n) * 2, kBT, 0, s>>>(y, x, n);
+  WF_CUDA(cudaGetLastError());
+}
+
+__global__ void k_copy_scalar(double* dst, const double* src, int n) {
+  int i = threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s) {
+  k_copy_scalar<<<1, 1024, 0, s>>>(dst, src, nrhs);
+  WF_CUDA(cudaGetLastError());
+}
+
+}  // namespace wf

@@ -1,0 +1,116 @@
+// Host-side internals of libwf: the handle, device buffers and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "wf_common.cuh"
+
+namespace wf {
+
+// Error carried from a failing step up to the C-ABI boundary (never crosses it).
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define WF_CUDA(call)                                                                           \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      throw ::wf::Error(3 /*WF_ECUDA*/, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+// Owning device allocation (cudaMalloc / cudaFree), zero-filled on allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // make sure at least nbytes are held; contents are zero after a (re)allocation
+  void ensure(size_t nbytes, cudaStream_t s) {
+    if (nbytes <= bytes) return;
+    release();
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error(2 /*WF_ENOMEM*/, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    bytes = nbytes;
+    WF_CUDA(cudaMemsetAsync(p, 0, nbytes, s));
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// ----------------------------------------------------------------------------
+// Launchers (defined in the .cu files)
+// ----------------------------------------------------------------------------
+template <typename R> struct LineArgs;
+
+template <typename R>
+void launch_line(const LineArgs<R>& a, int src, cudaStream_t s);
+
+template <typename R>
+struct MArgs {
+  Geom g;
+  int parity;
+  int nrhs;
+  const Cx<R>* psi_p;  // own parity  [nrhs][Nl][12][tp]
+  const Cx<R>* psi_q;  // other parity
+  const Cx<R>* ut;     // U_t of the own parity
+  const Cx<R>* us_out; // forward spatial links, own parity
+  const Cx<R>* us_nbr; // forward spatial links, other parity
+  const Cx<R>* x;      // out = x + a * (M psi) if x != nullptr
+  R a;
+  Cx<R>* out;
+  R mu, inv_gf, bc;
+};
+template <typename R>
+void launch_apply_M(const MArgs<R>& a, cudaStream_t s);
+
+// layout conversions
+template <typename R>
+void launch_import_spinor(const Geom& g, const Cx<double>* lex, Cx<R>* even, Cx<R>* odd, int nrhs, int g5,
+                          cudaStream_t s);
+template <typename R>
+void launch_export_spinor(const Geom& g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* lex, int nrhs, int g5,
+                          cudaStream_t s);
+template <typename R>
+void launch_import_compact(const Geom& g, const Cx<double>* cmp, Cx<R>* half, int nrhs, int g5, cudaStream_t s);
+template <typename R>
+void launch_export_compact(const Geom& g, const Cx<R>* half, Cx<double>* cmp, int nrhs, int g5, cudaStream_t s);
+void launch_import_gauge(const Geom& g, const Cx<double>* lex, Cx<double>* ut[2], Cx<double>* us[2],
+                         cudaStream_t s);
+void launch_tline_init(const Geom& g, const Cx<double>* ut, Cx<double>* lamb, Cx<double>* lamf, int* singular,
+                       cudaStream_t s);
+void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s);
+void launch_f2d(const Cx<float>* in, Cx<double>* out, size_t n, cudaStream_t s);
+
+// BLAS-1 on flat [nrhs][n] arrays; scalars live in device memory
+template <typename R>
+void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s);
+template <typename R>
+void launch_cg_xr(Cx<R>* x, Cx<R>* r, const Cx<R>* p, const Cx<R>* q, size_t n, int nrhs, const double* gamma,
+                  const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s);
+template <typename R>
+void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* gamma_new, const double* gamma_old,
+                 const int* active, cudaStream_t s);
+template <typename R>
+void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
+void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s);      // y += x
+void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s);
+
+}  // namespace wf

@@ -1,0 +1,296 @@
+// Time-line solves (T^-1, T^-dag) and the spatial hop D_s on the line layout.
+//
+// T^-1 (§II.A): psi(t) = (eta(t) + U_0(t) psi(t+1)) / mu for t = N_t-1 .. 0, with the
+// wrap psi(N_t) = s psi(0). T^-dag: psi(t) = (eta(t) + U_0^dag(t-1) psi(t-1)) / mu for
+// t = 0 .. N_t-1, with psi(-1) = s psi(N_t-1).
+//
+// The paper closes the wrap-around with the Sherman-Morrison-Woodbury correction
+// chi = T_0^-1 eta, q = Lambda W^dag chi, psi = chi - X q. Here the same exact
+// result is reached with a warp-parallel formulation: every lane owns n consecutive
+// times and turns them into one affine map psi_out = c + G psi_in (c the open-boundary
+// solution of its segment, G the product of U_0 / mu over the segment); a
+// Kogge-Stone scan of these maps across the lanes of the line gives every lane the
+// map from the line's open end to its own segment; the wrap-around is closed with the
+// per-line matrix Lambda = (I - s mu^-N_t P)^-1 (P the Polyakov product, precomputed
+// in FP64 at gauge load, §II.A step 1(b)); each lane then re-runs its n steps from
+// its true boundary value. Every input is read once and every output written once.
+#pragma once
+
+#include "wf_common.cuh"
+
+namespace wf {
+
+enum LineOp { OP_COPY = 0, OP_FWD = 1, OP_BWD = 2, OP_SKIP = 3 };
+enum LineSrc { SRC_LOAD = 0, SRC_HOP = 1 };
+
+template <typename R>
+struct LineArgs {
+  Geom g;
+  int parity;   // 3-D parity of the output lines
+  int nrhs;
+  int opu, opl; // LineOp for the upper (P_+) and lower (P_-) spin halves
+  // Spinor sources. SRC_LOAD reads the output site itself; SRC_HOP reads the six
+  // spatial neighbours (other parity). src_up / src_lo point at component 0 of the
+  // half that supplies spins 0-1 / spins 2-3 (line stride 12 * tp).
+  const Cx<R>* src_up;
+  const Cx<R>* src_lo;
+  // links: U_t of the output parity [Nl][9][tp]; forward spatial links of the output
+  // parity and of the neighbour parity, each [3][Nl][9][tp]
+  const Cx<R>* ut;
+  const Cx<R>* us_out;
+  const Cx<R>* us_nbr;
+  const Cx<R>* lamb;  // Lambda for T^-1, [Nl][9]
+  const Cx<R>* lamf;  // Lambda for T^-dag, [Nl][9]
+  // pre-solve axpy: v <- xpre + apre * v (skipped if xpre == nullptr)
+  const Cx<R>* xpre;
+  R apre;
+  // post-solve: out <- xpost + apost * result (plain store if xpost == nullptr)
+  const Cx<R>* xpost;
+  R apost;
+  int swap_out;  // store the upper result into the lower half and vice versa
+  Cx<R>* out;    // [nrhs][Nl][12][tp]
+  R inv_mu, bc;
+};
+
+template <typename R>
+__device__ __forceinline__ Mat3<R> ldmat(const Cx<R>* __restrict__ base, int tp, int slot) {
+  Mat3<R> U;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) U.e[k] = base[k * tp + slot];
+  return U;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> ldvec(const Cx<R>* __restrict__ base, int tp, int slot) {
+  Vec3<R> v;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = base[k * tp + slot];
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ void stvec(Cx<R>* __restrict__ base, int tp, int slot, const Vec3<R>& v) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) base[k * tp + slot] = v.c[k];
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> vzero() {
+  Vec3<R> v;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = czero<R>();
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> vaxpy(R a, const Vec3<R>& x, const Vec3<R>& y) {  // y + a x
+  Vec3<R> w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.c[k] = mk<R>(fma(a, x.c[k].re, y.c[k].re), fma(a, x.c[k].im, y.c[k].im));
+  return w;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> vscale(R a, const Vec3<R>& x) {
+  Vec3<R> w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.c[k] = a * x.c[k];
+  return w;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> vadd(const Vec3<R>& x, const Vec3<R>& y) {
+  Vec3<R> w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.c[k] = x.c[k] + y.c[k];
+  return w;
+}
+
+// ----------------------------------------------------------------------------
+// Time-line solve of NS colour vectors per site on the lane's N sites.
+// FWD = false: psi = T^-1 eta. FWD = true: psi = T^-dag eta.
+// v holds eta on entry and psi on exit. ut_line points at this line's U_t block
+// ([9][tp]); lam at its Lambda (9 complex). All lanes of the warp must call this.
+// ----------------------------------------------------------------------------
+template <typename R, int N, int NS, bool FWD>
+__device__ __forceinline__ void tline_solve(Vec3<R> (&v)[N][NS], const Cx<R>* __restrict__ ut_line,
+                                            const Cx<R>* __restrict__ lam, const Geom& g, int jj, R inv_mu, R bc) {
+  const int T = g.T, tp = g.tp, lpl = g.lpl;
+  constexpr bool KEEPU = (sizeof(R) == 4);
+  Mat3<R> Uk[KEEPU ? N : 1];
+
+  auto link_slot = [&](int m) {
+    int t = jj * N + m;
+    int tl = FWD ? (t == 0 ? T - 1 : t - 1) : t;
+    return (tl % N) * lpl + tl / N;
+  };
+  auto site_valid = [&](int m) { return jj * N + m < T; };
+
+  // pass 1: open solve of the segment (c) and its transfer matrix (G)
+  Vec3<R> c[NS];
+  Mat3<R> G = ident<R>();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) c[s] = vzero<R>();
+  bool any = false;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    const int m = FWD ? q : N - 1 - q;
+    if (!site_valid(m)) continue;
+    Mat3<R> U = ldmat(ut_line, tp, link_slot(m));
+    if (KEEPU) Uk[KEEPU ? m : 0] = U;
+    Mat3<R> A = FWD ? dagger(U) : U;
+    if (!any) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) c[s] = vscale(inv_mu, v[m][s]);
+      G = scale(inv_mu, A);
+      any = true;
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) c[s] = vscale(inv_mu, matvec_acc(A, c[s], v[m][s]));
+      G = scale(inv_mu, matmul(A, G));
+    }
+  }
+
+  // scan across the lanes of the line: suffix (T^-1) or prefix (T^-dag) composition
+  for (int d = 1; d < lpl; d <<= 1) {
+    Mat3<R> Gn;
+    Vec3<R> cn[NS];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Gn.e[k] = FWD ? shfl_up(G.e[k], d, lpl) : shfl_down(G.e[k], d, lpl);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cn[s].c[k] = FWD ? shfl_up(c[s].c[k], d, lpl) : shfl_down(c[s].c[k], d, lpl);
+    const bool has = FWD ? (jj >= d) : (jj + d < lpl);
+    if (has) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) c[s] = matvec_acc(G, cn[s], c[s]);
+      G = matmul(G, Gn);
+    }
+  }
+
+  // close the wrap: T^-1: psi(0) = Lambda c(lane 0); T^-dag: psi(N_t-1) = Lambda c(last lane)
+  const Mat3<R> Lam = ldmat(lam, 1, 0);
+  const int root = FWD ? lpl - 1 : 0;
+  Vec3<R> wrap[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    Vec3<R> w = matvec(Lam, c[s]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wrap[s].c[k] = bc * shfl_idx(w.c[k], root, lpl);
+  }
+  // boundary value entering this lane: from the neighbouring lane's scanned map
+  Vec3<R> e[NS];
+  {
+    Mat3<R> Gn;
+    Vec3<R> cn[NS];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Gn.e[k] = FWD ? shfl_up(G.e[k], 1, lpl) : shfl_down(G.e[k], 1, lpl);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cn[s].c[k] = FWD ? shfl_up(c[s].c[k], 1, lpl) : shfl_down(c[s].c[k], 1, lpl);
+    const bool edge = FWD ? (jj == 0) : (jj == lpl - 1);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) e[s] = edge ? wrap[s] : matvec_acc(Gn, wrap[s], cn[s]);
+  }
+
+  // pass 2: re-run the segment from its true boundary value
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    const int m = FWD ? q : N - 1 - q;
+    if (!site_valid(m)) continue;
+    Mat3<R> U = KEEPU ? Uk[KEEPU ? m : 0] : ldmat(ut_line, tp, link_slot(m));
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Vec3<R> a = FWD ? matvec_dag(U, e[s]) : matvec(U, e[s]);
+      e[s] = vscale(inv_mu, vadd(a, v[m][s]));
+      v[m][s] = e[s];
+    }
+  }
+}
+
+// i sigma_k applied to the two-spin vector (a0, a1): k = 0 (x), 1 (y), 2 (z)
+template <typename R>
+__device__ __forceinline__ void isigma(int k, const Vec3<R>& a0, const Vec3<R>& a1, Vec3<R>& r0, Vec3<R>& r1) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (k == 0) {
+      r0.c[c] = times_i(a1.c[c]);
+      r1.c[c] = times_i(a0.c[c]);
+    } else if (k == 1) {
+      r0.c[c] = a1.c[c];
+      r1.c[c] = mk<R>(-a0.c[c].re, -a0.c[c].im);
+    } else {
+      r0.c[c] = times_i(a0.c[c]);
+      r1.c[c] = times_mi(a1.c[c]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Spatial hop D_s (§II, Eq. for D_s) at the lane's N sites of line l (parity p):
+//   sum_k (1 - gamma_k)/2 U_k(x) psi(x + k) + (1 + gamma_k)/2 U_k^dag(x - k) psi(x - k).
+// Dirac-Pauli basis: with psi = (u, d) (upper, lower spin pairs),
+//   (1 - gamma_k) psi = (h, -i sigma_k h), h = u + i sigma_k d,
+//   (1 + gamma_k) psi = (h, +i sigma_k h), h = u - i sigma_k d,
+// so each direction costs two SU(3) matvecs on a half-spinor (App. B: 984 FLOPs/site).
+// ----------------------------------------------------------------------------
+template <typename R, int N>
+__device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[N][4], const LineArgs<R>& A, int rhs, int l, int jj) {
+  const Geom& g = A.g;
+  const int tp = g.tp, Nl = g.Nl, T = g.T;
+  int nb[6];
+  neighbour_lines(g, A.parity, l, nb);
+#pragma unroll
+  for (int m = 0; m < N; ++m)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) h[m][s] = vzero<R>();
+
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {  // 0: forward (x + k), 1: backward (x - k)
+      const int ln = nb[2 * k + dir];
+      const Cx<R>* up = A.src_up + (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
+      const Cx<R>* lo = A.src_lo + (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
+      const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * NLINK_C * tp
+                                 : A.us_nbr + (size_t)(k * Nl + ln) * NLINK_C * tp;
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        const int t = jj * N + m;
+        if (t >= T) continue;
+        const int sl = m * g.lpl + jj;
+        Vec3<R> u0 = ldvec(up, tp, sl), u1 = ldvec(up + 3 * tp, tp, sl);
+        Vec3<R> d0 = ldvec(lo, tp, sl), d1 = ldvec(lo + 3 * tp, tp, sl);
+        Mat3<R> U = ldmat(lk, tp, sl);
+        Vec3<R> s0, s1;
+        isigma(k, d0, d1, s0, s1);
+        const R half = R(0.5);
+        Vec3<R> h0, h1;
+        if (dir == 0) {
+          h0 = vscale(half, vadd(u0, s0));
+          h1 = vscale(half, vadd(u1, s1));
+        } else {
+          h0 = vscale(half, vaxpy(R(-1), s0, u0));
+          h1 = vscale(half, vaxpy(R(-1), s1, u1));
+        }
+        Vec3<R> w0 = dir == 0 ? matvec(U, h0) : matvec_dag(U, h0);
+        Vec3<R> w1 = dir == 0 ? matvec(U, h1) : matvec_dag(U, h1);
+        h[m][0] = vadd(h[m][0], w0);
+        h[m][1] = vadd(h[m][1], w1);
+        Vec3<R> r0, r1;
+        isigma(k, w0, w1, r0, r1);
+        if (dir == 0) {
+          h[m][2] = vaxpy(R(-1), r0, h[m][2]);
+          h[m][3] = vaxpy(R(-1), r1, h[m][3]);
+        } else {
+          h[m][2] = vadd(h[m][2], r0);
+          h[m][3] = vadd(h[m][3], r1);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace wf

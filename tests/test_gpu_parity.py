@@ -1,0 +1,142 @@
+"""GPU parity: every C-ABI apply and solve against the FP64 oracle (needs a GB300).
+
+Tolerances (relative 2-norm over the whole output): 1e-12 for FP64 applies and
+1e-6 for FP32 applies; solves must reach an FP64 true residual ||eta - M psi|| /
+||eta|| <= 1e-10, checked again here with the oracle's own M.
+
+Lattices span several warps and lines per warp, padded time lines (T not a
+multiple of the lane segment) and both boundary conditions.
+"""
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import solve as SV
+from oracle import wilson as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_0910_0992_gb300 as wf  # noqa: E402
+
+CASES = [
+    # L, T, kappa_s, xi, bc, eps, seed
+    (4, 16, 0.12, 3.0, -1, 0.3, 1),      # the 4^3 x 16 workload's parameters
+    (2, 6, 0.07, 3.0, -1, 0.4, 2),       # 3 sites per lane, 2 lanes per line
+    (4, 7, 0.08, 2.5, 1, 0.3, 3),        # odd T: padded slot, periodic
+    (6, 12, 0.075, 3.5, -1, 0.3, 4),     # L = 6
+    (4, 128, 0.074, 3.5, -1, 0.2, 5),    # 4 sites per lane, full warp per line
+    (8, 32, 0.07, 3.0, 1, 0.25, 6),      # many warps
+]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"L{c[0]}T{c[1]}bc{c[4]}")
+def case(request):
+    L, T, ks, xi, bc, eps, seed = request.param
+    p = W.Params(L, T, ks, xi=xi, bc=bc)
+    U = S.random_gauge(L, T, eps, seed)
+    eta = S.gaussian_source(L, T, seed + 100, nrhs=2)
+    w = wf.Wilson(L, T, ks, kappa_t=xi * ks, bc=bc)
+    w.load_gauge(U)
+    yield p, U, eta, w
+    w.close()
+
+
+def test_apply_M(case):
+    p, U, eta, w = case
+    x = _dev(eta)
+    ref = W.M(U, eta, p)
+    assert _rel(_host(w.apply_M(x)), ref) < 1e-12
+    refd = W.M_dag(U, eta, p)
+    assert _rel(_host(w.apply_M(x, dagger=True)), refd) < 1e-12
+    assert _rel(_host(w.apply_M(x, f32=True)), ref) < 1e-6
+
+
+def test_apply_Tinv(case):
+    p, U, eta, w = case
+    x = _dev(eta)
+    assert _rel(_host(w.apply_Tinv(x)), W.Tinv(U, eta, p)) < 1e-12
+    assert _rel(_host(w.apply_Tinv(x, dagger=True)), W.Tdag_inv(U, eta, p)) < 1e-12
+    assert _rel(_host(w.apply_Tinv(x, f32=True)), W.Tinv(U, eta, p)) < 1e-6
+
+
+def test_apply_C(case):
+    p, U, eta, w = case
+    x = _dev(eta)
+    assert _rel(_host(w.apply_C(x, 0)), W.C_L(U, eta, p)) < 1e-12
+    assert _rel(_host(w.apply_C(x, 1)), W.C_R(U, eta, p)) < 1e-12
+
+
+def test_apply_schur(case):
+    p, U, eta, w = case
+    par3 = W.parity3(p.L, p.T)
+    odd = par3 == 1
+    xo = SV.compact(eta, odd)
+    full = SV.expand(xo, odd)
+    ref = SV.compact(W.M_hat(U, full, p, par3), odd)
+    refd = SV.compact(W.M_hat_dag(U, full, p, par3), odd)
+    x = _dev(xo)
+    assert _rel(_host(w.apply_schur(x)), ref) < 1e-12
+    assert _rel(_host(w.apply_schur(x, dagger=True)), refd) < 1e-12
+    assert _rel(_host(w.apply_schur(x, f32=True)), ref) < 1e-6
+    assert _rel(_host(w.apply_schur(x, dagger=True, f32=True)), refd) < 1e-6
+
+
+def test_host_pointers_match_device(case):
+    p, U, eta, w = case
+    par3 = W.parity3(p.L, p.T)
+    xo = np.ascontiguousarray(SV.compact(eta, par3 == 1))
+    a = w.apply_schur(xo)               # NumPy in, NumPy out: host staging in the library
+    b = _host(w.apply_schur(_dev(xo)))
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [wf.WF_FP64, wf.WF_FP32])
+def test_solve_temporal_schur(case, precision):
+    p, U, eta, w = case
+    x, iters, res, status = w.solve(_dev(eta), tol=1e-10, precision=precision)
+    assert status == wf.WF_OK
+    assert all(r <= 1e-10 for r in res)
+    assert all(i > 0 for i in iters)
+    psi = _host(x)
+    for k in range(eta.shape[0]):
+        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+
+
+def test_solve_matches_oracle_solution():
+    """4^3 x 16 workload: the GPU solution equals the oracle's (unique solution, bound by kappa * tol)."""
+    prm, U, eta = S.workload("wilson_4c16_xi3")
+    p = W.Params(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    w.load_gauge(U)
+    psi_ref, it_ref, _ = SV.solve(U, eta[0], p, "temporal_schur", tol=1e-12)
+    x, iters, res, status = w.solve(_dev(eta), tol=1e-10, precision=wf.WF_FP32)
+    assert status == wf.WF_OK and res[0] <= 1e-10
+    assert _rel(_host(x)[0], psi_ref) < 1e-7
+    w.close()
+
+
+def test_singular_preconditioner_is_reported():
+    """mu = 1 (kappa_t = 1/2), periodic, unit links: T has a zero mode, so Lambda does not exist."""
+    L, T = 2, 4
+    w = wf.Wilson(L, T, 0.25, kappa_t=0.5, bc=1)
+    with pytest.raises(wf.WFError) as e:
+        w.load_gauge(S.unit_gauge(L, T))
+    assert e.value.code == wf.WF_ESINGULAR
+    w.close()
