@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the temporally preconditioned Wilson solve on GB300.
+
+A step is one complete solve of the 24^3 x 128, xi = 3.5 anisotropic Wilson
+workload for its 12 spin-colour point sources (one batched wf_solve call): source
+preparation with S_L, CGNR on the temporal + 3-D Schur operator M-hat with FP32
+applies and FP64 reliable updates, reconstruction with S_R, FP64 true residual
+||eta - M psi|| / ||eta|| <= 1e-10 for every source.
+
+value = algorithmic HBM bytes of all M-hat applies in the timed steps / device
+time of the steps (GB/s). The roofline entry reports the dominant kernel's
+algorithmic bytes per launch over its CUDA-event duration against the measured
+HBM copy bandwidth. cpu_baseline (and --impl reference) time the FP64 NumPy
+oracle's M-hat apply on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "precond Wilson apply HBM GB/s & %roofline; time-to-solve 1e-10, 24^3x128 ξ=3.5"
+WORKLOAD = "wilson_24c128_xi3.5"
+
+# Algorithmic bytes per odd site of one M-hat apply, by kernel, FP32 storage
+# (complex = 8 B; half spinor 48 B, full spinor 96 B, SU(3) link 72 B):
+#   K-a  y = C_R^o x               : x upper half in, U_t, y upper half out        = 48 + 72 + 48
+#   K-b  z = C_R^e C_L^e D_s^eo y   : neighbour spinor (read once), 6 spatial links, U_t, z out
+#                                                                                  = 96 + 432 + 72 + 96
+#   K-c  out = x - C_L^o D_s^oe z   : neighbour z, 6 links, U_t, x, out             = 96 + 432 + 72 + 96 + 96
+# FP64 storage doubles every figure.
+KERNEL_BYTES_F32 = {"schur_a_tdag": 168, "schur_b_hop_tsolve": 696, "schur_c_hop_tinv_axpy": 792}
+APPLY_BYTES_F32 = sum(KERNEL_BYTES_F32.values())  # 1656 B per odd site
+
+
+def paper_flops_per_apply(L, T):
+    """(3432 N_t - 576)(V_s / 2) FLOPs per M-hat apply (App. B, Wilson temporal + Schur)."""
+    return (3432 * T - 576) * (L ** 3 // 2)
+
+
+def kernel_bytes(name):
+    for base, b in KERNEL_BYTES_F32.items():
+        if name == base + "_f32":
+            return b
+        if name == base + "_f64":
+            return 2 * b
+    return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0910_0992_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("source_hash") != source_hash():
+        return None
+    e = t.get("kernels", {}).get(kernel)
+    if not e or e.get("workload") != WORKLOAD:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def oracle_sample(target_s, prm):
+    """Time the FP64 oracle's M-hat apply on a lattice of the workload's couplings sized for ~target_s.
+
+    Returns (GB/s in the FP64 model bytes, description, threads used, seconds).
+    """
+    import numpy as np
+
+    import synthetic as S
+    from oracle import wilson as W
+
+    per_site_s = 37.4 / (24 ** 3 * 128)  # oracle cost measured on an 8-core x86 host, for sizing only
+    L = int(round((target_s / (per_site_s * prm["T"])) ** (1.0 / 3.0)))
+    L = max(4, min(prm["L"], L - (L % 2)))
+    T = prm["T"]
+    p = W.Params(L, T, prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    U = S.random_gauge(L, T, prm["eps"], prm["seed"])
+    par3 = W.parity3(L, T)
+    x = W.restrict(S.gaussian_source(L, T, prm["seed"] + 7), par3 == 1)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    W.M_hat(U, x, p, par3)
+    dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    threads = max(1, int(round(cpu / dt)))
+    odd_sites = L ** 3 * T // 2
+    gbs = 2 * APPLY_BYTES_F32 * odd_sites / dt / 1e9
+    desc = (f"one FP64 oracle M-hat apply on a {L}^3x{T} lattice with the workload's couplings "
+            f"(1 source; the full 24^3x128 x 12-source step is {24 ** 3 / L ** 3 * 12:.0f}x larger)")
+    return gbs, desc, threads, dt
+
+
+def run_reference(args, prm):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    vals, desc, threads, secs = [], "", 1, []
+    for i in range(args.warmup + args.steps):
+        gbs, desc, threads, dt = oracle_sample(per_step, prm)
+        if i >= args.warmup:
+            vals.append(gbs)
+            secs.append(dt)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, prm, U, eta):
+    import numpy as np
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prec = wf.WF_FP32 if args.precision == "fp32" else wf.WF_FP64
+    stream = torch.cuda.Stream()
+    w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    w.set_stream(stream.cuda_stream)
+    w.load_gauge(U)
+    nsrc = eta.shape[0]
+    rhs = torch.from_numpy(eta).cuda()
+    x = torch.empty_like(rhs)
+
+    def solve(r, xx):
+        st, it, res = wf.wf_solve(w.h, r, xx, nsrc, args.tol, wf.WF_TEMPORAL_SCHUR, prec, 0)
+        if st != wf.WF_OK or max(res) > args.tol:
+            raise RuntimeError(f"solve failed: status {st}, residuals {res}")
+        return it, res
+
+    for _ in range(args.warmup):
+        solve(rhs, x)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    wf.wf_profile(w.h, 1)
+    n0 = wf.wf_launch_count(w.h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = None
+    for _ in range(args.steps):
+        iters, res = solve(rhs, x)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = wf.wf_launch_count(w.h) - n0
+    clk = clocks.stop()
+    prof = wf.wf_profile_get(w.h)
+    wf.wf_profile(w.h, 0)
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    odd_sites = prm["L"] ** 3 * prm["T"] // 2
+    applies_f32 = prof.get("schur_c_hop_tinv_axpy_f32", (0, 0))[0]
+    applies_f64 = prof.get("schur_c_hop_tinv_axpy_f64", (0, 0))[0]
+    # every M-hat launch sequence works on all nsrc sources at once
+    apply_bytes = (applies_f32 + 2 * applies_f64) * APPLY_BYTES_F32 * odd_sites * nsrc
+    value = world * apply_bytes / (ms * 1e-3) / 1e9
+    flops = (applies_f32 + applies_f64) * paper_flops_per_apply(prm["L"], prm["T"]) * nsrc
+
+    # roofline: the dominant kernel by time
+    cand = {k: v for k, v in prof.items() if kernel_bytes(k) is not None and v[0] > 0}
+    dom = max(cand, key=lambda k: cand[k][1])
+    n_l, ms_l = cand[dom]
+    bytes_launch = kernel_bytes(dom) * odd_sites * nsrc
+    achieved = bytes_launch / (ms_l / n_l * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = traffic_for(dom)
+    schur_ms = sum(cand[k][1] for k in cand)
+    total_prof_ms = sum(v[1] for v in prof.values())
+
+    # end to end through the C-ABI with host (pinned) buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_rhs = torch.from_numpy(eta).pin_memory()
+        h_x = torch.empty_like(h_rhs).pin_memory()
+        solve(h_rhs, h_x)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            solve(h_rhs, h_x)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * apply_bytes / e2e_s / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(h_rhs.numel() * 16), "d2h_bytes_per_step": int(h_x.numel() * 16),
+               "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gbs, desc, threads, dt = oracle_sample(20.0, prm)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == wf.WF_FP32 else "f64", "data": "synthetic",
+            "config": {
+                "workload": f"{WORKLOAD}: 24^3x128, xi=3.5, kappa_s={prm['kappa_s']:.6f}, "
+                            f"kappa_t={prm['kappa_t']:.6f}, antiperiodic, eps=0.2 random SU(3) links, "
+                            f"12 point sources solved in one batched call",
+                "method": "temporal + 3-D Schur preconditioned CGNR (S_L prep, S_R reconstruction)",
+                "precision": ("FP32 M-hat applies, FP64 reliable updates, FP64 true residual"
+                              if prec == wf.WF_FP32 else "FP64 throughout"),
+                "tol": args.tol, "parallelism": f"replicas x{world} (sources per GPU fixed)",
+                "l2": "inputs larger than L2 (4.1 GB of sources, 2.5 GB of gauge copies)",
+            },
+            "time_to_solve_s": ms / args.steps / 1e3,
+            "iterations": iters,
+            "m_hat_applies_per_step": {"f32": applies_f32 // args.steps, "f64": applies_f64 // args.steps},
+            "gflops_paper_model": world * flops / (ms * 1e-3) / 1e9,
+            "schur_kernel_share": schur_ms / total_prof_ms if total_prof_ms else None,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
+                         "avg_launch_ms": ms_l / n_l},
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    w.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_apply(args, prm, U, eta):
+    """--mode apply: only M-hat applies (FP32, one source) for kernel profiling; prints per-kernel times."""
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+    import synthetic as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    w.load_gauge(U)
+    half = prm["L"] ** 3 * prm["T"] // 2 * 12
+    x = torch.from_numpy(S.gaussian_source(prm["L"], prm["T"], 77).reshape(-1)[:half].copy()).cuda()
+    out = torch.empty_like(x)
+    for _ in range(args.warmup):
+        wf.wf_apply_schur_f32(w.h, x, out, 0, 1)
+    wf.wf_profile(w.h, 1)
+    for _ in range(args.steps):
+        wf.wf_apply_schur_f32(w.h, x, out, 0, 1)
+    prof = wf.wf_profile_get(w.h)
+    odd_sites = prm["L"] ** 3 * prm["T"] // 2
+    rows = {}
+    for k, (n, ms) in prof.items():
+        b = kernel_bytes(k)
+        rows[k] = {"launches": n, "avg_ms": ms / n,
+                   "gbs": (b * odd_sites / (ms / n * 1e-3) / 1e9) if b else None}
+    print(json.dumps({"mode": "apply", "workload": WORKLOAD, "kernels": rows}))
+    w.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
+                    help="apply: only FP32 M-hat applies on one source (for kernel profiling)")
+    args = ap.parse_args()
+
+    import synthetic as S
+
+    prm = dict(S.WORKLOADS[WORKLOAD])
+    if args.impl == "reference":
+        return run_reference(args, prm)
+    _, U, eta = S.workload(WORKLOAD, with_sources=args.mode == "solve")
+    if args.mode == "apply":
+        return run_apply(args, prm, U, eta)
+    return run_ours(args, prm, U, eta)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -124,6 +124,9 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
              int flags, int* iters_out, double* true_resid_out);
 
+/* Number of kernels this handle has launched since it was created (all entry points). */
+long long wf_launch_count(const wf_handle_t* h);
+
 /* Per-kernel timing on the handle's stream (CUDA events around every launch), for
  * benchmarks. wf_profile(h, 1) clears the counters and starts recording; wf_profile(h, 0)
  * stops. wf_profile_get fills up to cap entries of (name, launches, total milliseconds) and

@@ -36,6 +36,7 @@ _SIGS = {
     "wf_apply_schur": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
+    "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_profile": (_i, [_vp, _i]),
     "wf_profile_get": (_i, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), _dp, _i]),
 }
@@ -136,6 +137,10 @@ def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):
     if code not in (WF_OK, WF_ENOCONV):
         _check(h, code)
     return code, list(iters), list(res)
+
+
+def wf_launch_count(h):
+    return lib.wf_launch_count(h)
 
 
 def wf_profile(h, on):

@@ -1,6 +1,7 @@
 """Build libwf.so in-tree with nvcc for sm_103a (GB300).
 
-Usage: ``python -m paper_0910_0992_gb300.build_lib`` or ``build()`` from Python.
+Usage: ``python paper_0910_0992_gb300/build_lib.py`` (as a script: importing the
+package needs the built library) or ``__graft_entry__.build()``.
 Each CUDA translation unit is compiled in parallel, then linked into a shared
 library next to this file. Object files go to ``_build/`` (git-ignored).
 """

@@ -43,6 +43,7 @@ struct wf_handle {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<long long> prof_count;
   std::vector<double> prof_ms;
+  long long launches = 0;          // kernels launched by this handle
   double* host_scalars = nullptr;  // pinned
 
   template <typename T>
@@ -88,7 +89,8 @@ struct Prof {
   wf_handle* h;
   ProfRec rec{};
   bool on;
-  Prof(wf_handle* hh, const char* name) : h(hh), on(hh->prof) {
+  Prof(wf_handle* hh, const char* name, int nlaunch = 1) : h(hh), on(hh->prof) {
+    h->launches += nlaunch;
     if (!on) return;
     auto it = h->prof_ids.find(name);
     if (it == h->prof_ids.end()) {
@@ -408,7 +410,7 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
   // r64 = b - M-hat y (FP64) or b
   auto true_schur_residual = [&]() {
     schur_apply<double>(h, y, r64, 0, nrhs, ty64, tz64);
-    launch_axpby<double>(r64, b, nt, 1.0, -1.0, s);  // r64 = b - M-hat y
+    { Prof P(h, "axpby_f64"); launch_axpby<double>(r64, b, nt, 1.0, -1.0, s); }  // r64 = b - M-hat y
   };
   if (x0) {
     true_schur_residual();
@@ -418,14 +420,14 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
   }
   // working residual in precision R; x increment accumulates in R
   if (mixed) {
-    launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s);
+    { Prof P(h, "d2f"); launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s); }
     WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<R>), s));
   } else {
     WF_CUDA(cudaMemcpyAsync(r, r64, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
   }
   Cx<R>* xacc = mixed ? xi : reinterpret_cast<Cx<R>*>(y);
 
-  launch_norm2<double>(r64, n, nrhs, partial, rr, s);
+  { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
   std::vector<double> rnorm2 = read_scalars(h, rr, nrhs);
   std::vector<double> rmax(nrhs);
   for (int k = 0; k < nrhs; ++k) {
@@ -442,13 +444,13 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
 
   schur_apply<R>(h, r, sv, 1, nrhs, ty, tz);  // s = M-hat^dag r
   WF_CUDA(cudaMemcpyAsync(p, sv, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
-  launch_norm2<R>(sv, n, nrhs, partial, gam, s);
+  { Prof P(h, pname<R>("norm2"), 2); launch_norm2<R>(sv, n, nrhs, partial, gam, s); }
 
   const double delta = 0.1;  // reliable-update trigger: residual dropped by this factor
   for (int it = 0; it < maxiter; ++it) {
     schur_apply<R>(h, p, q, 0, nrhs, ty, tz);  // q = M-hat p
-    launch_norm2<R>(q, n, nrhs, partial, qq, s);
-    launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s);
+    { Prof P(h, pname<R>("norm2"), 2); launch_norm2<R>(q, n, nrhs, partial, qq, s); }
+    { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s); }
     for (int k = 0; k < nrhs; ++k)
       if (act[k]) iters[k]++;
     std::vector<double> rrh = read_scalars(h, rr, nrhs);
@@ -466,11 +468,11 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
     }
     if (need_ru) {
       // reliable update: fold the FP32 increment into y, recompute the residual in FP64
-      launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);
+      { Prof P(h, "add_f_to_d"); launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s); }
       WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<R>), s));
       true_schur_residual();
-      launch_norm2<double>(r64, n, nrhs, partial, rr, s);
-      launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s);
+      { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
+      { Prof P(h, "d2f"); launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s); }
       std::vector<double> r64n = read_scalars(h, rr, nrhs);
       for (int k = 0; k < nrhs; ++k) {
         if (!act[k]) continue;
@@ -484,11 +486,14 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
     if (changed) WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     if (all_done()) break;
     schur_apply<R>(h, r, sv, 1, nrhs, ty, tz);  // s = M-hat^dag r
-    launch_norm2<R>(sv, n, nrhs, partial, gnew, s);
-    launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s);
-    launch_copy_scalar(gam, gnew, nrhs, s);
+    { Prof P(h, pname<R>("norm2"), 2); launch_norm2<R>(sv, n, nrhs, partial, gnew, s); }
+    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
+    { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s); }
   }
-  if (mixed) launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);
+  if (mixed) {
+    Prof P(h, "add_f_to_d");
+    launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);
+  }
   return iters;
 }
 
@@ -512,7 +517,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   double* sc = h->buf<double>("sv_scalars", 4 * (size_t)nrhs);
   double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
 
-  launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, s);
+  { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, s); }
   // source preparation (S_L): a_e = C_R^e C_L^e eta_e ; b_o = C_L^o [eta_o + gamma_f^-1 D_s^oe a_e]
   line_load<double>(h, 0, eta_e, a_e, OP_FWD, OP_BWD, nrhs, "prep_tsolve");
   {
@@ -528,8 +533,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     launch_line<double>(a, SRC_HOP, s);
   }
   // |eta|^2 per rhs
-  launch_norm2<double>(eta_e, n, nrhs, partial, sc, s);
-  launch_norm2<double>(eta_o, n, nrhs, partial, sc + nrhs, s);
+  { Prof P(h, "norm2_f64", 4); launch_norm2<double>(eta_e, n, nrhs, partial, sc, s); launch_norm2<double>(eta_o, n, nrhs, partial, sc + nrhs, s); }
   std::vector<double> e2 = read_scalars(h, sc, 2 * nrhs);
   std::vector<double> eta2(nrhs), target(nrhs);
   for (int k = 0; k < nrhs; ++k) {
@@ -541,7 +545,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   if (x0) {
     // initial guess: y_o = (C_R^o)^-1 psi_o; use only the odd part of the guess
     Cx<double>* g_e = r_e;
-    launch_import_spinor<double>(h->g, x_lex, g_e, psi_o, nrhs, 0, s);
+    { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex, g_e, psi_o, nrhs, 0, s); }
     // (C_R^o)^-1 = P_- + P_+ T^dag is not needed exactly: start from y_o = psi_o
     WF_CUDA(cudaMemcpyAsync(y_o, psi_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
   }
@@ -570,8 +574,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     }
     // true residual r = eta - M psi in FP64
     m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
-    launch_norm2<double>(r_e, n, nrhs, partial, sc, s);
-    launch_norm2<double>(r_o, n, nrhs, partial, sc + nrhs, s);
+    { Prof P(h, "norm2_f64", 4); launch_norm2<double>(r_e, n, nrhs, partial, sc, s); launch_norm2<double>(r_o, n, nrhs, partial, sc + nrhs, s); }
     std::vector<double> r2 = read_scalars(h, sc, 2 * nrhs);
     bool ok = true;
     for (int k = 0; k < nrhs; ++k) {
@@ -585,7 +588,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     if (ok || status == WF_ENOCONV) break;
     if (pass == 5) status = WF_ENOCONV;
   }
-  launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, s);
+  { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, s); }
   for (int k = 0; k < nrhs; ++k) {
     if (iters_out) iters_out[k] = iters[k];
     if (resid_out) resid_out[k] = rel[k];
@@ -606,9 +609,9 @@ int apply_schur_abi(wf_handle* h, const double* in_odd, double* out_odd, int dag
   Cx<R>* o = h->buf<Cx<R>>(pname<R>("ap_o"), nt);
   Cx<R>* y = h->buf<Cx<R>>(pname<R>("ap_y"), nt);
   Cx<R>* z = h->buf<Cx<R>>(pname<R>("ap_z"), nt);
-  launch_import_compact<R>(h->g, din, x, nrhs, 0, h->stream);
+  { Prof P(h, pname<R>("import_compact")); launch_import_compact<R>(h->g, din, x, nrhs, 0, h->stream); }
   schur_apply<R>(h, x, o, dagger, nrhs, y, z);
-  launch_export_compact<R>(h->g, o, dout, nrhs, 0, h->stream);
+  { Prof P(h, pname<R>("export_compact")); launch_export_compact<R>(h->g, o, dout, nrhs, 0, h->stream); }
   finish_out(h, out_odd, dout, ce, staged);
   return WF_OK;
 }
@@ -626,9 +629,9 @@ int apply_M_abi(wf_handle* h, const double* in, double* out, int dagger, int nrh
   Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
   Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
   Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
-  launch_import_spinor<R>(h->g, din, ie, io, nrhs, dagger, h->stream);
+  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, dagger, h->stream); }
   m_apply<R>(h, ie, io, oe, oo, nullptr, nullptr, 0.0, nrhs);
-  launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, dagger, h->stream);
+  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, dagger, h->stream); }
   finish_out(h, out, dout, le, staged);
   return WF_OK;
 }
@@ -646,10 +649,10 @@ int apply_line_abi(wf_handle* h, const double* in, double* out, int opu, int opl
   Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
   Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
   Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
-  launch_import_spinor<R>(h->g, din, ie, io, nrhs, 0, h->stream);
+  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, 0, h->stream); }
   line_load<R>(h, 0, ie, oe, opu, opl, nrhs, name);
   line_load<R>(h, 1, io, oo, opu, opl, nrhs, name);
-  launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, 0, h->stream);
+  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, 0, h->stream); }
   finish_out(h, out, dout, le, staged);
   return WF_OK;
 }
@@ -745,6 +748,7 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
     WF_CUDA(cudaMemsetAsync(h->iflag.p, 0, sizeof(int), s));
     Cx<double>* ut[2] = {h->ut64[0].as<Cx<double>>(), h->ut64[1].as<Cx<double>>()};
     Cx<double>* us[2] = {h->us64[0].as<Cx<double>>(), h->us64[1].as<Cx<double>>()};
+    Prof P(h, "gauge_ingest", 1 + 2 * 5);
     launch_import_gauge(g, dU, ut, us, s);
     for (int p = 0; p < 2; ++p) {
       launch_tline_init(g, ut[p], h->lamb64[p].as<Cx<double>>(), h->lamf64[p].as<Cx<double>>(), h->iflag.as<int>(), s);
@@ -820,6 +824,8 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     return st;
   });
 }
+
+long long wf_launch_count(const wf_handle_t* h) { return h ? h->launches : 0; }
 
 int wf_profile(wf_handle_t* h, int on) {
   return guarded(h, [&]() {

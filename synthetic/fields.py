@@ -37,14 +37,26 @@ def _reunitarise(u):
     return q * phase[..., None, None]
 
 
+def _det3(u):
+    return (u[..., 0, 0] * (u[..., 1, 1] * u[..., 2, 2] - u[..., 1, 2] * u[..., 2, 1])
+            - u[..., 0, 1] * (u[..., 1, 0] * u[..., 2, 2] - u[..., 1, 2] * u[..., 2, 0])
+            + u[..., 0, 2] * (u[..., 1, 0] * u[..., 2, 1] - u[..., 1, 1] * u[..., 2, 0]))
+
+
 def random_su3(shape, eps, rng):
-    """exp(i eps H) with H = sum_a h_a lambda_a / 2, h_a ~ N(0, 1), one per entry of ``shape``."""
+    """exp(i eps H) with H = sum_a h_a lambda_a / 2, h_a ~ N(0, 1), one per entry of ``shape``.
+
+    The exponential is taken through the eigen-decomposition of H; one Newton step
+    of the polar iteration, u <- u (3 - u^dag u) / 2, and a cube-root phase fix of
+    the determinant then hold u in SU(3) to rounding.
+    """
     h = rng.standard_normal(size=tuple(shape) + (8,))
-    lam = gell_mann()
-    H = np.einsum("...a,aij->...ij", h, lam) * 0.5
+    lam = gell_mann().reshape(8, 9)
+    H = (h @ lam).reshape(tuple(shape) + (3, 3)) * 0.5
     w, v = np.linalg.eigh(H)
-    u = np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * eps * w), v.conj())
-    return _reunitarise(u)
+    u = (v * np.exp(1j * eps * w)[..., None, :]) @ np.swapaxes(v.conj(), -1, -2)
+    u = 0.5 * u @ (3.0 * np.eye(3) - np.swapaxes(u.conj(), -1, -2) @ u)
+    return u * np.exp(-1j * np.angle(_det3(u)) / 3.0)[..., None, None]
 
 
 def random_gauge(L, T, eps, seed):
