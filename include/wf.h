@@ -124,6 +124,24 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
              int flags, int* iters_out, double* true_resid_out);
 
+/* The FP64 M-hat apply of wf_apply_schur, with every byte of its work memory taken from one
+ * fixed device array that the library reserves, so this call allocates nothing. For callers
+ * that cannot have a library call cudaMalloc at apply time: applications whose own pool has
+ * reserved nearly all device memory, latency-critical loops (cudaFree synchronises the device),
+ * processes with a device-memory budget fixed at start-up. The paper has no counterpart; it is
+ * a deployment variant of the same operation.
+ *   - in_odd and out_odd must be device memory (odd fields as for wf_apply_schur).
+ *   - Work memory: WF_NOALLOC_SCRATCH_BYTES per device; it holds 4 internal odd fields of
+ *     nrhs right-hand sides, so roughly nrhs * L^3 * T <= 43,000 sites (e.g. 8^3 x 64 or
+ *     12^3 x 24 for nrhs = 1). Larger requests return WF_EINVAL with the size needed.
+ *   - The array exists on every GPU where the library's code is loaded and stays allocated
+ *     until the process exits. The first call on a device looks up its device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the array; each call clears what it uses first. Calls whose
+ *     device work overlaps (several streams, handles or host threads) race: order them. */
+#define WF_NOALLOC_SCRATCH_BYTES (16u << 20)
+int wf_apply_schur_noalloc(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+
 /* Number of kernels this handle has launched since it was created (all entry points). */
 long long wf_launch_count(const wf_handle_t* h);
 

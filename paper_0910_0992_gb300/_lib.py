@@ -35,6 +35,7 @@ _SIGS = {
     "wf_apply_C": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_schur_noalloc": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_profile": (_i, [_vp, _i]),
@@ -126,6 +127,7 @@ wf_apply_Tinv_f32 = _apply(lib.wf_apply_Tinv_f32)
 wf_apply_C = _apply(lib.wf_apply_C)
 wf_apply_schur = _apply(lib.wf_apply_schur)
 wf_apply_schur_f32 = _apply(lib.wf_apply_schur_f32)
+wf_apply_schur_noalloc = _apply(lib.wf_apply_schur_noalloc)
 
 
 def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):

@@ -15,110 +15,10 @@
 
 using namespace wf;
 
-// ----------------------------------------------------------------------------
-// Handle
-// ----------------------------------------------------------------------------
-struct ProfRec {
-  int id;
-  cudaEvent_t a, b;
-};
-
-struct wf_handle {
-  Geom g{};
-  double xi = 0, kappa_s = 0, kappa_t = 0;
-  cudaStream_t stream = 0;
-  int device = 0;
-  std::string err;
-  bool gauge = false;
-  // gauge, per parity: U_t [Nl][9][tp], spatial [3][Nl][9][tp], Lambda [Nl][9]
-  DevBuf ut64[2], us64[2], lamb64[2], lamf64[2];
-  DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];
-  DevBuf iflag;
-  std::map<std::string, std::unique_ptr<DevBuf>> ws;  // named work buffers
-  // profiling
-  bool prof = false;
-  std::vector<std::string> prof_names;
-  std::map<std::string, int> prof_ids;
-  std::vector<ProfRec> prof_pending;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<long long> prof_count;
-  std::vector<double> prof_ms;
-  long long launches = 0;          // kernels launched by this handle
-  double* host_scalars = nullptr;  // pinned
-
-  template <typename T>
-  T* buf(const std::string& name, size_t count) {
-    auto& b = ws[name];
-    if (!b) b.reset(new DevBuf());
-    b->ensure(count * sizeof(T), stream);
-    return b->as<T>();
-  }
-  size_t half_int() const { return (size_t)g.Nl * NSPIN_C * g.tp; }  // internal elements, one parity, one rhs
-  size_t lex_elems() const { return (size_t)g.L * g.L * g.L * g.T * NSPIN_C; }
-
-  // ---- profiling helpers
-  cudaEvent_t take_event() {
-    if (!ev_pool.empty()) {
-      cudaEvent_t e = ev_pool.back();
-      ev_pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    WF_CUDA(cudaEventCreate(&e));
-    return e;
-  }
-  void fold_pending() {
-    if (prof_pending.empty()) return;
-    WF_CUDA(cudaEventSynchronize(prof_pending.back().b));
-    for (auto& r : prof_pending) {
-      float ms = 0.f;
-      WF_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
-      prof_ms[r.id] += ms;
-      prof_count[r.id] += 1;
-      ev_pool.push_back(r.a);
-      ev_pool.push_back(r.b);
-    }
-    prof_pending.clear();
-  }
-};
+#include "wf_handle.h"
 
 namespace {
 
-// RAII: CUDA events around one kernel launch when profiling is on
-struct Prof {
-  wf_handle* h;
-  ProfRec rec{};
-  bool on;
-  Prof(wf_handle* hh, const char* name, int nlaunch = 1) : h(hh), on(hh->prof) {
-    h->launches += nlaunch;
-    if (!on) return;
-    auto it = h->prof_ids.find(name);
-    if (it == h->prof_ids.end()) {
-      int id = (int)h->prof_names.size();
-      h->prof_ids[name] = id;
-      h->prof_names.push_back(name);
-      h->prof_count.push_back(0);
-      h->prof_ms.push_back(0.0);
-      rec.id = id;
-    } else {
-      rec.id = it->second;
-    }
-    rec.a = h->take_event();
-    rec.b = h->take_event();
-    WF_CUDA(cudaEventRecord(rec.a, h->stream));
-  }
-  ~Prof() {
-    if (!on) return;
-    cudaEventRecord(rec.b, h->stream);
-    h->prof_pending.push_back(rec);
-    if (h->prof_pending.size() > 4096) {
-      try {
-        h->fold_pending();
-      } catch (...) {
-      }
-    }
-  }
-};
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -268,6 +168,9 @@ void line_load(wf_handle* h, int parity, const Cx<R>* in, Cx<R>* out, int opu, i
 //   K-a  y = C_R^o x                        (T^-dag on the upper half only)
 //   K-b  z = C_R^e C_L^e D_s^eo y           (hop, then T^-dag upper / T^-1 lower)
 //   K-c  out = x - gamma_f^-2 C_L^o D_s^oe z (hop, T^-1 lower, axpy)
+}  // namespace
+
+namespace wf {
 template <typename R>
 void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z) {
   const int tp = h->g.tp;
@@ -305,6 +208,11 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     launch_line<R>(a, SRC_HOP, h->stream);
   }
 }
+template void schur_apply<float>(wf_handle*, const Cx<float>*, Cx<float>*, int, int, Cx<float>*, Cx<float>*);
+template void schur_apply<double>(wf_handle*, const Cx<double>*, Cx<double>*, int, int, Cx<double>*, Cx<double>*);
+}  // namespace wf
+
+namespace {
 
 // out = M in (or x + a M in) on both parities
 template <typename R>
