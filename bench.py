@@ -34,28 +34,36 @@ METRIC = "precond Wilson apply HBM GB/s & %roofline; time-to-solve 1e-10, 24^3x1
 WORKLOAD = "wilson_24c128_xi3.5"
 
 # Algorithmic bytes per odd site of one M-hat apply, by kernel, FP32 storage
-# (complex = 8 B; half spinor 48 B, full spinor 96 B, SU(3) link 72 B):
-#   K-a  y = C_R^o x               : x upper half in, U_t, y upper half out        = 48 + 72 + 48
-#   K-b  z = C_R^e C_L^e D_s^eo y   : neighbour spinor (read once), 6 spatial links, U_t, z out
-#                                                                                  = 96 + 432 + 72 + 96
-#   K-c  out = x - C_L^o D_s^oe z   : neighbour z, 6 links, U_t, x, out             = 96 + 432 + 72 + 96 + 96
-# FP64 storage doubles every figure.
-KERNEL_BYTES_F32 = {"schur_a_tdag": 168, "schur_b_hop_tsolve": 696, "schur_c_hop_tinv_axpy": 792}
-APPLY_BYTES_F32 = sum(KERNEL_BYTES_F32.values())  # 1656 B per odd site
+# (complex = 8 B; half spinor 48 B, full spinor 96 B, SU(3) link 72 B), in the axial frame
+# the library works in by default (U_t = 1 on the line, so no U_t is read; the per-line P and
+# Lambda add 144 B per 128 sites and are left out):
+#   K-a  y = C_R^o x               : x upper half in, y upper half out             = 48 + 48
+#   K-b  z = C_R^e C_L^e D_s^eo y   : neighbour spinor (read once), 6 spatial links, z out
+#                                                                                  = 96 + 432 + 96
+#   K-c  out = x - C_L^o D_s^oe z   : neighbour z, 6 links, x, out                  = 96 + 432 + 96 + 96
+# FP64 storage doubles every figure. (Caller's-gauge frame: + 72 B of U_t in each kernel.)
+# With several right-hand sides the nrhs warps of a line run together and read its links
+# once (through L2), so a launch moves  odd_sites * (nrhs * spinor bytes + link bytes).
+KERNEL_BYTES_F32 = {"schur_a_tdag": (96, 0), "schur_b_hop_tsolve": (192, 432), "schur_c_hop_tinv_axpy": (288, 432)}
+APPLY_BYTES_F32 = sum(a + b for a, b in KERNEL_BYTES_F32.values())  # 1440 B per odd site, one source
+
+
+def launch_bytes(name, odd_sites, nrhs):
+    """Algorithmic bytes of one launch of a Schur kernel over nrhs sources, or None."""
+    for base, (spinor, links) in KERNEL_BYTES_F32.items():
+        for suffix, scale in (("_f32", 1), ("_f64", 2)):
+            if name == base + suffix:
+                return scale * odd_sites * (nrhs * spinor + links)
+    return None
+
+
+def apply_bytes(odd_sites, nrhs, scale=1):
+    return scale * odd_sites * sum(nrhs * a + b for a, b in KERNEL_BYTES_F32.values())
 
 
 def paper_flops_per_apply(L, T):
     """(3432 N_t - 576)(V_s / 2) FLOPs per M-hat apply (App. B, Wilson temporal + Schur)."""
     return (3432 * T - 576) * (L ** 3 // 2)
-
-
-def kernel_bytes(name):
-    for base, b in KERNEL_BYTES_F32.items():
-        if name == base + "_f32":
-            return b
-        if name == base + "_f64":
-            return 2 * b
-    return None
 
 
 def source_hash():
@@ -169,7 +177,7 @@ def oracle_sample(target_s, prm):
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     threads = max(1, int(round(cpu / dt)))
     odd_sites = L ** 3 * T // 2
-    gbs = 2 * APPLY_BYTES_F32 * odd_sites / dt / 1e9
+    gbs = apply_bytes(odd_sites, 1, 2) / dt / 1e9
     desc = (f"one FP64 oracle M-hat apply on a {L}^3x{T} lattice with the workload's couplings "
             f"(1 source; the full 24^3x128 x 12-source step is {24 ** 3 / L ** 3 * 12:.0f}x larger)")
     return gbs, desc, threads, dt
@@ -261,15 +269,15 @@ def run_ours(args, prm, U, eta):
     applies_f32 = prof.get("schur_c_hop_tinv_axpy_f32", (0, 0))[0]
     applies_f64 = prof.get("schur_c_hop_tinv_axpy_f64", (0, 0))[0]
     # every M-hat launch sequence works on all nsrc sources at once
-    apply_bytes = (applies_f32 + 2 * applies_f64) * APPLY_BYTES_F32 * odd_sites * nsrc
-    value = world * apply_bytes / (ms * 1e-3) / 1e9
+    step_bytes = applies_f32 * apply_bytes(odd_sites, nsrc) + applies_f64 * apply_bytes(odd_sites, nsrc, 2)
+    value = world * step_bytes / (ms * 1e-3) / 1e9
     flops = (applies_f32 + applies_f64) * paper_flops_per_apply(prm["L"], prm["T"]) * nsrc
 
     # roofline: the dominant kernel by time
-    cand = {k: v for k, v in prof.items() if kernel_bytes(k) is not None and v[0] > 0}
+    cand = {k: v for k, v in prof.items() if launch_bytes(k, 1, 1) is not None and v[0] > 0}
     dom = max(cand, key=lambda k: cand[k][1])
     n_l, ms_l = cand[dom]
-    bytes_launch = kernel_bytes(dom) * odd_sites * nsrc
+    bytes_launch = launch_bytes(dom, odd_sites, nsrc)
     achieved = bytes_launch / (ms_l / n_l * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
     traffic = traffic_for(dom)
@@ -288,7 +296,7 @@ def run_ours(args, prm, U, eta):
             solve(h_rhs, h_x)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": world * apply_bytes / e2e_s / 1e9, "unit": "GB/s",
+        e2e = {"value": world * step_bytes / e2e_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": int(h_rhs.numel() * 16), "d2h_bytes_per_step": int(h_x.numel() * 16),
                "ms_per_step": 1e3 * e2e_s / args.steps}
 
@@ -336,7 +344,7 @@ def run_ours(args, prm, U, eta):
 
 
 def run_apply(args, prm, U, eta):
-    """--mode apply: only M-hat applies (FP32, one source) for kernel profiling; prints per-kernel times."""
+    """--mode apply: only M-hat applies (FP32, --nrhs sources) for kernel profiling; prints per-kernel times."""
     import torch
 
     import paper_0910_0992_gb300 as wf
@@ -346,21 +354,21 @@ def run_apply(args, prm, U, eta):
     w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
     w.load_gauge(U)
     half = prm["L"] ** 3 * prm["T"] // 2 * 12
-    x = torch.from_numpy(S.gaussian_source(prm["L"], prm["T"], 77).reshape(-1)[:half].copy()).cuda()
+    nr = args.nrhs
+    x = torch.from_numpy(S.gaussian_source(prm["L"], prm["T"], 77).reshape(-1)[:half].copy()).cuda().repeat(nr)
     out = torch.empty_like(x)
     for _ in range(args.warmup):
-        wf.wf_apply_schur_f32(w.h, x, out, 0, 1)
+        wf.wf_apply_schur_f32(w.h, x, out, 0, nr)
     wf.wf_profile(w.h, 1)
     for _ in range(args.steps):
-        wf.wf_apply_schur_f32(w.h, x, out, 0, 1)
+        wf.wf_apply_schur_f32(w.h, x, out, 0, nr)
     prof = wf.wf_profile_get(w.h)
     odd_sites = prm["L"] ** 3 * prm["T"] // 2
     rows = {}
     for k, (n, ms) in prof.items():
-        b = kernel_bytes(k)
-        rows[k] = {"launches": n, "avg_ms": ms / n,
-                   "gbs": (b * odd_sites / (ms / n * 1e-3) / 1e9) if b else None}
-    print(json.dumps({"mode": "apply", "workload": WORKLOAD, "kernels": rows}))
+        b = launch_bytes(k, odd_sites, nr)
+        rows[k] = {"launches": n, "avg_ms": ms / n, "gbs": (b / (ms / n * 1e-3) / 1e9) if b else None}
+    print(json.dumps({"mode": "apply", "workload": WORKLOAD, "nrhs": nr, "kernels": rows}))
     w.close()
     return 0
 
@@ -376,7 +384,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
-                    help="apply: only FP32 M-hat applies on one source (for kernel profiling)")
+                    help="apply: only FP32 M-hat applies (for kernel profiling)")
+    ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")
     args = ap.parse_args()
 
     import synthetic as S

@@ -79,6 +79,14 @@ int wf_set_stream(wf_handle_t* h, void* stream);
 /* Message of the last error on h (never null; empty after success). */
 const char* wf_last_error(const wf_handle_t* h);
 
+/* Choose the frame the library works in, before wf_load_gauge (a later call discards the loaded
+ * field). axial = 1 (the default): at load the field is rotated, per time line, to the axial
+ * (temporal) gauge, U_t(t) = 1 for t < T-1 and U_t(T-1) = P the Polyakov product (§II.C,
+ * "axial gauge"; App. C), so T^-1 needs no U_t and no 3x3 products; inputs and outputs are
+ * rotated in and out, so every result is the same as in the caller's gauge. axial = 0: the
+ * field is used as given and T^-1 composes 3x3 affine maps along each line. */
+int wf_set_gauge_frame(wf_handle_t* h, int axial);
+
 /* Sizes of the arrays the handle works on: complex128 elements per right-hand side. */
 long long wf_field_elems(const wf_handle_t* h);  /* full field: 12 L^3 T */
 long long wf_half_elems(const wf_handle_t* h);   /* one parity: 6 L^3 T  */

@@ -25,6 +25,7 @@ _SIGS = {
     "wf_destroy": (_i, [_vp]),
     "wf_set_stream": (_i, [_vp, _vp]),
     "wf_last_error": (ctypes.c_char_p, [_vp]),
+    "wf_set_gauge_frame": (_i, [_vp, _i]),
     "wf_field_elems": (ctypes.c_longlong, [_vp]),
     "wf_half_elems": (ctypes.c_longlong, [_vp]),
     "wf_load_gauge": (_i, [_vp, _vp]),
@@ -102,6 +103,10 @@ def wf_last_error(h):
     return (lib.wf_last_error(h) or b"").decode()
 
 
+def wf_set_gauge_frame(h, axial):
+    return _check(h, lib.wf_set_gauge_frame(h, int(axial)))
+
+
 def wf_field_elems(h):
     return lib.wf_field_elems(h)
 
@@ -164,9 +169,10 @@ def wf_profile_get(h, cap=64):
 class Wilson:
     """A handle with its parameters; methods allocate outputs like their inputs (torch or NumPy)."""
 
-    def __init__(self, L, T, kappa_s, kappa_t=0.0, xi=0.0, bc=-1):
+    def __init__(self, L, T, kappa_s, kappa_t=0.0, xi=0.0, bc=-1, axial=True):
         self.L, self.T, self.bc = int(L), int(T), int(bc)
         self.h = wf_create(L, T, xi, kappa_s, kappa_t, bc)
+        wf_set_gauge_frame(self.h, 1 if axial else 0)
 
     def close(self):
         if self.h is not None:

@@ -29,9 +29,14 @@ def nvcc():
     return path
 
 
+def _env_flags():
+    """Extra nvcc flags from WF_NVCC_FLAGS (tuning sweeps, e.g. -DWF_LINE_MINB=3)."""
+    return os.environ.get("WF_NVCC_FLAGS", "").split()
+
+
 def _compile(src, extra):
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + _env_flags() + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

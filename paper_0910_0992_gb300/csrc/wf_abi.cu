@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -81,6 +82,7 @@ void finish_out(wf_handle* h, double* p, const Cx<double>* d, size_t elems, bool
 template <typename R>
 struct Gauge {
   const Cx<R>* ut[2];
+  const Cx<R>* pl[2];
   const Cx<R>* us[2];
   const Cx<R>* lamb[2];
   const Cx<R>* lamf[2];
@@ -92,6 +94,7 @@ Gauge<double> gauge_of<double>(wf_handle* h) {
   Gauge<double> G;
   for (int p = 0; p < 2; ++p) {
     G.ut[p] = h->ut64[p].as<Cx<double>>();
+    G.pl[p] = h->pl64[p].as<Cx<double>>();
     G.us[p] = h->us64[p].as<Cx<double>>();
     G.lamb[p] = h->lamb64[p].as<Cx<double>>();
     G.lamf[p] = h->lamf64[p].as<Cx<double>>();
@@ -103,6 +106,7 @@ Gauge<float> gauge_of<float>(wf_handle* h) {
   Gauge<float> G;
   for (int p = 0; p < 2; ++p) {
     G.ut[p] = h->ut32[p].as<Cx<float>>();
+    G.pl[p] = h->pl32[p].as<Cx<float>>();
     G.us[p] = h->us32[p].as<Cx<float>>();
     G.lamb[p] = h->lamb32[p].as<Cx<float>>();
     G.lamf[p] = h->lamf32[p].as<Cx<float>>();
@@ -119,6 +123,7 @@ LineArgs<R> line_args(wf_handle* h, int parity, int nrhs) {
   a.parity = parity;
   a.nrhs = nrhs;
   a.ut = G.ut[parity];
+  a.pl = G.pl[parity];
   a.us_out = G.us[parity];
   a.us_nbr = G.us[1 - parity];
   a.lamb = G.lamb[parity];
@@ -159,9 +164,10 @@ void line_load(wf_handle* h, int parity, const Cx<R>* in, Cx<R>* out, int opu, i
   a.src_lo = in + 6 * h->g.tp;
   a.opu = opu;
   a.opl = opl;
+  a.src = SRC_LOAD;
   a.out = out;
   Prof P(h, pname<R>(name));
-  launch_line<R>(a, SRC_LOAD, h->stream);
+  launch_line<R>(a, LK_GENERIC, h->axial, h->stream);
 }
 
 // M-hat (dagger: gamma_5 M-hat gamma_5) on odd internal fields: three fused kernels
@@ -172,7 +178,8 @@ void line_load(wf_handle* h, int parity, const Cx<R>* in, Cx<R>* out, int opu, i
 
 namespace wf {
 template <typename R>
-void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z) {
+void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z,
+                 double* norm2) {
   const int tp = h->g.tp;
   {
     LineArgs<R> a = line_args<R>(h, 1, nrhs);
@@ -182,7 +189,7 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     a.opl = OP_SKIP;
     a.out = y;
     Prof P(h, pname<R>("schur_a_tdag"));
-    launch_line<R>(a, SRC_LOAD, h->stream);
+    launch_line<R>(a, LK_SCHUR_A, h->axial, h->stream);
   }
   {
     LineArgs<R> a = line_args<R>(h, 0, nrhs);
@@ -192,7 +199,7 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     a.opl = OP_BWD;
     a.out = z;
     Prof P(h, pname<R>("schur_b_hop_tsolve"));
-    launch_line<R>(a, SRC_HOP, h->stream);
+    launch_line<R>(a, LK_SCHUR_B, h->axial, h->stream);
   }
   {
     LineArgs<R> a = line_args<R>(h, 1, nrhs);
@@ -204,12 +211,16 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     a.apost = (R)(-1.0 / (h->g.gamma_f * h->g.gamma_f));
     a.swap_out = dagger;
     a.out = out;
+    a.norm2 = norm2;
+    if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nrhs * sizeof(double), h->stream));
     Prof P(h, pname<R>("schur_c_hop_tinv_axpy"));
-    launch_line<R>(a, SRC_HOP, h->stream);
+    launch_line<R>(a, LK_SCHUR_C, h->axial, h->stream);
   }
 }
-template void schur_apply<float>(wf_handle*, const Cx<float>*, Cx<float>*, int, int, Cx<float>*, Cx<float>*);
-template void schur_apply<double>(wf_handle*, const Cx<double>*, Cx<double>*, int, int, Cx<double>*, Cx<double>*);
+template void schur_apply<float>(wf_handle*, const Cx<float>*, Cx<float>*, int, int, Cx<float>*, Cx<float>*,
+                                 double*);
+template void schur_apply<double>(wf_handle*, const Cx<double>*, Cx<double>*, int, int, Cx<double>*, Cx<double>*,
+                                  double*);
 }  // namespace wf
 
 namespace {
@@ -228,6 +239,7 @@ void m_apply(wf_handle* h, const Cx<R>* in_e, const Cx<R>* in_o, Cx<R>* out_e, C
     m.psi_p = p ? in_o : in_e;
     m.psi_q = p ? in_e : in_o;
     m.ut = G.ut[p];
+    m.pl = G.pl[p];
     m.us_out = G.us[p];
     m.us_nbr = G.us[1 - p];
     m.x = p ? x_o : x_e;
@@ -237,7 +249,7 @@ void m_apply(wf_handle* h, const Cx<R>* in_e, const Cx<R>* in_o, Cx<R>* out_e, C
     m.inv_gf = (R)(1.0 / h->g.gamma_f);
     m.bc = (R)h->g.bc;
     Prof P(h, pname<R>("apply_M"));
-    launch_apply_M<R>(m, h->stream);
+    launch_apply_M<R>(m, h->axial, h->stream);
   }
 }
 
@@ -350,14 +362,18 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
   };
   if (all_done()) return iters;
 
-  schur_apply<R>(h, r, sv, 1, nrhs, ty, tz);  // s = M-hat^dag r
+  schur_apply<R>(h, r, sv, 1, nrhs, ty, tz, gam);  // s = M-hat^dag r, |s|^2
   WF_CUDA(cudaMemcpyAsync(p, sv, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
-  { Prof P(h, pname<R>("norm2"), 2); launch_norm2<R>(sv, n, nrhs, partial, gam, s); }
 
-  const double delta = 0.1;  // reliable-update trigger: residual dropped by this factor
+  // reliable-update trigger: the FP32 residual has dropped by this factor since the last
+  // FP64 recomputation (environment WF_RELIABLE_DELTA overrides)
+  double delta = 0.01;
+  if (const char* e = std::getenv("WF_RELIABLE_DELTA")) {
+    const double v = std::atof(e);
+    if (v > 0.0 && v < 1.0) delta = v;
+  }
   for (int it = 0; it < maxiter; ++it) {
-    schur_apply<R>(h, p, q, 0, nrhs, ty, tz);  // q = M-hat p
-    { Prof P(h, pname<R>("norm2"), 2); launch_norm2<R>(q, n, nrhs, partial, qq, s); }
+    schur_apply<R>(h, p, q, 0, nrhs, ty, tz, qq);  // q = M-hat p, |q|^2
     { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s); }
     for (int k = 0; k < nrhs; ++k)
       if (act[k]) iters[k]++;
@@ -393,8 +409,7 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
     }
     if (changed) WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     if (all_done()) break;
-    schur_apply<R>(h, r, sv, 1, nrhs, ty, tz);  // s = M-hat^dag r
-    { Prof P(h, pname<R>("norm2"), 2); launch_norm2<R>(sv, n, nrhs, partial, gnew, s); }
+    schur_apply<R>(h, r, sv, 1, nrhs, ty, tz, gnew);  // s = M-hat^dag r, |s|^2
     { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
     { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s); }
   }
@@ -425,7 +440,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   double* sc = h->buf<double>("sv_scalars", 4 * (size_t)nrhs);
   double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
 
-  { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, s); }
+  { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
   // source preparation (S_L): a_e = C_R^e C_L^e eta_e ; b_o = C_L^o [eta_o + gamma_f^-1 D_s^oe a_e]
   line_load<double>(h, 0, eta_e, a_e, OP_FWD, OP_BWD, nrhs, "prep_tsolve");
   {
@@ -436,9 +451,10 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     a.apre = igf;
     a.opu = OP_COPY;
     a.opl = OP_BWD;
+    a.src = SRC_HOP;
     a.out = b_o;
     Prof P(h, "prep_hop_f64");
-    launch_line<double>(a, SRC_HOP, s);
+    launch_line<double>(a, LK_GENERIC, h->axial, s);
   }
   // |eta|^2 per rhs
   { Prof P(h, "norm2_f64", 4); launch_norm2<double>(eta_e, n, nrhs, partial, sc, s); launch_norm2<double>(eta_o, n, nrhs, partial, sc + nrhs, s); }
@@ -453,7 +469,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   if (x0) {
     // initial guess: y_o = (C_R^o)^-1 psi_o; use only the odd part of the guess
     Cx<double>* g_e = r_e;
-    { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex, g_e, psi_o, nrhs, 0, s); }
+    { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex, g_e, psi_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
     // (C_R^o)^-1 = P_- + P_+ T^dag is not needed exactly: start from y_o = psi_o
     WF_CUDA(cudaMemcpyAsync(y_o, psi_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
   }
@@ -476,9 +492,10 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
       a.apre = igf;
       a.opu = OP_FWD;
       a.opl = OP_BWD;
+      a.src = SRC_HOP;
       a.out = psi_e;
       Prof P(h, "recon_hop_f64");
-      launch_line<double>(a, SRC_HOP, s);
+      launch_line<double>(a, LK_GENERIC, h->axial, s);
     }
     // true residual r = eta - M psi in FP64
     m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
@@ -496,7 +513,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     if (ok || status == WF_ENOCONV) break;
     if (pass == 5) status = WF_ENOCONV;
   }
-  { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, s); }
+  { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
   for (int k = 0; k < nrhs; ++k) {
     if (iters_out) iters_out[k] = iters[k];
     if (resid_out) resid_out[k] = rel[k];
@@ -517,9 +534,9 @@ int apply_schur_abi(wf_handle* h, const double* in_odd, double* out_odd, int dag
   Cx<R>* o = h->buf<Cx<R>>(pname<R>("ap_o"), nt);
   Cx<R>* y = h->buf<Cx<R>>(pname<R>("ap_y"), nt);
   Cx<R>* z = h->buf<Cx<R>>(pname<R>("ap_z"), nt);
-  { Prof P(h, pname<R>("import_compact")); launch_import_compact<R>(h->g, din, x, nrhs, 0, h->stream); }
+  { Prof P(h, pname<R>("import_compact")); launch_import_compact<R>(h->g, din, x, nrhs, 0, frame_rot(h, 1), h->stream); }
   schur_apply<R>(h, x, o, dagger, nrhs, y, z);
-  { Prof P(h, pname<R>("export_compact")); launch_export_compact<R>(h->g, o, dout, nrhs, 0, h->stream); }
+  { Prof P(h, pname<R>("export_compact")); launch_export_compact<R>(h->g, o, dout, nrhs, 0, frame_rot(h, 1), h->stream); }
   finish_out(h, out_odd, dout, ce, staged);
   return WF_OK;
 }
@@ -537,9 +554,9 @@ int apply_M_abi(wf_handle* h, const double* in, double* out, int dagger, int nrh
   Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
   Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
   Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
-  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, dagger, h->stream); }
+  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, dagger, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
   m_apply<R>(h, ie, io, oe, oo, nullptr, nullptr, 0.0, nrhs);
-  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, dagger, h->stream); }
+  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, dagger, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
   finish_out(h, out, dout, le, staged);
   return WF_OK;
 }
@@ -557,10 +574,10 @@ int apply_line_abi(wf_handle* h, const double* in, double* out, int opu, int opl
   Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
   Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
   Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
-  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, 0, h->stream); }
+  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
   line_load<R>(h, 0, ie, oe, opu, opl, nrhs, name);
   line_load<R>(h, 1, io, oo, opu, opl, nrhs, name);
-  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, 0, h->stream); }
+  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
   finish_out(h, out, dout, le, staged);
   return WF_OK;
 }
@@ -632,6 +649,15 @@ int wf_set_stream(wf_handle_t* h, void* stream) {
 
 const char* wf_last_error(const wf_handle_t* h) { return h ? h->err.c_str() : "null handle"; }
 
+int wf_set_gauge_frame(wf_handle_t* h, int axial) {
+  return guarded(h, [&]() {
+    if (axial != 0 && axial != 1) throw Error(WF_EINVAL, "axial must be 0 or 1");
+    h->axial = axial != 0;
+    h->gauge = false;  // the stored field belongs to the old frame: load the gauge field again
+    return WF_OK;
+  });
+}
+
 long long wf_field_elems(const wf_handle_t* h) { return h ? (long long)h->g.L * h->g.L * h->g.L * h->g.T * 12 : 0; }
 long long wf_half_elems(const wf_handle_t* h) { return h ? (long long)h->g.L * h->g.L * h->g.L * h->g.T * 6 : 0; }
 
@@ -647,7 +673,7 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
       h->us64[p].ensure(nus * sizeof(Cx<double>), s);
       h->lamb64[p].ensure(nlam * sizeof(Cx<double>), s);
       h->lamf64[p].ensure(nlam * sizeof(Cx<double>), s);
-      h->ut32[p].ensure(nut * sizeof(Cx<float>), s);
+      if (!h->axial) h->ut32[p].ensure(nut * sizeof(Cx<float>), s);
       h->us32[p].ensure(nus * sizeof(Cx<float>), s);
       h->lamb32[p].ensure(nlam * sizeof(Cx<float>), s);
       h->lamf32[p].ensure(nlam * sizeof(Cx<float>), s);
@@ -658,12 +684,28 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
     Cx<double>* us[2] = {h->us64[0].as<Cx<double>>(), h->us64[1].as<Cx<double>>()};
     Prof P(h, "gauge_ingest", 1 + 2 * 5);
     launch_import_gauge(g, dU, ut, us, s);
-    for (int p = 0; p < 2; ++p) {
-      launch_tline_init(g, ut[p], h->lamb64[p].as<Cx<double>>(), h->lamf64[p].as<Cx<double>>(), h->iflag.as<int>(), s);
-      launch_d2f(ut[p], h->ut32[p].as<Cx<float>>(), nut, s);
-      launch_d2f(us[p], h->us32[p].as<Cx<float>>(), nus, s);
-      launch_d2f(h->lamb64[p].as<Cx<double>>(), h->lamb32[p].as<Cx<float>>(), nlam, s);
-      launch_d2f(h->lamf64[p].as<Cx<double>>(), h->lamf32[p].as<Cx<float>>(), nlam, s);
+    if (h->axial) {
+      // axial frame: ut becomes the rotation g, spatial links rotated in place, P and Lambda per line
+      for (int p = 0; p < 2; ++p) {
+        h->pl64[p].ensure(nlam * sizeof(Cx<double>), s);
+        h->pl32[p].ensure(nlam * sizeof(Cx<float>), s);
+        launch_axial_frame(g, ut[p], h->pl64[p].as<Cx<double>>(), h->lamb64[p].as<Cx<double>>(), h->iflag.as<int>(), s);
+      }
+      const Cx<double>* gg[2] = {ut[0], ut[1]};
+      launch_rotate_links(g, us, gg, s);
+      for (int p = 0; p < 2; ++p) {
+        launch_d2f(us[p], h->us32[p].as<Cx<float>>(), nus, s);
+        launch_d2f(h->pl64[p].as<Cx<double>>(), h->pl32[p].as<Cx<float>>(), nlam, s);
+        launch_d2f(h->lamb64[p].as<Cx<double>>(), h->lamb32[p].as<Cx<float>>(), nlam, s);
+      }
+    } else {
+      for (int p = 0; p < 2; ++p) {
+        launch_tline_init(g, ut[p], h->lamb64[p].as<Cx<double>>(), h->lamf64[p].as<Cx<double>>(), h->iflag.as<int>(), s);
+        launch_d2f(ut[p], h->ut32[p].as<Cx<float>>(), nut, s);
+        launch_d2f(us[p], h->us32[p].as<Cx<float>>(), nus, s);
+        launch_d2f(h->lamb64[p].as<Cx<double>>(), h->lamb32[p].as<Cx<float>>(), nlam, s);
+        launch_d2f(h->lamf64[p].as<Cx<double>>(), h->lamf32[p].as<Cx<float>>(), nlam, s);
+      }
     }
     int flag = 0;
     WF_CUDA(cudaMemcpyAsync(&flag, h->iflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -35,12 +35,12 @@ template <typename R>
 __global__ void __launch_bounds__(kBT) k_norm2(const Cx<R>* __restrict__ x, size_t n, double* partial) {
   const int rhs = blockIdx.y;
   const Cx<R>* xr = x + (size_t)rhs * n;
-  double acc = 0.0;
+  R part = R(0);  // per-thread partial sum in the field's precision; FP64 across threads
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
     const Cx<R> v = xr[i];
-    acc += (double)v.re * v.re + (double)v.im * v.im;
+    part = fma(v.re, v.re, fma(v.im, v.im, part));
   }
-  acc = block_sum(acc);
+  double acc = block_sum((double)part);
   if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = acc;
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __r
   const double qn = qq[rhs];
   const R alpha = (on && qn > 0.0) ? (R)(gamma[rhs] / qn) : R(0);
   const size_t off = (size_t)rhs * n;
-  double acc = 0.0;
+  R part = R(0);  // per-thread partial |r|^2 in the field's precision; FP64 across threads
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
     const Cx<R> pv = p[off + i], qv = q[off + i];
     Cx<R> xv = x[off + i], rv = r[off + i];
@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __r
     rv.im = fma(-alpha, qv.im, rv.im);
     x[off + i] = xv;
     r[off + i] = rv;
-    acc += (double)rv.re * rv.re + (double)rv.im * rv.im;
+    part = fma(rv.re, rv.re, fma(rv.im, rv.im, part));
   }
-  acc = block_sum(acc);
+  double acc = block_sum((double)part);
   if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = acc;
 }
 

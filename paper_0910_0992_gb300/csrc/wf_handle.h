@@ -24,9 +24,12 @@ struct wf_handle {
   int device = 0;
   std::string err;
   bool gauge = false;
+  bool axial = true;  // solve in the axial frame (U_t = 1 but for P at t = N_t - 1)
   // gauge, per parity: U_t [Nl][9][tp], spatial [3][Nl][9][tp], Lambda [Nl][9]
   wf::DevBuf ut64[2], us64[2], lamb64[2], lamf64[2];
   wf::DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];
+  // axial frame: ut64 holds the rotation g(x) instead of U_t; P per line
+  wf::DevBuf pl64[2], pl32[2];
   wf::DevBuf iflag;
   std::map<std::string, std::unique_ptr<wf::DevBuf>> ws;  // named work buffers
   // profiling
@@ -118,6 +121,12 @@ struct Prof {
 // M-hat (dagger: gamma_5 M-hat gamma_5) on internal odd fields x -> out; y (odd) and z (even)
 // are work fields of the same size as x.
 template <typename R>
-void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z);
+void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z,
+                 double* norm2 = nullptr);
+
+// colour rotation of parity p for imports/exports (axial frame), or null
+inline const Cx<double>* frame_rot(const wf_handle* h, int p) {
+  return h->axial ? h->ut64[p].as<Cx<double>>() : nullptr;
+}
 
 }  // namespace wf

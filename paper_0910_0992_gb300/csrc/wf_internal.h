@@ -60,8 +60,13 @@ struct DevBuf {
 // ----------------------------------------------------------------------------
 template <typename R> struct LineArgs;
 
+// which compiled variant of the line kernel to launch: the three Schur-operator kernels
+// have their source and solve ops fixed at compile time; LK_GENERIC reads them from the
+// arguments
+enum LineKind { LK_GENERIC = 0, LK_SCHUR_A = 1, LK_SCHUR_B = 2, LK_SCHUR_C = 3 };
+
 template <typename R>
-void launch_line(const LineArgs<R>& a, int src, cudaStream_t s);
+void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s);
 
 template <typename R>
 struct MArgs {
@@ -70,7 +75,8 @@ struct MArgs {
   int nrhs;
   const Cx<R>* psi_p;  // own parity  [nrhs][Nl][12][tp]
   const Cx<R>* psi_q;  // other parity
-  const Cx<R>* ut;     // U_t of the own parity
+  const Cx<R>* ut;     // U_t of the own parity (general frame)
+  const Cx<R>* pl;     // per-line boundary link P (axial frame)
   const Cx<R>* us_out; // forward spatial links, own parity
   const Cx<R>* us_nbr; // forward spatial links, other parity
   const Cx<R>* x;      // out = x + a * (M psi) if x != nullptr
@@ -79,23 +85,29 @@ struct MArgs {
   R mu, inv_gf, bc;
 };
 template <typename R>
-void launch_apply_M(const MArgs<R>& a, cudaStream_t s);
+void launch_apply_M(const MArgs<R>& a, bool axial, cudaStream_t s);
 
 // layout conversions
+// g_e / g_o (or gr): per-parity colour rotations of the axial frame, [l][9][tp] FP64, or null
 template <typename R>
 void launch_import_spinor(const Geom& g, const Cx<double>* lex, Cx<R>* even, Cx<R>* odd, int nrhs, int g5,
-                          cudaStream_t s);
+                          const Cx<double>* g_e, const Cx<double>* g_o, cudaStream_t s);
 template <typename R>
 void launch_export_spinor(const Geom& g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* lex, int nrhs, int g5,
-                          cudaStream_t s);
+                          const Cx<double>* g_e, const Cx<double>* g_o, cudaStream_t s);
 template <typename R>
-void launch_import_compact(const Geom& g, const Cx<double>* cmp, Cx<R>* half, int nrhs, int g5, cudaStream_t s);
+void launch_import_compact(const Geom& g, const Cx<double>* cmp, Cx<R>* half, int nrhs, int g5, const Cx<double>* gr,
+                           cudaStream_t s);
 template <typename R>
-void launch_export_compact(const Geom& g, const Cx<R>* half, Cx<double>* cmp, int nrhs, int g5, cudaStream_t s);
+void launch_export_compact(const Geom& g, const Cx<R>* half, Cx<double>* cmp, int nrhs, int g5, const Cx<double>* gr,
+                           cudaStream_t s);
 void launch_import_gauge(const Geom& g, const Cx<double>* lex, Cx<double>* ut[2], Cx<double>* us[2],
                          cudaStream_t s);
 void launch_tline_init(const Geom& g, const Cx<double>* ut, Cx<double>* lamb, Cx<double>* lamf, int* singular,
                        cudaStream_t s);
+void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, int* singular,
+                        cudaStream_t s);
+void launch_rotate_links(const Geom& g, Cx<double>* us[2], const Cx<double>* gg[2], cudaStream_t s);
 void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s);
 void launch_f2d(const Cx<float>* in, Cx<double>* out, size_t n, cudaStream_t s);
 

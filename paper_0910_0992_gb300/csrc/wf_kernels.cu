@@ -1,147 +1,208 @@
 // Line kernels of the temporal preconditioner and the Wilson matrix M.
 //
-// k_line is the one kernel behind every C_L / C_R / T^-1 / T^-dag application and
-// every fused "hop + time-line solve" step of the Schur operator (§II.A, §II.B):
+// k_line is the kernel behind every C_L / C_R / T^-1 / T^-dag application and every
+// fused "hop + time-line solve" step of the Schur operator (§II.A, §II.B):
 //   source   : the site's own spinor (SRC_LOAD) or D_s of the other parity (SRC_HOP)
 //   pre-axpy : v <- xpre + apre v
 //   solves   : per spin half, copy / T^-dag (forward) / T^-1 (backward) / skip
-//   post-axpy: out <- xpost + apost v, optionally with the two halves exchanged
-// One warp handles 32 / lpl time lines; lpl lanes share a line, n sites each.
+//   post-axpy: out <- xpost + apost v, optionally with the two halves exchanged,
+//              optionally accumulating |out|^2 per right-hand side
+// One warp handles 32 / lpl time lines; lpl lanes share a line, n sites each. The three
+// kernels of the Schur operator are compiled with their source and solve ops fixed, so
+// each carries only its own code; every other use goes through one kernel that selects
+// them at run time.
 #include "wf_internal.h"
 #include "wf_line.cuh"
 
 namespace wf {
 
 constexpr int kLineThreads = 128;
+#ifndef WF_LINE_MINB
+#define WF_LINE_MINB 3
+#endif
+// resident CTAs per SM the line kernels are compiled for (3: 168 registers; measured best
+// on GB300 against 1 and 4, where 4 spills)
+// right-hand sides are processed in groups of this many: within a group the warps of one
+// line run side by side and share its links through L2 (measured: groups of all 12 sources
+// beat groups of 4, whose links are re-read per group)
+constexpr int kRhsGroup = 16;
 
-template <typename R, int N, bool FWD>
-__device__ __forceinline__ void solve_half(Vec3<R> (&v)[N][4], int s0, const Cx<R>* ut_line, const Cx<R>* lam,
-                                           const Geom& g, int jj, R inv_mu, R bc) {
+// warp-line index -> (rhs, line): rhs groups outermost, lines, rhs within the group innermost
+__device__ __forceinline__ void line_rhs(int lg, int nrhs, int Nl, int& rhs, int& l) {
+  const int per_group = kRhsGroup * Nl;
+  const int grp = lg / per_group;
+  const int r = lg - grp * per_group;
+  const int gsize = min(kRhsGroup, nrhs - grp * kRhsGroup);
+  l = r / gsize;
+  rhs = grp * kRhsGroup + (r - l * gsize);
+}
+
+template <typename R, bool AX, bool FWD>
+__device__ __forceinline__ void solve_half(Vec3<R> (&v)[NMAX][4], int s0, const LineArgs<R>& A, int l, int jj) {
   constexpr int NS = sizeof(R) == 4 ? 2 : 1;
+  const Geom& g = A.g;
 #pragma unroll
   for (int sp = 0; sp < 2; sp += NS) {
-    Vec3<R> w[N][NS];
+    Vec3<R> w[NMAX][NS];
 #pragma unroll
-    for (int m = 0; m < N; ++m)
+    for (int m = 0; m < NMAX; ++m)
 #pragma unroll
       for (int s = 0; s < NS; ++s) w[m][s] = v[m][s0 + sp + s];
-    tline_solve<R, N, NS, FWD>(w, ut_line, lam, g, jj, inv_mu, bc);
+    if (AX)
+      tline_solve_axial<R, NS, FWD>(w, A.pl + (size_t)l * 9, A.lamb + (size_t)l * 9, g, jj, A.inv_mu, A.bc);
+    else
+      tline_solve_general<R, NS, FWD>(w, A.ut + (size_t)l * NLINK_C * g.tp,
+                                      (FWD ? A.lamf : A.lamb) + (size_t)l * 9, g, jj, A.inv_mu, A.bc);
 #pragma unroll
-    for (int m = 0; m < N; ++m)
+    for (int m = 0; m < NMAX; ++m)
 #pragma unroll
       for (int s = 0; s < NS; ++s) v[m][s0 + sp + s] = w[m][s];
   }
 }
 
-template <typename R, int N, int SRC>
-__global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<R> A) {
+template <typename R, bool AX>
+__device__ __forceinline__ void apply_op(int op, Vec3<R> (&v)[NMAX][4], int s0, const LineArgs<R>& A, int l, int jj) {
+  if (op == OP_FWD)
+    solve_half<R, AX, true>(v, s0, A, l, jj);
+  else if (op == OP_BWD)
+    solve_half<R, AX, false>(v, s0, A, l, jj);
+}
+
+// SRC, OPU, OPL < 0: taken from the arguments at run time
+template <typename R, bool AX, int SRC, int OPU, int OPL>
+__global__ void __launch_bounds__(kLineThreads, WF_LINE_MINB) k_line(const LineArgs<R> A) {
   const Geom& g = A.g;
+  const int src = SRC >= 0 ? SRC : A.src;
+  const int opu = OPU >= 0 ? OPU : A.opu;
+  const int opl = OPL >= 0 ? OPL : A.opl;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lg_raw = warp * g.lpw + lane / g.lpl;
   const bool active = lg_raw < A.nrhs * g.Nl;
   const int lg = active ? lg_raw : 0;  // idle lanes still join the warp shuffles
-  const int rhs = lg / g.Nl, l = lg - rhs * g.Nl;
+  int rhs, l;
+  line_rhs(lg, A.nrhs, g.Nl, rhs, l);
   const int jj = lane % g.lpl;
-  const int tp = g.tp;
-  const size_t base = (size_t)lg * NSPIN_C * tp;
+  const int tp = g.tp, n = g.n;
+  const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
 
-  Vec3<R> v[N][4];
-  if (SRC == SRC_HOP) {
-    hop_spatial<R, N>(v, A, rhs, l, jj);
+  Vec3<R> v[NMAX][4];
+  if (src == SRC_HOP) {
+    hop_spatial<R>(v, A, rhs, l, jj);
   } else {
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
+    for (int m = 0; m < NMAX; ++m) {
       const int sl = m * g.lpl + jj;
-      v[m][0] = ldvec(A.src_up + base, tp, sl);
-      v[m][1] = ldvec(A.src_up + base + 3 * tp, tp, sl);
-      v[m][2] = ldvec(A.src_lo + base, tp, sl);
-      v[m][3] = ldvec(A.src_lo + base + 3 * tp, tp, sl);
+      const bool ok = m < n;
+      const bool up = ok && opu != OP_SKIP, lo = ok && opl != OP_SKIP;
+      v[m][0] = up ? ldvec(A.src_up + base, tp, sl) : vzero<R>();
+      v[m][1] = up ? ldvec(A.src_up + base + 3 * tp, tp, sl) : vzero<R>();
+      v[m][2] = lo ? ldvec(A.src_lo + base, tp, sl) : vzero<R>();
+      v[m][3] = lo ? ldvec(A.src_lo + base + 3 * tp, tp, sl) : vzero<R>();
     }
   }
   if (A.xpre) {
 #pragma unroll
-    for (int m = 0; m < N; ++m)
+    for (int m = 0; m < NMAX; ++m) {
+      if (m >= n) continue;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) v[m][s] = vaxpy(A.apre, v[m][s], ldvec(A.xpre + base + 3 * s * tp, tp, m * g.lpl + jj));
+      for (int s = 0; s < 4; ++s)
+        v[m][s] = vaxpy(A.apre, v[m][s], ldvec(A.xpre + base + 3 * s * tp, tp, m * g.lpl + jj));
+    }
   }
 
-  const Cx<R>* ut_line = A.ut + (size_t)l * NLINK_C * tp;
-  if (A.opu == OP_FWD)
-    solve_half<R, N, true>(v, 0, ut_line, A.lamf + (size_t)l * 9, g, jj, A.inv_mu, A.bc);
-  else if (A.opu == OP_BWD)
-    solve_half<R, N, false>(v, 0, ut_line, A.lamb + (size_t)l * 9, g, jj, A.inv_mu, A.bc);
-  if (A.opl == OP_FWD)
-    solve_half<R, N, true>(v, 2, ut_line, A.lamf + (size_t)l * 9, g, jj, A.inv_mu, A.bc);
-  else if (A.opl == OP_BWD)
-    solve_half<R, N, false>(v, 2, ut_line, A.lamb + (size_t)l * 9, g, jj, A.inv_mu, A.bc);
+  apply_op<R, AX>(opu, v, 0, A, l, jj);
+  apply_op<R, AX>(opl, v, 2, A, l, jj);
 
-  if (!active) return;
+  R nrm = R(0);
+  const bool want_norm = A.norm2 != nullptr;
+  if (active) {
 #pragma unroll
-  for (int m = 0; m < N; ++m) {
-    const int sl = m * g.lpl + jj;
-    const bool valid = jj * N + m < g.T;
+    for (int m = 0; m < NMAX; ++m) {
+      if (m >= n) continue;
+      const int sl = m * g.lpl + jj;
+      const bool valid = jj * n + m < g.T;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int op = h ? A.opl : A.opu;
-      if (op == OP_SKIP) continue;
-      const int dh = A.swap_out ? 1 - h : h;
+      for (int h = 0; h < 2; ++h) {
+        const int op = h ? opl : opu;
+        if (op == OP_SKIP) continue;
+        const int dh = A.swap_out ? 1 - h : h;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int comp0 = dh * 6 + s * 3;
-        Vec3<R> val = valid ? v[m][2 * h + s] : vzero<R>();
-        if (A.xpost) val = vaxpy(A.apost, val, ldvec(A.xpost + base + comp0 * tp, tp, sl));
-        stvec(A.out + base + comp0 * tp, tp, sl, val);
+        for (int s = 0; s < 2; ++s) {
+          const int comp0 = dh * 6 + s * 3;
+          Vec3<R> val = valid ? v[m][2 * h + s] : vzero<R>();
+          if (A.xpost) val = vaxpy(A.apost, val, ldvec(A.xpost + base + comp0 * tp, tp, sl));
+          stvec(A.out + base + comp0 * tp, tp, sl, val);
+          if (want_norm) nrm += vnorm2(val);
+        }
       }
     }
+  }
+  if (want_norm) {
+    // lanes of one line share rhs; reduce over the warp per line group, one atomic per line
+    double dn = (double)nrm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_down_sync(0xffffffffu, dn, o);
+      if (o < g.lpl) dn += other;
+    }
+    if (active && jj == 0) atomicAdd(A.norm2 + rhs, dn);
   }
 }
 
 template <typename R>
-void launch_line(const LineArgs<R>& a, int src, cudaStream_t s) {
+static int line_blocks(const LineArgs<R>& a) {
   const int lines = a.nrhs * a.g.Nl;
   const int warps = (lines + a.g.lpw - 1) / a.g.lpw;
-  const int blocks = (warps * 32 + kLineThreads - 1) / kLineThreads;
-#define WF_LINE_CASE(NN)                                                          \
-  case NN:                                                                        \
-    if (src == SRC_HOP)                                                           \
-      k_line<R, NN, SRC_HOP><<<blocks, kLineThreads, 0, s>>>(a);                  \
-    else                                                                          \
-      k_line<R, NN, SRC_LOAD><<<blocks, kLineThreads, 0, s>>>(a);                 \
-    break;
-  switch (a.g.n) {
-    WF_LINE_CASE(1)
-    WF_LINE_CASE(2)
-    WF_LINE_CASE(3)
-    WF_LINE_CASE(4)
-    default:
-      throw Error(1, "unsupported sites per lane");
+  return (warps * 32 + kLineThreads - 1) / kLineThreads;
+}
+
+template <typename R>
+void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
+  if (a.g.n < 1 || a.g.n > NMAX) throw Error(1, "unsupported sites per lane");
+  const int b = line_blocks(a);
+#define WF_KL(AXV, SRCV, OPUV, OPLV) k_line<R, AXV, SRCV, OPUV, OPLV><<<b, kLineThreads, 0, s>>>(a)
+  if (axial) {
+    switch (kind) {
+      case LK_SCHUR_A: WF_KL(true, SRC_LOAD, OP_FWD, OP_SKIP); break;
+      case LK_SCHUR_B: WF_KL(true, SRC_HOP, OP_FWD, OP_BWD); break;
+      case LK_SCHUR_C: WF_KL(true, SRC_HOP, OP_COPY, OP_BWD); break;
+      default: WF_KL(true, -1, -1, -1); break;
+    }
+  } else {
+    switch (kind) {
+      case LK_SCHUR_A: WF_KL(false, SRC_LOAD, OP_FWD, OP_SKIP); break;
+      case LK_SCHUR_B: WF_KL(false, SRC_HOP, OP_FWD, OP_BWD); break;
+      case LK_SCHUR_C: WF_KL(false, SRC_HOP, OP_COPY, OP_BWD); break;
+      default: WF_KL(false, -1, -1, -1); break;
+    }
   }
-#undef WF_LINE_CASE
+#undef WF_KL
   WF_CUDA(cudaGetLastError());
 }
-template void launch_line<float>(const LineArgs<float>&, int, cudaStream_t);
-template void launch_line<double>(const LineArgs<double>&, int, cudaStream_t);
+template void launch_line<float>(const LineArgs<float>&, int, bool, cudaStream_t);
+template void launch_line<double>(const LineArgs<double>&, int, bool, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Wilson matrix M = mu - D_t - D_s / gamma_f (§II, Eq. for M) on the output parity:
 // out_p = mu psi_p - D_t psi_p - D_s psi_q / gamma_f   (or x + a * that).
 // Dirac-Pauli basis: P_- = (1 - gamma_t)/2 keeps spins 2-3, P_+ spins 0-1, so
 // D_t psi(t) = P_- U_t(t) psi(t+1) + P_+ U_t^dag(t-1) psi(t-1), sign bc across the wrap.
+// In the axial frame U_t(t) = 1 except U_t(N_t-1) = P.
 // ----------------------------------------------------------------------------
-template <typename R, int N>
+template <typename R, bool AX>
 __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
   const Geom& g = A.g;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lg = warp * g.lpw + lane / g.lpl;
   if (lg >= A.nrhs * g.Nl) return;
-  const int rhs = lg / g.Nl, l = lg - rhs * g.Nl;
+  int rhs, l;
+  line_rhs(lg, A.nrhs, g.Nl, rhs, l);
   const int jj = lane % g.lpl;
-  const int tp = g.tp, T = g.T;
-  const size_t base = (size_t)lg * NSPIN_C * tp;
+  const int tp = g.tp, T = g.T, n = g.n;
+  const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
 
-  // spatial hop from the other parity
   LineArgs<R> H;
   H.g = g;
   H.parity = A.parity;
@@ -149,14 +210,15 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
   H.src_lo = A.psi_q + 6 * tp;
   H.us_out = A.us_out;
   H.us_nbr = A.us_nbr;
-  Vec3<R> h[N][4];
-  hop_spatial<R, N>(h, H, rhs, l, jj);
+  Vec3<R> h[NMAX][4];
+  hop_spatial<R>(h, H, rhs, l, jj);
 
-  const Cx<R>* ut_line = A.ut + (size_t)l * NLINK_C * tp;
+  const Cx<R>* ut_line = AX ? nullptr : A.ut + (size_t)l * NLINK_C * tp;
   const Cx<R>* pp = A.psi_p + base;
 #pragma unroll
-  for (int m = 0; m < N; ++m) {
-    const int t = jj * N + m;
+  for (int m = 0; m < NMAX; ++m) {
+    if (m >= n) continue;
+    const int t = jj * n + m;
     const int sl = m * g.lpl + jj;
     Vec3<R> res[4];
     if (t < T) {
@@ -165,11 +227,20 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
       const R sf = t == T - 1 ? A.bc : R(1);
       const R sb = t == 0 ? A.bc : R(1);
       const int slf = slot_of(g, tf), slb = slot_of(g, tb);
-      const Mat3<R> Uf = ldmat(ut_line, tp, sl);
-      const Mat3<R> Ub = ldmat(ut_line, tp, slb);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        Vec3<R> dt = s < 2 ? matvec_dag(Ub, ldvec(pp + 3 * s * tp, tp, slb)) : matvec(Uf, ldvec(pp + 3 * s * tp, tp, slf));
+        Vec3<R> nb = ldvec(pp + 3 * s * tp, tp, s < 2 ? slb : slf);
+        Vec3<R> dt;
+        if (AX) {
+          if (s < 2 && t == 0)
+            dt = matvec_dag(ldmat(A.pl + (size_t)l * 9, 1, 0), nb);
+          else if (s >= 2 && t == T - 1)
+            dt = matvec(ldmat(A.pl + (size_t)l * 9, 1, 0), nb);
+          else
+            dt = nb;
+        } else {
+          dt = s < 2 ? matvec_dag(ldmat(ut_line, tp, slb), nb) : matvec(ldmat(ut_line, tp, sl), nb);
+        }
         const R sg = s < 2 ? sb : sf;
         Vec3<R> r = vscale(A.mu, ldvec(pp + 3 * s * tp, tp, sl));
         r = vaxpy(-sg, dt, r);
@@ -189,20 +260,18 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
 }
 
 template <typename R>
-void launch_apply_M(const MArgs<R>& a, cudaStream_t s) {
+void launch_apply_M(const MArgs<R>& a, bool axial, cudaStream_t s) {
+  if (a.g.n < 1 || a.g.n > NMAX) throw Error(1, "unsupported sites per lane");
   const int lines = a.nrhs * a.g.Nl;
   const int warps = (lines + a.g.lpw - 1) / a.g.lpw;
   const int blocks = (warps * 32 + kLineThreads - 1) / kLineThreads;
-  switch (a.g.n) {
-    case 1: k_apply_M<R, 1><<<blocks, kLineThreads, 0, s>>>(a); break;
-    case 2: k_apply_M<R, 2><<<blocks, kLineThreads, 0, s>>>(a); break;
-    case 3: k_apply_M<R, 3><<<blocks, kLineThreads, 0, s>>>(a); break;
-    case 4: k_apply_M<R, 4><<<blocks, kLineThreads, 0, s>>>(a); break;
-    default: throw Error(1, "unsupported sites per lane");
-  }
+  if (axial)
+    k_apply_M<R, true><<<blocks, kLineThreads, 0, s>>>(a);
+  else
+    k_apply_M<R, false><<<blocks, kLineThreads, 0, s>>>(a);
   WF_CUDA(cudaGetLastError());
 }
-template void launch_apply_M<float>(const MArgs<float>&, cudaStream_t);
-template void launch_apply_M<double>(const MArgs<double>&, cudaStream_t);
+template void launch_apply_M<float>(const MArgs<float>&, bool, cudaStream_t);
+template void launch_apply_M<double>(const MArgs<double>&, bool, cudaStream_t);
 
 }  // namespace wf

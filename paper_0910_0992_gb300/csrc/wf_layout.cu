@@ -21,94 +21,129 @@ __device__ __forceinline__ void site_coords(const Geom& g, size_t site, int& x, 
   t = (int)(r / g.L);
 }
 
-// gamma_5 = -[[0, 1], [1, 0]] in the Dirac-Pauli basis: component c <- -(component c +- 6)
+// gamma_5 = -[[0, 1], [1, 0]] in the Dirac-Pauli basis: spin s <- -(spin s +- 2).
+// Optional colour rotation per site (axial frame): import psi' = g psi, export psi = g^dag psi'.
+// g (if not null) is given per parity as [l][9][tp] in FP64.
+__device__ __forceinline__ void rotate3(const Cx<double>* __restrict__ gl, int tp, int sl, bool dag, Cx<double> (&v)[3]) {
+  Mat3<double> G;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) G.e[k] = gl[k * tp + sl];
+  Vec3<double> x;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) x.c[k] = v[k];
+  Vec3<double> y = dag ? matvec_dag(G, x) : matvec(G, x);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = y.c[k];
+}
+
 template <typename R>
 __global__ void k_import_spinor(const Geom g, const Cx<double>* __restrict__ lex, Cx<R>* even, Cx<R>* odd, int nrhs,
-                                int g5) {
+                                int g5, const Cx<double>* g_e, const Cx<double>* g_o) {
   const size_t V = (size_t)g.L * g.L * g.L * g.T;
-  const size_t total = (size_t)nrhs * V * NSPIN_C;
+  const size_t total = (size_t)nrhs * V * 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % NSPIN_C);
-    const size_t site = (i / NSPIN_C) % V;
-    const int rhs = (int)(i / (NSPIN_C * V));
+    const int sp = (int)(i % 4);
+    const size_t site = (i / 4) % V;
+    const int rhs = (int)(i / (4 * V));
     int x, y, z, t;
     site_coords(g, site, x, y, z, t);
     const int p = (x + y + z) & 1;
     Cx<R>* dst = p ? odd : even;
     if (!dst) continue;
-    Cx<double> val;
-    if (g5) {
-      val = lex[i - c + (c + 6) % 12];
-      val.re = -val.re;
-      val.im = -val.im;
-    } else {
-      val = lex[i];
-    }
+    const int ssrc = g5 ? (sp + 2) % 4 : sp;
+    const Cx<double>* src = lex + ((size_t)rhs * V + site) * NSPIN_C + ssrc * 3;
+    Cx<double> v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = g5 ? mk<double>(-src[c].re, -src[c].im) : src[c];
     const int l = line_of(g, x, y, z);
-    dst[((size_t)(rhs * g.Nl + l) * NSPIN_C + c) * g.tp + slot_of(g, t)] = mk<R>((R)val.re, (R)val.im);
+    const int sl = slot_of(g, t);
+    const Cx<double>* gr = p ? g_o : g_e;
+    if (gr) rotate3(gr + (size_t)l * 9 * g.tp, g.tp, sl, false, v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      dst[((size_t)(rhs * g.Nl + l) * NSPIN_C + sp * 3 + c) * g.tp + sl] = mk<R>((R)v[c].re, (R)v[c].im);
   }
 }
 
 template <typename R>
 __global__ void k_export_spinor(const Geom g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* __restrict__ lex,
-                                int nrhs, int g5) {
+                                int nrhs, int g5, const Cx<double>* g_e, const Cx<double>* g_o) {
   const size_t V = (size_t)g.L * g.L * g.L * g.T;
-  const size_t total = (size_t)nrhs * V * NSPIN_C;
+  const size_t total = (size_t)nrhs * V * 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % NSPIN_C);
-    const size_t site = (i / NSPIN_C) % V;
-    const int rhs = (int)(i / (NSPIN_C * V));
+    const int sp = (int)(i % 4);
+    const size_t site = (i / 4) % V;
+    const int rhs = (int)(i / (4 * V));
     int x, y, z, t;
     site_coords(g, site, x, y, z, t);
     const int p = (x + y + z) & 1;
     const Cx<R>* src = p ? odd : even;
-    const int cs = g5 ? (c + 6) % 12 : c;
+    const int ss = g5 ? (sp + 2) % 4 : sp;
     const int l = line_of(g, x, y, z);
-    Cx<double> val = mk<double>(0.0, 0.0);
-    if (src) {
-      Cx<R> v = src[((size_t)(rhs * g.Nl + l) * NSPIN_C + cs) * g.tp + slot_of(g, t)];
-      val = mk<double>((double)v.re, (double)v.im);
-      if (g5) val = mk<double>(-val.re, -val.im);
+    const int sl = slot_of(g, t);
+    Cx<double> v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = mk<double>(0.0, 0.0);
+      if (src) {
+        Cx<R> w = src[((size_t)(rhs * g.Nl + l) * NSPIN_C + ss * 3 + c) * g.tp + sl];
+        v[c] = mk<double>((double)w.re, (double)w.im);
+      }
     }
-    lex[i] = val;
+    const Cx<double>* gr = p ? g_o : g_e;
+    if (gr && src) rotate3(gr + (size_t)l * 9 * g.tp, g.tp, sl, true, v);
+    Cx<double>* dst = lex + ((size_t)rhs * V + site) * NSPIN_C + sp * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[c] = g5 ? mk<double>(-v[c].re, -v[c].im) : v[c];
   }
 }
 
 // compact half-lattice array of one parity: [rhs][t][l][12] (sites in lexicographic order)
 template <typename R>
-__global__ void k_import_compact(const Geom g, const Cx<double>* __restrict__ cmp, Cx<R>* half, int nrhs, int g5) {
-  const size_t total = (size_t)nrhs * g.T * g.Nl * NSPIN_C;
+__global__ void k_import_compact(const Geom g, const Cx<double>* __restrict__ cmp, Cx<R>* half, int nrhs, int g5,
+                                 const Cx<double>* gr) {
+  const size_t total = (size_t)nrhs * g.T * g.Nl * 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % NSPIN_C);
-    const size_t k = i / NSPIN_C;
+    const int sp = (int)(i % 4);
+    const size_t k = i / 4;
     const int l = (int)(k % g.Nl);
     const int t = (int)((k / g.Nl) % g.T);
     const int rhs = (int)(k / ((size_t)g.Nl * g.T));
-    Cx<double> val;
-    if (g5) {
-      val = cmp[i - c + (c + 6) % 12];
-      val = mk<double>(-val.re, -val.im);
-    } else {
-      val = cmp[i];
-    }
-    half[((size_t)(rhs * g.Nl + l) * NSPIN_C + c) * g.tp + slot_of(g, t)] = mk<R>((R)val.re, (R)val.im);
+    const int ssrc = g5 ? (sp + 2) % 4 : sp;
+    const Cx<double>* src = cmp + k * NSPIN_C + ssrc * 3;
+    Cx<double> v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = g5 ? mk<double>(-src[c].re, -src[c].im) : src[c];
+    const int sl = slot_of(g, t);
+    if (gr) rotate3(gr + (size_t)l * 9 * g.tp, g.tp, sl, false, v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      half[((size_t)(rhs * g.Nl + l) * NSPIN_C + sp * 3 + c) * g.tp + sl] = mk<R>((R)v[c].re, (R)v[c].im);
   }
 }
 
 template <typename R>
-__global__ void k_export_compact(const Geom g, const Cx<R>* half, Cx<double>* __restrict__ cmp, int nrhs, int g5) {
-  const size_t total = (size_t)nrhs * g.T * g.Nl * NSPIN_C;
+__global__ void k_export_compact(const Geom g, const Cx<R>* half, Cx<double>* __restrict__ cmp, int nrhs, int g5,
+                                 const Cx<double>* gr) {
+  const size_t total = (size_t)nrhs * g.T * g.Nl * 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % NSPIN_C);
-    const size_t k = i / NSPIN_C;
+    const int sp = (int)(i % 4);
+    const size_t k = i / 4;
     const int l = (int)(k % g.Nl);
     const int t = (int)((k / g.Nl) % g.T);
     const int rhs = (int)(k / ((size_t)g.Nl * g.T));
-    const int cs = g5 ? (c + 6) % 12 : c;
-    Cx<R> v = half[((size_t)(rhs * g.Nl + l) * NSPIN_C + cs) * g.tp + slot_of(g, t)];
-    Cx<double> val = mk<double>((double)v.re, (double)v.im);
-    if (g5) val = mk<double>(-val.re, -val.im);
-    cmp[i] = val;
+    const int ss = g5 ? (sp + 2) % 4 : sp;
+    const int sl = slot_of(g, t);
+    Cx<double> v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<R> w = half[((size_t)(rhs * g.Nl + l) * NSPIN_C + ss * 3 + c) * g.tp + sl];
+      v[c] = mk<double>((double)w.re, (double)w.im);
+    }
+    if (gr) rotate3(gr + (size_t)l * 9 * g.tp, g.tp, sl, true, v);
+    Cx<double>* dst = cmp + k * NSPIN_C + sp * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[c] = g5 ? mk<double>(-v[c].re, -v[c].im) : v[c];
   }
 }
 
@@ -196,6 +231,53 @@ __global__ void k_tline_init(const Geom g, const Cx<double>* __restrict__ ut, Cx
   }
 }
 
+// Axial (temporal) frame (§II.C; App. C): per line, g(t) = U_t(0) U_t(1) ... U_t(t-1), g(0) = 1,
+// so that U_t'(t) = g(t) U_t(t) g(t+1)^dag = 1 for t < N_t - 1 and U_t'(N_t - 1) = g(N_t - 1) U_t(N_t - 1)
+// = P, the Polyakov product. Written in place of U_t (ut becomes g); P and
+// Lambda = (1 - s mu^-N_t P)^-1 per line.
+__global__ void k_axial_frame(const Geom g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, int* singular) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= g.Nl) return;
+  Cx<double>* line = ut_to_g + (size_t)l * 9 * g.tp;
+  Mat3<double> run = ident<double>();
+  for (int t = 0; t < g.T; ++t) {
+    const int sl = slot_of(g, t);
+    const Mat3<double> u = ldmat_d(line, g.tp, sl);
+    for (int k = 0; k < 9; ++k) line[k * g.tp + sl] = run.e[k];
+    run = matmul(run, u);
+  }
+  const double f = g.bc * pow(g.mu, -(double)g.T);
+  Mat3<double> A, Ai;
+  for (int k = 0; k < 9; ++k) {
+    const double id = (k % 4 == 0) ? 1.0 : 0.0;
+    A.e[k] = mk<double>(id - f * run.e[k].re, -f * run.e[k].im);
+  }
+  const double d = inv3(A, Ai);
+  if (!(d > 1e-12)) atomicExch(singular, 1);
+  for (int k = 0; k < 9; ++k) {
+    pl[(size_t)l * 9 + k] = run.e[k];
+    lamb[(size_t)l * 9 + k] = Ai.e[k];
+  }
+}
+
+// spatial links into the axial frame, in place: U_k'(x) = g(x) U_k(x) g(x + k)^dag
+__global__ void k_rotate_links(const Geom g, int p, Cx<double>* us_p, const Cx<double>* g_p, const Cx<double>* g_q) {
+  const size_t total = (size_t)3 * g.Nl * g.T;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i % g.T);
+    const int l = (int)((i / g.T) % g.Nl);
+    const int k = (int)(i / ((size_t)g.T * g.Nl));
+    int nb[6];
+    neighbour_lines(g, p, l, nb);
+    const int sl = slot_of(g, t);
+    Cx<double>* U = us_p + ((size_t)k * g.Nl + l) * 9 * g.tp;
+    const Mat3<double> gx = ldmat_d(g_p + (size_t)l * 9 * g.tp, g.tp, sl);
+    const Mat3<double> gy = ldmat_d(g_q + (size_t)nb[2 * k] * 9 * g.tp, g.tp, sl);
+    const Mat3<double> r = matmul(matmul(gx, ldmat_d(U, g.tp, sl)), dagger(gy));
+    for (int e = 0; e < 9; ++e) U[e * g.tp + sl] = r.e[e];
+  }
+}
+
 __global__ void k_d2f(const Cx<double>* __restrict__ in, Cx<float>* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = mk<float>((float)in[i].re, (float)in[i].im);
@@ -212,36 +294,41 @@ static int grid_for(size_t n) {
 
 template <typename R>
 void launch_import_spinor(const Geom& g, const Cx<double>* lex, Cx<R>* even, Cx<R>* odd, int nrhs, int g5,
-                          cudaStream_t s) {
-  size_t n = (size_t)nrhs * g.L * g.L * g.L * g.T * NSPIN_C;
-  k_import_spinor<R><<<grid_for(n), kThreads, 0, s>>>(g, lex, even, odd, nrhs, g5);
+                          const Cx<double>* g_e, const Cx<double>* g_o, cudaStream_t s) {
+  size_t n = (size_t)nrhs * g.L * g.L * g.L * g.T * 4;
+  k_import_spinor<R><<<grid_for(n), kThreads, 0, s>>>(g, lex, even, odd, nrhs, g5, g_e, g_o);
   WF_CUDA(cudaGetLastError());
 }
 template <typename R>
 void launch_export_spinor(const Geom& g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* lex, int nrhs, int g5,
-                          cudaStream_t s) {
-  size_t n = (size_t)nrhs * g.L * g.L * g.L * g.T * NSPIN_C;
-  k_export_spinor<R><<<grid_for(n), kThreads, 0, s>>>(g, even, odd, lex, nrhs, g5);
+                          const Cx<double>* g_e, const Cx<double>* g_o, cudaStream_t s) {
+  size_t n = (size_t)nrhs * g.L * g.L * g.L * g.T * 4;
+  k_export_spinor<R><<<grid_for(n), kThreads, 0, s>>>(g, even, odd, lex, nrhs, g5, g_e, g_o);
   WF_CUDA(cudaGetLastError());
 }
 template <typename R>
-void launch_import_compact(const Geom& g, const Cx<double>* cmp, Cx<R>* half, int nrhs, int g5, cudaStream_t s) {
-  size_t n = (size_t)nrhs * g.T * g.Nl * NSPIN_C;
-  k_import_compact<R><<<grid_for(n), kThreads, 0, s>>>(g, cmp, half, nrhs, g5);
+void launch_import_compact(const Geom& g, const Cx<double>* cmp, Cx<R>* half, int nrhs, int g5,
+                           const Cx<double>* gr, cudaStream_t s) {
+  size_t n = (size_t)nrhs * g.T * g.Nl * 4;
+  k_import_compact<R><<<grid_for(n), kThreads, 0, s>>>(g, cmp, half, nrhs, g5, gr);
   WF_CUDA(cudaGetLastError());
 }
 template <typename R>
-void launch_export_compact(const Geom& g, const Cx<R>* half, Cx<double>* cmp, int nrhs, int g5, cudaStream_t s) {
-  size_t n = (size_t)nrhs * g.T * g.Nl * NSPIN_C;
-  k_export_compact<R><<<grid_for(n), kThreads, 0, s>>>(g, half, cmp, nrhs, g5);
+void launch_export_compact(const Geom& g, const Cx<R>* half, Cx<double>* cmp, int nrhs, int g5,
+                           const Cx<double>* gr, cudaStream_t s) {
+  size_t n = (size_t)nrhs * g.T * g.Nl * 4;
+  k_export_compact<R><<<grid_for(n), kThreads, 0, s>>>(g, half, cmp, nrhs, g5, gr);
   WF_CUDA(cudaGetLastError());
 }
-#define WF_INST(R)                                                                                             \
-  template void launch_import_spinor<R>(const Geom&, const Cx<double>*, Cx<R>*, Cx<R>*, int, int, cudaStream_t); \
-  template void launch_export_spinor<R>(const Geom&, const Cx<R>*, const Cx<R>*, Cx<double>*, int, int,         \
-                                        cudaStream_t);                                                         \
-  template void launch_import_compact<R>(const Geom&, const Cx<double>*, Cx<R>*, int, int, cudaStream_t);      \
-  template void launch_export_compact<R>(const Geom&, const Cx<R>*, Cx<double>*, int, int, cudaStream_t);
+#define WF_INST(R)                                                                                          \
+  template void launch_import_spinor<R>(const Geom&, const Cx<double>*, Cx<R>*, Cx<R>*, int, int,             \
+                                        const Cx<double>*, const Cx<double>*, cudaStream_t);                \
+  template void launch_export_spinor<R>(const Geom&, const Cx<R>*, const Cx<R>*, Cx<double>*, int, int,      \
+                                        const Cx<double>*, const Cx<double>*, cudaStream_t);                \
+  template void launch_import_compact<R>(const Geom&, const Cx<double>*, Cx<R>*, int, int, const Cx<double>*, \
+                                         cudaStream_t);                                                     \
+  template void launch_export_compact<R>(const Geom&, const Cx<R>*, Cx<double>*, int, int, const Cx<double>*, \
+                                         cudaStream_t);
 WF_INST(float)
 WF_INST(double)
 #undef WF_INST
@@ -255,6 +342,18 @@ void launch_import_gauge(const Geom& g, const Cx<double>* lex, Cx<double>* ut[2]
 void launch_tline_init(const Geom& g, const Cx<double>* ut, Cx<double>* lamb, Cx<double>* lamf, int* singular,
                        cudaStream_t s) {
   k_tline_init<<<(g.Nl + 127) / 128, 128, 0, s>>>(g, ut, lamb, lamf, singular);
+  WF_CUDA(cudaGetLastError());
+}
+
+void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, int* singular,
+                        cudaStream_t s) {
+  k_axial_frame<<<(g.Nl + 127) / 128, 128, 0, s>>>(g, ut_to_g, pl, lamb, singular);
+  WF_CUDA(cudaGetLastError());
+}
+
+void launch_rotate_links(const Geom& g, Cx<double>* us[2], const Cx<double>* gg[2], cudaStream_t s) {
+  size_t n = (size_t)3 * g.Nl * g.T;
+  for (int p = 0; p < 2; ++p) k_rotate_links<<<grid_for(n), kThreads, 0, s>>>(g, p, us[p], gg[p], gg[1 - p]);
   WF_CUDA(cudaGetLastError());
 }
 

@@ -5,20 +5,28 @@
 // t = 0 .. N_t-1, with psi(-1) = s psi(N_t-1).
 //
 // The paper closes the wrap-around with the Sherman-Morrison-Woodbury correction
-// chi = T_0^-1 eta, q = Lambda W^dag chi, psi = chi - X q. Here the same exact
-// result is reached with a warp-parallel formulation: every lane owns n consecutive
-// times and turns them into one affine map psi_out = c + G psi_in (c the open-boundary
-// solution of its segment, G the product of U_0 / mu over the segment); a
-// Kogge-Stone scan of these maps across the lanes of the line gives every lane the
-// map from the line's open end to its own segment; the wrap-around is closed with the
-// per-line matrix Lambda = (I - s mu^-N_t P)^-1 (P the Polyakov product, precomputed
-// in FP64 at gauge load, §II.A step 1(b)); each lane then re-runs its n steps from
-// its true boundary value. Every input is read once and every output written once.
+// chi = T_0^-1 eta, q = Lambda W^dag chi, psi = chi - X q. Here the same exact result is
+// reached warp-parallel: each lane owns n consecutive times and turns them into one affine
+// map psi_out = c + G psi_in (c: open-boundary solution of its segment; G: product of
+// U_0 / mu over the segment); a Kogge-Stone scan of these maps over the lanes of the line
+// gives every lane the map from the line's open end to its segment; the wrap is closed with
+// the per-line Lambda = (I - s mu^-N_t P)^-1 (P the Polyakov product, precomputed in FP64
+// at gauge load, §II.A step 1(b)); each lane then re-runs its n steps from its true
+// boundary value. Every input is read once and every output written once.
+//
+// Two frames:
+// * general: U_0 as given; G is a 3x3 matrix (tline_solve_general).
+// * axial: the gauge field was rotated once at load so that U_0(t) = 1 for t < N_t - 1
+//   and U_0(N_t - 1) = P (§II.C, "axial gauge"; App. C). Then every lane's G is the scalar
+//   mu^-k, the scan composes scalars and vectors only, no U_0 is read, and P enters once,
+//   at the wrap (tline_solve_axial).
 #pragma once
 
 #include "wf_common.cuh"
 
 namespace wf {
+
+constexpr int NMAX = 4;  // sites per lane, at most (T <= 32 * NMAX)
 
 enum LineOp { OP_COPY = 0, OP_FWD = 1, OP_BWD = 2, OP_SKIP = 3 };
 enum LineSrc { SRC_LOAD = 0, SRC_HOP = 1 };
@@ -28,19 +36,22 @@ struct LineArgs {
   Geom g;
   int parity;   // 3-D parity of the output lines
   int nrhs;
-  int opu, opl; // LineOp for the upper (P_+) and lower (P_-) spin halves
+  int opu, opl; // LineOp for the upper (P_+) and lower (P_-) spin halves (runtime-op kernel)
+  int src;      // LineSrc (runtime-op kernel)
   // Spinor sources. SRC_LOAD reads the output site itself; SRC_HOP reads the six
   // spatial neighbours (other parity). src_up / src_lo point at component 0 of the
   // half that supplies spins 0-1 / spins 2-3 (line stride 12 * tp).
   const Cx<R>* src_up;
   const Cx<R>* src_lo;
-  // links: U_t of the output parity [Nl][9][tp]; forward spatial links of the output
-  // parity and of the neighbour parity, each [3][Nl][9][tp]
+  // links: U_t of the output parity [Nl][9][tp] (general frame), the per-line boundary
+  // link P [Nl][9] (axial frame), forward spatial links of the output parity and of the
+  // neighbour parity, each [3][Nl][9][tp]
   const Cx<R>* ut;
+  const Cx<R>* pl;
   const Cx<R>* us_out;
   const Cx<R>* us_nbr;
   const Cx<R>* lamb;  // Lambda for T^-1, [Nl][9]
-  const Cx<R>* lamf;  // Lambda for T^-dag, [Nl][9]
+  const Cx<R>* lamf;  // Lambda for T^-dag, [Nl][9] (general frame; axial uses lamb^dag)
   // pre-solve axpy: v <- xpre + apre * v (skipped if xpre == nullptr)
   const Cx<R>* xpre;
   R apre;
@@ -49,6 +60,7 @@ struct LineArgs {
   R apost;
   int swap_out;  // store the upper result into the lower half and vice versa
   Cx<R>* out;    // [nrhs][Nl][12][tp]
+  double* norm2; // if set: atomically add |stored result|^2 per rhs (FP64)
   R inv_mu, bc;
 };
 
@@ -106,35 +118,66 @@ __device__ __forceinline__ Vec3<R> vadd(const Vec3<R>& x, const Vec3<R>& y) {
   return w;
 }
 
+// |x|^2 in the field's own precision (GB300's FP64 rate is far below its FP32 rate, so FP32
+// kernels keep FP64 for the final cross-thread sums only)
+template <typename R>
+__device__ __forceinline__ R vnorm2(const Vec3<R>& x) {
+  R s = R(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s = fma(x.c[k].re, x.c[k].re, fma(x.c[k].im, x.c[k].im, s));
+  return s;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> vshfl_down(const Vec3<R>& v, int d, int w) {
+  Vec3<R> r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.c[k] = shfl_down(v.c[k], d, w);
+  return r;
+}
+template <typename R>
+__device__ __forceinline__ Vec3<R> vshfl_up(const Vec3<R>& v, int d, int w) {
+  Vec3<R> r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.c[k] = shfl_up(v.c[k], d, w);
+  return r;
+}
+template <typename R>
+__device__ __forceinline__ Vec3<R> vshfl_idx(const Vec3<R>& v, int src, int w) {
+  Vec3<R> r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.c[k] = shfl_idx(v.c[k], src, w);
+  return r;
+}
+
 // ----------------------------------------------------------------------------
-// Time-line solve of NS colour vectors per site on the lane's N sites.
-// FWD = false: psi = T^-1 eta. FWD = true: psi = T^-dag eta.
-// v holds eta on entry and psi on exit. ut_line points at this line's U_t block
-// ([9][tp]); lam at its Lambda (9 complex). All lanes of the warp must call this.
+// General frame: time-line solve of NS colour vectors per site on the lane's n sites.
+// FWD = false: psi = T^-1 eta. FWD = true: psi = T^-dag eta. v holds eta on entry and
+// psi on exit. ut_line: this line's U_t block ([9][tp]); lam: its Lambda. Warp-collective.
 // ----------------------------------------------------------------------------
-template <typename R, int N, int NS, bool FWD>
-__device__ __forceinline__ void tline_solve(Vec3<R> (&v)[N][NS], const Cx<R>* __restrict__ ut_line,
-                                            const Cx<R>* __restrict__ lam, const Geom& g, int jj, R inv_mu, R bc) {
-  const int T = g.T, tp = g.tp, lpl = g.lpl;
+template <typename R, int NS, bool FWD>
+__device__ __forceinline__ void tline_solve_general(Vec3<R> (&v)[NMAX][NS], const Cx<R>* __restrict__ ut_line,
+                                                    const Cx<R>* __restrict__ lam, const Geom& g, int jj, R inv_mu,
+                                                    R bc) {
+  const int T = g.T, tp = g.tp, lpl = g.lpl, n = g.n;
   constexpr bool KEEPU = (sizeof(R) == 4);
-  Mat3<R> Uk[KEEPU ? N : 1];
+  Mat3<R> Uk[KEEPU ? NMAX : 1];
 
   auto link_slot = [&](int m) {
-    int t = jj * N + m;
+    int t = jj * n + m;
     int tl = FWD ? (t == 0 ? T - 1 : t - 1) : t;
-    return (tl % N) * lpl + tl / N;
+    return (tl % n) * lpl + tl / n;
   };
-  auto site_valid = [&](int m) { return jj * N + m < T; };
+  auto site_valid = [&](int m) { return m < n && jj * n + m < T; };
 
-  // pass 1: open solve of the segment (c) and its transfer matrix (G)
   Vec3<R> c[NS];
   Mat3<R> G = ident<R>();
 #pragma unroll
   for (int s = 0; s < NS; ++s) c[s] = vzero<R>();
   bool any = false;
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
-    const int m = FWD ? q : N - 1 - q;
+  for (int q = 0; q < NMAX; ++q) {
+    const int m = FWD ? q : NMAX - 1 - q;
     if (!site_valid(m)) continue;
     Mat3<R> U = ldmat(ut_line, tp, link_slot(m));
     if (KEEPU) Uk[KEEPU ? m : 0] = U;
@@ -151,16 +194,13 @@ __device__ __forceinline__ void tline_solve(Vec3<R> (&v)[N][NS], const Cx<R>* __
     }
   }
 
-  // scan across the lanes of the line: suffix (T^-1) or prefix (T^-dag) composition
   for (int d = 1; d < lpl; d <<= 1) {
     Mat3<R> Gn;
     Vec3<R> cn[NS];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Gn.e[k] = FWD ? shfl_up(G.e[k], d, lpl) : shfl_down(G.e[k], d, lpl);
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cn[s].c[k] = FWD ? shfl_up(c[s].c[k], d, lpl) : shfl_down(c[s].c[k], d, lpl);
+    for (int s = 0; s < NS; ++s) cn[s] = FWD ? vshfl_up(c[s], d, lpl) : vshfl_down(c[s], d, lpl);
     const bool has = FWD ? (jj >= d) : (jj + d < lpl);
     if (has) {
 #pragma unroll
@@ -169,17 +209,11 @@ __device__ __forceinline__ void tline_solve(Vec3<R> (&v)[N][NS], const Cx<R>* __
     }
   }
 
-  // close the wrap: T^-1: psi(0) = Lambda c(lane 0); T^-dag: psi(N_t-1) = Lambda c(last lane)
   const Mat3<R> Lam = ldmat(lam, 1, 0);
   const int root = FWD ? lpl - 1 : 0;
   Vec3<R> wrap[NS];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    Vec3<R> w = matvec(Lam, c[s]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) wrap[s].c[k] = bc * shfl_idx(w.c[k], root, lpl);
-  }
-  // boundary value entering this lane: from the neighbouring lane's scanned map
+  for (int s = 0; s < NS; ++s) wrap[s] = vscale(bc, vshfl_idx(matvec(Lam, c[s]), root, lpl));
   Vec3<R> e[NS];
   {
     Mat3<R> Gn;
@@ -187,24 +221,95 @@ __device__ __forceinline__ void tline_solve(Vec3<R> (&v)[N][NS], const Cx<R>* __
 #pragma unroll
     for (int k = 0; k < 9; ++k) Gn.e[k] = FWD ? shfl_up(G.e[k], 1, lpl) : shfl_down(G.e[k], 1, lpl);
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cn[s].c[k] = FWD ? shfl_up(c[s].c[k], 1, lpl) : shfl_down(c[s].c[k], 1, lpl);
+    for (int s = 0; s < NS; ++s) cn[s] = FWD ? vshfl_up(c[s], 1, lpl) : vshfl_down(c[s], 1, lpl);
     const bool edge = FWD ? (jj == 0) : (jj == lpl - 1);
 #pragma unroll
     for (int s = 0; s < NS; ++s) e[s] = edge ? wrap[s] : matvec_acc(Gn, wrap[s], cn[s]);
   }
 
-  // pass 2: re-run the segment from its true boundary value
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
-    const int m = FWD ? q : N - 1 - q;
+  for (int q = 0; q < NMAX; ++q) {
+    const int m = FWD ? q : NMAX - 1 - q;
     if (!site_valid(m)) continue;
     Mat3<R> U = KEEPU ? Uk[KEEPU ? m : 0] : ldmat(ut_line, tp, link_slot(m));
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       Vec3<R> a = FWD ? matvec_dag(U, e[s]) : matvec(U, e[s]);
       e[s] = vscale(inv_mu, vadd(a, v[m][s]));
+      v[m][s] = e[s];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Axial frame: U_0 = 1 except U_0(N_t-1) = P. Lane maps are psi_out = c + a psi_in with a
+// scalar a = mu^-(sites); the value entering the top of the line is P s psi(0) (T^-1) and
+// the value entering its bottom is P^dag s psi(N_t-1) (T^-dag). Closure: psi(0) = Lambda C_0,
+// psi(N_t-1) = Lambda^dag C_last, since (1 - s mu^-N_t P^dag)^-1 = Lambda^dag.
+// ----------------------------------------------------------------------------
+template <typename R, int NS, bool FWD>
+__device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NMAX][NS], const Cx<R>* __restrict__ P_line,
+                                                  const Cx<R>* __restrict__ lam, const Geom& g, int jj, R inv_mu, R bc) {
+  const int T = g.T, lpl = g.lpl, n = g.n;
+  auto site_valid = [&](int m) { return m < n && jj * n + m < T; };
+
+  Vec3<R> c[NS];
+  R a = R(1);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) c[s] = vzero<R>();
+#pragma unroll
+  for (int q = 0; q < NMAX; ++q) {
+    const int m = FWD ? q : NMAX - 1 - q;
+    if (!site_valid(m)) continue;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) c[s] = vscale(inv_mu, vadd(v[m][s], c[s]));
+    a *= inv_mu;
+  }
+
+  for (int d = 1; d < lpl; d <<= 1) {
+    const R an = FWD ? __shfl_up_sync(0xffffffffu, a, d, lpl) : __shfl_down_sync(0xffffffffu, a, d, lpl);
+    Vec3<R> cn[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) cn[s] = FWD ? vshfl_up(c[s], d, lpl) : vshfl_down(c[s], d, lpl);
+    const bool has = FWD ? (jj >= d) : (jj + d < lpl);
+    if (has) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) c[s] = vaxpy(a, cn[s], c[s]);
+      a *= an;
+    }
+  }
+
+  const int root = FWD ? lpl - 1 : 0;
+  Vec3<R> wrap[NS];
+  {
+    const Mat3<R> Lam = ldmat(lam, 1, 0);
+    const Mat3<R> P = ldmat(P_line, 1, 0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      // T^-1 : psi(0) = Lambda C_0, entering value P s psi(0)
+      // T^-dag: psi(N_t-1) = Lambda^dag C_last, entering value P^dag s psi(N_t-1)
+      Vec3<R> w = FWD ? matvec_dag(P, matvec_dag(Lam, c[s])) : matvec(P, matvec(Lam, c[s]));
+      wrap[s] = vscale(bc, vshfl_idx(w, root, lpl));
+    }
+  }
+  Vec3<R> e[NS];
+  {
+    const R an = FWD ? __shfl_up_sync(0xffffffffu, a, 1, lpl) : __shfl_down_sync(0xffffffffu, a, 1, lpl);
+    const bool edge = FWD ? (jj == 0) : (jj == lpl - 1);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Vec3<R> cn = FWD ? vshfl_up(c[s], 1, lpl) : vshfl_down(c[s], 1, lpl);
+      e[s] = edge ? wrap[s] : vaxpy(an, wrap[s], cn);
+    }
+  }
+
+#pragma unroll
+  for (int q = 0; q < NMAX; ++q) {
+    const int m = FWD ? q : NMAX - 1 - q;
+    if (!site_valid(m)) continue;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      e[s] = vscale(inv_mu, vadd(v[m][s], e[s]));
       v[m][s] = e[s];
     }
   }
@@ -229,21 +334,21 @@ __device__ __forceinline__ void isigma(int k, const Vec3<R>& a0, const Vec3<R>& 
 }
 
 // ----------------------------------------------------------------------------
-// Spatial hop D_s (§II, Eq. for D_s) at the lane's N sites of line l (parity p):
+// Spatial hop D_s (§II, Eq. for D_s) at the lane's n sites of line l (parity p):
 //   sum_k (1 - gamma_k)/2 U_k(x) psi(x + k) + (1 + gamma_k)/2 U_k^dag(x - k) psi(x - k).
 // Dirac-Pauli basis: with psi = (u, d) (upper, lower spin pairs),
 //   (1 - gamma_k) psi = (h, -i sigma_k h), h = u + i sigma_k d,
 //   (1 + gamma_k) psi = (h, +i sigma_k h), h = u - i sigma_k d,
 // so each direction costs two SU(3) matvecs on a half-spinor (App. B: 984 FLOPs/site).
 // ----------------------------------------------------------------------------
-template <typename R, int N>
-__device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[N][4], const LineArgs<R>& A, int rhs, int l, int jj) {
+template <typename R>
+__device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArgs<R>& A, int rhs, int l, int jj) {
   const Geom& g = A.g;
-  const int tp = g.tp, Nl = g.Nl, T = g.T;
+  const int tp = g.tp, Nl = g.Nl, T = g.T, n = g.n;
   int nb[6];
   neighbour_lines(g, A.parity, l, nb);
 #pragma unroll
-  for (int m = 0; m < N; ++m)
+  for (int m = 0; m < NMAX; ++m)
 #pragma unroll
     for (int s = 0; s < 4; ++s) h[m][s] = vzero<R>();
 
@@ -257,9 +362,8 @@ __device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[N][4], const LineArgs<R
       const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * NLINK_C * tp
                                  : A.us_nbr + (size_t)(k * Nl + ln) * NLINK_C * tp;
 #pragma unroll
-      for (int m = 0; m < N; ++m) {
-        const int t = jj * N + m;
-        if (t >= T) continue;
+      for (int m = 0; m < NMAX; ++m) {
+        if (m >= n || jj * n + m >= T) continue;
         const int sl = m * g.lpl + jj;
         Vec3<R> u0 = ldvec(up, tp, sl), u1 = ldvec(up + 3 * tp, tp, sl);
         Vec3<R> d0 = ldvec(lo, tp, sl), d1 = ldvec(lo + 3 * tp, tp, sl);

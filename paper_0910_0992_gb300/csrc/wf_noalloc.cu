@@ -83,10 +83,10 @@ int noalloc_apply(wf_handle* h, const double* in_odd, double* out_odd, int dagge
   const bool prof = h->prof;
   h->prof = false;  // no event creation on this path
   try {
-    launch_import_compact<double>(h->g, reinterpret_cast<const Cx<double>*>(in_odd), x, nrhs, 0, s);
+    launch_import_compact<double>(h->g, reinterpret_cast<const Cx<double>*>(in_odd), x, nrhs, 0, frame_rot(h, 1), s);
     h->launches += 1;
     schur_apply<double>(h, x, o, dagger ? 1 : 0, nrhs, y, z);
-    launch_export_compact<double>(h->g, o, reinterpret_cast<Cx<double>*>(out_odd), nrhs, 0, s);
+    launch_export_compact<double>(h->g, o, reinterpret_cast<Cx<double>*>(out_odd), nrhs, 0, frame_rot(h, 1), s);
     h->launches += 1;
   } catch (...) {
     h->prof = prof;

@@ -46,13 +46,17 @@ def _host(t):
     return t.cpu().numpy()
 
 
-@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"L{c[0]}T{c[1]}bc{c[4]}")
+FRAMES = [True, False]  # axial frame (default), caller's gauge
+
+
+@pytest.fixture(scope="module", params=[(c, ax) for c in CASES for ax in FRAMES],
+                ids=lambda ca: f"L{ca[0][0]}T{ca[0][1]}bc{ca[0][4]}-{'axial' if ca[1] else 'general'}")
 def case(request):
-    L, T, ks, xi, bc, eps, seed = request.param
+    (L, T, ks, xi, bc, eps, seed), axial = request.param
     p = W.Params(L, T, ks, xi=xi, bc=bc)
     U = S.random_gauge(L, T, eps, seed)
     eta = S.gaussian_source(L, T, seed + 100, nrhs=2)
-    w = wf.Wilson(L, T, ks, kappa_t=xi * ks, bc=bc)
+    w = wf.Wilson(L, T, ks, kappa_t=xi * ks, bc=bc, axial=axial)
     w.load_gauge(U)
     yield p, U, eta, w
     w.close()
@@ -132,10 +136,11 @@ def test_solve_matches_oracle_solution():
     w.close()
 
 
-def test_singular_preconditioner_is_reported():
+@pytest.mark.parametrize("axial", FRAMES)
+def test_singular_preconditioner_is_reported(axial):
     """mu = 1 (kappa_t = 1/2), periodic, unit links: T has a zero mode, so Lambda does not exist."""
     L, T = 2, 4
-    w = wf.Wilson(L, T, 0.25, kappa_t=0.5, bc=1)
+    w = wf.Wilson(L, T, 0.25, kappa_t=0.5, bc=1, axial=axial)
     with pytest.raises(wf.WFError) as e:
         w.load_gauge(S.unit_gauge(L, T))
     assert e.value.code == wf.WF_ESINGULAR
