@@ -300,6 +300,35 @@ def run_ours(args, prm, U, eta):
                "h2d_bytes_per_step": int(h_rhs.numel() * 16), "d2h_bytes_per_step": int(h_x.numel() * 16),
                "ms_per_step": 1e3 * e2e_s / args.steps}
 
+    # same-GPU comparison (outside the timed region): the standard 4-D even-odd solve of the
+    # same sources, batched and single-source, against the temporal + 3-D Schur solve
+    compare = None
+    if not args.no_compare:
+        def timed(method, r, xx, nr, reps):
+            st, it, res = wf.wf_solve(w.h, r, xx, nr, args.tol, method, prec, 0)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                st, it, res = wf.wf_solve(w.h, r, xx, nr, args.tol, method, prec, 0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != wf.WF_OK or max(res) > args.tol:
+                raise RuntimeError(f"comparison solve failed: method {method}, status {st}, residuals {res}")
+            return e0.elapsed_time(e1) / reps / 1e3, it
+
+        r1, x1 = rhs[:1].contiguous(), x[:1].contiguous()
+        t_eo, it_eo = timed(wf.WF_EO4D, rhs, x, nsrc, 2)
+        t_ts1, it_ts1 = timed(wf.WF_TEMPORAL_SCHUR, r1, x1, 1, 3)
+        t_eo1, it_eo1 = timed(wf.WF_EO4D, r1, x1, 1, 3)
+        t_ts = ms / args.steps / 1e3
+        compare = {
+            "baseline_method": "standard 4-D even-odd (Schur) CGNR, same GPU, same precision scheme",
+            "batched": {"nrhs": nsrc, "temporal_schur_s": t_ts, "eo4d_s": t_eo, "speedup": t_eo / t_ts,
+                        "temporal_schur_iterations": iters, "eo4d_iterations": it_eo},
+            "single": {"nrhs": 1, "temporal_schur_s": t_ts1, "eo4d_s": t_eo1, "speedup": t_eo1 / t_ts1,
+                       "temporal_schur_iterations": it_ts1[0], "eo4d_iterations": it_eo1[0]},
+        }
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, desc, threads, dt = oracle_sample(20.0, prm)
@@ -334,6 +363,7 @@ def run_ours(args, prm, U, eta):
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": e2e,
+            "vs_eo4d_same_gpu": compare,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -383,6 +413,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the same-GPU 4-D even-odd comparison")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
                     help="apply: only FP32 M-hat applies (for kernel profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")

@@ -116,7 +116,15 @@ int wf_apply_C(wf_handle_t* h, const double* in, double* out, int which, int nrh
  *   M-hat = 1 - gamma_f^-2 C_L^o D_s^oe C_R^e C_L^e D_s^eo C_R^o. */
 int wf_apply_schur(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
 
+/* The comparator of the paper's preconditioner: out = M-hat_4 in (dagger = 0) or gamma_5 M-hat_4
+ * gamma_5 in (dagger = 1), the standard 4-D even-odd Schur operator
+ *   M-hat_4 = mu - mu^-1 D_w^oe D_w^eo,   D_w = D_t + D_s / gamma_f   (§II.B, 4D-Schur; App. B),
+ * on arrays of the sites with (x + y + z + t) odd, in lexicographic order: [rhs][V/2][spin][colour],
+ * site k = (x + L (y + L (z + L t))) / 2. Needs an even T. */
+int wf_apply_eo4d(wf_handle_t* h, const double* in_odd4, double* out_odd4, int dagger, int nrhs);
+
 /* FP32 variants: same contracts, FP64 in and out, every internal step in FP32. */
+int wf_apply_eo4d_f32(wf_handle_t* h, const double* in_odd4, double* out_odd4, int dagger, int nrhs);
 int wf_apply_M_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 int wf_apply_Tinv_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);

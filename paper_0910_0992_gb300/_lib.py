@@ -37,6 +37,8 @@ _SIGS = {
     "wf_apply_schur": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur_noalloc": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_eo4d": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_eo4d_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_profile": (_i, [_vp, _i]),
@@ -133,6 +135,8 @@ wf_apply_C = _apply(lib.wf_apply_C)
 wf_apply_schur = _apply(lib.wf_apply_schur)
 wf_apply_schur_f32 = _apply(lib.wf_apply_schur_f32)
 wf_apply_schur_noalloc = _apply(lib.wf_apply_schur_noalloc)
+wf_apply_eo4d = _apply(lib.wf_apply_eo4d)
+wf_apply_eo4d_f32 = _apply(lib.wf_apply_eo4d_f32)
 
 
 def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):
@@ -226,6 +230,12 @@ class Wilson:
         out = self._like(x_odd)
         (wf_apply_schur_f32 if f32 else wf_apply_schur)(self.h, x_odd, out, dagger,
                                                          self._nrhs(x_odd, wf_half_elems(self.h)))
+        return out
+
+    def apply_eo4d(self, x_odd4, dagger=False, f32=False):
+        out = self._like(x_odd4)
+        (wf_apply_eo4d_f32 if f32 else wf_apply_eo4d)(self.h, x_odd4, out, dagger,
+                                                       self._nrhs(x_odd4, wf_half_elems(self.h)))
         return out
 
     def solve(self, rhs, tol=1e-10, method=WF_TEMPORAL_SCHUR, precision=WF_FP64, x0=None):

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -299,13 +300,18 @@ std::vector<double> read_scalars(wf_handle* h, const double* d, int n) {
   return v;
 }
 
-// CGNR on M-hat with operator applies in precision R (R = double: plain FP64 CG; R = float:
-// FP32 iterations with FP64 reliable updates of the residual). Solves for y_o given b_o
-// (FP64 internal odd fields) to |b - M-hat y| <= target[k] for every rhs k. Returns iterations.
+// A linear operator on internal vectors of one method: y = A x (dagger = 0) or A^dag x
+// (dagger = 1) for all right-hand sides; if norm2 is set, |y|^2 per rhs lands there.
 template <typename R>
-std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, int nrhs, const std::vector<double>& target,
-                            int maxiter, bool x0) {
-  const size_t n = h->half_int();
+using OpFn = std::function<void(const Cx<R>* x, Cx<R>* y, int dagger, double* norm2)>;
+
+// CGNR, CG on A^dag A y = A^dag b, with operator applies in precision R (R = double: plain
+// FP64 CG; R = float: FP32 iterations with FP64 reliable updates of the residual, using A64).
+// b and y are FP64 internal vectors of n complex numbers per rhs; stops when |b - A y| <=
+// target[k] for every rhs k. Returns the iterations per rhs.
+template <typename R>
+std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, const Cx<double>* b, Cx<double>* y,
+                      int nrhs, size_t n, const std::vector<double>& target, int maxiter, bool x0) {
   const size_t nt = n * nrhs;
   cudaStream_t s = h->stream;
   double* sc = h->buf<double>("cg_scalars", 16 * (size_t)nrhs);
@@ -320,17 +326,13 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
   Cx<R>* p = h->buf<Cx<R>>(pname<R>("cg_p"), nt);
   Cx<R>* q = h->buf<Cx<R>>(pname<R>("cg_q"), nt);
   Cx<R>* xi = h->buf<Cx<R>>(pname<R>("cg_x"), nt);
-  Cx<R>* ty = h->buf<Cx<R>>(pname<R>("cg_ty"), nt);
-  Cx<R>* tz = h->buf<Cx<R>>(pname<R>("cg_tz"), nt);
   Cx<double>* r64 = h->buf<Cx<double>>("cg_r64", nt);
-  Cx<double>* ty64 = h->buf<Cx<double>>("cg_ty64", nt);
-  Cx<double>* tz64 = h->buf<Cx<double>>("cg_tz64", nt);
   const bool mixed = sizeof(R) == 4;
 
-  // r64 = b - M-hat y (FP64) or b
+  // r64 = b - A y (FP64) or b
   auto true_schur_residual = [&]() {
-    schur_apply<double>(h, y, r64, 0, nrhs, ty64, tz64);
-    { Prof P(h, "axpby_f64"); launch_axpby<double>(r64, b, nt, 1.0, -1.0, s); }  // r64 = b - M-hat y
+    A64(y, r64, 0, nullptr);
+    { Prof P(h, "axpby_f64"); launch_axpby<double>(r64, b, nt, 1.0, -1.0, s); }  // r64 = b - A y
   };
   if (x0) {
     true_schur_residual();
@@ -362,7 +364,7 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
   };
   if (all_done()) return iters;
 
-  schur_apply<R>(h, r, sv, 1, nrhs, ty, tz, gam);  // s = M-hat^dag r, |s|^2
+  A(r, sv, 1, gam);  // s = A^dag r, |s|^2
   WF_CUDA(cudaMemcpyAsync(p, sv, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
 
   // reliable-update trigger: the FP32 residual has dropped by this factor since the last
@@ -373,7 +375,7 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
     if (v > 0.0 && v < 1.0) delta = v;
   }
   for (int it = 0; it < maxiter; ++it) {
-    schur_apply<R>(h, p, q, 0, nrhs, ty, tz, qq);  // q = M-hat p, |q|^2
+    A(p, q, 0, qq);  // q = A p, |q|^2
     { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s); }
     for (int k = 0; k < nrhs; ++k)
       if (act[k]) iters[k]++;
@@ -409,7 +411,7 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
     }
     if (changed) WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     if (all_done()) break;
-    schur_apply<R>(h, r, sv, 1, nrhs, ty, tz, gnew);  // s = M-hat^dag r, |s|^2
+    A(r, sv, 1, gnew);  // s = A^dag r, |s|^2
     { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
     { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s); }
   }
@@ -418,6 +420,15 @@ std::vector<int> cgnr_schur(wf_handle* h, const Cx<double>* b, Cx<double>* y, in
     launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);
   }
   return iters;
+}
+
+// M-hat (temporal + 3-D Schur, §II.B) as a CGNR operator on odd internal fields
+template <typename R>
+OpFn<R> schur_op(wf_handle* h, int nrhs) {
+  const size_t nt = h->half_int() * nrhs;
+  Cx<R>* ty = h->buf<Cx<R>>(pname<R>("op_ty"), nt);
+  Cx<R>* tz = h->buf<Cx<R>>(pname<R>("op_tz"), nt);
+  return [=](const Cx<R>* x, Cx<R>* y, int dagger, double* norm2) { schur_apply<R>(h, x, y, dagger, nrhs, ty, tz, norm2); };
 }
 
 // Temporal + 3-D Schur solve (§II.B): prepare with S_L, CGNR on M-hat, reconstruct with S_R,
@@ -478,8 +489,11 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   const int maxiter = 100000;
   int status = WF_OK;
   for (int pass = 0; pass < 6; ++pass) {
-    std::vector<int> it = precision == WF_FP32 ? cgnr_schur<float>(h, b_o, y_o, nrhs, target, maxiter, have_x0)
-                                               : cgnr_schur<double>(h, b_o, y_o, nrhs, target, maxiter, have_x0);
+    std::vector<int> it = precision == WF_FP32
+                              ? cgnr<float>(h, schur_op<float>(h, nrhs), schur_op<double>(h, nrhs), b_o, y_o, nrhs, n,
+                                            target, maxiter, have_x0)
+                              : cgnr<double>(h, schur_op<double>(h, nrhs), schur_op<double>(h, nrhs), b_o, y_o, nrhs,
+                                             n, target, maxiter, have_x0);
     for (int k = 0; k < nrhs; ++k) iters[k] += it[k];
     have_x0 = true;
     // reconstruction (S_R): psi_o = C_R^o y_o ; psi_e = C_R^e C_L^e [eta_e + gamma_f^-1 D_s^eo psi_o]
@@ -519,6 +533,333 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     if (resid_out) resid_out[k] = rel[k];
   }
   return status;
+}
+
+// ----------------------------------------------------------------------------
+// Comparators: 4-D even-odd Schur, unpreconditioned M, temporal-only M~ = C_L M C_R
+// ----------------------------------------------------------------------------
+template <typename R>
+EoArgs<R> eo_args(wf_handle* h, int par, int nrhs) {
+  Gauge<R> G = gauge_of<R>(h);
+  EoArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = h->g;
+  a.par = par;
+  a.nrhs = nrhs;
+  for (int p = 0; p < 2; ++p) {
+    a.ut[p] = G.ut[p];
+    a.pl[p] = G.pl[p];
+    a.us[p] = G.us[p];
+  }
+  a.inv_gf = (R)(1.0 / h->g.gamma_f);
+  a.bc = (R)h->g.bc;
+  a.a = R(1);
+  return a;
+}
+
+size_t eo_elems(const wf_handle* h) { return (size_t)h->g.L * h->g.L * h->g.L * NSPIN_C * (h->g.T / 2); }
+
+// M-hat_4 = mu - mu^-1 D_w^oe D_w^eo on odd 4-D fields (dagger: S M-hat_4 S), two dslash kernels
+template <typename R>
+void eo4d_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* he, double* norm2) {
+  const double mu = h->g.mu;
+  {
+    EoArgs<R> a = eo_args<R>(h, 0, nrhs);
+    a.in = x;
+    a.swap_in = dagger;
+    a.out = he;
+    Prof P(h, pname<R>("eo4d_dslash_eo"));
+    launch_dslash4<R>(a, h->axial, h->stream);
+  }
+  {
+    EoArgs<R> a = eo_args<R>(h, 1, nrhs);
+    a.in = he;
+    a.a = (R)(-1.0 / mu);
+    a.x1 = x;
+    a.b1 = (R)mu;
+    a.swap_out = dagger;
+    a.out = out;
+    a.norm2 = norm2;
+    if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nrhs * sizeof(double), h->stream));
+    Prof P(h, pname<R>("eo4d_dslash_oe_axpy"));
+    launch_dslash4<R>(a, h->axial, h->stream);
+  }
+}
+
+template <typename R>
+OpFn<R> eo4d_op(wf_handle* h, int nrhs) {
+  Cx<R>* he = h->buf<Cx<R>>(pname<R>("op_he"), eo_elems(h) * nrhs);
+  return [=](const Cx<R>* x, Cx<R>* y, int dagger, double* norm2) { eo4d_apply<R>(h, x, y, dagger, nrhs, he, norm2); };
+}
+
+std::vector<double> eo_norms(wf_handle* h, const Cx<double>* a, const Cx<double>* b, size_t n, int nrhs) {
+  double* sc = h->buf<double>("sv_scalars", 4 * (size_t)nrhs);
+  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
+  {
+    Prof P(h, "norm2_f64", 4);
+    launch_norm2<double>(a, n, nrhs, partial, sc, h->stream);
+    launch_norm2<double>(b, n, nrhs, partial, sc + nrhs, h->stream);
+  }
+  std::vector<double> v = read_scalars(h, sc, 2 * nrhs), out(nrhs);
+  for (int k = 0; k < nrhs; ++k) out[k] = v[k] + v[nrhs + k];
+  return out;
+}
+
+// Standard 4-D even-odd solve (§II.B, 4D-Schur): b_o = eta_o + mu^-1 D_w^oe eta_e, CGNR on
+// M-hat_4, psi_e = mu^-1 (eta_e + D_w^eo psi_o); true residual with M = mu - D_w.
+int solve_eo4d(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol, int precision,
+               bool x0, int* iters_out, double* resid_out) {
+  if (h->g.T % 2) throw Error(WF_EINVAL, "the 4-D even-odd method needs an even T");
+  const size_t n = eo_elems(h), nt = n * nrhs;
+  cudaStream_t s = h->stream;
+  const double mu = h->g.mu;
+  Cx<double>* eta_e = h->buf<Cx<double>>("eo_eta_e", nt);
+  Cx<double>* eta_o = h->buf<Cx<double>>("eo_eta_o", nt);
+  Cx<double>* b_o = h->buf<Cx<double>>("eo_b_o", nt);
+  Cx<double>* psi_e = h->buf<Cx<double>>("eo_psi_e", nt);
+  Cx<double>* psi_o = h->buf<Cx<double>>("eo_psi_o", nt);
+  Cx<double>* r_e = h->buf<Cx<double>>("eo_r_e", nt);
+  Cx<double>* r_o = h->buf<Cx<double>>("eo_r_o", nt);
+  {
+    Prof P(h, "import_eo_f64");
+    launch_import_eo<double>(h->g, eta_lex, eta_e, eta_o, nrhs, frame_rot(h, 0), frame_rot(h, 1), -1, s);
+  }
+  {
+    EoArgs<double> a = eo_args<double>(h, 1, nrhs);
+    a.in = eta_e;
+    a.a = 1.0 / mu;
+    a.x1 = eta_o;
+    a.b1 = 1.0;
+    a.out = b_o;
+    Prof P(h, "eo4d_prep_f64");
+    launch_dslash4<double>(a, h->axial, s);
+  }
+  if (x0) {
+    Prof P(h, "import_eo_f64");
+    launch_import_eo<double>(h->g, x_lex, r_e, psi_o, nrhs, frame_rot(h, 0), frame_rot(h, 1), -1, s);
+  }
+  std::vector<double> eta2 = eo_norms(h, eta_e, eta_o, n, nrhs), target(nrhs);
+  for (int k = 0; k < nrhs; ++k) target[k] = tol * std::sqrt(eta2[k]);  // |eta - M psi| = |b_o - M-hat_4 psi_o|
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> rel(nrhs, 0.0);
+  const int maxiter = 100000;
+  int status = WF_OK;
+  bool have_x0 = x0;
+  for (int pass = 0; pass < 6; ++pass) {
+    std::vector<int> it = precision == WF_FP32
+                              ? cgnr<float>(h, eo4d_op<float>(h, nrhs), eo4d_op<double>(h, nrhs), b_o, psi_o, nrhs, n,
+                                            target, maxiter, have_x0)
+                              : cgnr<double>(h, eo4d_op<double>(h, nrhs), eo4d_op<double>(h, nrhs), b_o, psi_o, nrhs,
+                                             n, target, maxiter, have_x0);
+    for (int k = 0; k < nrhs; ++k) iters[k] += it[k];
+    have_x0 = true;
+    {
+      EoArgs<double> a = eo_args<double>(h, 0, nrhs);  // psi_e = mu^-1 (eta_e + D_w^eo psi_o)
+      a.in = psi_o;
+      a.a = 1.0 / mu;
+      a.x1 = eta_e;
+      a.b1 = 1.0 / mu;
+      a.out = psi_e;
+      Prof P(h, "eo4d_recon_f64");
+      launch_dslash4<double>(a, h->axial, s);
+    }
+    for (int p = 0; p < 2; ++p) {  // r = eta - mu psi + D_w psi
+      EoArgs<double> a = eo_args<double>(h, p, nrhs);
+      a.in = p ? psi_e : psi_o;
+      a.a = 1.0;
+      a.x1 = p ? eta_o : eta_e;
+      a.b1 = 1.0;
+      a.x2 = p ? psi_o : psi_e;
+      a.b2 = -mu;
+      a.out = p ? r_o : r_e;
+      Prof P(h, "eo4d_residual_f64");
+      launch_dslash4<double>(a, h->axial, s);
+    }
+    std::vector<double> r2 = eo_norms(h, r_e, r_o, n, nrhs);
+    bool ok = true;
+    for (int k = 0; k < nrhs; ++k) {
+      rel[k] = std::sqrt(r2[k] / (eta2[k] > 0 ? eta2[k] : 1.0));
+      if (rel[k] > tol) {
+        ok = false;
+        target[k] *= 0.5 * tol / rel[k];
+      }
+      if (iters[k] >= maxiter) status = WF_ENOCONV;
+    }
+    if (ok || status == WF_ENOCONV) break;
+    if (pass == 5) status = WF_ENOCONV;
+  }
+  {
+    Prof P(h, "export_eo_f64");
+    launch_export_eo<double>(h->g, psi_e, psi_o, x_lex, nrhs, frame_rot(h, 0), frame_rot(h, 1), -1, s);
+  }
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters_out) iters_out[k] = iters[k];
+    if (resid_out) resid_out[k] = rel[k];
+  }
+  return status;
+}
+
+// Full-lattice operators (one right-hand side; a vector is [even half][odd half] of the line
+// layout): M (unpreconditioned) and M~ = C_L M C_R (temporal only, §II.A). Daggers use
+// gamma_5-hermiticity, M^dag = S M S and M~^dag = S M~ S with S the spin-half exchange.
+template <typename R>
+OpFn<R> full_op(wf_handle* h, bool temporal) {
+  const size_t hn = h->half_int();
+  Cx<R>* t1 = h->buf<Cx<R>>(pname<R>("op_t1"), 2 * hn);
+  Cx<R>* t2 = h->buf<Cx<R>>(pname<R>("op_t2"), 2 * hn);
+  double* partial = h->buf<double>("op_partial", 1024);
+  return [=](const Cx<R>* x, Cx<R>* y, int dagger, double* norm2) {
+    const int tp = h->g.tp;
+    auto mrun = [&](const Cx<R>* in, Cx<R>* out, int swap) {
+      Gauge<R> G = gauge_of<R>(h);
+      for (int p = 0; p < 2; ++p) {
+        MArgs<R> m;
+        std::memset(&m, 0, sizeof(m));
+        m.g = h->g;
+        m.parity = p;
+        m.nrhs = 1;
+        m.psi_p = in + p * hn;
+        m.psi_q = in + (1 - p) * hn;
+        m.ut = G.ut[p];
+        m.pl = G.pl[p];
+        m.us_out = G.us[p];
+        m.us_nbr = G.us[1 - p];
+        m.swap = swap;
+        m.out = out + p * hn;
+        m.mu = (R)h->g.mu;
+        m.inv_gf = (R)(1.0 / h->g.gamma_f);
+        m.bc = (R)h->g.bc;
+        Prof P(h, pname<R>("apply_M"));
+        launch_apply_M<R>(m, h->axial, h->stream);
+      }
+    };
+    if (!temporal) {
+      mrun(x, y, dagger);
+    } else {
+      // C_R (reading the halves exchanged for the dagger), M, C_L (writing them exchanged)
+      for (int p = 0; p < 2; ++p) {
+        LineArgs<R> a = line_args<R>(h, p, 1);
+        a.src_up = x + p * hn + (dagger ? 6 * tp : 0);
+        a.src_lo = x + p * hn + (dagger ? 0 : 6 * tp);
+        a.opu = OP_FWD;
+        a.opl = OP_COPY;
+        a.src = SRC_LOAD;
+        a.out = t1 + p * hn;
+        Prof P(h, pname<R>("c_right"));
+        launch_line<R>(a, LK_GENERIC, h->axial, h->stream);
+      }
+      mrun(t1, t2, 0);
+      for (int p = 0; p < 2; ++p) {
+        LineArgs<R> a = line_args<R>(h, p, 1);
+        a.src_up = t2 + p * hn;
+        a.src_lo = t2 + p * hn + 6 * tp;
+        a.opu = OP_COPY;
+        a.opl = OP_BWD;
+        a.src = SRC_LOAD;
+        a.swap_out = dagger;
+        a.out = y + p * hn;
+        Prof P(h, pname<R>("c_left"));
+        launch_line<R>(a, LK_GENERIC, h->axial, h->stream);
+      }
+    }
+    if (norm2) {
+      Prof P(h, pname<R>("norm2"), 2);
+      launch_norm2<R>(y, 2 * hn, 1, partial, norm2, h->stream);
+    }
+  };
+}
+
+// Unpreconditioned (CGNR on M) or temporal-only (CGNR on C_L M C_R, source C_L eta, solution
+// C_R y) solve, one right-hand side at a time.
+int solve_full(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol, int precision,
+               bool x0, bool temporal, int* iters_out, double* resid_out) {
+  const size_t hn = h->half_int(), le = h->lex_elems();
+  cudaStream_t s = h->stream;
+  Cx<double>* eta = h->buf<Cx<double>>("fu_eta", 2 * hn);
+  Cx<double>* b = h->buf<Cx<double>>("fu_b", 2 * hn);
+  Cx<double>* y = h->buf<Cx<double>>("fu_y", 2 * hn);
+  Cx<double>* psi = h->buf<Cx<double>>("fu_psi", 2 * hn);
+  Cx<double>* r = h->buf<Cx<double>>("fu_r", 2 * hn);
+  const double cl_bound = temporal ? 1.0 + h->g.mu : 1.0;  // |C_L^-1| <= 1 + mu
+  int status = WF_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    {
+      Prof P(h, "import_spinor_f64");
+      launch_import_spinor<double>(h->g, eta_lex + k * le, eta, eta + hn, 1, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+    }
+    if (temporal) {
+      line_load<double>(h, 0, eta, b, OP_COPY, OP_BWD, 1, "c_left");
+      line_load<double>(h, 1, eta + hn, b + hn, OP_COPY, OP_BWD, 1, "c_left");
+    } else {
+      WF_CUDA(cudaMemcpyAsync(b, eta, 2 * hn * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+    }
+    if (x0) {
+      Prof P(h, "import_spinor_f64");
+      launch_import_spinor<double>(h->g, x_lex + k * le, y, y + hn, 1, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+    }
+    std::vector<double> eta2 = eo_norms(h, eta, eta + hn, hn, 1);
+    std::vector<double> target{tol * std::sqrt(eta2[0]) / cl_bound};
+    int its = 0;
+    double rel = 0.0;
+    bool have_x0 = x0;
+    for (int pass = 0; pass < 6; ++pass) {
+      std::vector<int> it = precision == WF_FP32
+                                ? cgnr<float>(h, full_op<float>(h, temporal), full_op<double>(h, temporal), b, y, 1,
+                                              2 * hn, target, 100000, have_x0)
+                                : cgnr<double>(h, full_op<double>(h, temporal), full_op<double>(h, temporal), b, y, 1,
+                                               2 * hn, target, 100000, have_x0);
+      its += it[0];
+      have_x0 = true;
+      if (temporal) {
+        line_load<double>(h, 0, y, psi, OP_FWD, OP_COPY, 1, "c_right");
+        line_load<double>(h, 1, y + hn, psi + hn, OP_FWD, OP_COPY, 1, "c_right");
+      } else {
+        WF_CUDA(cudaMemcpyAsync(psi, y, 2 * hn * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+      }
+      m_apply<double>(h, psi, psi + hn, r, r + hn, eta, eta + hn, -1.0, 1);
+      std::vector<double> r2 = eo_norms(h, r, r + hn, hn, 1);
+      rel = std::sqrt(r2[0] / (eta2[0] > 0 ? eta2[0] : 1.0));
+      if (rel <= tol) break;
+      if (its >= 100000 || pass == 5) {
+        status = WF_ENOCONV;
+        break;
+      }
+      target[0] *= 0.5 * tol / rel;
+    }
+    {
+      Prof P(h, "export_spinor_f64");
+      launch_export_spinor<double>(h->g, psi, psi + hn, x_lex + k * le, 1, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+    }
+    if (iters_out) iters_out[k] = its;
+    if (resid_out) resid_out[k] = rel;
+  }
+  return status;
+}
+
+template <typename R>
+int apply_eo4d_abi(wf_handle* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  if (h->g.T % 2) throw Error(WF_EINVAL, "the 4-D even-odd operator needs an even T");
+  const size_t ce = (size_t)nrhs * h->g.L * h->g.L * h->g.L * h->g.T / 2 * NSPIN_C;
+  const size_t nt = eo_elems(h) * nrhs;
+  const Cx<double>* din = dev_in(h, in_odd, ce, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out_odd, ce, "stage_out", staged);
+  Cx<R>* x = h->buf<Cx<R>>(pname<R>("ap_x"), nt);
+  Cx<R>* o = h->buf<Cx<R>>(pname<R>("ap_o"), nt);
+  Cx<R>* he = h->buf<Cx<R>>(pname<R>("ap_y"), nt);
+  {
+    Prof P(h, pname<R>("import_eo"));
+    launch_import_eo<R>(h->g, din, nullptr, x, nrhs, frame_rot(h, 0), frame_rot(h, 1), 1, h->stream);
+  }
+  eo4d_apply<R>(h, x, o, dagger, nrhs, he, nullptr);
+  {
+    Prof P(h, pname<R>("export_eo"));
+    launch_export_eo<R>(h->g, nullptr, o, dout, nrhs, frame_rot(h, 0), frame_rot(h, 1), 1, h->stream);
+  }
+  finish_out(h, out_odd, dout, ce, staged);
+  return WF_OK;
 }
 
 template <typename R>
@@ -751,6 +1092,13 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
   return guarded(h, [&]() { return apply_schur_abi<float>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
 }
 
+int wf_apply_eo4d(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_eo4d_abi<double>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+int wf_apply_eo4d_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_eo4d_abi<float>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision, int flags,
              int* iters_out, double* true_resid_out) {
   return guarded(h, [&]() {
@@ -767,8 +1115,12 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     int st;
     if (method == WF_TEMPORAL_SCHUR)
       st = solve_temporal_schur(h, drhs, dx, nrhs, tol, precision, x0, iters_out, true_resid_out);
+    else if (method == WF_EO4D)
+      st = solve_eo4d(h, drhs, dx, nrhs, tol, precision, x0, iters_out, true_resid_out);
+    else if (method == WF_UNPREC || method == WF_TEMPORAL)
+      st = solve_full(h, drhs, dx, nrhs, tol, precision, x0, method == WF_TEMPORAL, iters_out, true_resid_out);
     else
-      throw Error(WF_EINVAL, "method not available");
+      throw Error(WF_EINVAL, "unknown method");
     finish_out(h, x, dx, le, staged);
     if (st == WF_ENOCONV) h->err = "solver did not reach tol";
     return st;

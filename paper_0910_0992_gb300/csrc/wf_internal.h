@@ -81,6 +81,7 @@ struct MArgs {
   const Cx<R>* us_nbr; // forward spatial links, other parity
   const Cx<R>* x;      // out = x + a * (M psi) if x != nullptr
   R a;
+  int swap;            // read psi and write the result with the spin halves exchanged (M^dag = S M S)
   Cx<R>* out;
   R mu, inv_gf, bc;
 };
@@ -124,5 +125,36 @@ template <typename R>
 void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s);      // y += x
 void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s);
+
+// 4-D even-odd comparator (wf_eo4d.cu)
+template <typename R>
+struct EoArgs {
+  Geom g;
+  int par;          // 4-D parity of the output sites
+  int nrhs;
+  const Cx<R>* in;  // field of the other parity, [rhs][L^3][12][T/2]
+  // out = a * D_w in + b1 * x1 + b2 * x2 (x1, x2 of the output parity; null = absent)
+  const Cx<R>* x1;
+  R b1;
+  const Cx<R>* x2;
+  R b2;
+  R a;
+  int swap_in, swap_out;  // read / write the P_+ and P_- spin halves exchanged (gamma_5 up to sign)
+  Cx<R>* out;
+  double* norm2;          // if set: atomically add |out|^2 per rhs
+  const Cx<R>* ut[2];     // general frame: U_t per 3-D parity, line layout
+  const Cx<R>* pl[2];     // axial frame: boundary link P per line
+  const Cx<R>* us[2];     // spatial forward links per 3-D parity, line layout
+  R inv_gf, bc;
+};
+template <typename R>
+void launch_dslash4(const EoArgs<R>& a, bool axial, cudaStream_t s);
+// compact_par < 0: full lexicographic fields; 0 / 1: arrays of the sites of that 4-D parity only
+template <typename R>
+void launch_import_eo(const Geom& g, const Cx<double>* lex, Cx<R>* even, Cx<R>* odd, int nrhs, const Cx<double>* g0,
+                      const Cx<double>* g1, int compact_par, cudaStream_t s);
+template <typename R>
+void launch_export_eo(const Geom& g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* lex, int nrhs,
+                      const Cx<double>* g0, const Cx<double>* g1, int compact_par, cudaStream_t s);
 
 }  // namespace wf

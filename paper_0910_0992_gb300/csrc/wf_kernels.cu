@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
   LineArgs<R> H;
   H.g = g;
   H.parity = A.parity;
-  H.src_up = A.psi_q;
-  H.src_lo = A.psi_q + 6 * tp;
+  H.src_up = A.psi_q + (A.swap ? 6 * tp : 0);
+  H.src_lo = A.psi_q + (A.swap ? 0 : 6 * tp);
   H.us_out = A.us_out;
   H.us_nbr = A.us_nbr;
   Vec3<R> h[NMAX][4];
@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
       const int slf = slot_of(g, tf), slb = slot_of(g, tb);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        Vec3<R> nb = ldvec(pp + 3 * s * tp, tp, s < 2 ? slb : slf);
+        const int sr = A.swap ? (s + 2) % 4 : s;  // spin read for result spin s
+        Vec3<R> nb = ldvec(pp + 3 * sr * tp, tp, s < 2 ? slb : slf);
         Vec3<R> dt;
         if (AX) {
           if (s < 2 && t == 0)
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
           dt = s < 2 ? matvec_dag(ldmat(ut_line, tp, slb), nb) : matvec(ldmat(ut_line, tp, sl), nb);
         }
         const R sg = s < 2 ? sb : sf;
-        Vec3<R> r = vscale(A.mu, ldvec(pp + 3 * s * tp, tp, sl));
+        Vec3<R> r = vscale(A.mu, ldvec(pp + 3 * sr * tp, tp, sl));
         r = vaxpy(-sg, dt, r);
         res[s] = vaxpy(-A.inv_gf, h[m][s], r);
       }
@@ -252,9 +253,10 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
+      const int so = A.swap ? (s + 2) % 4 : s;
       Vec3<R> val = res[s];
-      if (A.x) val = vaxpy(A.a, val, ldvec(A.x + base + 3 * s * tp, tp, sl));
-      stvec(A.out + base + 3 * s * tp, tp, sl, val);
+      if (A.x) val = vaxpy(A.a, val, ldvec(A.x + base + 3 * so * tp, tp, sl));
+      stvec(A.out + base + 3 * so * tp, tp, sl, val);
     }
   }
 }

@@ -145,3 +145,53 @@ def test_singular_preconditioner_is_reported(axial):
         w.load_gauge(S.unit_gauge(L, T))
     assert e.value.code == wf.WF_ESINGULAR
     w.close()
+
+
+def test_apply_eo4d(case):
+    """The 4-D even-odd comparator M-hat_4 (§II.B, 4D-Schur) against the oracle, odd 4-D sites."""
+    p, U, eta, w = case
+    if p.T % 2:
+        pytest.skip("the 4-D checkerboard needs an even T")
+    par4 = W.parity4(p.L, p.T)
+    odd = par4 == 1
+    xo = SV.compact(eta, odd)
+    full = SV.expand(xo, odd)
+    ref = SV.compact(W.M_hat4(U, full, p, par4), odd)
+    refd = SV.compact(W.M_hat4_dag(U, full, p, par4), odd)
+    x = _dev(xo)
+    assert _rel(_host(w.apply_eo4d(x)), ref) < 1e-12
+    assert _rel(_host(w.apply_eo4d(x, dagger=True)), refd) < 1e-12
+    assert _rel(_host(w.apply_eo4d(x, f32=True)), ref) < 1e-6
+
+
+@pytest.mark.parametrize("method", [wf.WF_EO4D, wf.WF_UNPREC, wf.WF_TEMPORAL])
+@pytest.mark.parametrize("precision", [wf.WF_FP64, wf.WF_FP32])
+def test_solve_comparators(case, method, precision):
+    """Every comparator method reaches the unique solution: FP64 true residual <= 1e-10, checked
+    with the oracle's M."""
+    p, U, eta, w = case
+    if method == wf.WF_EO4D and p.T % 2:
+        pytest.skip("the 4-D checkerboard needs an even T")
+    x, iters, res, status = w.solve(_dev(eta), tol=1e-10, method=method, precision=precision)
+    assert status == wf.WF_OK
+    assert all(r <= 1e-10 for r in res)
+    psi = _host(x)
+    for k in range(eta.shape[0]):
+        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+
+
+def test_fp64_iterations_match_oracle():
+    """FP64 CGNR on the GPU takes the oracle's iteration count for each method (same algorithm)."""
+    L, T = 4, 8
+    p = W.Params(L, T, 0.075, xi=3.5, bc=-1)
+    U = S.random_gauge(L, T, 0.3, 21)
+    eta = S.gaussian_source(L, T, 22)
+    w = wf.Wilson(L, T, 0.075, kappa_t=3.5 * 0.075, bc=-1)
+    w.load_gauge(U)
+    for method, name in [(wf.WF_UNPREC, "unprec"), (wf.WF_EO4D, "eo4d"), (wf.WF_TEMPORAL, "temporal"),
+                         (wf.WF_TEMPORAL_SCHUR, "temporal_schur")]:
+        _, it_ref, _ = SV.solve(U, eta, p, name, tol=1e-10)
+        _, iters, res, status = w.solve(_dev(eta[None]), tol=1e-10, method=method, precision=wf.WF_FP64)
+        assert status == wf.WF_OK
+        assert abs(iters[0] - it_ref) <= max(2, it_ref // 20), (name, iters[0], it_ref)
+    w.close()
