@@ -12,9 +12,11 @@ Modules:
   solve   -- CGNR and the four solve methods, FP64 true residual
   dense   -- dense matrices and singular values on tiny lattices
   flops   -- the paper's FLOP-count model (App. B, App. C)
+  force   -- pseudofermion action phi^dag (M-hat^dag M-hat)^-1 phi and its force dS/dU (FP64 adjoint
+             through the six factors of M-hat), pinned by central finite differences
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``
 except where its docstring says "parity unpinned".
 """
 
-from . import wilson, solve, dense, flops  # noqa: F401
+from . import wilson, solve, dense, flops, force  # noqa: F401
