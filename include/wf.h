@@ -158,6 +158,19 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
 #define WF_NOALLOC_SCRATCH_BYTES (16u << 20)
 int wf_apply_schur_noalloc(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
 
+/* Pseudofermion force of the temporally preconditioned operator. For the action
+ *   S = phi^dag (M-hat^dag M-hat)^-1 phi,   phi an odd field (as for wf_apply_schur, one source),
+ * writes F[t][z][y][x][mu][a] (real, 8 per link, mu = x, y, z, t) = dS/d eps for the perturbation
+ * U_mu(x) -> exp(i eps T_a) U_mu(x), T_a = lambda_a / 2 (the Gell-Mann matrices halved), in the
+ * caller's gauge. X = (M-hat^dag M-hat)^-1 phi by CG to |phi - M-hat^dag M-hat X| <= tol |phi|
+ * (precision: FP64, or FP32 iterations with FP64 reliable updates); then, with Y = M-hat X,
+ * dS = -2 Re(Y^dag dM-hat X) summed over the six factors of M-hat (§II.B), all in FP64. The
+ * paper proposes the HMC use of the preconditioner without working it out (§IV). action (host,
+ * may be null) receives S = |Y|^2; iters (host, may be null) the CG iterations. F may be host
+ * or device memory, or null to compute the action alone. */
+int wf_force(wf_handle_t* h, const double* phi_odd, double* F, int precision, double tol, double* action,
+             int* iters);
+
 /* Number of kernels this handle has launched since it was created (all entry points). */
 long long wf_launch_count(const wf_handle_t* h);
 

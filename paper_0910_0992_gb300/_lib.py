@@ -40,6 +40,7 @@ _SIGS = {
     "wf_apply_eo4d": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_eo4d_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
+    "wf_force": (_i, [_vp, _vp, _vp, _i, _d, _dp, _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_profile": (_i, [_vp, _i]),
     "wf_profile_get": (_i, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), _dp, _i]),
@@ -148,6 +149,26 @@ def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):
     if code not in (WF_OK, WF_ENOCONV):
         _check(h, code)
     return code, list(iters), list(res)
+
+
+def wf_force(h, phi_odd, F, precision=WF_FP64, tol=1e-12):
+    """Fills F (shape (..., 4, 8) float64) with dS/dU (F None: action only); returns (S, CG iterations)."""
+    import numpy as np
+    if F is None:
+        fp = None
+    elif hasattr(F, "data_ptr"):
+        import torch
+        if F.dtype != torch.float64 or not F.is_contiguous():
+            raise TypeError("F must be a contiguous float64 tensor")
+        fp = F.data_ptr()
+    else:
+        if not isinstance(F, np.ndarray) or F.dtype != np.float64 or not F.flags["C_CONTIGUOUS"]:
+            raise TypeError("F must be a C-contiguous float64 array")
+        fp = F.ctypes.data
+    S = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(h, lib.wf_force(h, _ptr(phi_odd), fp, int(precision), float(tol), ctypes.byref(S), ctypes.byref(it)))
+    return S.value, it.value
 
 
 def wf_launch_count(h):

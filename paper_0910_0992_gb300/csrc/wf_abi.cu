@@ -836,6 +836,202 @@ int solve_full(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
   return status;
 }
 
+// ----------------------------------------------------------------------------
+// Pseudofermion force (HMC use of the preconditioner, proposed in §IV)
+// ----------------------------------------------------------------------------
+
+// CG on the normal operator A^dag A x = b in precision R (FP64 reliable updates for R = float);
+// stops when |b - A^dag A x| <= tol |b|. One right-hand side. Returns the iterations.
+template <typename R>
+int cg_normal(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, const Cx<double>* b, Cx<double>* x, size_t n,
+              double tol, int maxiter) {
+  cudaStream_t s = h->stream;
+  double* sc = h->buf<double>("cn_scalars", 8);
+  double *rr = sc, *rrn = sc + 1, *tt = sc + 2, *b2 = sc + 3;
+  int* active = h->buf<int>("cg_active", 1);
+  double* partial = h->buf<double>("cg_partial", 1024);
+  const int one = 1;
+  WF_CUDA(cudaMemcpyAsync(active, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+  Cx<R>* r = h->buf<Cx<R>>(pname<R>("cn_r"), n);
+  Cx<R>* p = h->buf<Cx<R>>(pname<R>("cn_p"), n);
+  Cx<R>* t = h->buf<Cx<R>>(pname<R>("cn_t"), n);
+  Cx<R>* q = h->buf<Cx<R>>(pname<R>("cn_q"), n);
+  Cx<R>* xi = h->buf<Cx<R>>(pname<R>("cn_x"), n);
+  Cx<double>* r64 = h->buf<Cx<double>>("cn_r64", n);
+  Cx<double>* t64 = h->buf<Cx<double>>("cn_t64", n);
+  const bool mixed = sizeof(R) == 4;
+  WF_CUDA(cudaMemsetAsync(x, 0, n * sizeof(Cx<double>), s));
+  WF_CUDA(cudaMemsetAsync(xi, 0, n * sizeof(Cx<R>), s));
+  Cx<R>* xacc = mixed ? xi : reinterpret_cast<Cx<R>*>(x);
+  if (mixed) {
+    Prof P(h, "d2f");
+    launch_d2f(b, reinterpret_cast<Cx<float>*>(r), n, s);
+  } else {
+    WF_CUDA(cudaMemcpyAsync(r, b, n * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  }
+  WF_CUDA(cudaMemcpyAsync(p, r, n * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  {
+    Prof P(h, "norm2_f64", 2);
+    launch_norm2<double>(b, n, 1, partial, b2, s);
+  }
+  WF_CUDA(cudaMemcpyAsync(rr, b2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const double bn2 = read_scalars(h, b2, 1)[0];
+  const double target2 = tol * tol * bn2;
+  double rmax = std::sqrt(bn2);
+  double delta = 0.01;
+  if (const char* e = std::getenv("WF_RELIABLE_DELTA")) {
+    const double v = std::atof(e);
+    if (v > 0.0 && v < 1.0) delta = v;
+  }
+  int it = 0;
+  if (bn2 == 0.0) return 0;
+  for (; it < maxiter; ++it) {
+    A(p, t, 0, tt);       // t = A p, |t|^2 = <p, A^dag A p>
+    A(t, q, 1, nullptr);  // q = A^dag A p
+    {
+      Prof P(h, pname<R>("cg_xr"), 2);
+      launch_cg_xr<R>(xacc, r, p, q, n, 1, rr, tt, active, partial, rrn, s);
+    }
+    const double rn2 = read_scalars(h, rrn, 1)[0];
+    bool done = false;
+    if (mixed && (std::sqrt(rn2) < delta * rmax || rn2 <= target2)) {
+      {
+        Prof P(h, "add_f_to_d");
+        launch_add_f_to_d(x, reinterpret_cast<const Cx<float>*>(xi), n, s);
+      }
+      WF_CUDA(cudaMemsetAsync(xi, 0, n * sizeof(Cx<R>), s));
+      A64(x, t64, 0, nullptr);
+      A64(t64, r64, 1, nullptr);
+      {
+        Prof P(h, "axpby_f64");
+        launch_axpby<double>(r64, b, n, 1.0, -1.0, s);
+      }
+      {
+        Prof P(h, "norm2_f64", 2);
+        launch_norm2<double>(r64, n, 1, partial, rrn, s);
+      }
+      {
+        Prof P(h, "d2f");
+        launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), n, s);
+      }
+      const double t2 = read_scalars(h, rrn, 1)[0];
+      rmax = std::sqrt(t2);
+      done = t2 <= target2;
+    } else if (!mixed) {
+      done = rn2 <= target2;
+    }
+    if (done) {
+      ++it;
+      break;
+    }
+    {
+      Prof P(h, pname<R>("cg_p"));
+      launch_cg_p<R>(p, r, n, 1, rrn, rr, active, s);
+    }
+    {
+      Prof P(h, "copy_scalar");
+      launch_copy_scalar(rr, rrn, 1, s);
+    }
+  }
+  if (mixed) {
+    Prof P(h, "add_f_to_d");
+    launch_add_f_to_d(x, reinterpret_cast<const Cx<float>*>(xi), n, s);
+  }
+  return it;
+}
+
+int force_abi(wf_handle* h, const double* phi_odd, double* F, int precision, double tol, double* action,
+              int* iters_out) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
+  const Geom& g = h->g;
+  const size_t n = h->half_int();
+  const size_t V = (size_t)g.L * g.L * g.L * g.T;
+  const size_t ce = V / 2 * NSPIN_C;
+  cudaStream_t s = h->stream;
+  const Cx<double>* dphi = dev_in(h, phi_odd, ce, "stage_in");
+  const bool want_force = F != nullptr;  // null: the action only
+  const bool staged = want_force && !is_device_ptr(F);
+  double* dF = staged ? h->buf<double>("stage_force", V * 32) : F;
+  const char* nm[] = {"fo_phi", "fo_X", "fo_Y", "fo_v1", "fo_v2", "fo_v3", "fo_v4", "fo_v5", "fo_v6",
+                      "fo_w1", "fo_w2", "fo_w3", "fo_w4", "fo_w5", "fo_w6"};
+  Cx<double>* f[15];
+  for (int k = 0; k < 15; ++k) f[k] = h->buf<Cx<double>>(nm[k], n);
+  Cx<double>*phi = f[0], *X = f[1], *Y = f[2], *v1 = f[3], *v2 = f[4], *v3 = f[5], *v4 = f[6], *v5 = f[7],
+  *v6 = f[8], *w1 = f[9], *w2 = f[10], *w3 = f[11], *w4 = f[12], *w5 = f[13], *w6 = f[14];
+  {
+    Prof P(h, "import_compact_f64");
+    launch_import_compact<double>(g, dphi, phi, 1, 0, frame_rot(h, 1), s);
+  }
+  // X = (M-hat^dag M-hat)^-1 phi
+  int its = precision == WF_FP32 ? cg_normal<float>(h, schur_op<float>(h, 1), schur_op<double>(h, 1), phi, X, n, tol, 100000)
+                                 : cg_normal<double>(h, schur_op<double>(h, 1), schur_op<double>(h, 1), phi, X, n, tol, 100000);
+  if (iters_out) *iters_out = its;
+  // Y = M-hat X and S = phi^dag X = |Y|^2
+  double* sc = h->buf<double>("fo_scalars", 2);
+  schur_op<double>(h, 1)(X, Y, 0, sc);
+  const double S = read_scalars(h, sc, 1)[0];
+  if (action) *action = S;
+  if (!want_force) return WF_OK;
+  const int tp = g.tp;
+  auto line = [&](int par, const Cx<double>* in, Cx<double>* out, int opu, int opl) {
+    line_load<double>(h, par, in, out, opu, opl, 1, "force_chain_c");
+  };
+  auto hop = [&](int par_out, const Cx<double>* in, Cx<double>* out, bool adjoint) {
+    LineArgs<double> a = line_args<double>(h, par_out, 1);  // D_s^dag = S D_s S (gamma_5-hermiticity)
+    a.src_up = in + (adjoint ? 6 * tp : 0);
+    a.src_lo = in + (adjoint ? 0 : 6 * tp);
+    a.swap_out = adjoint ? 1 : 0;
+    a.opu = OP_COPY;
+    a.opl = OP_COPY;
+    a.src = SRC_HOP;
+    a.out = out;
+    Prof P(h, "force_chain_hop_f64");
+    launch_line<double>(a, LK_GENERIC, h->axial, s);
+  };
+  // right chain
+  line(1, X, v1, OP_FWD, OP_COPY);   // C_R^o
+  hop(0, v1, v2, false);             // D^eo
+  line(0, v2, v3, OP_COPY, OP_BWD);  // C_L^e
+  line(0, v3, v4, OP_FWD, OP_COPY);  // C_R^e
+  hop(1, v4, v5, false);             // D^oe
+  line(1, v5, v6, OP_COPY, OP_BWD);  // C_L^o
+  // left chain (adjoints): C_L^dag = P_+ + P_- T^-dag, C_R^dag = P_- + P_+ T^-1
+  line(1, Y, w1, OP_COPY, OP_FWD);
+  hop(0, w1, w2, true);
+  line(0, w2, w3, OP_BWD, OP_COPY);
+  line(0, w3, w4, OP_COPY, OP_FWD);
+  hop(1, w4, w5, true);
+  line(1, w5, w6, OP_BWD, OP_COPY);
+  Gauge<double> G = gauge_of<double>(h);
+  for (int p = 0; p < 2; ++p) {
+    ForceArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.parity = p;
+    a.axial = h->axial;
+    a.a = p ? w1 : w4;
+    a.b = p ? v6 : v3;
+    a.c = p ? w6 : w3;
+    a.e = p ? v1 : v4;
+    a.w = p ? w1 : w4;
+    a.v = p ? v4 : v1;
+    a.vr = p ? v1 : v4;
+    a.wr = p ? w4 : w1;
+    a.ut = G.ut[p];
+    a.pl = G.pl[p];
+    a.us_p = G.us[p];
+    a.coef = 2.0 / (g.gamma_f * g.gamma_f);
+    a.bc = g.bc;
+    a.F = dF;
+    Prof P(h, "force_outer_products_f64", 2);
+    launch_force(a, s);
+  }
+  if (staged) WF_CUDA(cudaMemcpyAsync(F, dF, V * 32 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  return WF_OK;
+}
+
 template <typename R>
 int apply_eo4d_abi(wf_handle* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
   if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
@@ -1090,6 +1286,14 @@ int wf_apply_schur(wf_handle_t* h, const double* in_odd, double* out_odd, int da
 }
 int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
   return guarded(h, [&]() { return apply_schur_abi<float>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+
+int wf_force(wf_handle_t* h, const double* phi_odd, double* F, int precision, double tol, double* action,
+             int* iters) {
+  return guarded(h, [&]() {
+    if (precision != WF_FP64 && precision != WF_FP32) throw Error(WF_EINVAL, "unknown precision");
+    return force_abi(h, phi_odd, F, precision, tol, action, iters);
+  });
 }
 
 int wf_apply_eo4d(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {

@@ -157,4 +157,29 @@ template <typename R>
 void launch_export_eo(const Geom& g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* lex, int nrhs,
                       const Cx<double>* g0, const Cx<double>* g1, int compact_par, cudaStream_t s);
 
+// pseudofermion force: link outer products (wf_force.cu)
+struct ForceArgs {
+  Geom g;
+  int parity;  // 3-D parity of the links' base sites
+  bool axial;
+  // temporal: C_L pair (a, b) and C_R pair (c, e), fields of this parity [Nl][12][tp]
+  const Cx<double>* a;
+  const Cx<double>* b;
+  const Cx<double>* c;
+  const Cx<double>* e;
+  // spatial: Q uses w (this parity) and v (other parity, at x + k); R uses vr (this parity)
+  // and wr (other parity, at x + k)
+  const Cx<double>* w;
+  const Cx<double>* v;
+  const Cx<double>* vr;
+  const Cx<double>* wr;
+  const Cx<double>* ut;      // general frame: U_t [Nl][9][tp]; axial frame: rotation g
+  const Cx<double>* pl;      // axial frame: P per line
+  const Cx<double>* us_p;    // spatial links of this parity (frame of the solve)
+  double coef;               // 2 / gamma_f^2
+  double bc;
+  double* F;                 // [V][4][8], caller's gauge
+};
+void launch_force(const ForceArgs& a, cudaStream_t s);
+
 }  // namespace wf
