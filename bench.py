@@ -33,32 +33,46 @@ sys.path.insert(0, ROOT)
 METRIC = "precond Wilson apply HBM GB/s & %roofline; time-to-solve 1e-10, 24^3x128 ξ=3.5"
 WORKLOAD = "wilson_24c128_xi3.5"
 
-# Algorithmic bytes per odd site of one M-hat apply, by kernel, FP32 storage
-# (complex = 8 B; half spinor 48 B, full spinor 96 B, SU(3) link 72 B), in the axial frame
-# the library works in by default (U_t = 1 on the line, so no U_t is read; the per-line P and
-# Lambda add 144 B per 128 sites and are left out):
-#   K-a  y = C_R^o x               : x upper half in, y upper half out             = 48 + 48
-#   K-b  z = C_R^e C_L^e D_s^eo y   : neighbour spinor (read once), 6 spatial links, z out
-#                                                                                  = 96 + 432 + 96
-#   K-c  out = x - C_L^o D_s^oe z   : neighbour z, 6 links, x, out                  = 96 + 432 + 96 + 96
-# FP64 storage doubles every figure. (Caller's-gauge frame: + 72 B of U_t in each kernel.)
+# Algorithmic bytes per odd site of one M-hat apply, by kernel, in the axial frame the
+# library works in by default (U_t = 1 on the line, so no U_t is read; the per-line P and
+# Lambda add 144 B per 128 sites and are left out). FP32 storage: complex 8 B, half spinor
+# 48 B, spinor 96 B, spatial link 48 B (two rows, the third rebuilt from SU(3)); FP64 storage:
+# complex 16 B, spatial link 144 B (nine entries).
+#   K-a  y = C_R^o x               : x upper half in, y upper half out                  (spinor 96)
+#   K-b  z = C_R^e C_L^e D_s^eo y   : neighbour spinor (read once), z out; 6 spatial links (192; links)
+#   K-c  out = x - C_L^o D_s^oe z   : neighbour z, x, out; 6 spatial links                (288; links)
 # With several right-hand sides the nrhs warps of a line run together and read its links
 # once (through L2), so a launch moves  odd_sites * (nrhs * spinor bytes + link bytes).
-KERNEL_BYTES_F32 = {"schur_a_tdag": (96, 0), "schur_b_hop_tsolve": (192, 432), "schur_c_hop_tinv_axpy": (288, 432)}
-APPLY_BYTES_F32 = sum(a + b for a, b in KERNEL_BYTES_F32.values())  # 1440 B per odd site, one source
+KERNEL_SPINOR_BYTES_F32 = {"schur_a_tdag": 96, "schur_b_hop_tsolve": 192, "schur_c_hop_tinv_axpy": 288}
+KERNEL_LINKS = {"schur_a_tdag": 0, "schur_b_hop_tsolve": 6, "schur_c_hop_tinv_axpy": 6}
+# The 4-D even-odd comparator per odd 4-D site (axial frame: temporal hops read no link):
+#   dslash_eo: other-parity spinor (read once) + out; dslash_oe_axpy: + x. 6 spatial links each.
+EO4D_SPINOR_BYTES_F32 = {"eo4d_dslash_eo": 192, "eo4d_dslash_oe_axpy": 288}
+LINK_BYTES = {"_f32": 48, "_f64": 144}
+APPLY_BYTES_F32 = sum(KERNEL_SPINOR_BYTES_F32.values()) + 12 * LINK_BYTES["_f32"]  # 1152 B per odd site
 
 
 def launch_bytes(name, odd_sites, nrhs):
     """Algorithmic bytes of one launch of a Schur kernel over nrhs sources, or None."""
-    for base, (spinor, links) in KERNEL_BYTES_F32.items():
+    for base, spinor in KERNEL_SPINOR_BYTES_F32.items():
         for suffix, scale in (("_f32", 1), ("_f64", 2)):
             if name == base + suffix:
-                return scale * odd_sites * (nrhs * spinor + links)
+                return odd_sites * (nrhs * scale * spinor + KERNEL_LINKS[base] * LINK_BYTES[suffix])
+    return None
+
+
+def eo4d_launch_bytes(name, odd_sites, nrhs):
+    for base, spinor in EO4D_SPINOR_BYTES_F32.items():
+        for suffix, scale in (("_f32", 1), ("_f64", 2)):
+            if name == base + suffix:
+                return odd_sites * (nrhs * scale * spinor + 6 * LINK_BYTES[suffix])
     return None
 
 
 def apply_bytes(odd_sites, nrhs, scale=1):
-    return scale * odd_sites * sum(nrhs * a + b for a, b in KERNEL_BYTES_F32.values())
+    """Algorithmic bytes of one M-hat apply over nrhs sources (scale 2: FP64)."""
+    suffix = "_f32" if scale == 1 else "_f64"
+    return sum(launch_bytes(k + suffix, odd_sites, nrhs) for k in KERNEL_SPINOR_BYTES_F32)
 
 
 def paper_flops_per_apply(L, T):
@@ -387,16 +401,17 @@ def run_apply(args, prm, U, eta):
     nr = args.nrhs
     x = torch.from_numpy(S.gaussian_source(prm["L"], prm["T"], 77).reshape(-1)[:half].copy()).cuda().repeat(nr)
     out = torch.empty_like(x)
+    apply = wf.wf_apply_eo4d_f32 if args.op == "eo4d" else wf.wf_apply_schur_f32
     for _ in range(args.warmup):
-        wf.wf_apply_schur_f32(w.h, x, out, 0, nr)
+        apply(w.h, x, out, 0, nr)
     wf.wf_profile(w.h, 1)
     for _ in range(args.steps):
-        wf.wf_apply_schur_f32(w.h, x, out, 0, nr)
+        apply(w.h, x, out, 0, nr)
     prof = wf.wf_profile_get(w.h)
     odd_sites = prm["L"] ** 3 * prm["T"] // 2
     rows = {}
     for k, (n, ms) in prof.items():
-        b = launch_bytes(k, odd_sites, nr)
+        b = launch_bytes(k, odd_sites, nr) or eo4d_launch_bytes(k, odd_sites, nr)
         rows[k] = {"launches": n, "avg_ms": ms / n, "gbs": (b / (ms / n * 1e-3) / 1e9) if b else None}
     print(json.dumps({"mode": "apply", "workload": WORKLOAD, "nrhs": nr, "kernels": rows}))
     w.close()
@@ -417,6 +432,7 @@ def main():
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
                     help="apply: only FP32 M-hat applies (for kernel profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")
+    ap.add_argument("--op", choices=["schur", "eo4d"], default="schur", help="operator of --mode apply")
     args = ap.parse_args()
 
     import synthetic as S

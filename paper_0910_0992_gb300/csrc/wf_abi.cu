@@ -369,7 +369,7 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
 
   // reliable-update trigger: the FP32 residual has dropped by this factor since the last
   // FP64 recomputation (environment WF_RELIABLE_DELTA overrides)
-  double delta = 0.01;
+  double delta = 1e-4;
   if (const char* e = std::getenv("WF_RELIABLE_DELTA")) {
     const double v = std::atof(e);
     if (v > 0.0 && v < 1.0) delta = v;
@@ -878,7 +878,7 @@ int cg_normal(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, const Cx<
   const double bn2 = read_scalars(h, b2, 1)[0];
   const double target2 = tol * tol * bn2;
   double rmax = std::sqrt(bn2);
-  double delta = 0.01;
+  double delta = 1e-4;
   if (const char* e = std::getenv("WF_RELIABLE_DELTA")) {
     const double v = std::atof(e);
     if (v > 0.0 && v < 1.0) delta = v;
@@ -1204,6 +1204,7 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
     const size_t V = (size_t)g.L * g.L * g.L * g.T;
     const Cx<double>* dU = dev_in(h, U, V * 36, "stage_gauge");
     const size_t nut = (size_t)g.Nl * 9 * g.tp, nus = 3 * nut, nlam = (size_t)g.Nl * 9;
+    const size_t nus32 = (size_t)3 * g.Nl * SpatialLinkNC<float>::value * g.tp;
     cudaStream_t s = h->stream;
     for (int p = 0; p < 2; ++p) {
       h->ut64[p].ensure(nut * sizeof(Cx<double>), s);
@@ -1211,7 +1212,7 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
       h->lamb64[p].ensure(nlam * sizeof(Cx<double>), s);
       h->lamf64[p].ensure(nlam * sizeof(Cx<double>), s);
       if (!h->axial) h->ut32[p].ensure(nut * sizeof(Cx<float>), s);
-      h->us32[p].ensure(nus * sizeof(Cx<float>), s);
+      h->us32[p].ensure(nus32 * sizeof(Cx<float>), s);
       h->lamb32[p].ensure(nlam * sizeof(Cx<float>), s);
       h->lamf32[p].ensure(nlam * sizeof(Cx<float>), s);
     }
@@ -1231,7 +1232,7 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
       const Cx<double>* gg[2] = {ut[0], ut[1]};
       launch_rotate_links(g, us, gg, s);
       for (int p = 0; p < 2; ++p) {
-        launch_d2f(us[p], h->us32[p].as<Cx<float>>(), nus, s);
+        launch_d2f_links(us[p], h->us32[p].as<Cx<float>>(), (size_t)3 * g.Nl, g.tp, s);
         launch_d2f(h->pl64[p].as<Cx<double>>(), h->pl32[p].as<Cx<float>>(), nlam, s);
         launch_d2f(h->lamb64[p].as<Cx<double>>(), h->lamb32[p].as<Cx<float>>(), nlam, s);
       }
@@ -1239,7 +1240,7 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
       for (int p = 0; p < 2; ++p) {
         launch_tline_init(g, ut[p], h->lamb64[p].as<Cx<double>>(), h->lamf64[p].as<Cx<double>>(), h->iflag.as<int>(), s);
         launch_d2f(ut[p], h->ut32[p].as<Cx<float>>(), nut, s);
-        launch_d2f(us[p], h->us32[p].as<Cx<float>>(), nus, s);
+        launch_d2f_links(us[p], h->us32[p].as<Cx<float>>(), (size_t)3 * g.Nl, g.tp, s);
         launch_d2f(h->lamb64[p].as<Cx<double>>(), h->lamb32[p].as<Cx<float>>(), nlam, s);
         launch_d2f(h->lamf64[p].as<Cx<double>>(), h->lamf32[p].as<Cx<float>>(), nlam, s);
       }

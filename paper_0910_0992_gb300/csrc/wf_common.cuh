@@ -205,4 +205,16 @@ __host__ __device__ __forceinline__ void neighbour_lines(const Geom& g, int p, i
 constexpr int NSPIN_C = 12;
 constexpr int NLINK_C = 9;
 
+// Spatial links are stored with 9 complex entries in FP64 and with their first two rows only
+// (6 entries) in FP32: for an SU(3) matrix the third row is the complex conjugate of the cross
+// product of the first two, so the FP32 kernels rebuild it instead of reading it.
+template <typename R>
+struct SpatialLinkNC {
+  static constexpr int value = 9;
+};
+template <>
+struct SpatialLinkNC<float> {
+  static constexpr int value = 6;
+};
+
 }  // namespace wf

@@ -16,12 +16,17 @@
 namespace wf {
 
 constexpr int kEoThreads = 128;
+// resident CTAs per SM the dslash is compiled for (4: 128 registers; measured on GB300 1.36x
+// faster than 1, and ahead of 6 and 8, which spill)
+#ifndef WF_EO_MINB
+#define WF_EO_MINB 4
+#endif
 
 
 __device__ __forceinline__ int eo_t0(int par, int x, int y, int z) { return (par + x + y + z) & 1; }
 
 template <typename R, bool AX>
-__global__ void __launch_bounds__(kEoThreads) k_dslash4(const EoArgs<R> A) {
+__global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs<R> A) {
   const Geom& g = A.g;
   const int Th = g.T / 2;
   const int L = g.L;
@@ -60,9 +65,10 @@ __global__ void __launch_bounds__(kEoThreads) k_dslash4(const EoArgs<R> A) {
       const Cx<R>* nb = A.in + ((size_t)rhs * V3 + s3n) * fstride;
       Vec3<R> u0 = ldvec(nb + cu * Th, Th, h), u1 = ldvec(nb + (cu + 3) * Th, Th, h);
       Vec3<R> d0 = ldvec(nb + cl * Th, Th, h), d1 = ldvec(nb + (cl + 3) * Th, Th, h);
-      const Cx<R>* lk = dir == 0 ? A.us[p3] + ((size_t)k * g.Nl + l) * NLINK_C * tp
-                                 : A.us[1 - p3] + ((size_t)k * g.Nl + line_of(g, nbx[d], nby[d], nbz[d])) * NLINK_C * tp;
-      const Mat3<R> U = ldmat(lk, tp, sl);
+      constexpr int LNC = SpatialLinkNC<R>::value;
+      const Cx<R>* lk = dir == 0 ? A.us[p3] + ((size_t)k * g.Nl + l) * LNC * tp
+                                 : A.us[1 - p3] + ((size_t)k * g.Nl + line_of(g, nbx[d], nby[d], nbz[d])) * LNC * tp;
+      const Mat3<R> U = ldlink(lk, tp, sl);
       Vec3<R> s0, s1;
       isigma(k, d0, d1, s0, s1);
       Vec3<R> h0, h1;

@@ -110,6 +110,8 @@ void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<d
                         cudaStream_t s);
 void launch_rotate_links(const Geom& g, Cx<double>* us[2], const Cx<double>* gg[2], cudaStream_t s);
 void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s);
+// FP32 copy of spatial links in their two-row storage (nlinks = 3 Nl per parity)
+void launch_d2f_links(const Cx<double>* in, Cx<float>* out, size_t nlinks, int tp, cudaStream_t s);
 void launch_f2d(const Cx<float>* in, Cx<double>* out, size_t n, cudaStream_t s);
 
 // BLAS-1 on flat [nrhs][n] arrays; scalars live in device memory

@@ -45,7 +45,7 @@ struct LineArgs {
   const Cx<R>* src_lo;
   // links: U_t of the output parity [Nl][9][tp] (general frame), the per-line boundary
   // link P [Nl][9] (axial frame), forward spatial links of the output parity and of the
-  // neighbour parity, each [3][Nl][9][tp]
+  // neighbour parity, each [3][Nl][SpatialLinkNC][tp]
   const Cx<R>* ut;
   const Cx<R>* pl;
   const Cx<R>* us_out;
@@ -69,6 +69,25 @@ __device__ __forceinline__ Mat3<R> ldmat(const Cx<R>* __restrict__ base, int tp,
   Mat3<R> U;
 #pragma unroll
   for (int k = 0; k < 9; ++k) U.e[k] = base[k * tp + slot];
+  return U;
+}
+
+// a spatial link in its storage form (see SpatialLinkNC): 9 entries, or 2 rows and the
+// third rebuilt as conj(row0 x row1)
+template <typename R>
+__device__ __forceinline__ Mat3<R> ldlink(const Cx<R>* __restrict__ base, int tp, int slot) {
+  if (SpatialLinkNC<R>::value == 9) return ldmat(base, tp, slot);
+  Mat3<R> U;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) U.e[k] = base[k * tp + slot];
+  const Cx<R>* a = U.e;
+  const Cx<R>* b = U.e + 3;
+  const Cx<R> c0 = cmul(a[1], b[2]) - cmul(a[2], b[1]);
+  const Cx<R> c1 = cmul(a[2], b[0]) - cmul(a[0], b[2]);
+  const Cx<R> c2 = cmul(a[0], b[1]) - cmul(a[1], b[0]);
+  U.e[6] = mk<R>(c0.re, -c0.im);
+  U.e[7] = mk<R>(c1.re, -c1.im);
+  U.e[8] = mk<R>(c2.re, -c2.im);
   return U;
 }
 
@@ -359,15 +378,16 @@ __device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArg
       const int ln = nb[2 * k + dir];
       const Cx<R>* up = A.src_up + (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
       const Cx<R>* lo = A.src_lo + (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
-      const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * NLINK_C * tp
-                                 : A.us_nbr + (size_t)(k * Nl + ln) * NLINK_C * tp;
+      constexpr int LNC = SpatialLinkNC<R>::value;
+      const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * LNC * tp
+                                 : A.us_nbr + (size_t)(k * Nl + ln) * LNC * tp;
 #pragma unroll
       for (int m = 0; m < NMAX; ++m) {
         if (m >= n || jj * n + m >= T) continue;
         const int sl = m * g.lpl + jj;
         Vec3<R> u0 = ldvec(up, tp, sl), u1 = ldvec(up + 3 * tp, tp, sl);
         Vec3<R> d0 = ldvec(lo, tp, sl), d1 = ldvec(lo + 3 * tp, tp, sl);
-        Mat3<R> U = ldmat(lk, tp, sl);
+        Mat3<R> U = ldlink(lk, tp, sl);
         Vec3<R> s0, s1;
         isigma(k, d0, d1, s0, s1);
         const R half = R(0.5);
