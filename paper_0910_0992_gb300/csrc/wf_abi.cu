@@ -72,9 +72,22 @@ Cx<double>* dev_out(wf_handle* h, double* p, size_t elems, const char* name, boo
   if (!staged) return reinterpret_cast<Cx<double>*>(p);
   return h->buf<Cx<double>>(name, elems);
 }
+// a bounded wait in a TMA-fed kernel ran out: report it (the kernels returned without result)
+void check_device_error(wf_handle* h) {
+  if (!h->tma_err.p) return;
+  int e = 0;
+  WF_CUDA(cudaMemcpyAsync(&e, h->tma_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  WF_CUDA(cudaStreamSynchronize(h->stream));
+  if (e) {
+    WF_CUDA(cudaMemsetAsync(h->tma_err.p, 0, sizeof(int), h->stream));
+    throw Error(WF_ETIMEOUT, "a bounded wait for a bulk copy expired in a TMA-fed kernel");
+  }
+}
+
 void finish_out(wf_handle* h, double* p, const Cx<double>* d, size_t elems, bool staged) {
   if (staged) WF_CUDA(cudaMemcpyAsync(p, d, elems * sizeof(Cx<double>), cudaMemcpyDeviceToHost, h->stream));
   WF_CUDA(cudaStreamSynchronize(h->stream));
+  check_device_error(h);
 }
 
 // ----------------------------------------------------------------------------
@@ -133,6 +146,7 @@ LineArgs<R> line_args(wf_handle* h, int parity, int nrhs) {
   a.bc = (R)h->g.bc;
   a.opu = OP_COPY;
   a.opl = OP_COPY;
+  a.drop_job = -1;
   return a;
 }
 
@@ -175,6 +189,33 @@ void line_load(wf_handle* h, int parity, const Cx<R>* in, Cx<R>* out, int opu, i
 //   K-a  y = C_R^o x                        (T^-dag on the upper half only)
 //   K-b  z = C_R^e C_L^e D_s^eo y           (hop, then T^-dag upper / T^-1 lower)
 //   K-c  out = x - gamma_f^-2 C_L^o D_s^oe z (hop, T^-1 lower, axpy)
+// the TMA-fed hop kernels (wf_tma.cu) can serve FP32 in the axial frame with 32 lanes per
+// line; they are opt-in (environment WF_TMA=1): on GB300 they measured 1.4-1.8x slower than
+// the register-fed line kernel, which keeps twice as many warps resident per SM
+template <typename R>
+bool use_tma_kernels(wf_handle* h) {
+  if (sizeof(R) != 4 || !h->axial || !tma_supported(h->g)) return false;
+  if (h->use_tma < 0) {
+    const char* e = std::getenv("WF_TMA");
+    h->use_tma = (e && e[0] == '1') ? 1 : 0;
+  }
+  if (h->use_tma && !h->tma_err.p) h->tma_err.ensure(sizeof(int), h->stream);
+  return h->use_tma != 0;
+}
+
+template <typename R>
+void launch_schur_hop(wf_handle* h, const LineArgs<R>& a, int kind, bool tma) {
+  if constexpr (sizeof(R) == 4) {
+    if (tma) {
+      LineArgs<R> b = a;
+      if (const char* e = std::getenv("WF_TEST_DROP_COPY")) b.drop_job = std::atoi(e);  // fault injection (tests)
+      launch_line_tma(b, kind, h->tma_err.as<int>(), h->stream);
+      return;
+    }
+  }
+  launch_line<R>(a, kind, h->axial, h->stream);
+}
+
 }  // namespace
 
 namespace wf {
@@ -192,6 +233,7 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     Prof P(h, pname<R>("schur_a_tdag"));
     launch_line<R>(a, LK_SCHUR_A, h->axial, h->stream);
   }
+  const bool tma = use_tma_kernels<R>(h);
   {
     LineArgs<R> a = line_args<R>(h, 0, nrhs);
     a.src_up = y;
@@ -200,7 +242,7 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     a.opl = OP_BWD;
     a.out = z;
     Prof P(h, pname<R>("schur_b_hop_tsolve"));
-    launch_line<R>(a, LK_SCHUR_B, h->axial, h->stream);
+    launch_schur_hop<R>(h, a, LK_SCHUR_B, tma);
   }
   {
     LineArgs<R> a = line_args<R>(h, 1, nrhs);
@@ -215,7 +257,7 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     a.norm2 = norm2;
     if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nrhs * sizeof(double), h->stream));
     Prof P(h, pname<R>("schur_c_hop_tinv_axpy"));
-    launch_line<R>(a, LK_SCHUR_C, h->axial, h->stream);
+    launch_schur_hop<R>(h, a, LK_SCHUR_C, tma);
   }
 }
 template void schur_apply<float>(wf_handle*, const Cx<float>*, Cx<float>*, int, int, Cx<float>*, Cx<float>*,
@@ -295,6 +337,7 @@ std::vector<double> read_scalars(wf_handle* h, const double* d, int n) {
   WF_CUDA(cudaMemcpyAsync(h->host_scalars, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   WF_CUDA(cudaStreamSynchronize(h->stream));
   std::memcpy(v.data(), h->host_scalars, n * sizeof(double));
+  check_device_error(h);
   for (double x : v)
     if (!std::isfinite(x)) throw Error(WF_ENAN, "NaN or Inf in a solver norm");
   return v;

@@ -30,6 +30,8 @@ struct wf_handle {
   wf::DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];
   // axial frame: ut64 holds the rotation g(x) instead of U_t; P per line
   wf::DevBuf pl64[2], pl32[2];
+  wf::DevBuf tma_err;  // error word of the TMA-fed kernels (bounded waits)
+  int use_tma = -1;    // -1: not decided yet (environment WF_TMA=1 turns the TMA-fed hop kernels on)
   wf::DevBuf iflag;
   std::map<std::string, std::unique_ptr<wf::DevBuf>> ws;  // named work buffers
   // profiling

@@ -68,6 +68,10 @@ enum LineKind { LK_GENERIC = 0, LK_SCHUR_A = 1, LK_SCHUR_B = 2, LK_SCHUR_C = 3 }
 template <typename R>
 void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s);
 
+// TMA-fed FP32 axial variant of the Schur hop kernels (wf_tma.cu); err: device error word
+bool tma_supported(const Geom& g);
+void launch_line_tma(const LineArgs<float>& a, int kind, int* err, cudaStream_t s);
+
 template <typename R>
 struct MArgs {
   Geom g;

@@ -62,6 +62,7 @@ struct LineArgs {
   Cx<R>* out;    // [nrhs][Nl][12][tp]
   double* norm2; // if set: atomically add |stored result|^2 per rhs (FP64)
   R inv_mu, bc;
+  int drop_job;  // TMA-fed kernel only: skip the bulk copy of this job (fault injection), -1: none
 };
 
 template <typename R>
