@@ -413,7 +413,7 @@ def run_apply(args, prm, U, eta):
     for k, (n, ms) in prof.items():
         b = launch_bytes(k, odd_sites, nr) or eo4d_launch_bytes(k, odd_sites, nr)
         rows[k] = {"launches": n, "avg_ms": ms / n, "gbs": (b / (ms / n * 1e-3) / 1e9) if b else None}
-    print(json.dumps({"mode": "apply", "workload": WORKLOAD, "nrhs": nr, "kernels": rows}))
+    print(json.dumps({"mode": "apply", "workload": f"{prm['L']}^3x{prm['T']}", "nrhs": nr, "kernels": rows}))
     w.close()
     return 0
 
@@ -433,14 +433,20 @@ def main():
                     help="apply: only FP32 M-hat applies (for kernel profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")
     ap.add_argument("--op", choices=["schur", "eo4d"], default="schur", help="operator of --mode apply")
+    ap.add_argument("--workload", default=None, help="--mode apply only: another synthetic workload by name")
     args = ap.parse_args()
 
     import synthetic as S
 
-    prm = dict(S.WORKLOADS[WORKLOAD])
+    name = WORKLOAD
+    if args.workload:
+        if args.mode != "apply" or args.workload not in S.WORKLOADS:
+            ap.error("--workload needs --mode apply and a known workload name")
+        name = args.workload
+    prm = dict(S.WORKLOADS[name])
     if args.impl == "reference":
         return run_reference(args, prm)
-    _, U, eta = S.workload(WORKLOAD, with_sources=args.mode == "solve")
+    _, U, eta = S.workload(name, with_sources=args.mode == "solve")
     if args.mode == "apply":
         return run_apply(args, prm, U, eta)
     return run_ours(args, prm, U, eta)

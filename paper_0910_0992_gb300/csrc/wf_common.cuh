@@ -169,6 +169,7 @@ struct Geom {
   int lpl;      // lanes per line (power of two, <= 32)
   int tp;       // padded line length n * lpl
   int lpw;      // lines per warp: 32 / lpl
+  int by;       // y rows per traversal tile of the line kernels (a divisor of L)
   double mu;    // 1 / (2 kappa_t)
   double gamma_f;
   double bc;    // +1 periodic, -1 antiperiodic in time

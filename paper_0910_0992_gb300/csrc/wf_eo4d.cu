@@ -138,9 +138,12 @@ __global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs
     for (int s = 0; s < 4; ++s) {
       const int so = A.swap_out ? (s + 2) % 4 : s;  // result spin s goes to slot so
       Vec3<R> val = vscale(A.a, acc[s]);
-      if (A.x1) val = vaxpy(A.b1, ldvec(A.x1 + ((size_t)rhs * V3 + s3) * fstride + so * 3 * Th, Th, h), val);
-      if (A.x2) val = vaxpy(A.b2, ldvec(A.x2 + ((size_t)rhs * V3 + s3) * fstride + so * 3 * Th, Th, h), val);
-      stvec(o + so * 3 * Th, Th, h, val);
+      if (A.x1) val = vaxpy(A.b1, ldvec_stream(A.x1 + ((size_t)rhs * V3 + s3) * fstride + so * 3 * Th, Th, h), val);
+      if (A.x2) val = vaxpy(A.b2, ldvec_stream(A.x2 + ((size_t)rhs * V3 + s3) * fstride + so * 3 * Th, Th, h), val);
+      if (A.stream_out)
+        stvec_stream(o + so * 3 * Th, Th, h, val);
+      else
+        stvec(o + so * 3 * Th, Th, h, val);
       if (A.norm2) nrm += vnorm2(val);
     }
   }

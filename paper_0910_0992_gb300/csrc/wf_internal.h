@@ -68,6 +68,11 @@ enum LineKind { LK_GENERIC = 0, LK_SCHUR_A = 1, LK_SCHUR_B = 2, LK_SCHUR_C = 3 }
 template <typename R>
 void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s);
 
+// axial-frame line kernels with one thread per time site (wf_wide.cu), same arguments
+bool wide_supported(const Geom& g);
+template <typename R>
+void launch_line_wide(const LineArgs<R>& a, int kind, cudaStream_t s);
+
 // TMA-fed FP32 axial variant of the Schur hop kernels (wf_tma.cu); err: device error word
 bool tma_supported(const Geom& g);
 void launch_line_tma(const LineArgs<float>& a, int kind, int* err, cudaStream_t s);
@@ -110,8 +115,8 @@ void launch_import_gauge(const Geom& g, const Cx<double>* lex, Cx<double>* ut[2]
                          cudaStream_t s);
 void launch_tline_init(const Geom& g, const Cx<double>* ut, Cx<double>* lamb, Cx<double>* lamf, int* singular,
                        cudaStream_t s);
-void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, int* singular,
-                        cudaStream_t s);
+void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, Cx<double>* wrap,
+                        int* singular, cudaStream_t s);
 void launch_rotate_links(const Geom& g, Cx<double>* us[2], const Cx<double>* gg[2], cudaStream_t s);
 void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s);
 // FP32 copy of spatial links in their two-row storage (nlinks = 3 Nl per parity)
@@ -146,6 +151,7 @@ struct EoArgs {
   R b2;
   R a;
   int swap_in, swap_out;  // read / write the P_+ and P_- spin halves exchanged (gamma_5 up to sign)
+  int stream_out;         // store with the evict-first cache policy (the result is not read again soon)
   Cx<R>* out;
   double* norm2;          // if set: atomically add |out|^2 per rhs
   const Cx<R>* ut[2];     // general frame: U_t per 3-D parity, line layout

@@ -11,6 +11,8 @@
 // kernels of the Schur operator are compiled with their source and solve ops fixed, so
 // each carries only its own code; every other use goes through one kernel that selects
 // them at run time.
+#include <cstdlib>
+
 #include "wf_internal.h"
 #include "wf_line.cuh"
 
@@ -22,21 +24,6 @@ constexpr int kLineThreads = 128;
 #endif
 // resident CTAs per SM the line kernels are compiled for (3: 168 registers; measured best
 // on GB300 against 1 and 4, where 4 spills)
-// right-hand sides are processed in groups of this many: within a group the warps of one
-// line run side by side and share its links through L2 (measured: groups of all 12 sources
-// beat groups of 4, whose links are re-read per group)
-constexpr int kRhsGroup = 16;
-
-// warp-line index -> (rhs, line): rhs groups outermost, lines, rhs within the group innermost
-__device__ __forceinline__ void line_rhs(int lg, int nrhs, int Nl, int& rhs, int& l) {
-  const int per_group = kRhsGroup * Nl;
-  const int grp = lg / per_group;
-  const int r = lg - grp * per_group;
-  const int gsize = min(kRhsGroup, nrhs - grp * kRhsGroup);
-  l = r / gsize;
-  rhs = grp * kRhsGroup + (r - l * gsize);
-}
-
 template <typename R, bool AX, bool FWD>
 __device__ __forceinline__ void solve_half(Vec3<R> (&v)[NMAX][4], int s0, const LineArgs<R>& A, int l, int jj) {
   constexpr int NS = sizeof(R) == 4 ? 2 : 1;
@@ -81,7 +68,7 @@ __global__ void __launch_bounds__(kLineThreads, WF_LINE_MINB) k_line(const LineA
   const bool active = lg_raw < A.nrhs * g.Nl;
   const int lg = active ? lg_raw : 0;  // idle lanes still join the warp shuffles
   int rhs, l;
-  line_rhs(lg, A.nrhs, g.Nl, rhs, l);
+  line_rhs(lg, A.nrhs, g, rhs, l);
   const int jj = lane % g.lpl;
   const int tp = g.tp, n = g.n;
   const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
@@ -157,8 +144,27 @@ static int line_blocks(const LineArgs<R>& a) {
   return (warps * 32 + kLineThreads - 1) / kLineThreads;
 }
 
+// In the axial frame the FP32 hop kernels of the Schur operator (K-b, K-c) run as the
+// one-thread-per-site kernels of wf_wide.cu: measured on GB300 (24^3 x 128) 1.15-1.3x faster
+// than k_line. The scan-heavy, memory-light K-a and the FP64 kernels (bound by GB300's FP64
+// rate) stay on k_line, which amortises the scan over n sites per lane. Environment WF_WIDE=0
+// disables the wide kernels, WF_WIDE=2 uses them for every axial line operation.
+static bool use_wide(const Geom& g, int kind, bool fp32) {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = std::getenv("WF_WIDE");
+    mode = (e && e[0] == '0') ? 0 : (e && e[0] == '2') ? 2 : 1;
+  }
+  if (!mode || !wide_supported(g)) return false;
+  return mode == 2 || (fp32 && (kind == LK_SCHUR_B || kind == LK_SCHUR_C));
+}
+
 template <typename R>
 void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
+  if (axial && use_wide(a.g, kind, sizeof(R) == 4)) {
+    launch_line_wide(a, kind, s);
+    return;
+  }
   if (a.g.n < 1 || a.g.n > NMAX) throw Error(1, "unsupported sites per lane");
   const int b = line_blocks(a);
 #define WF_KL(AXV, SRCV, OPUV, OPLV) k_line<R, AXV, SRCV, OPUV, OPLV><<<b, kLineThreads, 0, s>>>(a)
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_M(const MArgs<R> A) {
   const int lg = warp * g.lpw + lane / g.lpl;
   if (lg >= A.nrhs * g.Nl) return;
   int rhs, l;
-  line_rhs(lg, A.nrhs, g.Nl, rhs, l);
+  line_rhs(lg, A.nrhs, g, rhs, l);
   const int jj = lane % g.lpl;
   const int tp = g.tp, T = g.T, n = g.n;
   const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;

@@ -233,9 +233,11 @@ __global__ void k_tline_init(const Geom g, const Cx<double>* __restrict__ ut, Cx
 
 // Axial (temporal) frame (§II.C; App. C): per line, g(t) = U_t(0) U_t(1) ... U_t(t-1), g(0) = 1,
 // so that U_t'(t) = g(t) U_t(t) g(t+1)^dag = 1 for t < N_t - 1 and U_t'(N_t - 1) = g(N_t - 1) U_t(N_t - 1)
-// = P, the Polyakov product. Written in place of U_t (ut becomes g); P and
-// Lambda = (1 - s mu^-N_t P)^-1 per line.
-__global__ void k_axial_frame(const Geom g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, int* singular) {
+// = P, the Polyakov product. Written in place of U_t (ut becomes g); P,
+// Lambda = (1 - s mu^-N_t P)^-1 and the wrap matrix K = P Lambda per line. Lambda is a function
+// of P, so K = Lambda P as well and K^dag = Lambda^dag P^dag closes T^-dag.
+__global__ void k_axial_frame(const Geom g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, Cx<double>* wrap,
+                              int* singular) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= g.Nl) return;
   Cx<double>* line = ut_to_g + (size_t)l * 9 * g.tp;
@@ -254,9 +256,11 @@ __global__ void k_axial_frame(const Geom g, Cx<double>* ut_to_g, Cx<double>* pl,
   }
   const double d = inv3(A, Ai);
   if (!(d > 1e-12)) atomicExch(singular, 1);
+  const Mat3<double> K = matmul(run, Ai);
   for (int k = 0; k < 9; ++k) {
     pl[(size_t)l * 9 + k] = run.e[k];
     lamb[(size_t)l * 9 + k] = Ai.e[k];
+    wrap[(size_t)l * 9 + k] = K.e[k];
   }
 }
 
@@ -345,9 +349,9 @@ void launch_tline_init(const Geom& g, const Cx<double>* ut, Cx<double>* lamb, Cx
   WF_CUDA(cudaGetLastError());
 }
 
-void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, int* singular,
-                        cudaStream_t s) {
-  k_axial_frame<<<(g.Nl + 127) / 128, 128, 0, s>>>(g, ut_to_g, pl, lamb, singular);
+void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, Cx<double>* wrap,
+                        int* singular, cudaStream_t s) {
+  k_axial_frame<<<(g.Nl + 127) / 128, 128, 0, s>>>(g, ut_to_g, pl, lamb, wrap, singular);
   WF_CUDA(cudaGetLastError());
 }
 

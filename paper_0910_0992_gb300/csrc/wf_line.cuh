@@ -51,7 +51,8 @@ struct LineArgs {
   const Cx<R>* us_out;
   const Cx<R>* us_nbr;
   const Cx<R>* lamb;  // Lambda for T^-1, [Nl][9]
-  const Cx<R>* lamf;  // Lambda for T^-dag, [Nl][9] (general frame; axial uses lamb^dag)
+  const Cx<R>* lamf;  // general frame: Lambda for T^-dag, [Nl][9]; axial frame: the wrap matrix
+                      // K = P Lambda, [Nl][9] (T^-1 closes with K, T^-dag with K^dag)
   // pre-solve axpy: v <- xpre + apre * v (skipped if xpre == nullptr)
   const Cx<R>* xpre;
   R apre;
@@ -59,11 +60,42 @@ struct LineArgs {
   const Cx<R>* xpost;
   R apost;
   int swap_out;  // store the upper result into the lower half and vice versa
+  int stream_out;  // store with the evict-first cache policy (the result is not read again soon)
   Cx<R>* out;    // [nrhs][Nl][12][tp]
   double* norm2; // if set: atomically add |stored result|^2 per rhs (FP64)
   R inv_mu, bc;
   int drop_job;  // TMA-fed kernel only: skip the bulk copy of this job (fault injection), -1: none
 };
+
+// Order in which the line kernels visit (rhs, line) pairs. Right-hand sides are processed in
+// groups of kRhsGroup; within a group every line is visited for all of the group's
+// right-hand sides side by side, so the line's links are shared through L2 (measured: groups
+// of all 12 sources beat groups of 4, whose links are re-read per group). Lines are visited in
+// tiles of all x times g.by rows of y, each tile streamed along z: a neighbour line's spinor
+// is then read again by the other hops of the stencil while still in L2 (reuse distance about
+// Lh * by lines instead of Lh * L lines in lexicographic order; measured with 12 sources on
+// 24^3 x 128: lexicographic order read the neighbour spinors about three times from DRAM).
+#ifndef WF_RHS_GROUP
+#define WF_RHS_GROUP 16
+#endif
+constexpr int kRhsGroup = WF_RHS_GROUP;
+
+// traversal index -> (rhs, line)
+__device__ __forceinline__ void line_rhs(int lg, int nrhs, const Geom& g, int& rhs, int& l) {
+  const int per_group = kRhsGroup * g.Nl;
+  const int grp = lg / per_group;
+  const int r = lg - grp * per_group;
+  const int gsize = min(kRhsGroup, nrhs - grp * kRhsGroup);
+  const int pos = r / gsize;  // position of the line in the tiled order
+  rhs = grp * kRhsGroup + (r - pos * gsize);
+  const int xh = pos % g.Lh;
+  int u = pos / g.Lh;
+  const int yy = u % g.by;
+  u /= g.by;
+  const int z = u % g.L;
+  const int y = (u / g.L) * g.by + yy;
+  l = xh + g.Lh * (y + g.L * z);
+}
 
 template <typename R>
 __device__ __forceinline__ Mat3<R> ldmat(const Cx<R>* __restrict__ base, int tp, int slot) {
@@ -104,6 +136,35 @@ template <typename R>
 __device__ __forceinline__ void stvec(Cx<R>* __restrict__ base, int tp, int slot, const Vec3<R>& v) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) base[k * tp + slot] = v.c[k];
+}
+
+// single-use data: loads and stores with the evict-first ("streaming") cache policy, so that
+// they do not push reusable neighbour lines and links out of L2
+__device__ __forceinline__ Cx<float> ld_stream(const Cx<float>* p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+__device__ __forceinline__ Cx<double> ld_stream(const Cx<double>* p) {
+  const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+__device__ __forceinline__ void st_stream(Cx<float>* p, Cx<float> z) {
+  __stcs(reinterpret_cast<float2*>(p), make_float2(z.re, z.im));
+}
+__device__ __forceinline__ void st_stream(Cx<double>* p, Cx<double> z) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(z.re, z.im));
+}
+template <typename R>
+__device__ __forceinline__ Vec3<R> ldvec_stream(const Cx<R>* __restrict__ base, int tp, int slot) {
+  Vec3<R> v;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = ld_stream(base + k * tp + slot);
+  return v;
+}
+template <typename R>
+__device__ __forceinline__ void stvec_stream(Cx<R>* __restrict__ base, int tp, int slot, const Vec3<R>& v) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) st_stream(base + k * tp + slot, v.c[k]);
 }
 
 template <typename R>

@@ -106,13 +106,7 @@ struct Stage {
 
 // the CTA's j-th line: lines lg = blockIdx.x + j * gridDim.x, rhs groups as in the line kernel
 __device__ __forceinline__ void job_line(const LineArgs<float>& A, int lg, int& rhs, int& l) {
-  constexpr int G = 16;
-  const int per_group = G * A.g.Nl;
-  const int grp = lg / per_group;
-  const int r = lg - grp * per_group;
-  const int gsize = min(G, A.nrhs - grp * G);
-  l = r / gsize;
-  rhs = grp * G + (r - l * gsize);
+  line_rhs(lg, A.nrhs, A.g, rhs, l);
 }
 
 // issue the three bulk copies of direction d of line lg into stage st (lane 0 only)
