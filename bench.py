@@ -226,18 +226,15 @@ def run_ours(args, prm, U, eta):
 
     import paper_0910_0992_gb300 as wf
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    from paper_0910_0992_gb300.replicas import Replicas
+
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps = Replicas("nccl", device=torch.device("cuda", local))
+    world, rank = reps.world, reps.rank
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
 
     prec = wf.WF_FP32 if args.precision == "fp32" else wf.WF_FP64
@@ -274,17 +271,14 @@ def run_ours(args, prm, U, eta):
     prof = wf.wf_profile_get(w.h)
     wf.wf_profile(w.h, 0)
     ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reps.max(ms, device="cuda")
 
     odd_sites = prm["L"] ** 3 * prm["T"] // 2
     applies_f32 = prof.get("schur_c_hop_tinv_axpy_f32", (0, 0))[0]
     applies_f64 = prof.get("schur_c_hop_tinv_axpy_f64", (0, 0))[0]
     # every M-hat launch sequence works on all nsrc sources at once
     step_bytes = applies_f32 * apply_bytes(odd_sites, nsrc) + applies_f64 * apply_bytes(odd_sites, nsrc, 2)
-    value = world * step_bytes / (ms * 1e-3) / 1e9
+    value = reps.whole_job_rate(step_bytes, ms * 1e-3) / 1e9
     flops = (applies_f32 + applies_f64) * paper_flops_per_apply(prm["L"], prm["T"]) * nsrc
 
     # roofline: the dominant kernel by time
@@ -309,8 +303,8 @@ def run_ours(args, prm, U, eta):
         for _ in range(args.steps):
             solve(h_rhs, h_x)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        e2e = {"value": world * step_bytes / e2e_s / 1e9, "unit": "GB/s",
+        e2e_s = reps.max(time.perf_counter() - t0, device="cuda")
+        e2e = {"value": reps.whole_job_rate(step_bytes, e2e_s) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": int(h_rhs.numel() * 16), "d2h_bytes_per_step": int(h_x.numel() * 16),
                "ms_per_step": 1e3 * e2e_s / args.steps}
 
@@ -318,17 +312,17 @@ def run_ours(args, prm, U, eta):
     # same sources, batched and single-source, against the temporal + 3-D Schur solve
     compare = None
     if not args.no_compare:
-        def timed(method, r, xx, nr, reps):
+        def timed(method, r, xx, nr, nrep):
             st, it, res = wf.wf_solve(w.h, r, xx, nr, args.tol, method, prec, 0)  # warm-up
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(reps):
+            for _ in range(nrep):
                 st, it, res = wf.wf_solve(w.h, r, xx, nr, args.tol, method, prec, 0)
             e1.record(stream)
             torch.cuda.synchronize()
             if st != wf.WF_OK or max(res) > args.tol:
                 raise RuntimeError(f"comparison solve failed: method {method}, status {st}, residuals {res}")
-            return e0.elapsed_time(e1) / reps / 1e3, it
+            return e0.elapsed_time(e1) / nrep / 1e3, it
 
         r1, x1 = rhs[:1].contiguous(), x[:1].contiguous()
         t_eo, it_eo = timed(wf.WF_EO4D, rhs, x, nsrc, 2)
@@ -367,7 +361,7 @@ def run_ours(args, prm, U, eta):
             "time_to_solve_s": ms / args.steps / 1e3,
             "iterations": iters,
             "m_hat_applies_per_step": {"f32": applies_f32 // args.steps, "f64": applies_f64 // args.steps},
-            "gflops_paper_model": world * flops / (ms * 1e-3) / 1e9,
+            "gflops_paper_model": reps.whole_job_rate(flops, ms * 1e-3) / 1e9,
             "schur_kernel_share": schur_ms / total_prof_ms if total_prof_ms else None,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -382,8 +376,7 @@ def run_ours(args, prm, U, eta):
         }
         print(json.dumps(line))
     w.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
