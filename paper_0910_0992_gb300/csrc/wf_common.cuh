@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "wf_df64.cuh"
+
 namespace wf {
 
 // ----------------------------------------------------------------------------
@@ -61,17 +63,47 @@ __device__ __forceinline__ Cx<R> times_mi(Cx<R> a) { return mk<R>(a.im, -a.re); 
 template <typename R>
 __device__ __forceinline__ Cx<R> czero() { return mk<R>(R(0), R(0)); }
 
+// one complex element from / to device memory; double-float values live in memory as FP64
+template <typename R>
+__device__ __forceinline__ Cx<R> ldc(const Cx<R>* p) { return *p; }
+template <typename R>
+__device__ __forceinline__ void stc(Cx<R>* p, Cx<R> z) { *p = z; }
+__device__ __forceinline__ Cx<df64> ldc(const Cx<df64>* p) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  return mk<df64>(df_from_double(v.x), df_from_double(v.y));
+}
+__device__ __forceinline__ void stc(Cx<df64>* p, Cx<df64> z) {
+  *reinterpret_cast<double2*>(p) = make_double2(df_to_double(z.re), df_to_double(z.im));
+}
+
+// full-warp shuffles of one real value (float, double or a double-float pair)
+template <typename R>
+__device__ __forceinline__ R shfl_down_r(R v, int d, int width) { return __shfl_down_sync(0xffffffffu, v, d, width); }
+template <typename R>
+__device__ __forceinline__ R shfl_up_r(R v, int d, int width) { return __shfl_up_sync(0xffffffffu, v, d, width); }
+template <typename R>
+__device__ __forceinline__ R shfl_idx_r(R v, int src, int width) { return __shfl_sync(0xffffffffu, v, src, width); }
+__device__ __forceinline__ df64 shfl_down_r(df64 v, int d, int width) {
+  return df64(__shfl_down_sync(0xffffffffu, v.hi, d, width), __shfl_down_sync(0xffffffffu, v.lo, d, width));
+}
+__device__ __forceinline__ df64 shfl_up_r(df64 v, int d, int width) {
+  return df64(__shfl_up_sync(0xffffffffu, v.hi, d, width), __shfl_up_sync(0xffffffffu, v.lo, d, width));
+}
+__device__ __forceinline__ df64 shfl_idx_r(df64 v, int src, int width) {
+  return df64(__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width));
+}
+
 template <typename R>
 __device__ __forceinline__ Cx<R> shfl_down(Cx<R> v, int d, int width) {
-  return mk<R>(__shfl_down_sync(0xffffffffu, v.re, d, width), __shfl_down_sync(0xffffffffu, v.im, d, width));
+  return mk<R>(shfl_down_r(v.re, d, width), shfl_down_r(v.im, d, width));
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> shfl_up(Cx<R> v, int d, int width) {
-  return mk<R>(__shfl_up_sync(0xffffffffu, v.re, d, width), __shfl_up_sync(0xffffffffu, v.im, d, width));
+  return mk<R>(shfl_up_r(v.re, d, width), shfl_up_r(v.im, d, width));
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> shfl_idx(Cx<R> v, int src, int width) {
-  return mk<R>(__shfl_sync(0xffffffffu, v.re, src, width), __shfl_sync(0xffffffffu, v.im, src, width));
+  return mk<R>(shfl_idx_r(v.re, src, width), shfl_idx_r(v.im, src, width));
 }
 
 // ----------------------------------------------------------------------------

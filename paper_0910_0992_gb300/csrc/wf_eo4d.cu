@@ -10,6 +10,8 @@
 // site; consecutive threads take consecutive h, so every load is coalesced.
 // Links are the handle's (same frame as the temporal preconditioner: in the axial frame
 // U_t = 1 except the boundary link P), read through the line layout's index maps.
+#include <type_traits>
+
 #include "wf_internal.h"
 #include "wf_line.cuh"
 
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs
 }
 
 template <typename R>
-void launch_dslash4(const EoArgs<R>& a, bool axial, cudaStream_t s) {
+static void launch_dslash4_impl(const EoArgs<R>& a, bool axial, cudaStream_t s) {
   const size_t total = (size_t)a.nrhs * a.g.L * a.g.L * a.g.L * (a.g.T / 2);
   const int blocks = (int)((total + kEoThreads - 1) / kEoThreads);
   if (axial)
@@ -171,6 +173,46 @@ void launch_dslash4(const EoArgs<R>& a, bool axial, cudaStream_t s) {
   else
     k_dslash4<R, false><<<blocks, kEoThreads, 0, s>>>(a);
   WF_CUDA(cudaGetLastError());
+}
+
+// double-float arguments over the same FP64 arrays (see wf_df64.cuh)
+static EoArgs<df64> eo_args_df(const EoArgs<double>& a) {
+  auto cv = [](const Cx<double>* p) { return reinterpret_cast<const Cx<df64>*>(p); };
+  EoArgs<df64> b;
+  b.g = a.g;
+  b.par = a.par;
+  b.nrhs = a.nrhs;
+  b.in = cv(a.in);
+  b.x1 = cv(a.x1);
+  b.b1 = df64(a.b1);
+  b.x2 = cv(a.x2);
+  b.b2 = df64(a.b2);
+  b.a = df64(a.a);
+  b.swap_in = a.swap_in;
+  b.swap_out = a.swap_out;
+  b.stream_out = a.stream_out;
+  b.df = 0;
+  b.out = reinterpret_cast<Cx<df64>*>(a.out);
+  b.norm2 = a.norm2;
+  for (int p = 0; p < 2; ++p) {
+    b.ut[p] = cv(a.ut[p]);
+    b.pl[p] = cv(a.pl[p]);
+    b.us[p] = cv(a.us[p]);
+  }
+  b.inv_gf = df64(a.inv_gf);
+  b.bc = df64(a.bc);
+  return b;
+}
+
+template <typename R>
+void launch_dslash4(const EoArgs<R>& a, bool axial, cudaStream_t s) {
+  if constexpr (std::is_same<R, double>::value) {
+    if (a.df) {
+      launch_dslash4_impl<df64>(eo_args_df(a), axial, s);
+      return;
+    }
+  }
+  launch_dslash4_impl<R>(a, axial, s);
 }
 template void launch_dslash4<float>(const EoArgs<float>&, bool, cudaStream_t);
 template void launch_dslash4<double>(const EoArgs<double>&, bool, cudaStream_t);

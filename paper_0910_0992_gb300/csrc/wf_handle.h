@@ -25,6 +25,10 @@ struct wf_handle {
   std::string err;
   bool gauge = false;
   bool axial = true;  // solve in the axial frame (U_t = 1 but for P at t = N_t - 1)
+  // FP64 line and 4-D dslash operations run in double-float arithmetic while set (the
+  // high-precision steps of FP32-iteration solves; see wf_df64.cuh)
+  bool df_ops = false;
+  bool df_allowed = false;  // double-float steps enabled for this handle
   // gauge, per parity: U_t [Nl][9][tp], spatial [3][Nl][9][tp], Lambda [Nl][9]
   wf::DevBuf ut64[2], us64[2], lamb64[2], lamf64[2];
   wf::DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];

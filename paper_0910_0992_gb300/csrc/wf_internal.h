@@ -152,6 +152,7 @@ struct EoArgs {
   R a;
   int swap_in, swap_out;  // read / write the P_+ and P_- spin halves exchanged (gamma_5 up to sign)
   int stream_out;         // store with the evict-first cache policy (the result is not read again soon)
+  int df;                 // R = double only: compute in double-float (FP64 storage, FP32 arithmetic)
   Cx<R>* out;
   double* norm2;          // if set: atomically add |out|^2 per rhs
   const Cx<R>* ut[2];     // general frame: U_t per 3-D parity, line layout

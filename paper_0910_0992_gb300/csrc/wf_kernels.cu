@@ -12,6 +12,7 @@
 // each carries only its own code; every other use goes through one kernel that selects
 // them at run time.
 #include <cstdlib>
+#include <type_traits>
 
 #include "wf_internal.h"
 #include "wf_line.cuh"
@@ -146,9 +147,9 @@ static int line_blocks(const LineArgs<R>& a) {
 
 // In the axial frame the FP32 hop kernels of the Schur operator (K-b, K-c) run as the
 // one-thread-per-site kernels of wf_wide.cu: measured on GB300 (24^3 x 128) 1.15-1.3x faster
-// than k_line. The scan-heavy, memory-light K-a and the FP64 kernels (bound by GB300's FP64
-// rate) stay on k_line, which amortises the scan over n sites per lane. Environment WF_WIDE=0
-// disables the wide kernels, WF_WIDE=2 uses them for every axial line operation.
+// than k_line. The scan-heavy, memory-light K-a stays on k_line, which amortises the scan over
+// n sites per lane; FP64 arithmetic stays on k_line too. Environment WF_WIDE=0 disables the
+// wide FP32 kernels, WF_WIDE=2 uses them for every FP32 axial line operation.
 static bool use_wide(const Geom& g, int kind, bool fp32) {
   static int mode = -1;
   if (mode < 0) {
@@ -160,10 +161,12 @@ static bool use_wide(const Geom& g, int kind, bool fp32) {
 }
 
 template <typename R>
-void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
-  if (axial && use_wide(a.g, kind, sizeof(R) == 4)) {
-    launch_line_wide(a, kind, s);
-    return;
+static void launch_line_impl(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    if (axial && use_wide(a.g, kind, true)) {
+      launch_line_wide(a, kind, s);
+      return;
+    }
   }
   if (a.g.n < 1 || a.g.n > NMAX) throw Error(1, "unsupported sites per lane");
   const int b = line_blocks(a);
@@ -185,6 +188,54 @@ void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
   }
 #undef WF_KL
   WF_CUDA(cudaGetLastError());
+}
+
+// the same arguments for the double-float kernels: FP64 arrays are read and written as such
+// (Cx<df64> has the size and alignment of Cx<double>), scalars are split on the host
+template <typename A, typename B>
+static const Cx<A>* as_cx(const Cx<B>* p) { return reinterpret_cast<const Cx<A>*>(p); }
+static LineArgs<df64> line_args_df(const LineArgs<double>& a) {
+  LineArgs<df64> b;
+  b.g = a.g;
+  b.parity = a.parity;
+  b.nrhs = a.nrhs;
+  b.opu = a.opu;
+  b.opl = a.opl;
+  b.src = a.src;
+  b.src_up = as_cx<df64>(a.src_up);
+  b.src_lo = as_cx<df64>(a.src_lo);
+  b.ut = as_cx<df64>(a.ut);
+  b.pl = as_cx<df64>(a.pl);
+  b.us_out = as_cx<df64>(a.us_out);
+  b.us_nbr = as_cx<df64>(a.us_nbr);
+  b.lamb = as_cx<df64>(a.lamb);
+  b.lamf = as_cx<df64>(a.lamf);
+  b.xpre = as_cx<df64>(a.xpre);
+  b.apre = df64(a.apre);
+  b.xpost = as_cx<df64>(a.xpost);
+  b.apost = df64(a.apost);
+  b.swap_out = a.swap_out;
+  b.stream_out = a.stream_out;
+  b.out = reinterpret_cast<Cx<df64>*>(a.out);
+  b.norm2 = a.norm2;
+  b.inv_mu = df64(a.inv_mu);
+  b.bc = df64(a.bc);
+  b.drop_job = -1;
+  b.df = 0;
+  return b;
+}
+
+template <typename R>
+void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
+  if constexpr (std::is_same<R, double>::value) {
+    // double-float runs one site per thread (with n sites per lane the double-width state of
+    // k_line spills); the caller's-gauge frame stays in FP64
+    if (a.df && axial && wide_supported(a.g)) {
+      launch_line_wide(line_args_df(a), kind, s);
+      return;
+    }
+  }
+  launch_line_impl<R>(a, kind, axial, s);
 }
 template void launch_line<float>(const LineArgs<float>&, int, bool, cudaStream_t);
 template void launch_line<double>(const LineArgs<double>&, int, bool, cudaStream_t);

@@ -65,6 +65,7 @@ struct LineArgs {
   double* norm2; // if set: atomically add |stored result|^2 per rhs (FP64)
   R inv_mu, bc;
   int drop_job;  // TMA-fed kernel only: skip the bulk copy of this job (fault injection), -1: none
+  int df;        // R = double only: compute in double-float (FP64 storage, FP32 arithmetic)
 };
 
 // Order in which the line kernels visit (rhs, line) pairs. Right-hand sides are processed in
@@ -101,7 +102,7 @@ template <typename R>
 __device__ __forceinline__ Mat3<R> ldmat(const Cx<R>* __restrict__ base, int tp, int slot) {
   Mat3<R> U;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) U.e[k] = base[k * tp + slot];
+  for (int k = 0; k < 9; ++k) U.e[k] = ldc(base + k * tp + slot);
   return U;
 }
 
@@ -109,10 +110,12 @@ __device__ __forceinline__ Mat3<R> ldmat(const Cx<R>* __restrict__ base, int tp,
 // third rebuilt as conj(row0 x row1)
 template <typename R>
 __device__ __forceinline__ Mat3<R> ldlink(const Cx<R>* __restrict__ base, int tp, int slot) {
-  if (SpatialLinkNC<R>::value == 9) return ldmat(base, tp, slot);
+  if constexpr (SpatialLinkNC<R>::value == 9) {
+    return ldmat(base, tp, slot);
+  }
   Mat3<R> U;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) U.e[k] = base[k * tp + slot];
+  for (int k = 0; k < 6; ++k) U.e[k] = ldc(base + k * tp + slot);
   const Cx<R>* a = U.e;
   const Cx<R>* b = U.e + 3;
   const Cx<R> c0 = cmul(a[1], b[2]) - cmul(a[2], b[1]);
@@ -128,14 +131,14 @@ template <typename R>
 __device__ __forceinline__ Vec3<R> ldvec(const Cx<R>* __restrict__ base, int tp, int slot) {
   Vec3<R> v;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) v.c[k] = base[k * tp + slot];
+  for (int k = 0; k < 3; ++k) v.c[k] = ldc(base + k * tp + slot);
   return v;
 }
 
 template <typename R>
 __device__ __forceinline__ void stvec(Cx<R>* __restrict__ base, int tp, int slot, const Vec3<R>& v) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) base[k * tp + slot] = v.c[k];
+  for (int k = 0; k < 3; ++k) stc(base + k * tp + slot, v.c[k]);
 }
 
 // single-use data: loads and stores with the evict-first ("streaming") cache policy, so that
@@ -147,6 +150,13 @@ __device__ __forceinline__ Cx<float> ld_stream(const Cx<float>* p) {
 __device__ __forceinline__ Cx<double> ld_stream(const Cx<double>* p) {
   const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
   return mk<double>(v.x, v.y);
+}
+__device__ __forceinline__ Cx<df64> ld_stream(const Cx<df64>* p) {
+  const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  return mk<df64>(df_from_double(v.x), df_from_double(v.y));
+}
+__device__ __forceinline__ void st_stream(Cx<df64>* p, Cx<df64> z) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(df_to_double(z.re), df_to_double(z.im)));
 }
 __device__ __forceinline__ void st_stream(Cx<float>* p, Cx<float> z) {
   __stcs(reinterpret_cast<float2*>(p), make_float2(z.re, z.im));
@@ -188,6 +198,14 @@ __device__ __forceinline__ Vec3<R> vscale(R a, const Vec3<R>& x) {
   Vec3<R> w;
 #pragma unroll
   for (int k = 0; k < 3; ++k) w.c[k] = a * x.c[k];
+  return w;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec3<R> vneg(const Vec3<R>& x) {
+  Vec3<R> w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.c[k] = mk<R>(-x.c[k].re, -x.c[k].im);
   return w;
 }
 
@@ -348,7 +366,7 @@ __device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NMAX][NS], const 
   }
 
   for (int d = 1; d < lpl; d <<= 1) {
-    const R an = FWD ? __shfl_up_sync(0xffffffffu, a, d, lpl) : __shfl_down_sync(0xffffffffu, a, d, lpl);
+    const R an = FWD ? shfl_up_r(a, d, lpl) : shfl_down_r(a, d, lpl);
     Vec3<R> cn[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) cn[s] = FWD ? vshfl_up(c[s], d, lpl) : vshfl_down(c[s], d, lpl);
@@ -375,7 +393,7 @@ __device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NMAX][NS], const 
   }
   Vec3<R> e[NS];
   {
-    const R an = FWD ? __shfl_up_sync(0xffffffffu, a, 1, lpl) : __shfl_down_sync(0xffffffffu, a, 1, lpl);
+    const R an = FWD ? shfl_up_r(a, 1, lpl) : shfl_down_r(a, 1, lpl);
     const bool edge = FWD ? (jj == 0) : (jj == lpl - 1);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {

@@ -1,0 +1,414 @@
+// Wide line kernels for the axial frame: one thread per time site.
+//
+// The line kernel of wf_kernels.cu gives each lane n sites of a line (n = 4 for N_t = 128).
+// Its per-thread state -- n spinors of accumulator plus one direction's hop operands for n
+// sites -- needs about 170 registers, which leaves 12 warps per SM, too few loads in flight to
+// cover HBM latency (measured near 45 % of DRAM bandwidth, stalled on long scoreboard). Here
+// thread q of a line owns the single slot q of the line layout, i.e. the site
+//     t = n j + m   for slot q = m lpl + j,
+// so that every warp-wide load is one contiguous run of 32 elements, as in k_line. (A map
+// t = q, warps on consecutive times, touches four 64-byte runs per load and saturated the L1
+// data pipe instead.) The hop keeps one spinor of accumulator live, so several times more
+// warps fit per SM.
+//
+// The time-line solves of the axial frame (§II.C, App. C: U_t = 1 on the line except the
+// boundary link P) are the recurrences
+//     T^-dag: e(t) = mu^-1 (v(t) + e(t - 1)),   T^-1: e(t) = mu^-1 (v(t) + e(t + 1)),
+// closed at the wrap: the value entering the line is s K^dag C (T^-dag) or s K C (T^-1), with
+// K = P Lambda the per-line wrap matrix and C the line's composite with nothing entering.
+// Every site is the affine map e -> c + a e (c = mu^-1 v, a = mu^-1; the identity on padding).
+// The n sites of group j (t = n j .. n j + n - 1) sit in n different warps at lane j; their
+// maps are composed through shared memory, then the lpl group composites by a Kogge-Stone
+// shuffle scan over the lanes. A site's result is its in-group composite applied to the value
+// entering its group. One barrier serves both spin halves. Memory layout, arguments and
+// results are those of k_line.
+#pragma once
+
+#include <type_traits>
+
+#include "wf_internal.h"
+#include "wf_line.cuh"
+
+namespace wf {
+
+namespace wide {
+
+constexpr int kWideCta = 128;  // threads per CTA
+constexpr int kMapFields = 13;  // c (two spins x three colours, complex) and a
+#ifndef WF_WIDE_MINB_F32
+#define WF_WIDE_MINB_F32 5
+#endif
+#ifndef WF_WIDE_MINB_F64
+#define WF_WIDE_MINB_F64 3
+#endif
+template <typename R>
+struct WideMinBlocks {
+  static constexpr int value = WF_WIDE_MINB_F64;
+};
+template <>
+struct WideMinBlocks<float> {
+  static constexpr int value = WF_WIDE_MINB_F32;
+};
+#ifndef WF_WIDE_MINB_DF
+#define WF_WIDE_MINB_DF 3
+#endif
+template <>
+struct WideMinBlocks<df64> {
+  static constexpr int value = WF_WIDE_MINB_DF;
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// the affine map e -> c + a e on a spin half (two spins)
+template <typename R>
+struct HalfMap {
+  Vec3<R> c[2];
+  R a;
+};
+
+template <typename R>
+__device__ __forceinline__ HalfMap<R> identity_map() {
+  HalfMap<R> m;
+  m.c[0] = vzero<R>();
+  m.c[1] = vzero<R>();
+  m.a = R(1);
+  return m;
+}
+
+// later o earlier: apply `earlier` first, then `later`
+template <typename R>
+__device__ __forceinline__ HalfMap<R> compose(const HalfMap<R>& later, const HalfMap<R>& earlier) {
+  HalfMap<R> r;
+  r.c[0] = vaxpy(later.a, earlier.c[0], later.c[0]);
+  r.c[1] = vaxpy(later.a, earlier.c[1], later.c[1]);
+  r.a = later.a * earlier.a;
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ HalfMap<R> shfl_map(const HalfMap<R>& m, int d, int width, bool up) {
+  HalfMap<R> r;
+  r.c[0] = up ? vshfl_up(m.c[0], d, width) : vshfl_down(m.c[0], d, width);
+  r.c[1] = up ? vshfl_up(m.c[1], d, width) : vshfl_down(m.c[1], d, width);
+  r.a = up ? shfl_up_r(m.a, d, width) : shfl_down_r(m.a, d, width);
+  return r;
+}
+
+// shared-memory image of one map per thread, field-major (conflict-free)
+template <typename R>
+struct MapStore {
+  R f[kMapFields][kWideCta];
+};
+
+template <typename R>
+__device__ __forceinline__ void put_map(MapStore<R>& S, int q, const HalfMap<R>& m) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      S.f[6 * s + 2 * k][q] = m.c[s].c[k].re;
+      S.f[6 * s + 2 * k + 1][q] = m.c[s].c[k].im;
+    }
+  S.f[12][q] = m.a;
+}
+
+template <typename R>
+__device__ __forceinline__ HalfMap<R> get_map(const MapStore<R>& S, int q) {
+  HalfMap<R> m;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.c[s].c[k] = mk<R>(S.f[6 * s + 2 * k][q], S.f[6 * s + 2 * k + 1][q]);
+  m.a = S.f[12][q];
+  return m;
+}
+
+// The same hop with the direction loop kept rolled (one copy of the SU(3) code): the backward
+// hop uses the conjugate-transposed link, the projection and reconstruction signs are selected
+// per direction, and the common factor 1/2 of the projectors is applied once at the end (exact).
+// Used for double-float, whose unrolled hop overflows the instruction cache.
+template <typename R, int TPC>
+__device__ __forceinline__ void hop_site_rolled(Vec3<R> (&h)[4], const LineArgs<R>& A, int rhs, int l, int sl) {
+  const Geom& g = A.g;
+  const int tp = TPC ? TPC : g.tp, Nl = g.Nl;
+  int nb[6];
+  neighbour_lines(g, A.parity, l, nb);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) h[s] = vzero<R>();
+  constexpr int LNC = SpatialLinkNC<R>::value;
+#pragma unroll 1
+  for (int d = 0; d < 6; ++d) {
+    const int k = d >> 1, dir = d & 1;  // dir 0: forward (x + k), 1: backward (x - k)
+    const int ln = nb[d];
+    const size_t sb = (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
+    const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * LNC * tp
+                               : A.us_nbr + (size_t)(k * Nl + ln) * LNC * tp;
+    Mat3<R> U = ldlink(lk, tp, sl);
+    if (dir) U = dagger(U);
+    const Vec3<R> u0 = ldvec(A.src_up + sb, tp, sl), u1 = ldvec(A.src_up + sb + 3 * tp, tp, sl);
+    const Vec3<R> d0 = ldvec(A.src_lo + sb, tp, sl), d1 = ldvec(A.src_lo + sb + 3 * tp, tp, sl);
+    Vec3<R> s0, s1;
+    isigma(k, d0, d1, s0, s1);
+    if (dir) {
+      s0 = vneg(s0);
+      s1 = vneg(s1);
+    }
+    const Vec3<R> w0 = matvec(U, vadd(u0, s0)), w1 = matvec(U, vadd(u1, s1));
+    h[0] = vadd(h[0], w0);
+    h[1] = vadd(h[1], w1);
+    Vec3<R> r0, r1;
+    isigma(k, w0, w1, r0, r1);
+    if (!dir) {
+      r0 = vneg(r0);
+      r1 = vneg(r1);
+    }
+    h[2] = vadd(h[2], r0);
+    h[3] = vadd(h[3], r1);
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) h[s] = vscale(R(0.5), h[s]);
+}
+
+template <typename R>
+__device__ __forceinline__ HalfMap<R> site_map(const Vec3<R>& v0, const Vec3<R>& v1, bool valid, R inv_mu) {
+  HalfMap<R> m;
+  m.c[0] = valid ? vscale(inv_mu, v0) : vzero<R>();
+  m.c[1] = valid ? vscale(inv_mu, v1) : vzero<R>();
+  m.a = valid ? inv_mu : R(1);
+  return m;
+}
+
+// Solve one half after all site maps of the CTA are in S (thread q0 + mm lpl holds site
+// mm of this thread's group). FWD: T^-dag, time increasing; else T^-1, time decreasing.
+template <typename R, bool FWD>
+__device__ __forceinline__ void solve_half_wide(Vec3<R>& v0, Vec3<R>& v1, const MapStore<R>& S, bool member, int q0,
+                                                int m, int n, int lpl, int j, bool valid,
+                                                const Cx<R>* __restrict__ K_line, R bc) {
+  // composites within the group: up to this thread's site, and over the whole group
+  HalfMap<R> incl = identity_map<R>(), grp = identity_map<R>();
+  if (member) {
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+      if (i >= n) break;
+      const int mm = FWD ? i : n - 1 - i;
+      grp = compose(get_map(S, q0 + mm * lpl), grp);
+      if (mm == m) incl = grp;
+    }
+  }
+  // scan of the group composites over the lanes of the line, in time order
+  HalfMap<R> gs = grp;
+  for (int d = 1; d < lpl; d <<= 1) {
+    const HalfMap<R> o = shfl_map(gs, d, lpl, FWD);
+    if (FWD ? j >= d : j + d < lpl) gs = compose(gs, o);
+  }
+  // the line's composite sits at its last group in time order; the wrap value enters the first
+  Vec3<R> e[2];
+  {
+    const int last = FWD ? lpl - 1 : 0;
+    const Vec3<R> C0 = vshfl_idx(gs.c[0], last, lpl), C1 = vshfl_idx(gs.c[1], last, lpl);
+    const Mat3<R> K = ldmat(K_line, 1, 0);
+    e[0] = vscale(bc, FWD ? matvec_dag(K, C0) : matvec(K, C0));
+    e[1] = vscale(bc, FWD ? matvec_dag(K, C1) : matvec(K, C1));
+  }
+  // value entering this group: the composite of the groups before it, applied to the wrap
+  const HalfMap<R> prev = shfl_map(gs, 1, lpl, FWD);
+  if (FWD ? j > 0 : j < lpl - 1) {
+    e[0] = vaxpy(prev.a, e[0], prev.c[0]);
+    e[1] = vaxpy(prev.a, e[1], prev.c[1]);
+  }
+  v0 = valid ? vaxpy(incl.a, e[0], incl.c[0]) : vzero<R>();
+  v1 = valid ? vaxpy(incl.a, e[1], incl.c[1]) : vzero<R>();
+}
+
+// D_s (the spatial hop of hop_spatial, wf_line.cuh) at one site of line l
+template <typename R, int TPC>
+__device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, int rhs, int l, int sl) {
+  const Geom& g = A.g;
+  const int tp = TPC ? TPC : g.tp, Nl = g.Nl;
+  int nb[6];
+  neighbour_lines(g, A.parity, l, nb);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) h[s] = vzero<R>();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {  // 0: forward (x + k), 1: backward (x - k)
+      const int ln = nb[2 * k + dir];
+      const size_t sb = (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
+      const Cx<R>* up = A.src_up + sb;
+      const Cx<R>* lo = A.src_lo + sb;
+      constexpr int LNC = SpatialLinkNC<R>::value;
+      const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * LNC * tp
+                                 : A.us_nbr + (size_t)(k * Nl + ln) * LNC * tp;
+      const Vec3<R> u0 = ldvec(up, tp, sl), u1 = ldvec(up + 3 * tp, tp, sl);
+      const Vec3<R> d0 = ldvec(lo, tp, sl), d1 = ldvec(lo + 3 * tp, tp, sl);
+      const Mat3<R> U = ldlink(lk, tp, sl);
+      Vec3<R> s0, s1;
+      isigma(k, d0, d1, s0, s1);
+      const R half = R(0.5);
+      Vec3<R> h0, h1;
+      if (dir == 0) {
+        h0 = vscale(half, vadd(u0, s0));
+        h1 = vscale(half, vadd(u1, s1));
+      } else {
+        h0 = vscale(half, vaxpy(R(-1), s0, u0));
+        h1 = vscale(half, vaxpy(R(-1), s1, u1));
+      }
+      const Vec3<R> w0 = dir == 0 ? matvec(U, h0) : matvec_dag(U, h0);
+      const Vec3<R> w1 = dir == 0 ? matvec(U, h1) : matvec_dag(U, h1);
+      h[0] = vadd(h[0], w0);
+      h[1] = vadd(h[1], w1);
+      Vec3<R> r0, r1;
+      isigma(k, w0, w1, r0, r1);
+      if (dir == 0) {
+        h[2] = vaxpy(R(-1), r0, h[2]);
+        h[3] = vaxpy(R(-1), r1, h[3]);
+      } else {
+        h[2] = vadd(h[2], r0);
+        h[3] = vadd(h[3], r1);
+      }
+    }
+  }
+}
+
+// SRC, OPU, OPL < 0: taken from the arguments at run time. TPC: the line length tp as a
+// compile-time constant (128: n = 4 sites per group, 32 lanes, so that every load's component
+// offset is an immediate), or 0 to read the layout at run time.
+template <typename R, int SRC, int OPU, int OPL, int TPC>
+__global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide(const LineArgs<R> A) {
+  __shared__ MapStore<R> smap[2];
+  __shared__ double nrm_s[kWideCta];
+  const Geom& g = A.g;
+  const int src = SRC >= 0 ? SRC : A.src;
+  const int opu = OPU >= 0 ? OPU : A.opu;
+  const int opl = OPL >= 0 ? OPL : A.opl;
+  static_assert(TPC == 0 || TPC == 128, "compiled line lengths: run time or 128");
+  const int tp = TPC ? TPC : g.tp, n = TPC ? TPC / 32 : g.n, lpl = TPC ? 32 : g.lpl;
+  const int LPC = kWideCta / tp;  // lines per CTA; threads past LPC * tp idle
+  const int q = threadIdx.x;
+  const int li = q / tp;
+  const bool member = li < LPC;   // the thread belongs to one of the CTA's lines
+  const int sl = member ? q - li * tp : 0;  // its slot
+  const int m = sl / lpl;
+  const int j = q % lpl;          // = sl % lpl for members (tp and 32 are multiples of lpl)
+  const int t = n * j + m;
+  const int q0 = li * tp + j;     // the CTA thread holding site 0 of this thread's group
+  const int lg_raw = blockIdx.x * LPC + li;
+  const bool line_ok = member && lg_raw < A.nrhs * g.Nl;
+  int rhs, l;
+  line_rhs(line_ok ? lg_raw : 0, A.nrhs, g, rhs, l);
+  const bool valid = line_ok && t < g.T;  // owns a site (else padding or idle)
+  const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
+
+  Vec3<R> v[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) v[s] = vzero<R>();
+  if (valid) {
+    if (src == SRC_HOP) {
+      if constexpr (std::is_same<R, df64>::value)
+        hop_site_rolled<R, TPC>(v, A, rhs, l, sl);
+      else
+        hop_site<R, TPC>(v, A, rhs, l, sl);
+    } else {
+      if (opu != OP_SKIP) {
+        v[0] = ldvec(A.src_up + base, tp, sl);
+        v[1] = ldvec(A.src_up + base + 3 * tp, tp, sl);
+      }
+      if (opl != OP_SKIP) {
+        v[2] = ldvec(A.src_lo + base, tp, sl);
+        v[3] = ldvec(A.src_lo + base + 3 * tp, tp, sl);
+      }
+    }
+    if (A.xpre) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) v[s] = vaxpy(A.apre, v[s], ldvec(A.xpre + base + 3 * s * tp, tp, sl));
+    }
+  }
+
+  // time-line solves: site maps to shared memory, one barrier, in-group and lane composition
+  const bool solve_u = opu == OP_FWD || opu == OP_BWD;
+  const bool solve_l = opl == OP_FWD || opl == OP_BWD;
+  if (solve_u) put_map(smap[0], q, site_map(v[0], v[1], valid, A.inv_mu));
+  if (solve_l) put_map(smap[1], q, site_map(v[2], v[3], valid, A.inv_mu));
+  if (solve_u || solve_l) __syncthreads();
+  const Cx<R>* K_line = A.lamf + (size_t)l * 9;
+  if (opu == OP_FWD) solve_half_wide<R, true>(v[0], v[1], smap[0], member, q0, m, n, lpl, j, valid, K_line, A.bc);
+  if (opu == OP_BWD) solve_half_wide<R, false>(v[0], v[1], smap[0], member, q0, m, n, lpl, j, valid, K_line, A.bc);
+  if (opl == OP_FWD) solve_half_wide<R, true>(v[2], v[3], smap[1], member, q0, m, n, lpl, j, valid, K_line, A.bc);
+  if (opl == OP_BWD) solve_half_wide<R, false>(v[2], v[3], smap[1], member, q0, m, n, lpl, j, valid, K_line, A.bc);
+
+  R nrm = R(0);
+  if (line_ok) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int op = h ? opl : opu;
+      if (op == OP_SKIP) continue;
+      const int dh = A.swap_out ? 1 - h : h;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int comp0 = dh * 6 + s * 3;
+        Vec3<R> val = valid ? v[2 * h + s] : vzero<R>();
+        if (A.xpost) val = vaxpy(A.apost, val, ldvec_stream(A.xpost + base + comp0 * tp, tp, sl));
+        if (A.stream_out)
+          stvec_stream(A.out + base + comp0 * tp, tp, sl, val);
+        else
+          stvec(A.out + base + comp0 * tp, tp, sl, val);
+        if (A.norm2) nrm += vnorm2(val);
+      }
+    }
+  }
+  if (A.norm2) {
+    // one atomic per line: warp sums where a line is whole warps, else a per-line loop
+    const int lane = q & 31;
+    double dn = (double)nrm;
+    if (tp % 32 == 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(kFull, dn, o);
+      if (lane == 0) nrm_s[q >> 5] = dn;
+      __syncthreads();
+      if (line_ok && sl == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < tp / 32; ++i) sum += nrm_s[(li * tp >> 5) + i];
+        atomicAdd(A.norm2 + rhs, sum);
+      }
+    } else {
+      nrm_s[q] = dn;
+      __syncthreads();
+      if (line_ok && sl == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < tp; ++i) sum += nrm_s[li * tp + i];
+        atomicAdd(A.norm2 + rhs, sum);
+      }
+    }
+  }
+}
+
+}  // namespace wide
+
+// launch of the kernel variant for `kind` (LineKind) over all lines of all right-hand sides;
+// instantiated for float in wf_wide.cu and for double-float in wf_wide_df.cu
+template <typename R>
+void launch_line_wide(const LineArgs<R>& a, int kind, cudaStream_t s) {
+  if (!wide_supported(a.g)) throw Error(1, "wide line kernel: unsupported line layout");
+  const int LPC = wide::kWideCta / a.g.tp;
+  const int lines = a.nrhs * a.g.Nl;
+  const int blocks = (lines + LPC - 1) / LPC;
+  const bool t128 = a.g.tp == 128 && a.g.n == 4 && a.g.lpl == 32;
+#define WF_KW(SRCV, OPUV, OPLV)                                                         \
+  do {                                                                                  \
+    if (t128)                                                                           \
+      wide::k_line_wide<R, SRCV, OPUV, OPLV, 128><<<blocks, wide::kWideCta, 0, s>>>(a); \
+    else                                                                                \
+      wide::k_line_wide<R, SRCV, OPUV, OPLV, 0><<<blocks, wide::kWideCta, 0, s>>>(a);   \
+  } while (0)
+  switch (kind) {
+    case LK_SCHUR_A: WF_KW(SRC_LOAD, OP_FWD, OP_SKIP); break;
+    case LK_SCHUR_B: WF_KW(SRC_HOP, OP_FWD, OP_BWD); break;
+    case LK_SCHUR_C: WF_KW(SRC_HOP, OP_COPY, OP_BWD); break;
+    default: WF_KW(-1, -1, -1); break;
+  }
+#undef WF_KW
+  WF_CUDA(cudaGetLastError());
+}
+
+}  // namespace wf

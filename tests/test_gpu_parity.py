@@ -195,3 +195,24 @@ def test_fp64_iterations_match_oracle():
         assert status == wf.WF_OK
         assert abs(iters[0] - it_ref) <= max(2, it_ref // 20), (name, iters[0], it_ref)
     w.close()
+
+
+@pytest.mark.parametrize("L,T", [(4, 16), (4, 128), (4, 7)])
+@pytest.mark.parametrize("method", [wf.WF_TEMPORAL_SCHUR, wf.WF_EO4D, wf.WF_TEMPORAL])
+def test_solve_with_double_float_steps(monkeypatch, L, T, method):
+    """WF_DF64=1 at handle creation: the FP64 steps of an FP32 solve (reliable updates, S_L, S_R,
+    the comparators' reconstructions) run in double-float; the FP64 true residual still decides."""
+    if method == wf.WF_EO4D and T % 2:
+        pytest.skip("the 4-D checkerboard needs an even T")
+    monkeypatch.setenv("WF_DF64", "1")
+    p = W.Params(L, T, 0.074, xi=3.5, bc=-1)
+    U = S.random_gauge(L, T, 0.25, 41)
+    eta = S.gaussian_source(L, T, 42, nrhs=2)
+    w = wf.Wilson(L, T, 0.074, kappa_t=3.5 * 0.074, bc=-1)
+    w.load_gauge(U)
+    x, iters, res, status = w.solve(_dev(eta), tol=1e-10, method=method, precision=wf.WF_FP32)
+    assert status == wf.WF_OK and all(r <= 1e-10 for r in res)
+    psi = _host(x)
+    for k in range(eta.shape[0]):
+        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+    w.close()
