@@ -411,6 +411,118 @@ def run_apply(args, prm, U, eta):
     return 0
 
 
+def _timed_solve(wf, torch, w, stream, rhs, x, method, prec, tol, reps=1):
+    """(seconds per solve, iterations, true residuals) after one warm-up solve."""
+    nr = rhs.shape[0]
+    wf.wf_solve(w.h, rhs, x, nr, tol, method, prec, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        st, it, res = wf.wf_solve(w.h, rhs, x, nr, tol, method, prec, 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if st != wf.WF_OK or max(res) > tol:
+        raise RuntimeError(f"solve failed: method {method}, status {st}, residuals {res}")
+    return e0.elapsed_time(e1) / reps / 1e3, list(it), list(res)
+
+
+METHOD_NAMES = {0: "unprec", 1: "eo4d", 2: "temporal", 3: "temporal_schur"}
+
+
+def run_methods(args):
+    """--mode methods: 16^3 x 128, xi = 3.5, one Gaussian source; every method in FP64 and in FP32
+    with FP64 reliable updates: iterations, time to solution, FP64 true residual."""
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+    import synthetic as S
+
+    prm, U, eta = S.workload("wilson_16c128_xi3.5")
+    stream = torch.cuda.Stream()
+    w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    w.set_stream(stream.cuda_stream)
+    w.load_gauge(U)
+    rhs = torch.from_numpy(eta).cuda()
+    x = torch.empty_like(rhs)
+    rows = []
+    for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32")):
+        for method in (wf.WF_UNPREC, wf.WF_EO4D, wf.WF_TEMPORAL, wf.WF_TEMPORAL_SCHUR):
+            t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, method, prec, args.tol)
+            rows.append({"method": METHOD_NAMES[method], "precision": pname, "iterations": it[0],
+                         "time_s": t, "true_residual": res[0]})
+    w.close()
+    print(json.dumps({"mode": "methods", "workload": "wilson_16c128_xi3.5: 16^3x128, xi=3.5, 1 Gaussian source",
+                      "tol": args.tol, "results": rows}))
+    return 0
+
+
+def run_sweep(args):
+    """--mode sweep: xi in {1, 3, 4.5, 6} on 12^3 x 48, 16^3 x 96 and 16^3 x 128, four Gaussian
+    sources per lattice in one call, kappa_s = 0.9 of the free critical value: temporal + 3-D Schur
+    against 4-D even-odd (FP32 iterations, FP64 reliable updates, FP64 true residual)."""
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+    import synthetic as S
+
+    stream = torch.cuda.Stream()
+    rows = []
+    for xi in (1.0, 3.0, 4.5, 6.0):
+        for L, T in ((12, 48), (16, 96), (16, 128)):
+            name = f"sweep_xi{xi:g}_{L}c{T}"
+            prm, U, eta = S.workload(name)
+            w = wf.Wilson(L, T, prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+            w.set_stream(stream.cuda_stream)
+            w.load_gauge(U)
+            rhs = torch.from_numpy(eta).cuda()
+            x = torch.empty_like(rhs)
+            r = {"workload": name, "xi": xi, "L": L, "T": T, "kappa_s": prm["kappa_s"], "nsrc": eta.shape[0]}
+            for method in (wf.WF_TEMPORAL_SCHUR, wf.WF_EO4D):
+                t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, method, wf.WF_FP32, args.tol, reps=3)
+                r[METHOD_NAMES[method]] = {"time_s": t, "iterations": max(it), "max_true_residual": max(res)}
+            r["time_ratio_eo4d_over_temporal_schur"] = r["eo4d"]["time_s"] / r["temporal_schur"]["time_s"]
+            r["iteration_ratio"] = r["eo4d"]["iterations"] / r["temporal_schur"]["iterations"]
+            rows.append(r)
+            w.close()
+    print(json.dumps({"mode": "sweep", "tol": args.tol, "results": rows}))
+    return 0
+
+
+def run_force(args):
+    """--mode force: the pseudofermion force on 8^3 x 32 and 16^3 x 64 (xi = 3), one Gaussian
+    pseudofermion on the odd 3-D parity, FP64 and FP32-inner CG to 1e-12: time and iterations."""
+    import numpy as np
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+    import synthetic as S
+
+    rows = []
+    for name in ("force_8c32_xi3", "force_16c64_xi3"):
+        prm, U, _ = S.workload(name, with_sources=False)
+        L, T = prm["L"], prm["T"]
+        V = L ** 3 * T
+        full = S.gaussian_source(L, T, prm["seed"] + 7)
+        t_, z, y, x = np.meshgrid(np.arange(T), np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+        odd = ((x + y + z) % 2) == 1
+        phi = torch.from_numpy(np.ascontiguousarray(full[odd])).cuda()
+        w = wf.Wilson(L, T, prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+        w.load_gauge(U)
+        F = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
+        r = {"workload": name, "L": L, "T": T}
+        for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32_inner")):
+            wf.wf_force(w.h, phi, F, prec, 1e-12)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Sv, it = wf.wf_force(w.h, phi, F, prec, 1e-12)
+            torch.cuda.synchronize()
+            r[pname] = {"time_s": time.perf_counter() - t0, "cg_iterations": it, "action": Sv}
+        w.close()
+        rows.append(r)
+    print(json.dumps({"mode": "force", "results": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,8 +534,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the same-GPU 4-D even-odd comparison")
-    ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
-                    help="apply: only FP32 M-hat applies (for kernel profiling)")
+    ap.add_argument("--mode", choices=["solve", "apply", "methods", "sweep", "force"], default="solve",
+                    help="apply: only FP32 M-hat applies (for kernel profiling); methods: every solve method "
+                         "on 16^3x128; sweep: temporal+Schur vs 4-D even-odd over xi; force: force timings")
     ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")
     ap.add_argument("--op", choices=["schur", "eo4d"], default="schur", help="operator of --mode apply")
     ap.add_argument("--workload", default=None, help="--mode apply only: another synthetic workload by name")
@@ -431,6 +544,8 @@ def main():
 
     import synthetic as S
 
+    if args.mode in ("methods", "sweep", "force"):
+        return {"methods": run_methods, "sweep": run_sweep, "force": run_force}[args.mode](args)
     name = WORKLOAD
     if args.workload:
         if args.mode != "apply" or args.workload not in S.WORKLOADS:

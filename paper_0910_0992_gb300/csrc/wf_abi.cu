@@ -216,6 +216,30 @@ bool use_tma_kernels(wf_handle* h) {
   return h->use_tma != 0;
 }
 
+// index tables for the wide kernels (built once per handle and per nrhs, on the handle's stream)
+void attach_tables(wf_handle* h, LineArgs<float>& a) {
+  const Geom& g = h->g;
+  wf::DevBuf& nb = h->nbr_tab[a.parity];
+  if (!nb.p) {
+    std::vector<int> t((size_t)g.Nl * 6);
+    for (int l = 0; l < g.Nl; ++l) neighbour_lines(g, a.parity, l, &t[(size_t)l * 6]);
+    nb.ensure(t.size() * sizeof(int), h->stream);
+    WF_CUDA(cudaMemcpyAsync(nb.p, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    WF_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  auto& ob = h->order_tab[a.nrhs];
+  if (!ob) {
+    std::vector<int2> t((size_t)a.nrhs * g.Nl);
+    for (size_t i = 0; i < t.size(); ++i) line_rhs((int)i, a.nrhs, g, t[i].x, t[i].y);
+    ob.reset(new wf::DevBuf());
+    ob->ensure(t.size() * sizeof(int2), h->stream);
+    WF_CUDA(cudaMemcpyAsync(ob->p, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+    WF_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  a.nbr = nb.as<int>();
+  a.order = ob->as<int2>();
+}
+
 template <typename R>
 void launch_schur_hop(wf_handle* h, const LineArgs<R>& a, int kind, bool tma) {
   if constexpr (sizeof(R) == 4) {
@@ -223,6 +247,14 @@ void launch_schur_hop(wf_handle* h, const LineArgs<R>& a, int kind, bool tma) {
       LineArgs<R> b = a;
       if (const char* e = std::getenv("WF_TEST_DROP_COPY")) b.drop_job = std::atoi(e);  // fault injection (tests)
       launch_line_tma(b, kind, h->tma_err.as<int>(), h->stream);
+      return;
+    }
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (h->axial) {
+      LineArgs<R> b = a;
+      attach_tables(h, b);
+      launch_line<R>(b, kind, h->axial, h->stream);
       return;
     }
   }

@@ -245,9 +245,13 @@ template <typename R>
 struct SpatialLinkNC {
   static constexpr int value = 9;
 };
+#ifndef WF_F32_LINK_NC
+#define WF_F32_LINK_NC 6
+#endif
 template <>
 struct SpatialLinkNC<float> {
-  static constexpr int value = 6;
+  static_assert(WF_F32_LINK_NC == 6 || WF_F32_LINK_NC == 9, "FP32 links: 6 (two rows) or 9 entries");
+  static constexpr int value = WF_F32_LINK_NC;
 };
 
 }  // namespace wf

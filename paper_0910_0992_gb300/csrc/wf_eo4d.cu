@@ -10,6 +10,7 @@
 // site; consecutive threads take consecutive h, so every load is coalesced.
 // Links are the handle's (same frame as the temporal preconditioner: in the axial frame
 // U_t = 1 except the boundary link P), read through the line layout's index maps.
+#include <cstring>
 #include <type_traits>
 
 #include "wf_internal.h"
@@ -179,6 +180,7 @@ static void launch_dslash4_impl(const EoArgs<R>& a, bool axial, cudaStream_t s) 
 static EoArgs<df64> eo_args_df(const EoArgs<double>& a) {
   auto cv = [](const Cx<double>* p) { return reinterpret_cast<const Cx<df64>*>(p); };
   EoArgs<df64> b;
+  std::memset(&b, 0, sizeof(b));  // every field defined, including ones added later
   b.g = a.g;
   b.par = a.par;
   b.nrhs = a.nrhs;

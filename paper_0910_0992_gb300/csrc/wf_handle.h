@@ -35,6 +35,9 @@ struct wf_handle {
   // axial frame: ut64 holds the rotation g(x) instead of U_t; P per line
   wf::DevBuf pl64[2], pl32[2];
   wf::DevBuf tma_err;  // error word of the TMA-fed kernels (bounded waits)
+  // index tables of the wide kernels: neighbour lines per parity, traversal order per nrhs
+  wf::DevBuf nbr_tab[2];
+  std::map<int, std::unique_ptr<wf::DevBuf>> order_tab;
   int use_tma = -1;    // -1: not decided yet (environment WF_TMA=1 turns the TMA-fed hop kernels on)
   wf::DevBuf iflag;
   std::map<std::string, std::unique_ptr<wf::DevBuf>> ws;  // named work buffers

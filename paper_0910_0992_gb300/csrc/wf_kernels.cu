@@ -12,6 +12,7 @@
 // each carries only its own code; every other use goes through one kernel that selects
 // them at run time.
 #include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "wf_internal.h"
@@ -57,8 +58,16 @@ __device__ __forceinline__ void apply_op(int op, Vec3<R> (&v)[NMAX][4], int s0, 
 }
 
 // SRC, OPU, OPL < 0: taken from the arguments at run time
+#ifndef WF_LINE_MINB_F64
+#define WF_LINE_MINB_F64 3
+#endif
+template <typename R>
+struct LineMinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? WF_LINE_MINB : WF_LINE_MINB_F64;
+};
+
 template <typename R, bool AX, int SRC, int OPU, int OPL>
-__global__ void __launch_bounds__(kLineThreads, WF_LINE_MINB) k_line(const LineArgs<R> A) {
+__global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(const LineArgs<R> A) {
   const Geom& g = A.g;
   const int src = SRC >= 0 ? SRC : A.src;
   const int opu = OPU >= 0 ? OPU : A.opu;
@@ -196,6 +205,7 @@ template <typename A, typename B>
 static const Cx<A>* as_cx(const Cx<B>* p) { return reinterpret_cast<const Cx<A>*>(p); }
 static LineArgs<df64> line_args_df(const LineArgs<double>& a) {
   LineArgs<df64> b;
+  std::memset(&b, 0, sizeof(b));  // every field defined, including ones added later
   b.g = a.g;
   b.parity = a.parity;
   b.nrhs = a.nrhs;
@@ -222,6 +232,8 @@ static LineArgs<df64> line_args_df(const LineArgs<double>& a) {
   b.bc = df64(a.bc);
   b.drop_job = -1;
   b.df = 0;
+  b.order = a.order;
+  b.nbr = a.nbr;
   return b;
 }
 

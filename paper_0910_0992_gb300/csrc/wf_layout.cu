@@ -363,18 +363,19 @@ void launch_rotate_links(const Geom& g, Cx<double>* us[2], const Cx<double>* gg[
 
 // FP32 spatial links: rows 0 and 1 of every FP64 link ([3][Nl][9][tp] -> [3][Nl][6][tp])
 __global__ void k_d2f_links(const Cx<double>* __restrict__ in, Cx<float>* __restrict__ out, size_t nlinks, int tp) {
-  const size_t total = nlinks * 6 * (size_t)tp;
+  constexpr int NC = SpatialLinkNC<float>::value;
+  const size_t total = nlinks * NC * (size_t)tp;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t sl = i % tp;
-    const size_t e = (i / tp) % 6;
-    const size_t lk = i / ((size_t)tp * 6);
+    const size_t e = (i / tp) % NC;
+    const size_t lk = i / ((size_t)tp * NC);
     const Cx<double> v = in[(lk * 9 + e) * tp + sl];
     out[i] = mk<float>((float)v.re, (float)v.im);
   }
 }
 
 void launch_d2f_links(const Cx<double>* in, Cx<float>* out, size_t nlinks, int tp, cudaStream_t s) {
-  k_d2f_links<<<grid_for(nlinks * 6 * (size_t)tp), kThreads, 0, s>>>(in, out, nlinks, tp);
+  k_d2f_links<<<grid_for(nlinks * SpatialLinkNC<float>::value * (size_t)tp), kThreads, 0, s>>>(in, out, nlinks, tp);
   WF_CUDA(cudaGetLastError());
 }
 

@@ -66,6 +66,11 @@ struct LineArgs {
   R inv_mu, bc;
   int drop_job;  // TMA-fed kernel only: skip the bulk copy of this job (fault injection), -1: none
   int df;        // R = double only: compute in double-float (FP64 storage, FP32 arithmetic)
+  // optional index tables (wide kernels; null: computed in the kernel): the (rhs, line) of every
+  // traversal position [nrhs * Nl] (line_rhs), and the six neighbour lines of every output line
+  // [Nl][6] (neighbour_lines, output parity)
+  const int2* order;
+  const int* nbr;
 };
 
 // Order in which the line kernels visit (rhs, line) pairs. Right-hand sides are processed in
@@ -81,12 +86,13 @@ struct LineArgs {
 #endif
 constexpr int kRhsGroup = WF_RHS_GROUP;
 
-// traversal index -> (rhs, line)
-__device__ __forceinline__ void line_rhs(int lg, int nrhs, const Geom& g, int& rhs, int& l) {
+// traversal index -> (rhs, line); host and device (the wide kernels read it from a table)
+__host__ __device__ __forceinline__ void line_rhs(int lg, int nrhs, const Geom& g, int& rhs, int& l) {
   const int per_group = kRhsGroup * g.Nl;
   const int grp = lg / per_group;
   const int r = lg - grp * per_group;
-  const int gsize = min(kRhsGroup, nrhs - grp * kRhsGroup);
+  const int left = nrhs - grp * kRhsGroup;
+  const int gsize = left < kRhsGroup ? left : kRhsGroup;
   const int pos = r / gsize;  // position of the line in the tiled order
   rhs = grp * kRhsGroup + (r - pos * gsize);
   const int xh = pos % g.Lh;

@@ -35,8 +35,10 @@ namespace wide {
 
 constexpr int kWideCta = 128;  // threads per CTA
 constexpr int kMapFields = 13;  // c (two spins x three colours, complex) and a
+// resident CTAs per SM the kernels are compiled for. FP32: 7 (72 registers, no spills), measured
+// on GB300 with 12 sources 1.07-1.15x faster than 5 (96 registers) and level with 8 (spills)
 #ifndef WF_WIDE_MINB_F32
-#define WF_WIDE_MINB_F32 5
+#define WF_WIDE_MINB_F32 7
 #endif
 #ifndef WF_WIDE_MINB_F64
 #define WF_WIDE_MINB_F64 3
@@ -58,6 +60,23 @@ struct WideMinBlocks<df64> {
 };
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// the six neighbour lines of line l: from the table if the caller passed one
+template <typename R>
+__device__ __forceinline__ void neighbours(const LineArgs<R>& A, int l, int (&nb)[6]) {
+  if (A.nbr) {
+    const int2* t = reinterpret_cast<const int2*>(A.nbr + (size_t)l * 6);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int2 v = t[i];
+      nb[2 * i] = v.x;
+      nb[2 * i + 1] = v.y;
+    }
+  } else {
+    neighbour_lines(A.g, A.parity, l, nb);
+  }
+}
+
 
 // the affine map e -> c + a e on a spin half (two spins)
 template <typename R>
@@ -132,7 +151,7 @@ __device__ __forceinline__ void hop_site_rolled(Vec3<R> (&h)[4], const LineArgs<
   const Geom& g = A.g;
   const int tp = TPC ? TPC : g.tp, Nl = g.Nl;
   int nb[6];
-  neighbour_lines(g, A.parity, l, nb);
+  neighbours(A, l, nb);
 #pragma unroll
   for (int s = 0; s < 4; ++s) h[s] = vzero<R>();
   constexpr int LNC = SpatialLinkNC<R>::value;
@@ -226,7 +245,7 @@ __device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, 
   const Geom& g = A.g;
   const int tp = TPC ? TPC : g.tp, Nl = g.Nl;
   int nb[6];
-  neighbour_lines(g, A.parity, l, nb);
+  neighbours(A, l, nb);
 #pragma unroll
   for (int s = 0; s < 4; ++s) h[s] = vzero<R>();
 #pragma unroll
@@ -296,7 +315,13 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide
   const int lg_raw = blockIdx.x * LPC + li;
   const bool line_ok = member && lg_raw < A.nrhs * g.Nl;
   int rhs, l;
-  line_rhs(line_ok ? lg_raw : 0, A.nrhs, g, rhs, l);
+  if (A.order) {
+    const int2 o = A.order[line_ok ? lg_raw : 0];
+    rhs = o.x;
+    l = o.y;
+  } else {
+    line_rhs(line_ok ? lg_raw : 0, A.nrhs, g, rhs, l);
+  }
   const bool valid = line_ok && t < g.T;  // owns a site (else padding or idle)
   const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
 
