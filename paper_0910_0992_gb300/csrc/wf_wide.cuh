@@ -290,12 +290,70 @@ __device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, 
   }
 }
 
+// Time-line solve of one spin of a lane group's four sites (tp = 128: n = 4, 32 lanes), three
+// colours held by the thread: the recurrence over the four sites in registers, the group
+// composites scanned over the 32 lanes, the wrap through K within the warp.
+template <typename R, bool FWD>
+__device__ __forceinline__ void spin_solve4(Vec3<R> (&w)[4], int j, int T, const Cx<R>* __restrict__ K_line,
+                                            R inv_mu, R bc) {
+  Vec3<R> c = vzero<R>();
+  R a = R(1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int mm = FWD ? i : 3 - i;
+    if (4 * j + mm >= T) continue;  // padding: identity
+    c = vscale(inv_mu, vadd(w[mm], c));
+    a *= inv_mu;
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const R an = FWD ? shfl_up_r(a, d, 32) : shfl_down_r(a, d, 32);
+    const Vec3<R> cn = FWD ? vshfl_up(c, d, 32) : vshfl_down(c, d, 32);
+    if (FWD ? j >= d : j + d < 32) {
+      c = vaxpy(a, cn, c);
+      a *= an;
+    }
+  }
+  // the line's composite is at its last lane in time order; the wrap value enters the first
+  const Vec3<R> C = vshfl_idx(c, FWD ? 31 : 0, 32);
+  const Mat3<R> K = ldmat(K_line, 1, 0);
+  Vec3<R> e = vscale(bc, FWD ? matvec_dag(K, C) : matvec(K, C));
+  const R ap = FWD ? shfl_up_r(a, 1, 32) : shfl_down_r(a, 1, 32);
+  const Vec3<R> cp = FWD ? vshfl_up(c, 1, 32) : vshfl_down(c, 1, 32);
+  if (FWD ? j > 0 : j < 31) e = vaxpy(ap, e, cp);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int mm = FWD ? i : 3 - i;
+    if (4 * j + mm >= T) {
+      w[mm] = vzero<R>();
+      continue;
+    }
+    e = vscale(inv_mu, vadd(w[mm], e));
+    w[mm] = e;
+  }
+}
+
+// one atomic per line for |out|^2 (lines of whole warps)
+template <typename R>
+__device__ __forceinline__ void line_norm_whole_warps(double* nrm_s, R nrm, int q, int tp, int li, int sl, bool line_ok,
+                                                      double* norm2, int rhs) {
+  double dn = (double)nrm;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(kFull, dn, o);
+  if ((q & 31) == 0) nrm_s[q >> 5] = dn;
+  __syncthreads();
+  if (line_ok && sl == 0) {
+    double sum = 0.0;
+    for (int i = 0; i < tp / 32; ++i) sum += nrm_s[(li * tp >> 5) + i];
+    atomicAdd(norm2 + rhs, sum);
+  }
+}
+
 // SRC, OPU, OPL < 0: taken from the arguments at run time. TPC: the line length tp as a
 // compile-time constant (128: n = 4 sites per group, 32 lanes, so that every load's component
 // offset is an immediate), or 0 to read the layout at run time.
 template <typename R, int SRC, int OPU, int OPL, int TPC>
 __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide(const LineArgs<R> A) {
-  __shared__ MapStore<R> smap[2];
   __shared__ double nrm_s[kWideCta];
   const Geom& g = A.g;
   const int src = SRC >= 0 ? SRC : A.src;
@@ -350,6 +408,46 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide
     }
   }
 
+  if constexpr (TPC == 128) {
+    // transposed solve: thread (m, j) hands site t = 4 j + m to shared memory and takes back spin
+    // m of the four sites of group j (one line per CTA)
+    __shared__ Cx<R> tr[NSPIN_C][4][32];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tr[3 * s + c][m][j] = v[s].c[c];
+    __syncthreads();
+    const int sp = m;  // the spin this warp solves and stores
+    Vec3<R> w[4];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w[mm].c[c] = tr[3 * sp + c][mm][j];
+    const int h = sp >> 1;
+    const int op = h ? opl : opu;
+    const Cx<R>* K_line = A.lamf + (size_t)l * 9;
+    if (op == OP_FWD) spin_solve4<R, true>(w, j, g.T, K_line, A.inv_mu, A.bc);
+    if (op == OP_BWD) spin_solve4<R, false>(w, j, g.T, K_line, A.inv_mu, A.bc);
+    R nrm = R(0);
+    if (line_ok && op != OP_SKIP) {
+      const int dh = A.swap_out ? 1 - h : h;
+      const int comp0 = dh * 6 + (sp & 1) * 3;
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        const int slot = mm * 32 + j;
+        Vec3<R> val = 4 * j + mm < g.T ? w[mm] : vzero<R>();
+        if (A.xpost) val = vaxpy(A.apost, val, ldvec_stream(A.xpost + base + comp0 * tp, tp, slot));
+        if (A.stream_out)
+          stvec_stream(A.out + base + comp0 * tp, tp, slot, val);
+        else
+          stvec(A.out + base + comp0 * tp, tp, slot, val);
+        if (A.norm2) nrm += vnorm2(val);
+      }
+    }
+    if (A.norm2) line_norm_whole_warps(nrm_s, nrm, q, tp, li, sl, line_ok, A.norm2, rhs);
+    return;
+  } else {
+  __shared__ MapStore<R> smap[2];
   // time-line solves: site maps to shared memory, one barrier, in-group and lane composition
   const bool solve_u = opu == OP_FWD || opu == OP_BWD;
   const bool solve_l = opl == OP_FWD || opl == OP_BWD;
@@ -405,6 +503,7 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide
         atomicAdd(A.norm2 + rhs, sum);
       }
     }
+  }
   }
 }
 
