@@ -43,19 +43,26 @@ constexpr int kMapFields = 13;  // c (two spins x three colours, complex) and a
 #ifndef WF_WIDE_MINB_F64
 #define WF_WIDE_MINB_F64 3
 #endif
-template <typename R>
+#ifndef WF_EARLY_X
+#define WF_EARLY_X 1
+#endif
+#ifndef WF_WIDE_MINB_F32_C
+#define WF_WIDE_MINB_F32_C WF_WIDE_MINB_F32
+#endif
+// KC: the K-c variant (its own bound: it holds the early-loaded post-axpy operand)
+template <typename R, bool KC>
 struct WideMinBlocks {
   static constexpr int value = WF_WIDE_MINB_F64;
 };
-template <>
-struct WideMinBlocks<float> {
-  static constexpr int value = WF_WIDE_MINB_F32;
+template <bool KC>
+struct WideMinBlocks<float, KC> {
+  static constexpr int value = KC ? WF_WIDE_MINB_F32_C : WF_WIDE_MINB_F32;
 };
 #ifndef WF_WIDE_MINB_DF
 #define WF_WIDE_MINB_DF 3
 #endif
-template <>
-struct WideMinBlocks<df64> {
+template <bool KC>
+struct WideMinBlocks<df64, KC> {
   static constexpr int value = WF_WIDE_MINB_DF;
 };
 
@@ -353,7 +360,8 @@ __device__ __forceinline__ void line_norm_whole_warps(double* nrm_s, R nrm, int 
 // compile-time constant (128: n = 4 sites per group, 32 lanes, so that every load's component
 // offset is an immediate), or 0 to read the layout at run time.
 template <typename R, int SRC, int OPU, int OPL, int TPC>
-__global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide(const LineArgs<R> A) {
+__global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
+    k_line_wide(const LineArgs<R> A) {
   __shared__ double nrm_s[kWideCta];
   const Geom& g = A.g;
   const int src = SRC >= 0 ? SRC : A.src;
@@ -412,31 +420,46 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R>::value) k_line_wide
     // transposed solve: thread (m, j) hands site t = 4 j + m to shared memory and takes back spin
     // m of the four sites of group j (one line per CTA)
     __shared__ Cx<R> tr[NSPIN_C][4][32];
+    const int sp = m;  // the spin this warp solves and stores
+    const int h = sp >> 1;
+    const int op = h ? opl : opu;
+    const int dh = A.swap_out ? 1 - h : h;
+    const int comp0 = dh * 6 + (sp & 1) * 3;
+    // K-c's post-axpy operand is loaded now, so that its latency overlaps the solve (the other
+    // variants load it at the store)
+    constexpr bool kEarlyX = WF_EARLY_X && SRC == SRC_HOP && OPU == OP_COPY && OPL == OP_BWD;
+    Vec3<R> xp[4];
+    if constexpr (kEarlyX) {
+      const bool want_x = A.xpost && line_ok && op != OP_SKIP;
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm)
+        xp[mm] = want_x ? ldvec_stream(A.xpost + base + comp0 * tp, tp, mm * 32 + j) : vzero<R>();
+    }
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int c = 0; c < 3; ++c) tr[3 * s + c][m][j] = v[s].c[c];
     __syncthreads();
-    const int sp = m;  // the spin this warp solves and stores
     Vec3<R> w[4];
 #pragma unroll
     for (int mm = 0; mm < 4; ++mm)
 #pragma unroll
       for (int c = 0; c < 3; ++c) w[mm].c[c] = tr[3 * sp + c][mm][j];
-    const int h = sp >> 1;
-    const int op = h ? opl : opu;
     const Cx<R>* K_line = A.lamf + (size_t)l * 9;
     if (op == OP_FWD) spin_solve4<R, true>(w, j, g.T, K_line, A.inv_mu, A.bc);
     if (op == OP_BWD) spin_solve4<R, false>(w, j, g.T, K_line, A.inv_mu, A.bc);
     R nrm = R(0);
     if (line_ok && op != OP_SKIP) {
-      const int dh = A.swap_out ? 1 - h : h;
-      const int comp0 = dh * 6 + (sp & 1) * 3;
 #pragma unroll
       for (int mm = 0; mm < 4; ++mm) {
         const int slot = mm * 32 + j;
         Vec3<R> val = 4 * j + mm < g.T ? w[mm] : vzero<R>();
-        if (A.xpost) val = vaxpy(A.apost, val, ldvec_stream(A.xpost + base + comp0 * tp, tp, slot));
+        if (A.xpost) {
+          if constexpr (kEarlyX)
+            val = vaxpy(A.apost, val, xp[mm]);
+          else
+            val = vaxpy(A.apost, val, ldvec_stream(A.xpost + base + comp0 * tp, tp, slot));
+        }
         if (A.stream_out)
           stvec_stream(A.out + base + comp0 * tp, tp, slot, val);
         else
