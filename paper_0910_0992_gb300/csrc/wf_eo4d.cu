@@ -74,13 +74,13 @@ __global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs
       const Mat3<R> U = ldlink(lk, tp, sl);
       Vec3<R> s0, s1;
       isigma(k, d0, d1, s0, s1);
-      Vec3<R> h0, h1;
+      Vec3<R> h0, h1;  // the projectors' factor 1/2 joins 1 / gamma_f below (exact)
       if (dir == 0) {
-        h0 = vscale(R(0.5), vadd(u0, s0));
-        h1 = vscale(R(0.5), vadd(u1, s1));
+        h0 = vadd(u0, s0);
+        h1 = vadd(u1, s1);
       } else {
-        h0 = vscale(R(0.5), vaxpy(R(-1), s0, u0));
-        h1 = vscale(R(0.5), vaxpy(R(-1), s1, u1));
+        h0 = vaxpy(R(-1), s0, u0);
+        h1 = vaxpy(R(-1), s1, u1);
       }
       Vec3<R> w0 = dir == 0 ? matvec(U, h0) : matvec_dag(U, h0);
       Vec3<R> w1 = dir == 0 ? matvec(U, h1) : matvec_dag(U, h1);
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs
     }
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) acc[s] = vscale(A.inv_gf, acc[s]);
+  for (int s = 0; s < 4; ++s) acc[s] = vscale(R(0.5) * A.inv_gf, acc[s]);
 
   // temporal hops: P_- U_t(t) psi(t+1) on spins 2-3, P_+ U_t^dag(t-1) psi(t-1) on spins 0-1
   {

@@ -476,14 +476,13 @@ __device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArg
         Mat3<R> U = ldlink(lk, tp, sl);
         Vec3<R> s0, s1;
         isigma(k, d0, d1, s0, s1);
-        const R half = R(0.5);
-        Vec3<R> h0, h1;
+        Vec3<R> h0, h1;  // the projectors' factor 1/2 is applied once at the end (exact)
         if (dir == 0) {
-          h0 = vscale(half, vadd(u0, s0));
-          h1 = vscale(half, vadd(u1, s1));
+          h0 = vadd(u0, s0);
+          h1 = vadd(u1, s1);
         } else {
-          h0 = vscale(half, vaxpy(R(-1), s0, u0));
-          h1 = vscale(half, vaxpy(R(-1), s1, u1));
+          h0 = vaxpy(R(-1), s0, u0);
+          h1 = vaxpy(R(-1), s1, u1);
         }
         Vec3<R> w0 = dir == 0 ? matvec(U, h0) : matvec_dag(U, h0);
         Vec3<R> w1 = dir == 0 ? matvec(U, h1) : matvec_dag(U, h1);
@@ -501,6 +500,10 @@ __device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArg
       }
     }
   }
+#pragma unroll
+  for (int m = 0; m < NMAX; ++m)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) h[m][s] = vscale(R(0.5), h[m][s]);
 }
 
 }  // namespace wf

@@ -271,14 +271,13 @@ __device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, 
       const Mat3<R> U = ldlink(lk, tp, sl);
       Vec3<R> s0, s1;
       isigma(k, d0, d1, s0, s1);
-      const R half = R(0.5);
-      Vec3<R> h0, h1;
+      Vec3<R> h0, h1;  // the projectors' factor 1/2 is applied once at the end (exact)
       if (dir == 0) {
-        h0 = vscale(half, vadd(u0, s0));
-        h1 = vscale(half, vadd(u1, s1));
+        h0 = vadd(u0, s0);
+        h1 = vadd(u1, s1);
       } else {
-        h0 = vscale(half, vaxpy(R(-1), s0, u0));
-        h1 = vscale(half, vaxpy(R(-1), s1, u1));
+        h0 = vaxpy(R(-1), s0, u0);
+        h1 = vaxpy(R(-1), s1, u1);
       }
       const Vec3<R> w0 = dir == 0 ? matvec(U, h0) : matvec_dag(U, h0);
       const Vec3<R> w1 = dir == 0 ? matvec(U, h1) : matvec_dag(U, h1);
@@ -295,6 +294,8 @@ __device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, 
       }
     }
   }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) h[s] = vscale(R(0.5), h[s]);
 }
 
 // Time-line solve of one spin of a lane group's four sites (tp = 128: n = 4, 32 lanes), three
