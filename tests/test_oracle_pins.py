@@ -291,7 +291,7 @@ def test_condition_ordering_anisotropic():
 
 
 def test_condition_isotropic_no_gain():
-    """xi = 1 (§III.D, 'no advantage in the isotropic case'): kappa(temporal+Schur) >= kappa(4D eo)."""
+    """xi = 1 (§III.D: the paper finds no gain for isotropic lattices): kappa(temporal+Schur) >= kappa(4D eo)."""
     p = W.Params(2, 8, 0.11, kappa_t=0.11, bc=-1)
     U = S.random_gauge(2, 8, 0.3, 2)
     r = _sigma_ratios(U, p)
