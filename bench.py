@@ -368,6 +368,7 @@ def run_ours(args, prm, U, eta):
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
                          "avg_launch_ms": ms_l / n_l},
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "hop_kernels_autotuned": _hop_config(wf, w, nsrc),
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": e2e,
@@ -409,6 +410,14 @@ def run_apply(args, prm, U, eta):
     print(json.dumps({"mode": "apply", "workload": f"{prm['L']}^3x{prm['T']}", "nrhs": nr, "kernels": rows}))
     w.close()
     return 0
+
+
+def _hop_config(wf, w, nrhs):
+    c = wf.wf_hop_config(w.h, nrhs)
+    if c is None:
+        return None
+    return {"variant": {1: "one thread per site", 2: "sites per lane"}.get(c[0], c[0]), "tile_rows": c[1],
+            "kb_plus_kc_ms_x3": c[2]}
 
 
 def _timed_solve(wf, torch, w, stream, rhs, x, method, prec, tol, reps=1):
@@ -481,6 +490,7 @@ def run_sweep(args):
                 t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, method, wf.WF_FP32, args.tol, reps=3)
                 r[METHOD_NAMES[method]] = {"time_s": t, "iterations": max(it), "max_true_residual": max(res)}
             r["time_ratio_eo4d_over_temporal_schur"] = r["eo4d"]["time_s"] / r["temporal_schur"]["time_s"]
+            r["hop_kernels_autotuned"] = _hop_config(wf, w, eta.shape[0])
             r["iteration_ratio"] = r["eo4d"]["iterations"] / r["temporal_schur"]["iterations"]
             rows.append(r)
             w.close()

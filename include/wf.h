@@ -171,6 +171,14 @@ int wf_apply_schur_noalloc(wf_handle_t* h, const double* in_odd, double* out_odd
 int wf_force(wf_handle_t* h, const double* phi_odd, double* F, int precision, double tol, double* action,
              int* iters);
 
+/* Autotuned configuration of the FP32 hop kernels of M-hat (no counterpart in the paper): the
+ * first FP32 Schur apply of a handle for a given nrhs times every candidate and keeps the fastest
+ * (environment WF_AUTOTUNE=0 at the first apply keeps the built-in choice). variant: 1 one thread
+ * per site, 2 n sites per lane; tile_rows: rows of y per traversal tile; ms: the chosen
+ * candidate's K-b + K-c time over three runs. Any output pointer may be null. WF_EINVAL if that
+ * nrhs has not been tuned (yet). */
+int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float* ms);
+
 /* Number of kernels this handle has launched since it was created (all entry points). */
 long long wf_launch_count(const wf_handle_t* h);
 

@@ -42,6 +42,7 @@ _SIGS = {
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
     "wf_force": (_i, [_vp, _vp, _vp, _i, _d, _dp, _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
+    "wf_hop_config": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
     "wf_profile": (_i, [_vp, _i]),
     "wf_profile_get": (_i, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), _dp, _i]),
 }
@@ -173,6 +174,14 @@ def wf_force(h, phi_odd, F, precision=WF_FP64, tol=1e-12):
 
 def wf_launch_count(h):
     return lib.wf_launch_count(h)
+
+
+def wf_hop_config(h, nrhs):
+    """The autotuned FP32 hop-kernel configuration for nrhs: (variant, tile_rows, ms), or None."""
+    v, r, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    if lib.wf_hop_config(h, int(nrhs), ctypes.byref(v), ctypes.byref(r), ctypes.byref(ms)) != WF_OK:
+        return None
+    return v.value, r.value, ms.value
 
 
 def wf_profile(h, on):

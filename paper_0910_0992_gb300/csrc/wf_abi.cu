@@ -227,7 +227,7 @@ void attach_tables(wf_handle* h, LineArgs<float>& a) {
     WF_CUDA(cudaMemcpyAsync(nb.p, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     WF_CUDA(cudaStreamSynchronize(h->stream));
   }
-  auto& ob = h->order_tab[a.nrhs];
+  auto& ob = h->order_tab[a.nrhs * 64 + a.g.by];
   if (!ob) {
     std::vector<int2> t((size_t)a.nrhs * g.Nl);
     for (size_t i = 0; i < t.size(); ++i) line_rhs((int)i, a.nrhs, g, t[i].x, t[i].y);
@@ -238,6 +238,60 @@ void attach_tables(wf_handle* h, LineArgs<float>& a) {
   }
   a.nbr = nb.as<int>();
   a.order = ob->as<int2>();
+}
+
+// Autotuner of the FP32 hop kernels K-b and K-c: the first time a handle applies M-hat to a
+// given number of right-hand sides, every candidate (one thread per site or n sites per lane;
+// traversal tiles of each divisor of L from 2 to 12 rows of y) runs K-b and K-c on the call's own
+// buffers, once untimed and three times timed with CUDA events; the fastest is kept for the
+// handle. The timed runs write only the work fields K-b and K-c own (no norms); the call then
+// computes its result as usual.
+static bool autotune_on(wf_handle* h) {
+  if (h->autotune < 0) {
+    const char* e = std::getenv("WF_AUTOTUNE");
+    h->autotune = (e && e[0] == '0') ? 0 : 1;
+  }
+  return h->autotune != 0;
+}
+
+static wf_handle::HopTune tune_hops(wf_handle* h, const LineArgs<float>& ab, const LineArgs<float>& ac) {
+  wf_handle::HopTune best{0, h->g.by, 0.f};
+  if (!autotune_on(h) || !h->axial) return best;
+  auto it = h->hop_tune.find(ab.nrhs);
+  if (it != h->hop_tune.end()) return it->second;
+  std::vector<int> rows;
+  for (int b = 2; b <= 12 && b <= h->g.L; ++b)
+    if (h->g.L % b == 0) rows.push_back(b);
+  if (rows.empty()) rows.push_back(h->g.by);
+  cudaEvent_t e0, e1;
+  WF_CUDA(cudaEventCreate(&e0));
+  WF_CUDA(cudaEventCreate(&e1));
+  best.ms = 1e30f;
+  for (int variant = 1; variant <= 2; ++variant) {
+    if (variant == 1 && !wide_supported(h->g)) continue;
+    for (int by : rows) {
+      LineArgs<float> b = ab, c = ac;
+      b.variant = c.variant = variant;
+      b.g.by = c.g.by = by;
+      c.norm2 = nullptr;
+      attach_tables(h, b);
+      attach_tables(h, c);
+      float ms = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        if (rep == 1) WF_CUDA(cudaEventRecord(e0, h->stream));
+        launch_line<float>(b, LK_SCHUR_B, true, h->stream);
+        launch_line<float>(c, LK_SCHUR_C, true, h->stream);
+      }
+      WF_CUDA(cudaEventRecord(e1, h->stream));
+      WF_CUDA(cudaEventSynchronize(e1));
+      WF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best.ms) best = wf_handle::HopTune{variant, by, ms};
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->hop_tune[ab.nrhs] = best;
+  return best;
 }
 
 template <typename R>
@@ -279,31 +333,38 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     launch_line<R>(a, LK_SCHUR_A, h->axial, h->stream);
   }
   const bool tma = use_tma_kernels<R>(h);
-  {
-    LineArgs<R> a = line_args<R>(h, 0, nrhs);
-    a.src_up = y;
-    a.src_lo = dagger ? x : x + 6 * tp;
-    a.opu = OP_FWD;
-    a.opl = OP_BWD;
-    a.out = z;
-    Prof P(h, pname<R>("schur_b_hop_tsolve"));
-    launch_schur_hop<R>(h, a, LK_SCHUR_B, tma);
+  LineArgs<R> ab = line_args<R>(h, 0, nrhs);
+  ab.src_up = y;
+  ab.src_lo = dagger ? x : x + 6 * tp;
+  ab.opu = OP_FWD;
+  ab.opl = OP_BWD;
+  ab.out = z;
+  LineArgs<R> ac = line_args<R>(h, 1, nrhs);
+  ac.src_up = z;
+  ac.src_lo = z + 6 * tp;
+  ac.opu = OP_COPY;
+  ac.opl = OP_BWD;
+  ac.xpost = x;
+  ac.apost = (R)(-1.0 / (h->g.gamma_f * h->g.gamma_f));
+  ac.swap_out = dagger;
+  ac.stream_out = 1;  // the operator's result is next read by the solver's vector update
+  ac.out = out;
+  ac.norm2 = norm2;
+  if constexpr (sizeof(R) == 4) {
+    if (!tma) {
+      const wf_handle::HopTune t = tune_hops(h, ab, ac);
+      ab.variant = ac.variant = t.variant;
+      ab.g.by = ac.g.by = t.by;
+    }
   }
   {
-    LineArgs<R> a = line_args<R>(h, 1, nrhs);
-    a.src_up = z;
-    a.src_lo = z + 6 * tp;
-    a.opu = OP_COPY;
-    a.opl = OP_BWD;
-    a.xpost = x;
-    a.apost = (R)(-1.0 / (h->g.gamma_f * h->g.gamma_f));
-    a.swap_out = dagger;
-    a.stream_out = 1;  // the operator's result is next read by the solver's vector update
-    a.out = out;
-    a.norm2 = norm2;
+    Prof P(h, pname<R>("schur_b_hop_tsolve"));
+    launch_schur_hop<R>(h, ab, LK_SCHUR_B, tma);
+  }
+  {
     if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nrhs * sizeof(double), h->stream));
     Prof P(h, pname<R>("schur_c_hop_tinv_axpy"));
-    launch_schur_hop<R>(h, a, LK_SCHUR_C, tma);
+    launch_schur_hop<R>(h, ac, LK_SCHUR_C, tma);
   }
 }
 template void schur_apply<float>(wf_handle*, const Cx<float>*, Cx<float>*, int, int, Cx<float>*, Cx<float>*,
@@ -1445,6 +1506,17 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     finish_out(h, x, dx, le, staged);
     if (st == WF_ENOCONV) h->err = "solver did not reach tol";
     return st;
+  });
+}
+
+int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float* ms) {
+  return guarded(h, [&]() {
+    auto it = h->hop_tune.find(nrhs);
+    if (it == h->hop_tune.end()) throw Error(WF_EINVAL, "no tuned hop configuration for this nrhs yet");
+    if (variant) *variant = it->second.variant;
+    if (tile_rows) *tile_rows = it->second.by;
+    if (ms) *ms = it->second.ms;
+    return WF_OK;
   });
 }
 

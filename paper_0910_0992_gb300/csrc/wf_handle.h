@@ -37,7 +37,15 @@ struct wf_handle {
   wf::DevBuf tma_err;  // error word of the TMA-fed kernels (bounded waits)
   // index tables of the wide kernels: neighbour lines per parity, traversal order per nrhs
   wf::DevBuf nbr_tab[2];
-  std::map<int, std::unique_ptr<wf::DevBuf>> order_tab;
+  std::map<int, std::unique_ptr<wf::DevBuf>> order_tab;  // key: nrhs * 64 + tile rows
+  // autotuned FP32 hop-kernel configuration per nrhs: kernel family and traversal tile rows
+  struct HopTune {
+    int variant;
+    int by;
+    float ms;  // K-b + K-c time of the choice when measured
+  };
+  std::map<int, HopTune> hop_tune;
+  int autotune = -1;  // -1: not decided yet (environment WF_AUTOTUNE=0 keeps the built-in choice)
   int use_tma = -1;    // -1: not decided yet (environment WF_TMA=1 turns the TMA-fed hop kernels on)
   wf::DevBuf iflag;
   std::map<std::string, std::unique_ptr<wf::DevBuf>> ws;  // named work buffers

@@ -172,7 +172,8 @@ static bool use_wide(const Geom& g, int kind, bool fp32) {
 template <typename R>
 static void launch_line_impl(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
   if constexpr (sizeof(R) == 4) {
-    if (axial && use_wide(a.g, kind, true)) {
+    const bool wide = a.variant == 1 ? wide_supported(a.g) : a.variant == 2 ? false : use_wide(a.g, kind, true);
+    if (axial && wide) {
       launch_line_wide(a, kind, s);
       return;
     }

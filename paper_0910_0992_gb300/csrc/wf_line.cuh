@@ -71,6 +71,7 @@ struct LineArgs {
   // [Nl][6] (neighbour_lines, output parity)
   const int2* order;
   const int* nbr;
+  int variant;  // FP32 axial hop kernels: 0 the built-in choice, 1 one thread per site, 2 n sites per lane
 };
 
 // Order in which the line kernels visit (rhs, line) pairs. Right-hand sides are processed in

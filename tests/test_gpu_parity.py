@@ -216,3 +216,28 @@ def test_solve_with_double_float_steps(monkeypatch, L, T, method):
     for k in range(eta.shape[0]):
         assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
     w.close()
+
+
+@pytest.mark.parametrize("L,T", [(4, 128), (8, 32), (6, 12)])
+def test_autotuned_hop_kernels(monkeypatch, L, T):
+    """The first FP32 Schur apply tunes the hop kernels (family, tile rows); the result of every
+    later apply, and of the tuning call itself, matches the oracle. WF_AUTOTUNE=0: no tuning."""
+    p = W.Params(L, T, 0.07, xi=3.0, bc=-1)
+    U = S.random_gauge(L, T, 0.3, 61)
+    eta = S.gaussian_source(L, T, 62, nrhs=3)
+    par3 = W.parity3(L, T)
+    xo = np.ascontiguousarray(SV.compact(eta, par3 == 1))
+    ref = SV.compact(W.M_hat(U, SV.expand(xo, par3 == 1), p, par3), par3 == 1)
+    for tune in ("1", "0"):
+        monkeypatch.setenv("WF_AUTOTUNE", tune)
+        w = wf.Wilson(L, T, 0.07, kappa_t=0.21, bc=-1)
+        w.load_gauge(U)
+        assert wf.wf_hop_config(w.h, 3) is None
+        for _ in range(2):
+            assert _rel(_host(w.apply_schur(_dev(xo), f32=True)), ref) < 1e-6
+        cfg = wf.wf_hop_config(w.h, 3)
+        if tune == "1":
+            assert cfg is not None and cfg[0] in (1, 2) and L % cfg[1] == 0 and cfg[2] > 0
+        else:
+            assert cfg is None
+        w.close()
