@@ -271,6 +271,7 @@ static wf_handle::HopTune tune_hops(wf_handle* h, const LineArgs<float>& ab, con
     if (variant == 1 && !wide_supported(h->g)) continue;
     for (int by : rows) {
       LineArgs<float> b = ab, c = ac;
+      b.active = c.active = nullptr;
       b.variant = c.variant = variant;
       b.g.by = c.g.by = by;
       c.norm2 = nullptr;
@@ -324,6 +325,7 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
   const int tp = h->g.tp;
   {
     LineArgs<R> a = line_args<R>(h, 1, nrhs);
+    a.active = h->op_active;
     a.src_up = dagger ? x + 6 * tp : x;
     a.src_lo = dagger ? x : x + 6 * tp;
     a.opu = OP_FWD;
@@ -334,12 +336,14 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
   }
   const bool tma = use_tma_kernels<R>(h);
   LineArgs<R> ab = line_args<R>(h, 0, nrhs);
+  ab.active = h->op_active;
   ab.src_up = y;
   ab.src_lo = dagger ? x : x + 6 * tp;
   ab.opu = OP_FWD;
   ab.opl = OP_BWD;
   ab.out = z;
   LineArgs<R> ac = line_args<R>(h, 1, nrhs);
+  ac.active = h->op_active;
   ac.src_up = z;
   ac.src_lo = z + 6 * tp;
   ac.opu = OP_COPY;
@@ -476,7 +480,11 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
   cudaStream_t s = h->stream;
   double* sc = h->buf<double>("cg_scalars", 16 * (size_t)nrhs);
   double *gam = sc, *gnew = sc + nrhs, *qq = sc + 2 * nrhs, *rr = sc + 3 * nrhs;
-  int* active = h->buf<int>("cg_active", nrhs);
+  // device bookkeeping per right-hand side: active, state (0 running, 1 converged, 2 wants a
+  // reliable update), iterations; limits: target^2 and the reliable-update threshold^2
+  int* ist = h->buf<int>("cg_istate", 3 * (size_t)nrhs);
+  int *active = ist, *state = ist + nrhs, *dits = ist + 2 * nrhs;
+  double* lim = h->buf<double>("cg_limits", 2 * (size_t)nrhs);
   double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
   std::vector<int> act(nrhs, 1), iters(nrhs, 0);
   WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -491,7 +499,10 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
 
   // r64 = b - A y (FP64) or b
   auto true_schur_residual = [&]() {
+    const int* keep = h->op_active;
+    h->op_active = nullptr;  // every right-hand side's residual
     A64(y, r64, 0, nullptr);
+    h->op_active = keep;
     { Prof P(h, "axpby_f64"); launch_axpby<double>(r64, b, nt, 1.0, -1.0, s); }  // r64 = b - A y
   };
   if (x0) {
@@ -537,51 +548,168 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
     const double v = std::atof(e);
     if (v > 0.0 && v < 1.0) delta = v;
   }
-  for (int it = 0; it < maxiter; ++it) {
+  // Iterations run in blocks without host synchronisation: convergence and the reliable-update
+  // trigger are decided on the device after every x, r update (k_cg_check); the host reads the
+  // state once per block, performs reliable updates, and sizes the next block from the observed
+  // convergence rate. With a stream of its own and profiling off, one iteration is captured
+  // once as a CUDA graph and replayed (environment WF_GRAPH=0: plain launches).
+  std::vector<double> tgt2(nrhs), ru2(nrhs);
+  std::vector<int> st(nrhs, 0), cnt(nrhs, 0);
+  for (int k = 0; k < nrhs; ++k) {
+    tgt2[k] = target[k] * target[k];
+    ru2[k] = mixed ? (delta * rmax[k]) * (delta * rmax[k]) : 0.0;
+    if (!act[k]) st[k] = 1;
+  }
+  auto upload_state = [&]() {
+    WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(state, st.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(lim, tgt2.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(lim + nrhs, ru2.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  };
+  upload_state();
+  WF_CUDA(cudaMemsetAsync(dits, 0, nrhs * sizeof(int), s));
+
+  auto iteration = [&]() {
     A(p, q, 0, qq);  // q = A p, |q|^2
     { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s); }
-    for (int k = 0; k < nrhs; ++k)
-      if (act[k]) iters[k]++;
-    std::vector<double> rrh = read_scalars(h, rr, nrhs);
-    bool changed = false;
-    bool need_ru = false;
-    for (int k = 0; k < nrhs; ++k) {
-      if (!act[k]) continue;
-      const double rn = std::sqrt(rrh[k]);
-      if (rrh[k] <= target[k] * target[k]) {
-        // converged on the iterated residual. With FP32 iterations it differs from the true
-        // one by about eps_32 times the residual at the last reliable update (<= delta times
-        // smaller than the start), far below the target; the caller's FP64 check of
-        // eta - M psi decides, and runs another pass from this solution if it is not met.
-        act[k] = 0;
-        changed = true;
-      } else if (mixed && rn < delta * rmax[k]) {
-        need_ru = true;
+    { Prof P(h, "cg_check"); launch_cg_check(rr, active, state, dits, lim, lim + nrhs, nrhs, s); }
+    A(r, sv, 1, gnew);  // s = A^dag r, |s|^2
+    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
+    { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
+  };
+
+  bool graphs = h->stream != 0 && !h->prof;
+  if (const char* e = std::getenv("WF_GRAPH"))
+    if (e[0] == '0') graphs = false;
+  cudaGraphExec_t gexec = nullptr;
+  long long per_iter = 0;
+  auto run_block = [&](int nb) {
+    for (int i = 0; i < nb; ++i) {
+      if (gexec) {
+        WF_CUDA(cudaGraphLaunch(gexec, s));
+        h->launches += per_iter;
+        continue;
       }
+      if (graphs && i > 0) {
+        // capture one iteration (buffers, tables and tuning already exist after a plain one); the
+        // launch counter counts the captured kernels once per replay
+        const long long l0 = h->launches;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        long long captured = 0;
+        if (ok) {
+          try {
+            iteration();
+          } catch (...) {
+            ok = false;
+          }
+          captured = h->launches - l0;
+          const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+          ok = ok && ee == cudaSuccess && graph != nullptr;
+          if (ok) ok = cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+          if (graph) cudaGraphDestroy(graph);
+        }
+        (void)cudaGetLastError();  // a failed capture leaves a non-sticky error behind
+        h->launches = l0;
+        if (!ok) {
+          if (gexec) cudaGraphExecDestroy(gexec);
+          gexec = nullptr;
+          graphs = false;
+          iteration();
+          continue;
+        }
+        per_iter = captured;
+        WF_CUDA(cudaGraphLaunch(gexec, s));
+        h->launches += per_iter;
+        continue;
+      }
+      iteration();
     }
+  };
+
+  // the Schur operator's kernels skip right-hand sides that stopped (converged, or waiting for
+  // a reliable update) while the blocks run
+  struct ActiveScope {
+    wf_handle* h;
+    ActiveScope(wf_handle* hh, const int* a) : h(hh) { h->op_active = a; }
+    ~ActiveScope() { h->op_active = nullptr; }
+  } active_scope(h, active);
+  std::vector<double> rr_prev(nrhs, 0.0), rrh(nrhs);
+  int total = 0, nb = 1;
+  while (total < maxiter) {
+    nb = std::min(nb, maxiter - total);
+    run_block(nb);
+    total += nb;
+    WF_CUDA(cudaMemcpyAsync(h->host_scalars, rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int* hist = reinterpret_cast<int*>(h->host_scalars + nrhs);
+    WF_CUDA(cudaMemcpyAsync(hist, ist, 3 * nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    check_device_error(h);
+    std::memcpy(rrh.data(), h->host_scalars, nrhs * sizeof(double));
+    for (int k = 0; k < nrhs; ++k) {
+      if (!std::isfinite(rrh[k])) throw Error(WF_ENAN, "NaN or Inf in a solver norm");
+      act[k] = hist[k];
+      st[k] = hist[nrhs + k];
+      cnt[k] = hist[2 * nrhs + k];
+    }
+    bool need_ru = false;
+    for (int k = 0; k < nrhs; ++k) need_ru = need_ru || st[k] == 2;
     if (need_ru) {
-      // reliable update: fold the FP32 increment into y, recompute the residual in FP64
+      // reliable update: fold the FP32 increment into y, recompute the residual in FP64. The
+      // sources that asked for it stopped right after their x, r update; they now take the rest
+      // of that iteration (s = A^dag r, p = s + beta p) with the recomputed residual, the others
+      // masked out.
       { Prof P(h, "add_f_to_d"); launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s); }
       WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<R>), s));
       true_schur_residual();
       { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
       { Prof P(h, "d2f"); launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s); }
       std::vector<double> r64n = read_scalars(h, rr, nrhs);
+      std::vector<int> resume(nrhs, 0);
+      bool any_resume = false;
       for (int k = 0; k < nrhs; ++k) {
-        if (!act[k]) continue;
+        if (st[k] == 1) continue;
         rmax[k] = std::sqrt(r64n[k]);
-        if (r64n[k] <= target[k] * target[k]) {
+        ru2[k] = (delta * rmax[k]) * (delta * rmax[k]);
+        rrh[k] = r64n[k];
+        if (r64n[k] <= tgt2[k]) {
           act[k] = 0;
-          changed = true;
+          st[k] = 1;
+        } else if (st[k] == 2) {
+          resume[k] = 1;
+          any_resume = true;
+          st[k] = 0;
+          act[k] = 1;
         }
       }
+      if (any_resume) {
+        WF_CUDA(cudaMemcpyAsync(active, resume.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+        A(r, sv, 1, gnew);
+        { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
+        { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
+      }
+      upload_state();
     }
-    if (changed) WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (all_done()) break;
-    A(r, sv, 1, gnew);  // s = A^dag r, |s|^2
-    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
-    { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s); }
+    bool done = true;
+    for (int a : act) done = done && !a;
+    if (done) break;
+    // next block: about the iterations the slowest running source still needs at its observed
+    // rate (at least 1, at most 16; 2 right after a reliable update)
+    // (and no further than the first source's expected reliable-update trigger)
+    double need = 1.0, to_ru = 16.0;
+    for (int k = 0; k < nrhs; ++k) {
+      if (!act[k]) continue;
+      const double rho = rr_prev[k] > 0.0 && !need_ru ? std::pow(rrh[k] / rr_prev[k], 1.0 / nb) : 0.0;
+      const bool rate = rho > 0.0 && rho < 1.0;
+      need = std::max(need, rate ? std::log(tgt2[k] / rrh[k]) / std::log(rho) : 2.0);
+      if (mixed && rate && ru2[k] > 0.0 && ru2[k] < rrh[k])
+        to_ru = std::min(to_ru, std::log(ru2[k] / rrh[k]) / std::log(rho) + 1.0);
+    }
+    for (int k = 0; k < nrhs; ++k) rr_prev[k] = rrh[k];
+    nb = (int)std::max(1.0, std::min({16.0, std::floor(0.8 * need), std::ceil(to_ru)}));
   }
+  if (gexec) cudaGraphExecDestroy(gexec);
+  for (int k = 0; k < nrhs; ++k) iters[k] = cnt[k];
   if (mixed) {
     Prof P(h, "add_f_to_d");
     launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s);

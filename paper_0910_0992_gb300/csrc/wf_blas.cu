@@ -162,12 +162,36 @@ void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t
   WF_CUDA(cudaGetLastError());
 }
 
-__global__ void k_copy_scalar(double* dst, const double* src, int n) {
-  int i = threadIdx.x;
-  if (i < n) dst[i] = src[i];
+// After the x, r update of a CG iteration, per right-hand side: count the iteration, stop a
+// source whose residual met its target (state 1), stop and flag one whose residual fell below
+// its reliable-update threshold (state 2: it waits for the host to recompute its residual)
+__global__ void k_cg_check(const double* __restrict__ rr, int* __restrict__ active, int* __restrict__ state,
+                           int* __restrict__ iters, const double* __restrict__ tgt2, const double* __restrict__ ru2,
+                           int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n || !active[k]) return;
+  iters[k] += 1;
+  if (rr[k] <= tgt2[k]) {
+    active[k] = 0;
+    state[k] = 1;
+  } else if (rr[k] < ru2[k]) {
+    active[k] = 0;
+    state[k] = 2;
+  }
 }
-void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s) {
-  k_copy_scalar<<<1, 1024, 0, s>>>(dst, src, nrhs);
+void launch_cg_check(const double* rr, int* active, int* state, int* iters, const double* tgt2, const double* ru2,
+                     int nrhs, cudaStream_t s) {
+  k_cg_check<<<(nrhs + 127) / 128, 128, 0, s>>>(rr, active, state, iters, tgt2, ru2, nrhs);
+  WF_CUDA(cudaGetLastError());
+}
+
+// dst = src for the active right-hand sides (all of them if active is null)
+__global__ void k_copy_scalar(double* dst, const double* src, const int* active, int n) {
+  int i = threadIdx.x;
+  if (i < n && (!active || active[i])) dst[i] = src[i];
+}
+void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s, const int* active) {
+  k_copy_scalar<<<1, 1024, 0, s>>>(dst, src, active, nrhs);
   WF_CUDA(cudaGetLastError());
 }
 

@@ -29,6 +29,9 @@ struct wf_handle {
   // high-precision steps of FP32-iteration solves; see wf_df64.cuh)
   bool df_ops = false;
   bool df_allowed = false;  // double-float steps enabled for this handle
+  // while a CG runs: its device flags of active right-hand sides; the Schur operator's kernels
+  // skip the others
+  const int* op_active = nullptr;
   // gauge, per parity: U_t [Nl][9][tp], spatial [3][Nl][9][tp], Lambda [Nl][9]
   wf::DevBuf ut64[2], us64[2], lamb64[2], lamf64[2];
   wf::DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];

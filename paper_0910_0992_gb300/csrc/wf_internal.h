@@ -135,7 +135,9 @@ void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* ga
 template <typename R>
 void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s);      // y += x
-void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s);
+void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s, const int* active = nullptr);
+void launch_cg_check(const double* rr, int* active, int* state, int* iters, const double* tgt2, const double* ru2,
+                     int nrhs, cudaStream_t s);
 
 // 4-D even-odd comparator (wf_eo4d.cu)
 template <typename R>

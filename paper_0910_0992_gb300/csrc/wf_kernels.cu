@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(
   const int jj = lane % g.lpl;
   const int tp = g.tp, n = g.n;
   const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
+  if (A.active && g.lpw == 1 && !A.active[rhs]) return;  // one line per warp: the whole warp leaves
 
   Vec3<R> v[NMAX][4];
   if (src == SRC_HOP) {
@@ -235,6 +236,7 @@ static LineArgs<df64> line_args_df(const LineArgs<double>& a) {
   b.df = 0;
   b.order = a.order;
   b.nbr = a.nbr;
+  b.active = a.active;
   return b;
 }
 

@@ -72,6 +72,9 @@ struct LineArgs {
   const int2* order;
   const int* nbr;
   int variant;  // FP32 axial hop kernels: 0 the built-in choice, 1 one thread per site, 2 n sites per lane
+  // if set: [nrhs] flags; right-hand sides whose flag is 0 are skipped (kernels whose CTA or
+  // warp holds lines of one right-hand side only; their outputs for those sources are left as is)
+  const int* active;
 };
 
 // Order in which the line kernels visit (rhs, line) pairs. Right-hand sides are processed in

@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
   }
   const bool valid = line_ok && t < g.T;  // owns a site (else padding or idle)
   const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
+  if constexpr (TPC == 128) {
+    if (A.active && !A.active[rhs]) return;  // one line per CTA: the whole CTA leaves
+  }
 
   Vec3<R> v[4];
 #pragma unroll
