@@ -140,6 +140,17 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
              int flags, int* iters_out, double* true_resid_out);
 
+/* Several independent solves in one call: handle hs[i] (one lattice each, possibly of different
+ * sizes; the handles must be distinct) solves nrhs[i] sources rhs[i] into x[i], with the arguments
+ * and conventions of wf_solve. Every solve runs on a host thread of its own and on its handle's
+ * stream (a temporary stream for handles on the default stream), so the GPU works on all lattices
+ * at once: ragged batches such as a sweep over lattice sizes at one anisotropy. No counterpart in the
+ * paper (its solves are independent problems). iters_out, resid_out and status_out may be null,
+ * or hold n pointers (n statuses); returns WF_OK or the first non-OK status. */
+int wf_solve_many(int n, wf_handle_t* const* hs, const double* const* rhs, double* const* x, const int* nrhs,
+                  double tol, int method, int precision, int flags, int* const* iters_out,
+                  double* const* resid_out, int* status_out);
+
 /* The FP64 M-hat apply of wf_apply_schur, with every byte of its work memory taken from one
  * fixed device array that the library reserves, so this call allocates nothing. For callers
  * that cannot have a library call cudaMalloc at apply time: applications whose own pool has

@@ -41,6 +41,8 @@ _SIGS = {
     "wf_apply_eo4d_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
     "wf_force": (_i, [_vp, _vp, _vp, _i, _d, _dp, _ip]),
+    "wf_solve_many": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _d, _i, _i, _i,
+                           ctypes.POINTER(_ip), ctypes.POINTER(_dp), _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_hop_config": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
     "wf_profile": (_i, [_vp, _i]),
@@ -150,6 +152,25 @@ def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):
     if code not in (WF_OK, WF_ENOCONV):
         _check(h, code)
     return code, list(iters), list(res)
+
+
+def wf_solve_many(hs, rhs, x, nrhs, tol, method, precision, flags=0):
+    """Independent solves on several handles (lattices) at once; returns (status, per-handle
+    (status, iterations, true residuals))."""
+    n = len(hs)
+    if not (len(rhs) == len(x) == len(nrhs) == n):
+        raise ValueError("hs, rhs, x and nrhs must have the same length")
+    Hs = (_vp * n)(*[ctypes.c_void_p(h.value if isinstance(h, ctypes.c_void_p) else h) for h in hs])
+    R = (_vp * n)(*[_ptr(a) for a in rhs])
+    X = (_vp * n)(*[_ptr(a) for a in x])
+    N = (ctypes.c_int * n)(*[int(k) for k in nrhs])
+    its = [(ctypes.c_int * int(k))() for k in nrhs]
+    res = [(ctypes.c_double * int(k))() for k in nrhs]
+    I = (_ip * n)(*[ctypes.cast(a, _ip) for a in its])
+    D = (_dp * n)(*[ctypes.cast(a, _dp) for a in res])
+    S = (ctypes.c_int * n)()
+    st = lib.wf_solve_many(n, Hs, R, X, N, float(tol), int(method), int(precision), int(flags), I, D, S)
+    return st, [(S[i], list(its[i]), list(res[i])) for i in range(n)]
 
 
 def wf_force(h, phi_odd, F, precision=WF_FP64, tol=1e-12):

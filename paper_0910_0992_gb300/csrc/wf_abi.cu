@@ -8,6 +8,8 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -163,11 +165,15 @@ struct DfScope {
   ~DfScope() { h->df_ops = old; }
 };
 
+// "<base>_f64" / "<base>_f32": buffer and profile names per precision (interned; the map is
+// shared by the threads of wf_solve_many)
+std::mutex g_pname_mu;
 template <typename R>
 const char* pname(const char* base);
 template <>
 const char* pname<double>(const char* base) {
   static std::map<std::string, std::string> m;
+  std::lock_guard<std::mutex> lock(g_pname_mu);
   auto& s = m[base];
   if (s.empty()) s = std::string(base) + "_f64";
   return s.c_str();
@@ -175,6 +181,7 @@ const char* pname<double>(const char* base) {
 template <>
 const char* pname<float>(const char* base) {
   static std::map<std::string, std::string> m;
+  std::lock_guard<std::mutex> lock(g_pname_mu);
   auto& s = m[base];
   if (s.empty()) s = std::string(base) + "_f32";
   return s.c_str();
@@ -1635,6 +1642,61 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     if (st == WF_ENOCONV) h->err = "solver did not reach tol";
     return st;
   });
+}
+
+int wf_solve_many(int n, wf_handle_t* const* hs, const double* const* rhs, double* const* x, const int* nrhs,
+                  double tol, int method, int precision, int flags, int* const* iters_out,
+                  double* const* resid_out, int* status_out) {
+  if (n < 1 || !hs || !rhs || !x || !nrhs) return WF_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return WF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return WF_EINVAL;  // one handle per lattice: a handle is not shared
+  }
+  std::vector<int> st(n, WF_OK);
+  std::vector<cudaStream_t> own(n, nullptr);
+  try {
+    // every solve on a stream of its own (a temporary one for handles on the default stream)
+    for (int i = 0; i < n; ++i) {
+      if (hs[i]->stream) continue;
+      int prev = 0;
+      if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(hs[i]->device) != cudaSuccess) throw Error(WF_ECUDA, "device");
+      const cudaError_t e = cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking);
+      cudaSetDevice(prev);
+      if (e != cudaSuccess) throw Error(WF_ECUDA, "cudaStreamCreateWithFlags");
+      hs[i]->stream = own[i];
+    }
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int i = 0; i < n; ++i)
+      th.emplace_back([&, i]() {
+        if (cudaSetDevice(hs[i]->device) != cudaSuccess) {
+          st[i] = WF_ECUDA;
+          return;
+        }
+        st[i] = wf_solve(hs[i], rhs[i], x[i], nrhs[i], tol, method, precision, flags,
+                         iters_out ? iters_out[i] : nullptr, resid_out ? resid_out[i] : nullptr);
+      });
+    for (auto& t : th) t.join();
+  } catch (const Error& e) {
+    for (int i = 0; i < n; ++i)
+      if (st[i] == WF_OK) st[i] = e.code;
+  } catch (...) {
+    for (int i = 0; i < n; ++i)
+      if (st[i] == WF_OK) st[i] = WF_ENOMEM;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!own[i]) continue;
+    cudaStreamSynchronize(own[i]);
+    hs[i]->stream = nullptr;
+    cudaStreamDestroy(own[i]);
+  }
+  int first = WF_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status_out) status_out[i] = st[i];
+    if (first == WF_OK && st[i] != WF_OK) first = st[i];
+  }
+  return first;
 }
 
 int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float* ms) {

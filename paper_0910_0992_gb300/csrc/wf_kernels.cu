@@ -161,11 +161,10 @@ static int line_blocks(const LineArgs<R>& a) {
 // n sites per lane; FP64 arithmetic stays on k_line too. Environment WF_WIDE=0 disables the
 // wide FP32 kernels, WF_WIDE=2 uses them for every FP32 axial line operation.
 static bool use_wide(const Geom& g, int kind, bool fp32) {
-  static int mode = -1;
-  if (mode < 0) {
+  static const int mode = []() {  // read once (thread-safe initialisation)
     const char* e = std::getenv("WF_WIDE");
-    mode = (e && e[0] == '0') ? 0 : (e && e[0] == '2') ? 2 : 1;
-  }
+    return (e && e[0] == '0') ? 0 : (e && e[0] == '2') ? 2 : 1;
+  }();
   if (!mode || !wide_supported(g)) return false;
   return mode == 2 || (fp32 && (kind == LK_SCHUR_B || kind == LK_SCHUR_C));
 }

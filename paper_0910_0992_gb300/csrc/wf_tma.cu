@@ -13,6 +13,9 @@
 // on expiry the kernel sets an error word, drains its outstanding copies (bounded as well) and
 // returns; the host reports WF_ETIMEOUT. The expiry path is tested by skipping one copy on the
 // host's request (environment WF_TEST_DROP_COPY=<job>), never by a fault.
+#include <map>
+#include <mutex>
+
 #include "wf_internal.h"
 #include "wf_line.cuh"
 
@@ -265,14 +268,23 @@ __global__ void __launch_bounds__(32) k_line_tma(const LineArgs<float> A, int* e
 template <int OPU, int OPL>
 static void launch_tma_variant(const LineArgs<float>& a, int* err, cudaStream_t s) {
   const size_t smem = (size_t)kStages * 18 * a.g.tp * sizeof(Cx<float>) + kStages * sizeof(uint64_t);
-  static int ctas_per_sm = 0, sms = 0;
-  if (!ctas_per_sm) {
-    int dev = 0;
-    WF_CUDA(cudaGetDevice(&dev));
-    WF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WF_CUDA(cudaFuncSetAttribute(k_line_tma<OPU, OPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_line_tma<OPU, OPL>, 32, smem));
-    if (ctas_per_sm < 1) ctas_per_sm = 1;
+  // resident CTAs per SM for this shared-memory size, looked up once (shared by threads)
+  static std::mutex mu;
+  static std::map<size_t, int> occ;
+  int ctas_per_sm = 0, sms = 0, dev = 0;
+  WF_CUDA(cudaGetDevice(&dev));
+  WF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = occ.find(smem);
+    if (it == occ.end()) {
+      WF_CUDA(cudaFuncSetAttribute(k_line_tma<OPU, OPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_line_tma<OPU, OPL>, 32, smem));
+      if (ctas_per_sm < 1) ctas_per_sm = 1;
+      occ[smem] = ctas_per_sm;
+    } else {
+      ctas_per_sm = it->second;
+    }
   }
   WF_CUDA(cudaFuncSetAttribute(k_line_tma<OPU, OPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int lines = a.nrhs * a.g.Nl;

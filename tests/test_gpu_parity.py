@@ -241,3 +241,43 @@ def test_autotuned_hop_kernels(monkeypatch, L, T):
         else:
             assert cfg is None
         w.close()
+
+
+@pytest.mark.parametrize("method", [wf.WF_TEMPORAL_SCHUR, wf.WF_EO4D])
+def test_solve_many_ragged_lattices(method):
+    """wf_solve_many: three lattices of different sizes in one call, each on its own stream and host
+    thread; every solution meets the FP64 true residual and the iteration counts of the same solves
+    made one at a time (within one iteration: the norms' summation order differs)."""
+    shapes = [(4, 16, 0.074), (6, 12, 0.07), (4, 8, 0.075)]
+    hs, ws, rhs, xs, refs, prms = [], [], [], [], [], []
+    for i, (L, T, ks) in enumerate(shapes):
+        p = W.Params(L, T, ks, xi=3.5, bc=-1)
+        U = S.random_gauge(L, T, 0.25, 70 + i)
+        eta = S.gaussian_source(L, T, 80 + i, nrhs=2)
+        w = wf.Wilson(L, T, ks, kappa_t=3.5 * ks, bc=-1)
+        w.load_gauge(U)
+        _, it1, _, st1 = w.solve(_dev(eta), tol=1e-10, method=method, precision=wf.WF_FP32)
+        assert st1 == wf.WF_OK
+        ws.append(w); hs.append(w.h); rhs.append(_dev(eta)); xs.append(torch.empty_like(rhs[-1]))
+        refs.append((U, eta, it1)); prms.append(p)
+    st, per = wf.wf_solve_many(hs, rhs, xs, [2, 2, 2], 1e-10, method, wf.WF_FP32)
+    assert st == wf.WF_OK
+    for (U, eta, it1), p, x, (sti, its, res) in zip(refs, prms, xs, per):
+        assert sti == wf.WF_OK and max(res) <= 1e-10
+        assert all(abs(a - b) <= 1 for a, b in zip(its, it1))
+        psi = _host(x)
+        for k in range(eta.shape[0]):
+            assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+    for w in ws:
+        w.close()
+
+
+def test_solve_many_rejects_a_shared_handle():
+    L, T = 4, 8
+    w = wf.Wilson(L, T, 0.075, kappa_t=0.26, bc=-1)
+    w.load_gauge(S.random_gauge(L, T, 0.2, 90))
+    eta = _dev(S.gaussian_source(L, T, 91, nrhs=1))
+    x = torch.empty_like(eta)
+    st, _ = wf.wf_solve_many([w.h, w.h], [eta, eta], [x, x], [1, 1], 1e-10, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)
+    assert st == wf.WF_EINVAL
+    w.close()
