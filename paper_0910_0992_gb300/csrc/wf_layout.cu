@@ -36,32 +36,52 @@ __device__ __forceinline__ void rotate3(const Cx<double>* __restrict__ gl, int t
   for (int k = 0; k < 3; ++k) v[k] = y.c[k];
 }
 
+// One thread per (rhs, parity, line, slot): all four spins of the site, so that the stores (import)
+// and loads (export) of the line layout are coalesced over the slots, the rotation g is loaded
+// once per site, and the lexicographic side moves each site's 192 contiguous bytes. Padding
+// slots (t >= T) are written as zero on import.
+__device__ __forceinline__ int slot_time(const Geom& g, int sl) { return (sl % g.lpl) * g.n + sl / g.lpl; }
+
 template <typename R>
 __global__ void k_import_spinor(const Geom g, const Cx<double>* __restrict__ lex, Cx<R>* even, Cx<R>* odd, int nrhs,
                                 int g5, const Cx<double>* g_e, const Cx<double>* g_o) {
   const size_t V = (size_t)g.L * g.L * g.L * g.T;
-  const size_t total = (size_t)nrhs * V * 4;
+  const size_t per_p = (size_t)g.Nl * g.tp;
+  const size_t total = (size_t)nrhs * 2 * per_p;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int sp = (int)(i % 4);
-    const size_t site = (i / 4) % V;
-    const int rhs = (int)(i / (4 * V));
-    int x, y, z, t;
-    site_coords(g, site, x, y, z, t);
-    const int p = (x + y + z) & 1;
+    const int sl = (int)(i % g.tp);
+    const int l = (int)((i / g.tp) % g.Nl);
+    const int p = (int)((i / per_p) % 2);
+    const int rhs = (int)(i / (2 * per_p));
     Cx<R>* dst = p ? odd : even;
     if (!dst) continue;
-    const int ssrc = g5 ? (sp + 2) % 4 : sp;
-    const Cx<double>* src = lex + ((size_t)rhs * V + site) * NSPIN_C + ssrc * 3;
-    Cx<double> v[3];
+    Cx<R>* out = dst + (size_t)(rhs * g.Nl + l) * NSPIN_C * g.tp + sl;
+    const int t = slot_time(g, sl);
+    if (t >= g.T) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = g5 ? mk<double>(-src[c].re, -src[c].im) : src[c];
-    const int l = line_of(g, x, y, z);
-    const int sl = slot_of(g, t);
+      for (int k = 0; k < NSPIN_C; ++k) out[(size_t)k * g.tp] = mk<R>(R(0), R(0));
+      continue;
+    }
+    int x, y, z;
+    line_coords(g, p, l, x, y, z);
+    const size_t site = (size_t)x + g.L * ((size_t)y + g.L * ((size_t)z + (size_t)g.L * t));
+    const Cx<double>* src = lex + ((size_t)rhs * V + site) * NSPIN_C;
     const Cx<double>* gr = p ? g_o : g_e;
-    if (gr) rotate3(gr + (size_t)l * 9 * g.tp, g.tp, sl, false, v);
+    Mat3<double> G;
+    if (gr) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      dst[((size_t)(rhs * g.Nl + l) * NSPIN_C + sp * 3 + c) * g.tp + sl] = mk<R>((R)v[c].re, (R)v[c].im);
+      for (int k = 0; k < 9; ++k) G.e[k] = gr[((size_t)l * 9 + k) * g.tp + sl];
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int ssrc = g5 ? (sp + 2) % 4 : sp;
+      Vec3<double> v;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v.c[c] = g5 ? mk<double>(-src[ssrc * 3 + c].re, -src[ssrc * 3 + c].im) : src[ssrc * 3 + c];
+      if (gr) v = matvec(G, v);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[(size_t)(sp * 3 + c) * g.tp] = mk<R>((R)v.c[c].re, (R)v.c[c].im);
+    }
   }
 }
 
@@ -69,32 +89,45 @@ template <typename R>
 __global__ void k_export_spinor(const Geom g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* __restrict__ lex,
                                 int nrhs, int g5, const Cx<double>* g_e, const Cx<double>* g_o) {
   const size_t V = (size_t)g.L * g.L * g.L * g.T;
-  const size_t total = (size_t)nrhs * V * 4;
+  const size_t per_p = (size_t)g.Nl * g.tp;
+  const size_t total = (size_t)nrhs * 2 * per_p;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int sp = (int)(i % 4);
-    const size_t site = (i / 4) % V;
-    const int rhs = (int)(i / (4 * V));
-    int x, y, z, t;
-    site_coords(g, site, x, y, z, t);
-    const int p = (x + y + z) & 1;
+    const int sl = (int)(i % g.tp);
+    const int l = (int)((i / g.tp) % g.Nl);
+    const int p = (int)((i / per_p) % 2);
+    const int rhs = (int)(i / (2 * per_p));
+    const int t = slot_time(g, sl);
+    if (t >= g.T) continue;
+    int x, y, z;
+    line_coords(g, p, l, x, y, z);
+    const size_t site = (size_t)x + g.L * ((size_t)y + g.L * ((size_t)z + (size_t)g.L * t));
+    Cx<double>* dst = lex + ((size_t)rhs * V + site) * NSPIN_C;
     const Cx<R>* src = p ? odd : even;
-    const int ss = g5 ? (sp + 2) % 4 : sp;
-    const int l = line_of(g, x, y, z);
-    const int sl = slot_of(g, t);
-    Cx<double> v[3];
+    if (!src) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      v[c] = mk<double>(0.0, 0.0);
-      if (src) {
-        Cx<R> w = src[((size_t)(rhs * g.Nl + l) * NSPIN_C + ss * 3 + c) * g.tp + sl];
-        v[c] = mk<double>((double)w.re, (double)w.im);
-      }
+      for (int k = 0; k < NSPIN_C; ++k) dst[k] = mk<double>(0.0, 0.0);
+      continue;
     }
+    const Cx<R>* in = src + (size_t)(rhs * g.Nl + l) * NSPIN_C * g.tp + sl;
     const Cx<double>* gr = p ? g_o : g_e;
-    if (gr && src) rotate3(gr + (size_t)l * 9 * g.tp, g.tp, sl, true, v);
-    Cx<double>* dst = lex + ((size_t)rhs * V + site) * NSPIN_C + sp * 3;
+    Mat3<double> G;
+    if (gr) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dst[c] = g5 ? mk<double>(-v[c].re, -v[c].im) : v[c];
+      for (int k = 0; k < 9; ++k) G.e[k] = gr[((size_t)l * 9 + k) * g.tp + sl];
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int ss = g5 ? (sp + 2) % 4 : sp;
+      Vec3<double> v;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const Cx<R> w = in[(size_t)(ss * 3 + c) * g.tp];
+        v.c[c] = mk<double>((double)w.re, (double)w.im);
+      }
+      if (gr) v = matvec_dag(G, v);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dst[sp * 3 + c] = g5 ? mk<double>(-v.c[c].re, -v.c[c].im) : v.c[c];
+    }
   }
 }
 
@@ -299,14 +332,14 @@ static int grid_for(size_t n) {
 template <typename R>
 void launch_import_spinor(const Geom& g, const Cx<double>* lex, Cx<R>* even, Cx<R>* odd, int nrhs, int g5,
                           const Cx<double>* g_e, const Cx<double>* g_o, cudaStream_t s) {
-  size_t n = (size_t)nrhs * g.L * g.L * g.L * g.T * 4;
+  const size_t n = (size_t)nrhs * 2 * g.Nl * g.tp;
   k_import_spinor<R><<<grid_for(n), kThreads, 0, s>>>(g, lex, even, odd, nrhs, g5, g_e, g_o);
   WF_CUDA(cudaGetLastError());
 }
 template <typename R>
 void launch_export_spinor(const Geom& g, const Cx<R>* even, const Cx<R>* odd, Cx<double>* lex, int nrhs, int g5,
                           const Cx<double>* g_e, const Cx<double>* g_o, cudaStream_t s) {
-  size_t n = (size_t)nrhs * g.L * g.L * g.L * g.T * 4;
+  const size_t n = (size_t)nrhs * 2 * g.Nl * g.tp;
   k_export_spinor<R><<<grid_for(n), kThreads, 0, s>>>(g, even, odd, lex, nrhs, g5, g_e, g_o);
   WF_CUDA(cudaGetLastError());
 }
