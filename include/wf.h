@@ -48,7 +48,7 @@ enum wf_status {
   WF_ESINGULAR = 4,  /* the temporal preconditioner does not exist: det(1 - bc mu^-T P) ~ 0 */
   WF_ENOCONV = 5,    /* solver stopped at its iteration limit; outputs are still written */
   WF_ENAN = 6,       /* NaN or Inf met in a norm during a solve */
-  WF_ETIMEOUT = 7    /* reserved for bounded device-side waits */
+  WF_ETIMEOUT = 7    /* a bounded device-side wait expired (the opt-in TMA-fed kernels, WF_TMA=1) */
 };
 
 enum wf_method {
@@ -60,7 +60,7 @@ enum wf_method {
 
 enum wf_precision {
   WF_FP64 = 0,  /* every operator apply in FP64 */
-  WF_FP32 = 1   /* FP32 operator applies, FP64 reliable updates and true residual */
+  WF_FP32 = 1   /* FP32 operator applies, FP64 reliable updates, S_L / S_R and true residual */
 };
 
 #define WF_X0 1 /* wf_solve flag: x holds the initial guess on entry */
@@ -135,6 +135,11 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
  * when the FP64 true residual ||rhs - M x||_2 / ||rhs||_2 <= tol, computed with the full M.
  * iters_out[k] (CG iterations) and true_resid_out[k] are written for every right-hand side
  * (host arrays of nrhs entries; either may be null). flags: WF_X0 to start from x.
+ * WF_FP32: the residual is recomputed in FP64 whenever the FP32 one fell by 1e-5 (environment
+ * WF_RELIABLE_DELTA); CG iterations run in blocks whose convergence checks happen on the device,
+ * one iteration replayed as a CUDA graph when the handle has a stream of its own (environment
+ * WF_GRAPH=0: plain launches). The first FP32 solve or apply for a given nrhs also tunes the
+ * Schur operator's kernels (see wf_hop_config).
  * Returns WF_ENOCONV (outputs written) if some right-hand side missed tol within 100000
  * iterations, WF_ENAN if a norm became NaN or Inf. */
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
