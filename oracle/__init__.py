@@ -14,9 +14,11 @@ Modules:
   flops   -- the paper's FLOP-count model (App. B, App. C)
   force   -- pseudofermion action phi^dag (M-hat^dag M-hat)^-1 phi and its force dS/dU (FP64 adjoint
              through the six factors of M-hat), pinned by central finite differences
+  determinant -- log det(mu - D_t) = log|det M| - log|det M-hat| from Polyakov products, and its
+             force; the extra Hamiltonian term of the temporal preconditioner in HMC (§IV)
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``
 except where its docstring says "parity unpinned".
 """
 
-from . import wilson, solve, dense, flops, force  # noqa: F401
+from . import wilson, solve, dense, flops, force, determinant  # noqa: F401

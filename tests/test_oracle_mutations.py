@@ -1,8 +1,8 @@
 """Planted mistakes in the oracle must be caught by its pins (CPU only).
 
 Each case patches one plausible error into the oracle (a flipped sign, a dropped
-factor, a transposed link, a wrong recurrence sign) and checks that at least
-one pin of ``test_oracle_pins`` then fails.
+factor, a transposed link, a wrong recurrence sign, a reversed product) and checks
+that at least one pin of ``test_oracle_pins`` or ``test_oracle_determinant`` then fails.
 """
 
 import numpy as np
@@ -95,3 +95,67 @@ def test_swapped_projectors_in_CL_is_caught(monkeypatch):
     monkeypatch.setattr(W, "C_L", lambda U, psi, p: W.spin(W.P_MINUS, psi) + W.spin(W.P_PLUS, W.Tinv(U, psi, p)))
     with pytest.raises(AssertionError):
         P.test_temporal_factorisation(_medium())
+
+
+# --------------------------------------------------------------------------- determinant of mu - D_t
+def test_reversed_polyakov_order_is_caught(monkeypatch):
+    import test_oracle_determinant as PD
+    from oracle import determinant as DT
+
+    def bad(U, p):
+        U0 = W.link(U, W.MU_T)
+        P_ = np.broadcast_to(np.eye(3, dtype=np.complex128), U0.shape[1:]).copy()
+        for t in range(p.T):
+            P_ = U0[t] @ P_
+        return P_
+
+    monkeypatch.setattr(DT, "polyakov", bad)
+    with pytest.raises(AssertionError):
+        PD.test_per_site_determinant_matches_dense_T(2, 4, -1)
+
+
+def test_dropped_boundary_sign_in_determinant_is_caught(monkeypatch):
+    import test_oracle_determinant as PD
+    from oracle import determinant as DT
+
+    def bad(U, p):
+        _, la = np.linalg.slogdet(np.eye(3) - p.mu ** (-p.T) * DT.polyakov(U, p))
+        return 3 * p.T * np.log(p.mu) + la
+
+    monkeypatch.setattr(DT, "logdet_per_site", bad)
+    with pytest.raises(AssertionError):
+        PD.test_logdet_matches_dense_mu_minus_Dt(2, 4, -1)
+    with pytest.raises(AssertionError):
+        PD.test_det_M_is_det_M_hat_times_det_mu_minus_Dt(2, 4, -1)
+
+
+def test_adjoint_resolvent_in_force_is_caught(monkeypatch):
+    import test_oracle_determinant as PD
+    from oracle import determinant as DT
+    orig = DT.transported_resolvent
+    monkeypatch.setattr(DT, "transported_resolvent", lambda U, p: np.conj(np.swapaxes(orig(U, p), -1, -2)))
+    with pytest.raises(AssertionError):
+        PD.test_force_matches_finite_differences_of_dense_determinants(-1)
+
+
+def test_swapped_prefix_and_suffix_in_force_is_caught(monkeypatch):
+    import test_oracle_determinant as PD
+    from oracle import determinant as DT
+
+    def bad(U, p):
+        U0 = W.link(U, W.MU_T)
+        T = p.T
+        eye = np.broadcast_to(np.eye(3, dtype=np.complex128), U0.shape[1:])
+        A = [eye.copy()]
+        for t in range(T - 1):
+            A.append(A[-1] @ U0[t])
+        B = [None] * T
+        B[T - 1] = eye.copy()
+        for t in range(T - 2, -1, -1):
+            B[t] = U0[t + 1] @ B[t + 1]
+        R = p.mu ** (-T) * np.linalg.inv(np.eye(3) - p.bc * p.mu ** (-T) * (A[T - 1] @ U0[T - 1]))
+        return np.stack([U0[t] @ A[t] @ R @ B[t] for t in range(T)])
+
+    monkeypatch.setattr(DT, "transported_resolvent", bad)
+    with pytest.raises(AssertionError):
+        PD.test_force_matches_finite_differences_of_dense_determinants(-1)
