@@ -80,10 +80,16 @@ def paper_flops_per_apply(L, T):
     return (3432 * T - 576) * (L ** 3 // 2)
 
 
+# the sources that compile, launch or lay out the data of the Schur operator's kernels: a change
+# to any of them voids the DRAM traffic recorded in profiles/traffic.json
+HOP_KERNEL_SOURCES = ("wf_abi.cu", "wf_common.cuh", "wf_df64.cuh", "wf_handle.h", "wf_internal.h", "wf_kernels.cu",
+                      "wf_layout.cu", "wf_line.cuh", "wf_wide.cu", "wf_wide.cuh")
+
+
 def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0910_0992_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in HOP_KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -559,6 +565,59 @@ def run_force(args):
     return 0
 
 
+# GB300 FP64 rate: 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (maximum SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def run_logdet(args):
+    """--mode logdet: log det(mu - D_t) and its force (wf_temporal_logdet) on 24^3 x 128 and the two
+    force workloads, both frames: per-kernel CUDA-event times, and the force kernel against the
+    FP64 rate (two 3x3 complex products and the projection, 448 FLOP per site) and against HBM
+    (A(t) read 144 B, force written 256 B per site)."""
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+    import synthetic as S
+
+    peak_bw, peak_kind = measured_peak()
+    rows = []
+    for name in (WORKLOAD, "force_8c32_xi3", "force_16c64_xi3"):
+        prm, U, _ = S.workload(name, with_sources=False)
+        L, T = prm["L"], prm["T"]
+        V = L ** 3 * T
+        F = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
+        for axial in (True, False):
+            w = wf.Wilson(L, T, prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"], axial=axial)
+            w.load_gauge(U)
+            for _ in range(max(3, args.warmup)):
+                w.temporal_logdet(F)
+            torch.cuda.synchronize()
+            n0 = wf.wf_launch_count(w.h)
+            wf.wf_profile(w.h, 1)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                val = w.temporal_logdet(F)
+            call_ms = (time.perf_counter() - t0) / args.steps * 1e3
+            prof = wf.wf_profile_get(w.h)
+            wf.wf_profile(w.h, 0)
+            kern = {k: {"launches": n, "avg_ms": ms / n} for k, (n, ms) in prof.items()}
+            r = {"workload": name, "frame": "axial" if axial else "caller", "logdet": val, "call_ms": call_ms,
+                 "launches_per_call": (wf.wf_launch_count(w.h) - n0) / args.steps, "kernels": kern}
+            fk = kern.get("tdet_force_f64")
+            if fk:
+                sec = fk["avg_ms"] * 1e-3
+                tflops = 448.0 * V / sec / 1e12
+                gbs = 400.0 * V / sec / 1e9
+                r["force_kernel"] = {"fp64_tflops": tflops, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                                     "fp64_frac": tflops / FP64_PEAK_TFLOPS, "hbm_gbs": gbs,
+                                     "hbm_frac": gbs / peak_bw, "hbm_peak": peak_kind}
+            rows.append(r)
+            w.close()
+        del F
+    print(json.dumps({"mode": "logdet", "steps": args.steps, "results": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,9 +629,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the same-GPU 4-D even-odd comparison")
-    ap.add_argument("--mode", choices=["solve", "apply", "methods", "sweep", "force"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "apply", "methods", "sweep", "force", "logdet"], default="solve",
                     help="apply: only FP32 M-hat applies (for kernel profiling); methods: every solve method "
-                         "on 16^3x128; sweep: temporal+Schur vs 4-D even-odd over xi; force: force timings")
+                         "on 16^3x128; sweep: temporal+Schur vs 4-D even-odd over xi; force: force timings; "
+                         "logdet: the temporal-preconditioner determinant and its force")
     ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")
     ap.add_argument("--op", choices=["schur", "eo4d"], default="schur", help="operator of --mode apply")
     ap.add_argument("--workload", default=None, help="--mode apply only: another synthetic workload by name")
@@ -580,8 +640,8 @@ def main():
 
     import synthetic as S
 
-    if args.mode in ("methods", "sweep", "force"):
-        return {"methods": run_methods, "sweep": run_sweep, "force": run_force}[args.mode](args)
+    if args.mode in ("methods", "sweep", "force", "logdet"):
+        return {"methods": run_methods, "sweep": run_sweep, "force": run_force, "logdet": run_logdet}[args.mode](args)
     name = WORKLOAD
     if args.workload:
         if args.mode != "apply" or args.workload not in S.WORKLOADS:

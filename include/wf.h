@@ -187,6 +187,19 @@ int wf_apply_schur_noalloc(wf_handle_t* h, const double* in_odd, double* out_odd
 int wf_force(wf_handle_t* h, const double* phi_odd, double* F, int precision, double tol, double* action,
              int* iters);
 
+/* Determinant of the temporal preconditioner, the extra Hamiltonian term of hybrid Monte Carlo
+ * with the preconditioned operator (the paper anticipates such terms in §IV without deriving
+ * them). C_L^-1 C_R^-1 = mu - D_t (§II.A) and the 3-D Schur complement of C_L M C_R is M-hat
+ * (§II.B), so det M = det(M-hat) det(mu - D_t), and per spatial line det T = det(mu^N_t - s P)
+ * with P = U_t(0) ... U_t(N_t - 1), so
+ *   logdet = log det(mu - D_t) = 4 sum_x log|det(mu^N_t - s P(x))|   (real: det(mu - D_t) >= 0).
+ * Two flavours carry -2 logdet in their action beside phi^dag (M-hat^dag M-hat)^-1 phi.
+ * F (may be null; host or device memory) receives F[t][z][y][x][mu][a] = d logdet / d eps for
+ * U_mu(x) -> exp(i eps T_a) U_mu(x), T_a = lambda_a / 2, in the caller's gauge: 8 reals per link,
+ * zero for the spatial links (layout as for wf_force). logdet (host, may be null) receives the
+ * value. All in FP64 from the loaded gauge field. WF_EINVAL if no gauge field is loaded. */
+int wf_temporal_logdet(wf_handle_t* h, double* logdet, double* F);
+
 /* Autotuned configuration of the FP32 hop kernels of M-hat (no counterpart in the paper): the
  * first FP32 Schur apply of a handle for a given nrhs times every candidate and keeps the fastest
  * (environment WF_AUTOTUNE=0 at the first apply keeps the built-in choice). variant: 1 one thread

@@ -41,6 +41,7 @@ _SIGS = {
     "wf_apply_eo4d_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
     "wf_force": (_i, [_vp, _vp, _vp, _i, _d, _dp, _ip]),
+    "wf_temporal_logdet": (_i, [_vp, _dp, _vp]),
     "wf_solve_many": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _d, _i, _i, _i,
                            ctypes.POINTER(_ip), ctypes.POINTER(_dp), _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
@@ -193,6 +194,25 @@ def wf_force(h, phi_odd, F, precision=WF_FP64, tol=1e-12):
     return S.value, it.value
 
 
+def wf_temporal_logdet(h, F=None):
+    """log det(mu - D_t) of the loaded gauge field; fills F (shape (..., 4, 8) float64) with its force if given."""
+    import numpy as np
+    if F is None:
+        fp = None
+    elif hasattr(F, "data_ptr"):
+        import torch
+        if F.dtype != torch.float64 or not F.is_contiguous():
+            raise TypeError("F must be a contiguous float64 tensor")
+        fp = F.data_ptr()
+    else:
+        if not isinstance(F, np.ndarray) or F.dtype != np.float64 or not F.flags["C_CONTIGUOUS"]:
+            raise TypeError("F must be a C-contiguous float64 array")
+        fp = F.ctypes.data
+    v = ctypes.c_double()
+    _check(h, lib.wf_temporal_logdet(h, ctypes.byref(v), fp))
+    return v.value
+
+
 def wf_launch_count(h):
     return lib.wf_launch_count(h)
 
@@ -288,6 +308,10 @@ class Wilson:
         (wf_apply_eo4d_f32 if f32 else wf_apply_eo4d)(self.h, x_odd4, out, dagger,
                                                        self._nrhs(x_odd4, wf_half_elems(self.h)))
         return out
+
+    def temporal_logdet(self, F=None):
+        """log det(mu - D_t) of the loaded gauge field (F, if given, receives its force)."""
+        return wf_temporal_logdet(self.h, F)
 
     def solve(self, rhs, tol=1e-10, method=WF_TEMPORAL_SCHUR, precision=WF_FP64, x0=None):
         x = self._like(rhs) if x0 is None else x0

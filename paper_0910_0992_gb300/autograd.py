@@ -9,6 +9,11 @@ force F = dS/d eps for U -> exp(i eps T_a) U at U(theta), computed by the librar
 The forward pass keeps nothing of the solve: the backward pass runs the solve again, so
 memory stays at one force field.
 
+TemporalDeterminant.apply(theta, wilson, U0) returns log det(mu - D_t) at U(theta) with the
+same gradient convention (wf_temporal_logdet). det M = det(M-hat) det(mu - D_t), so a
+two-flavour action in terms of M-hat is
+    PseudofermionAction.apply(theta, w, U0, phi) - 2 * TemporalDeterminant.apply(theta, w, U0).
+
 Building U from theta (a 3x3 matrix exponential per link) is input preparation done with
 torch; every step of the action and the force runs in libwf.
 """
@@ -57,3 +62,19 @@ class PseudofermionAction(torch.autograd.Function):
         F = torch.empty(ctx.U.shape[:-2] + (8,), dtype=torch.float64, device=ctx.U.device)
         _lib.wf_force(ctx.wilson.h, ctx.phi, F, ctx.precision, ctx.tol)
         return grad_S * F, None, None, None, None, None
+
+
+class TemporalDeterminant(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, wilson, U0):
+        U = links_at(theta.detach(), U0).contiguous()
+        wilson.load_gauge(U)
+        ctx.wilson, ctx.U = wilson, U
+        return torch.tensor(_lib.wf_temporal_logdet(wilson.h), dtype=torch.float64, device=theta.device)
+
+    @staticmethod
+    def backward(ctx, grad_S):
+        ctx.wilson.load_gauge(ctx.U)
+        F = torch.empty(ctx.U.shape[:-2] + (8,), dtype=torch.float64, device=ctx.U.device)
+        _lib.wf_temporal_logdet(ctx.wilson.h, F)
+        return grad_S * F, None, None

@@ -3,7 +3,8 @@
 24^3 x 128, xi = 3.5: twelve right-hand sides per launch with the autotuned FP32 hop kernels.
 The oracle computes sampled outputs: one source of a batched M-hat apply against the oracle's
 full-lattice M-hat (FP32 tolerance, 1e-6 relative), and the solve of the twelve point sources
-checked by the oracle's M on two sampled sources (FP64 true residual <= 1e-10, with rounding room).
+checked by the oracle's M on two sampled sources (FP64 true residual <= 1e-10, with rounding room);
+and log det(mu - D_t) with its force on the whole lattice (1e-13 / 1e-11 relative).
 Each oracle evaluation at this size takes tens of seconds on the host.
 """
 
@@ -61,3 +62,16 @@ def test_full_size_point_source_solve_sampled(full):
     psi = x.cpu().numpy()
     for k in (0, 11):
         assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+
+
+def test_full_size_temporal_logdet(full):
+    """log det(mu - D_t) and its force on the whole 24^3 x 128 lattice (axial frame)."""
+    from oracle import determinant as DT
+    p, U, _, w = full
+    F = torch.empty((p.T, p.L, p.L, p.L, 4, 8), dtype=torch.float64, device="cuda")
+    got = w.temporal_logdet(F)
+    ref = DT.logdet_temporal(U, p)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+    Fr = DT.force_logdet_temporal(U, p)
+    Fg = F.cpu().numpy()
+    assert np.linalg.norm((Fg - Fr).ravel()) <= 1e-11 * np.linalg.norm(Fr.ravel())
