@@ -16,9 +16,11 @@ Modules:
              through the six factors of M-hat), pinned by central finite differences
   determinant -- log det(mu - D_t) = log|det M| - log|det M-hat| from Polyakov products, and its
              force; the extra Hamiltonian term of the temporal preconditioner in HMC (§IV)
+  clover  -- the SW clover term (clover-leaf field strength), M_SW = M + A, partial temporal
+             preconditioning with 3-D ILU (Eq. TPrecPartial, App. B's apply sequence) and its solve
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``
 except where its docstring says "parity unpinned".
 """
 
-from . import wilson, solve, dense, flops, force, determinant  # noqa: F401
+from . import wilson, solve, dense, flops, force, determinant, clover  # noqa: F401

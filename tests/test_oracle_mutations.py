@@ -2,7 +2,8 @@
 
 Each case patches one plausible error into the oracle (a flipped sign, a dropped
 factor, a transposed link, a wrong recurrence sign, a reversed product) and checks
-that at least one pin of ``test_oracle_pins`` or ``test_oracle_determinant`` then fails.
+that at least one pin of ``test_oracle_pins``, ``test_oracle_determinant`` or
+``test_oracle_clover`` then fails.
 """
 
 import numpy as np
@@ -159,3 +160,55 @@ def test_swapped_prefix_and_suffix_in_force_is_caught(monkeypatch):
     monkeypatch.setattr(DT, "transported_resolvent", bad)
     with pytest.raises(AssertionError):
         PD.test_force_matches_finite_differences_of_dense_determinants(-1)
+
+
+# --------------------------------------------------------------------------- clover, partial preconditioning, ILU
+def test_reversed_clover_leaf_is_caught(monkeypatch):
+    import test_oracle_clover as PC
+    from oracle import clover as CL
+    orig = CL.clover_leaves
+
+    def bad(U, mu, nu):
+        Um, Un = W.link(U, mu), W.link(U, nu)
+        first = Um @ CL._sh(Un, mu, 1) @ CL._dag(CL._sh(Um, nu, 1)) @ CL._dag(Un)
+        return orig(U, mu, nu) - first + CL._dag(first)   # one leaf traversed the other way
+
+    monkeypatch.setattr(CL, "clover_leaves", bad)
+    with pytest.raises(AssertionError):
+        PC.test_abelian_field_strength_spatial_plane()
+
+
+def test_kept_trace_in_field_strength_is_caught(monkeypatch):
+    import test_oracle_clover as PC
+    from oracle import clover as CL
+    monkeypatch.setattr(CL, "field_strength", lambda U, mu, nu: (CL.clover_leaves(U, mu, nu)
+                                                                 - CL._dag(CL.clover_leaves(U, mu, nu))) / 8.0)
+    with pytest.raises(AssertionError):
+        PC.test_trace_is_removed()
+
+
+def test_sigma_without_half_is_caught(monkeypatch):
+    import test_oracle_clover as PC
+    from oracle import clover as CL
+    monkeypatch.setattr(CL, "sigma", lambda mu, nu: W.GAMMA[mu] @ W.GAMMA[nu] - W.GAMMA[nu] @ W.GAMMA[mu])
+    with pytest.raises(AssertionError):
+        PC.test_abelian_field_strength_temporal_plane()
+
+
+def test_wrong_sign_in_ilu_sequence_is_caught(monkeypatch):
+    import test_oracle_clover as PC
+    from oracle import clover as CL
+
+    def bad(U, Acl, psi, p, par3=None):
+        if par3 is None:
+            par3 = W.parity3(p.L, p.T)
+        ev, od = par3 == 0, par3 == 1
+        psi_e, psi_o = W.restrict(psi, ev), W.restrict(psi, od)
+        t1 = W.Dbar_s(U, psi_o, p, 0, par3) / p.gamma_f
+        t2 = CL.Abar(U, Acl, t1 + psi_e, p, 0, par3)
+        chi_o = psi_o + CL.Abar(U, Acl, psi_o, p, 1, par3) + W.Dbar_s(U, t2 + t1, p, 1, par3) / p.gamma_f
+        return psi_e + t2 + chi_o
+
+    monkeypatch.setattr(CL, "M_ilu", bad)
+    with pytest.raises(AssertionError):
+        PC.test_ilu_sequence_is_S_L_M_S_R(-1)
