@@ -449,7 +449,7 @@ def _timed_solve(wf, torch, w, stream, rhs, x, method, prec, tol, reps=1):
     return e0.elapsed_time(e1) / reps / 1e3, list(it), list(res)
 
 
-METHOD_NAMES = {0: "unprec", 1: "eo4d", 2: "temporal", 3: "temporal_schur"}
+METHOD_NAMES = {0: "unprec", 1: "eo4d", 2: "temporal", 3: "temporal_schur", 4: "temporal_ilu"}
 
 
 def run_methods(args):
@@ -565,6 +565,74 @@ def run_force(args):
     return 0
 
 
+def spatial_plaquette(U):
+    """<(1/3) Re tr U_ij> over sites and spatial planes i < j (input preparation for Eq. ClovCoeffs)."""
+    import numpy as np
+    acc, n = 0.0, 0
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        Ui, Uj = U[..., i, :, :], U[..., j, :, :]
+        Uj_i = np.roll(Uj, -1, axis=3 - i)   # U_j(x + i); lattice axes 0..3 = t, z, y, x
+        Ui_j = np.roll(Ui, -1, axis=3 - j)   # U_i(x + j)
+        P = Ui @ Uj_i @ np.conj(np.swapaxes(Ui_j, -1, -2)) @ np.conj(np.swapaxes(Uj, -1, -2))
+        acc += float(np.real(np.trace(P, axis1=-2, axis2=-1)).sum()) / 3.0
+        n += P.shape[0] * P.shape[1] * P.shape[2] * P.shape[3]
+    return acc / n
+
+
+def run_clover(args):
+    """--mode clover: the clover operator with partial temporal preconditioning and 3-D ILU on
+    16^3 x 128, xi = 3.5, one Gaussian source, tree-level tadpole coefficients (Eq. ClovCoeffs,
+    u_t = 1, gamma_g = gamma_f = xi, u_s from the spatial plaquette): FP64 and FP32 (FP64
+    reliable updates) solves to 1e-10, the Wilson temporal + 3-D Schur solve of the same source
+    beside them, and per-kernel CUDA-event times of one FP32 ILU solve (the clover apply kernel
+    against HBM: half its chiral blocks, 576 B, and the spinor in and out, 192 B, per site in FP32)."""
+    import torch
+
+    import paper_0910_0992_gb300 as wf
+    import synthetic as S
+
+    name = "wilson_16c128_xi3.5"
+    prm, U, eta = S.workload(name)
+    xi = prm["kappa_t"] / prm["kappa_s"]
+    u_s = spatial_plaquette(U) ** 0.25
+    c_s = 1.0 / (u_s ** 3 * xi)
+    c_t = (1.0 + 1.0 / xi) / (2.0 * u_s ** 2)
+    stream = torch.cuda.Stream()
+    w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
+    w.set_stream(stream.cuda_stream)
+    rhs = torch.from_numpy(eta).cuda()
+    x = torch.empty_like(rhs)
+    rows = []
+    w.load_gauge(U)
+    for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32")):
+        t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, wf.WF_TEMPORAL_SCHUR, prec, args.tol)
+        rows.append({"operator": "wilson", "method": "temporal_schur", "precision": pname, "iterations": it[0],
+                     "time_s": t, "true_residual": res[0]})
+    w.load_gauge_clover(U, c_s, c_t)
+    for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32")):
+        t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, wf.WF_TEMPORAL_ILU, prec, args.tol)
+        rows.append({"operator": "clover", "method": "temporal_ilu", "precision": pname, "iterations": it[0],
+                     "time_s": t, "true_residual": res[0]})
+    wf.wf_profile(w.h, 1)
+    wf.wf_solve(w.h, rhs, x, 1, args.tol, wf.WF_TEMPORAL_ILU, wf.WF_FP32, 0)
+    prof = wf.wf_profile_get(w.h)
+    wf.wf_profile(w.h, 0)
+    sites = prm["L"] ** 3 * prm["T"] // 2
+    peak, kind = measured_peak()
+    kern = {}
+    for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        kern[k] = {"launches": n, "total_ms": ms, "avg_ms": ms / n}
+    ca = kern.get("clover_apply_f32")
+    if ca:
+        gbs = 768.0 * sites / (ca["avg_ms"] * 1e-3) / 1e9
+        ca.update({"gbs": gbs, "hbm_frac": gbs / peak, "hbm_peak": kind})
+    w.close()
+    print(json.dumps({"mode": "clover", "workload": f"{name}: 16^3x128, xi=3.5, 1 Gaussian source",
+                      "c_s": c_s, "c_t": c_t, "u_s": u_s, "tol": args.tol, "results": rows,
+                      "kernels_one_fp32_ilu_solve": kern}))
+    return 0
+
+
 # GB300 FP64 rate: 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (maximum SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -629,10 +697,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the same-GPU 4-D even-odd comparison")
-    ap.add_argument("--mode", choices=["solve", "apply", "methods", "sweep", "force", "logdet"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "apply", "methods", "sweep", "force", "logdet", "clover"], default="solve",
                     help="apply: only FP32 M-hat applies (for kernel profiling); methods: every solve method "
                          "on 16^3x128; sweep: temporal+Schur vs 4-D even-odd over xi; force: force timings; "
-                         "logdet: the temporal-preconditioner determinant and its force")
+                         "logdet: the temporal-preconditioner determinant and its force; clover: the clover operator "
+                         "with partial temporal preconditioning and 3-D ILU")
     ap.add_argument("--nrhs", type=int, default=1, help="sources per apply in --mode apply")
     ap.add_argument("--op", choices=["schur", "eo4d"], default="schur", help="operator of --mode apply")
     ap.add_argument("--workload", default=None, help="--mode apply only: another synthetic workload by name")
@@ -640,8 +709,9 @@ def main():
 
     import synthetic as S
 
-    if args.mode in ("methods", "sweep", "force", "logdet"):
-        return {"methods": run_methods, "sweep": run_sweep, "force": run_force, "logdet": run_logdet}[args.mode](args)
+    if args.mode in ("methods", "sweep", "force", "logdet", "clover"):
+        return {"methods": run_methods, "sweep": run_sweep, "force": run_force, "logdet": run_logdet,
+                "clover": run_clover}[args.mode](args)
     name = WORKLOAD
     if args.workload:
         if args.mode != "apply" or args.workload not in S.WORKLOADS:

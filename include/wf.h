@@ -55,7 +55,9 @@ enum wf_method {
   WF_UNPREC = 0,         /* CGNR on M */
   WF_EO4D = 1,           /* CGNR on the 4-D Schur (even-odd) operator (§II.B, 4D-Schur) */
   WF_TEMPORAL = 2,       /* CGNR on C_L M C_R (§II.A) */
-  WF_TEMPORAL_SCHUR = 3  /* CGNR on M-hat = 1 - gamma_f^-2 D-bar^oe D-bar^eo (§II.B, Eq. TPrecFull) */
+  WF_TEMPORAL_SCHUR = 3, /* CGNR on M-hat = 1 - gamma_f^-2 D-bar^oe D-bar^eo (§II.B, Eq. TPrecFull) */
+  WF_TEMPORAL_ILU = 4    /* CGNR on M-tilde_ILU = S_L (M + A) S_R, the clover operator with partial temporal
+                            preconditioning and 3-D ILU (§II.B, Eq. TPrecPartial; App. B) */
 };
 
 enum wf_precision {
@@ -173,6 +175,30 @@ int wf_solve_many(int n, wf_handle_t* const* hs, const double* const* rhs, doubl
  *     device work overlaps (several streams, handles or host threads) race: order them. */
 #define WF_NOALLOC_SCRATCH_BYTES (16u << 20)
 int wf_apply_schur_noalloc(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+
+/* Clover (SW) operator M_SW = A + mu - D_t - D_s / gamma_f (§II, Eq. for M and for A), with
+ *   A(x) = -[(c_t/2) sum_i sigma_i0 F_i0(x) + (c_s/2) sum_{i<j} sigma_ij F_ij(x)],
+ *   sigma_mu nu = [gamma_mu, gamma_nu] / 2 (Dirac-Pauli basis),
+ *   F_mu nu = (Q_mu nu - Q_mu nu^dag) / 8 with its trace removed, Q_mu nu(x) the sum of the four
+ *   plaquette leaves of the mu nu plane at x (orientation of U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag).
+ * c_s and c_t are the caller's (Eq. ClovCoeffs gives their tadpole-improved values).
+ * wf_load_gauge_clover: wf_load_gauge(h, U), then A built from the same U (FP64, stored with an
+ * FP32 copy, 2 x 36 complex per site); a later wf_load_gauge removes it. While a clover term is
+ * loaded, wf_solve accepts only WF_TEMPORAL_ILU (which solves M_SW) and wf_force returns WF_EINVAL;
+ * the apply entry points above keep applying the Wilson operators.
+ * wf_apply_clover: out = A in on full fields [rhs][V][spin][colour] (FP64).
+ * wf_apply_ilu: out = M-tilde_ILU in (dagger: gamma_5 M-tilde_ILU gamma_5) on full fields, with
+ *   M-tilde_ILU = S_L M_SW S_R (the Wilson S_L, S_R of §II.B applied to M_SW), applied by the
+ *   sequence of App. B: t1 = g Dbar^eo psi_o, t2 = Abar^ee (t1 + psi_e), chi_e = psi_e + t2,
+ *   chi_o = psi_o + Abar^oo psi_o + g Dbar^oe (t2 - t1), g = 1/gamma_f, Abar = C_L A C_R,
+ *   Dbar = C_L D_s C_R; without a clover term A = 0 and it is diag(1, M-hat). _f32: FP32 steps.
+ * wf_solve(..., WF_TEMPORAL_ILU, ...) solves M_SW x = rhs as M-tilde_ILU y = S_L rhs, x = S_R y,
+ * accepted on the FP64 true residual of M_SW; no initial guess (WF_X0 gives WF_EINVAL).
+ * Errors: WF_EINVAL (no gauge field; no clover term for wf_apply_clover; non-finite c_s, c_t). */
+int wf_load_gauge_clover(wf_handle_t* h, const double* U, double c_s, double c_t);
+int wf_apply_clover(wf_handle_t* h, const double* in, double* out, int nrhs);
+int wf_apply_ilu(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
+int wf_apply_ilu_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 
 /* Pseudofermion force of the temporally preconditioned operator. For the action
  *   S = phi^dag (M-hat^dag M-hat)^-1 phi,   phi an odd field (as for wf_apply_schur, one source),

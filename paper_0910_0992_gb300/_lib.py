@@ -7,7 +7,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "libwf.so")
 
 WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ESINGULAR, WF_ENOCONV, WF_ENAN, WF_ETIMEOUT = range(8)
-WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR = range(4)
+WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR, WF_TEMPORAL_ILU = range(5)
 WF_FP64, WF_FP32 = 0, 1
 WF_X0 = 1
 
@@ -42,6 +42,10 @@ _SIGS = {
     "wf_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _ip, _dp]),
     "wf_force": (_i, [_vp, _vp, _vp, _i, _d, _dp, _ip]),
     "wf_temporal_logdet": (_i, [_vp, _dp, _vp]),
+    "wf_load_gauge_clover": (_i, [_vp, _vp, _d, _d]),
+    "wf_apply_clover": (_i, [_vp, _vp, _vp, _i]),
+    "wf_apply_ilu": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_ilu_f32": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_solve_many": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _d, _i, _i, _i,
                            ctypes.POINTER(_ip), ctypes.POINTER(_dp), _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
@@ -126,6 +130,14 @@ def wf_load_gauge(h, U):
     return _check(h, lib.wf_load_gauge(h, _ptr(U)))
 
 
+def wf_load_gauge_clover(h, U, c_s, c_t):
+    return _check(h, lib.wf_load_gauge_clover(h, _ptr(U), float(c_s), float(c_t)))
+
+
+def wf_apply_clover(h, inp, out, nrhs=1):
+    return _check(h, lib.wf_apply_clover(h, _ptr(inp), _ptr(out), int(nrhs)))
+
+
 def _apply(fn):
     def call(h, inp, out, flag, nrhs=1):
         return _check(h, fn(h, _ptr(inp), _ptr(out), int(flag), int(nrhs)))
@@ -133,6 +145,8 @@ def _apply(fn):
 
 
 wf_apply_M = _apply(lib.wf_apply_M)
+wf_apply_ilu = _apply(lib.wf_apply_ilu)
+wf_apply_ilu_f32 = _apply(lib.wf_apply_ilu_f32)
 wf_apply_M_f32 = _apply(lib.wf_apply_M_f32)
 wf_apply_Tinv = _apply(lib.wf_apply_Tinv)
 wf_apply_Tinv_f32 = _apply(lib.wf_apply_Tinv_f32)
@@ -273,6 +287,19 @@ class Wilson:
 
     def load_gauge(self, U):
         wf_load_gauge(self.h, U)
+
+    def load_gauge_clover(self, U, c_s, c_t):
+        wf_load_gauge_clover(self.h, U, c_s, c_t)
+
+    def apply_clover(self, x):
+        out = self._like(x)
+        wf_apply_clover(self.h, x, out, self._nrhs(x, wf_field_elems(self.h)))
+        return out
+
+    def apply_ilu(self, x, dagger=False, f32=False):
+        out = self._like(x)
+        (wf_apply_ilu_f32 if f32 else wf_apply_ilu)(self.h, x, out, dagger, self._nrhs(x, wf_field_elems(self.h)))
+        return out
 
     def _nrhs(self, a, per):
         n = 1

@@ -1145,6 +1145,204 @@ int solve_full(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
 }
 
 // ----------------------------------------------------------------------------
+// Clover (SW) operator M_SW = M + A with partial temporal preconditioning and 3-D ILU
+// (§II.B, Eq. TPrecPartial; App. B): the Wilson C_L, C_R and S_L, S_R applied to M_SW give
+//   M-tilde_ILU = [[1 + Abar^ee, g Abar^ee Dbar^eo], [g Dbar^oe Abar^ee, 1 + Abar^oo - g^2 Dbar^oe (1 - Abar^ee) Dbar^eo]],
+// g = 1/gamma_f, Abar = C_L A C_R, Dbar = C_L D_s C_R; M_SW psi = eta is solved as
+// M-tilde_ILU y = S_L eta, psi = S_R y. Without a clover term A = 0 and M-tilde_ILU = diag(1, M-hat).
+// ----------------------------------------------------------------------------
+
+template <typename R>
+const Cx<R>* clover_blocks(wf_handle* h, int p);
+template <>
+const Cx<double>* clover_blocks<double>(wf_handle* h, int p) {
+  return h->clov64[p].as<Cx<double>>();
+}
+template <>
+const Cx<float>* clover_blocks<float>(wf_handle* h, int p) {
+  return h->clov32[p].as<Cx<float>>();
+}
+
+// out = D_s^{par_out, 1 - par_out} in
+template <typename R>
+void hop_to(wf_handle* h, int par_out, const Cx<R>* in, Cx<R>* out, const char* name) {
+  LineArgs<R> a = line_args<R>(h, par_out, 1);
+  a.src_up = in;
+  a.src_lo = in + 6 * h->g.tp;
+  a.opu = OP_COPY;
+  a.opl = OP_COPY;
+  a.src = SRC_HOP;
+  a.out = out;
+  Prof P(h, pname<R>(name));
+  launch_line<R>(a, LK_GENERIC, h->axial, h->stream);
+}
+
+// out = acc + alpha A^pp in
+template <typename R>
+void clover_on(wf_handle* h, int p, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc, double alpha, int nrhs) {
+  Prof P(h, pname<R>("clover_apply"));
+  launch_clover_apply<R>(h->g, clover_blocks<R>(h, p), in, out, acc, alpha, nrhs, h->stream);
+}
+
+// chi = M-tilde_ILU psi for one right-hand side, by the sequence of App. B:
+//   t1 = g Dbar^eo psi_o, t2 = Abar^ee (t1 + psi_e), chi_e = psi_e + t2,
+//   chi_o = psi_o + Abar^oo psi_o + g Dbar^oe (t2 - t1)
+template <typename R>
+void ilu_apply(wf_handle* h, const Cx<R>* pe, const Cx<R>* po, Cx<R>* ce, Cx<R>* co) {
+  const size_t hn = h->half_int();
+  cudaStream_t s = h->stream;
+  const double g = 1.0 / h->g.gamma_f;
+  const bool cl = h->clover;
+  Cx<R>* a = h->buf<Cx<R>>(pname<R>("il_a"), hn);
+  Cx<R>* b = h->buf<Cx<R>>(pname<R>("il_b"), hn);
+  Cx<R>* c = h->buf<Cx<R>>(pname<R>("il_c"), hn);
+  Cx<R>* d = h->buf<Cx<R>>(pname<R>("il_d"), hn);
+  Cx<R>* e = h->buf<Cx<R>>(pname<R>("il_e"), hn);
+  Cx<R>* f = h->buf<Cx<R>>(pname<R>("il_f"), hn);
+  Cx<R>* t1 = h->buf<Cx<R>>(pname<R>("il_t1"), hn);
+  Cx<R>* t2 = h->buf<Cx<R>>(pname<R>("il_t2"), hn);
+  auto copy = [&](Cx<R>* dst, const Cx<R>* src) {
+    WF_CUDA(cudaMemcpyAsync(dst, src, hn * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  };
+  auto axpby = [&](Cx<R>* y, const Cx<R>* x, double al, double be) {  // y = al x + be y
+    Prof P(h, pname<R>("il_axpby"));
+    launch_axpby<R>(y, x, hn, al, be, s);
+  };
+  line_load<R>(h, 1, po, a, OP_FWD, OP_COPY, 1, "il_c_right");  // a = C_R^o psi_o
+  hop_to<R>(h, 0, a, b, "il_hop");
+  line_load<R>(h, 0, b, t1, OP_COPY, OP_BWD, 1, "il_c_left");
+  axpby(t1, t1, 0.0, g);  // t1 = g Dbar^eo psi_o
+  copy(ce, pe);
+  if (cl) {
+    copy(f, t1);
+    axpby(f, pe, 1.0, 1.0);  // f = t1 + psi_e
+    line_load<R>(h, 0, f, c, OP_FWD, OP_COPY, 1, "il_c_right");
+    clover_on<R>(h, 0, c, d, nullptr, 1.0, 1);
+    line_load<R>(h, 0, d, t2, OP_COPY, OP_BWD, 1, "il_c_left");  // t2 = Abar^ee (t1 + psi_e)
+    axpby(ce, t2, 1.0, 1.0);
+    copy(f, t2);
+    axpby(f, t1, -1.0, 1.0);  // f = t2 - t1
+  } else {
+    copy(f, t1);
+    axpby(f, f, 0.0, -1.0);  // f = -t1
+  }
+  line_load<R>(h, 0, f, c, OP_FWD, OP_COPY, 1, "il_c_right");
+  hop_to<R>(h, 1, c, d, "il_hop");
+  line_load<R>(h, 1, d, e, OP_COPY, OP_BWD, 1, "il_c_left");  // e = Dbar^oe (t2 - t1)
+  copy(co, po);
+  axpby(co, e, g, 1.0);
+  if (cl) {
+    clover_on<R>(h, 1, a, d, nullptr, 1.0, 1);                  // d = A^oo C_R^o psi_o
+    line_load<R>(h, 1, d, e, OP_COPY, OP_BWD, 1, "il_c_left");  // e = Abar^oo psi_o
+    axpby(co, e, 1.0, 1.0);
+  }
+}
+
+// M-tilde_ILU on [even | odd] internal vectors (one right-hand side); the adjoint is
+// gamma_5 M-tilde_ILU gamma_5 (S_R^dag = gamma_5 S_L gamma_5, M_SW gamma_5-hermitian), applied
+// with the spin halves exchanged on both sides
+template <typename R>
+OpFn<R> ilu_op(wf_handle* h) {
+  return [=](const Cx<R>* x, Cx<R>* y, int dagger, double* norm2) {
+    const size_t hn = h->half_int();
+    cudaStream_t s = h->stream;
+    if (dagger) {
+      Cx<R>* xs = h->buf<Cx<R>>(pname<R>("il_xs"), 2 * hn);
+      Cx<R>* ys = h->buf<Cx<R>>(pname<R>("il_ys"), 2 * hn);
+      {
+        Prof P(h, pname<R>("il_swap"));
+        launch_swap_halves<R>(x, xs, 2 * hn, h->g.tp, s);
+      }
+      ilu_apply<R>(h, xs, xs + hn, ys, ys + hn);
+      Prof P(h, pname<R>("il_swap"));
+      launch_swap_halves<R>(ys, y, 2 * hn, h->g.tp, s);
+    } else {
+      ilu_apply<R>(h, x, x + hn, y, y + hn);
+    }
+    if (norm2) {
+      double* partial = h->buf<double>("op_partial", 1024);
+      Prof P(h, pname<R>("norm2"), 2);
+      launch_norm2<R>(y, 2 * hn, 1, partial, norm2, s);
+    }
+  };
+}
+
+// M_SW psi = eta for each right-hand side: b = S_L eta, CGNR on M-tilde_ILU y = b, psi = S_R y,
+// accepted on the FP64 true residual of M_SW (the inner target tightened until it is met)
+int solve_temporal_ilu(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
+                       int precision, int* iters_out, double* resid_out) {
+  const size_t hn = h->half_int(), le = h->lex_elems();
+  cudaStream_t s = h->stream;
+  DfScope dfs(h, precision == WF_FP32);
+  const double g = 1.0 / h->g.gamma_f;
+  Cx<double>* eta = h->buf<Cx<double>>("tl_eta", 2 * hn);
+  Cx<double>* b = h->buf<Cx<double>>("tl_b", 2 * hn);
+  Cx<double>* y = h->buf<Cx<double>>("tl_y", 2 * hn);
+  Cx<double>* psi = h->buf<Cx<double>>("tl_psi", 2 * hn);
+  Cx<double>* r = h->buf<Cx<double>>("tl_r", 2 * hn);
+  Cx<double>* u = h->buf<Cx<double>>("tl_u", hn);
+  Cx<double>* v = h->buf<Cx<double>>("tl_v", hn);
+  auto axpby = [&](Cx<double>* yy, const Cx<double>* xx, double al, double be) {
+    Prof P(h, "tl_axpby_f64");
+    launch_axpby<double>(yy, xx, hn, al, be, s);
+  };
+  int status = WF_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    {
+      Prof P(h, "import_spinor_f64");
+      launch_import_spinor<double>(h->g, eta_lex + k * le, eta, eta + hn, 1, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+    }
+    // b = S_L eta: b_e = C_L^e eta_e, b_o = C_L^o (eta_o + g D_s^oe C_R^e b_e)
+    line_load<double>(h, 0, eta, b, OP_COPY, OP_BWD, 1, "tl_c_left");
+    line_load<double>(h, 0, b, u, OP_FWD, OP_COPY, 1, "tl_c_right");
+    hop_to<double>(h, 1, u, v, "tl_hop");
+    axpby(v, eta + hn, 1.0, g);
+    line_load<double>(h, 1, v, b + hn, OP_COPY, OP_BWD, 1, "tl_c_left");
+    std::vector<double> eta2 = eo_norms(h, eta, eta + hn, hn, 1);
+    std::vector<double> target{tol * std::sqrt(eta2[0]) / (1.0 + h->g.mu)};
+    int its = 0;
+    double rel = 0.0;
+    bool have_x0 = false;
+    for (int pass = 0; pass < 6; ++pass) {
+      std::vector<int> it = precision == WF_FP32
+                                ? cgnr<float>(h, ilu_op<float>(h), ilu_op<double>(h), b, y, 1, 2 * hn, target, 100000,
+                                              have_x0)
+                                : cgnr<double>(h, ilu_op<double>(h), ilu_op<double>(h), b, y, 1, 2 * hn, target,
+                                               100000, have_x0);
+      its += it[0];
+      have_x0 = true;
+      // psi = S_R y: psi_o = C_R^o y_o, psi_e = C_R^e (y_e + g C_L^e D_s^eo C_R^o y_o)
+      line_load<double>(h, 1, y + hn, psi + hn, OP_FWD, OP_COPY, 1, "tl_c_right");
+      hop_to<double>(h, 0, psi + hn, u, "tl_hop");
+      line_load<double>(h, 0, u, v, OP_COPY, OP_BWD, 1, "tl_c_left");
+      axpby(v, y, 1.0, g);
+      line_load<double>(h, 0, v, psi, OP_FWD, OP_COPY, 1, "tl_c_right");
+      // r = eta - M_SW psi
+      m_apply<double>(h, psi, psi + hn, r, r + hn, eta, eta + hn, -1.0, 1);
+      if (h->clover) {
+        clover_on<double>(h, 0, psi, r, r, -1.0, 1);
+        clover_on<double>(h, 1, psi + hn, r + hn, r + hn, -1.0, 1);
+      }
+      std::vector<double> r2 = eo_norms(h, r, r + hn, hn, 1);
+      rel = std::sqrt(r2[0] / (eta2[0] > 0 ? eta2[0] : 1.0));
+      if (rel <= tol) break;
+      if (its >= 100000 || pass == 5) {
+        status = WF_ENOCONV;
+        break;
+      }
+      target[0] *= 0.5 * tol / rel;
+    }
+    {
+      Prof P(h, "export_spinor_f64");
+      launch_export_spinor<double>(h->g, psi, psi + hn, x_lex + k * le, 1, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+    }
+    if (iters_out) iters_out[k] = its;
+    if (resid_out) resid_out[k] = rel;
+  }
+  return status;
+}
+
+// ----------------------------------------------------------------------------
 // Pseudofermion force (HMC use of the preconditioner, proposed in §IV)
 // ----------------------------------------------------------------------------
 
@@ -1251,6 +1449,7 @@ int cg_normal(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, const Cx<
 int force_abi(wf_handle* h, const double* phi_odd, double* F, int precision, double tol, double* action,
               int* iters_out) {
   if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (h->clover) throw Error(WF_EINVAL, "the force is that of the Wilson operator: load the gauge field without a clover term");
   if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
   const Geom& g = h->g;
   const size_t n = h->half_int();
@@ -1427,6 +1626,49 @@ int apply_line_abi(wf_handle* h, const double* in, double* out, int opu, int opl
   return WF_OK;
 }
 
+// M-tilde_ILU (dagger: gamma_5 M-tilde_ILU gamma_5) on full fields
+template <typename R>
+int apply_ilu_abi(wf_handle* h, const double* in, double* out, int dagger, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  const size_t le = h->lex_elems() * nrhs;
+  const size_t hn = h->half_int(), nt = hn * nrhs;
+  const Cx<double>* din = dev_in(h, in, le, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out, le, "stage_out", staged);
+  Cx<R>* ie = h->buf<Cx<R>>(pname<R>("ap_ie"), nt);
+  Cx<R>* io = h->buf<Cx<R>>(pname<R>("ap_io"), nt);
+  Cx<R>* oe = h->buf<Cx<R>>(pname<R>("ap_oe"), nt);
+  Cx<R>* oo = h->buf<Cx<R>>(pname<R>("ap_oo"), nt);
+  { Prof P(h, pname<R>("import_spinor")); launch_import_spinor<R>(h->g, din, ie, io, nrhs, dagger, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
+  for (int k = 0; k < nrhs; ++k) ilu_apply<R>(h, ie + k * hn, io + k * hn, oe + k * hn, oo + k * hn);
+  { Prof P(h, pname<R>("export_spinor")); launch_export_spinor<R>(h->g, oe, oo, dout, nrhs, dagger, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
+  finish_out(h, out, dout, le, staged);
+  return WF_OK;
+}
+
+// out = A in (the clover term alone, site-diagonal) on full fields, FP64
+int apply_clover_abi(wf_handle* h, const double* in, double* out, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (!h->clover) throw Error(WF_EINVAL, "no clover term loaded (wf_load_gauge_clover)");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  const size_t le = h->lex_elems() * nrhs;
+  const size_t nt = h->half_int() * nrhs;
+  const Cx<double>* din = dev_in(h, in, le, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out, le, "stage_out", staged);
+  Cx<double>* ie = h->buf<Cx<double>>("ap_ie_f64", nt);
+  Cx<double>* io = h->buf<Cx<double>>("ap_io_f64", nt);
+  Cx<double>* oe = h->buf<Cx<double>>("ap_oe_f64", nt);
+  Cx<double>* oo = h->buf<Cx<double>>("ap_oo_f64", nt);
+  { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, din, ie, io, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
+  clover_on<double>(h, 0, ie, oe, nullptr, 1.0, nrhs);
+  clover_on<double>(h, 1, io, oo, nullptr, 1.0, nrhs);
+  { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, oe, oo, dout, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream); }
+  finish_out(h, out, dout, le, staged);
+  return WF_OK;
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------
@@ -1509,6 +1751,7 @@ long long wf_half_elems(const wf_handle_t* h) { return h ? (long long)h->g.L * h
 
 int wf_load_gauge(wf_handle_t* h, const double* U) {
   return guarded(h, [&]() {
+    h->clover = false;  // a clover term belongs to the field it was built from
     const Geom& g = h->g;
     const size_t V = (size_t)g.L * g.L * g.L * g.T;
     const Cx<double>* dU = dev_in(h, U, V * 36, "stage_gauge");
@@ -1567,6 +1810,48 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
     }
     return WF_OK;
   });
+}
+
+int wf_load_gauge_clover(wf_handle_t* h, const double* U, double c_s, double c_t) {
+  const int st = wf_load_gauge(h, U);
+  if (st != WF_OK) return st;
+  return guarded(h, [&]() {
+    if (!std::isfinite(c_s) || !std::isfinite(c_t)) throw Error(WF_EINVAL, "c_s and c_t must be finite");
+    const Geom& g = h->g;
+    const size_t V = (size_t)g.L * g.L * g.L * g.T;
+    cudaStream_t s = h->stream;
+    const Cx<double>* dU = dev_in(h, U, V * 36, "stage_gauge");
+    const size_t nh = (size_t)g.Nl * 72 * g.tp;
+    for (int p = 0; p < 2; ++p) {
+      h->clov64[p].ensure(nh * sizeof(Cx<double>), s);
+      h->clov32[p].ensure(nh * sizeof(Cx<float>), s);
+      WF_CUDA(cudaMemsetAsync(h->clov64[p].p, 0, nh * sizeof(Cx<double>), s));  // padding slots stay zero
+    }
+    Cx<double>* F = h->buf<Cx<double>>("clover_F", V * 54);
+    Cx<double>* H[2] = {h->clov64[0].as<Cx<double>>(), h->clov64[1].as<Cx<double>>()};
+    const Cx<double>* rot[2] = {frame_rot(h, 0), frame_rot(h, 1)};
+    {
+      Prof P(h, "clover_build", 2 + 2);
+      launch_clover_build(g, dU, h->axial ? rot : nullptr, c_s, c_t, F, H, s);
+      for (int p = 0; p < 2; ++p) launch_d2f(H[p], h->clov32[p].as<Cx<float>>(), nh, s);
+    }
+    WF_CUDA(cudaStreamSynchronize(s));
+    h->ws.erase("clover_F");  // V x 6 field-strength matrices: needed only while building
+    h->c_s = c_s;
+    h->c_t = c_t;
+    h->clover = true;
+    return WF_OK;
+  });
+}
+
+int wf_apply_clover(wf_handle_t* h, const double* in, double* out, int nrhs) {
+  return guarded(h, [&]() { return apply_clover_abi(h, in, out, nrhs); });
+}
+int wf_apply_ilu(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_ilu_abi<double>(h, in, out, dagger ? 1 : 0, nrhs); });
+}
+int wf_apply_ilu_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_ilu_abi<float>(h, in, out, dagger ? 1 : 0, nrhs); });
 }
 
 int wf_apply_M(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs) {
@@ -1629,8 +1914,13 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     bool staged;
     Cx<double>* dx = dev_out(h, x, le, "stage_out", staged);
     if (x0 && staged) WF_CUDA(cudaMemcpyAsync(dx, x, le * sizeof(Cx<double>), cudaMemcpyHostToDevice, h->stream));
+    if (h->clover && method != WF_TEMPORAL_ILU)
+      throw Error(WF_EINVAL, "a clover term is loaded: WF_TEMPORAL_ILU is the method that solves M + A");
+    if (method == WF_TEMPORAL_ILU && x0) throw Error(WF_EINVAL, "WF_TEMPORAL_ILU takes no initial guess");
     int st;
-    if (method == WF_TEMPORAL_SCHUR)
+    if (method == WF_TEMPORAL_ILU)
+      st = solve_temporal_ilu(h, drhs, dx, nrhs, tol, precision, iters_out, true_resid_out);
+    else if (method == WF_TEMPORAL_SCHUR)
       st = solve_temporal_schur(h, drhs, dx, nrhs, tol, precision, x0, iters_out, true_resid_out);
     else if (method == WF_EO4D)
       st = solve_eo4d(h, drhs, dx, nrhs, tol, precision, x0, iters_out, true_resid_out);

@@ -37,6 +37,11 @@ struct wf_handle {
   wf::DevBuf ut32[2], us32[2], lamb32[2], lamf32[2];
   // axial frame: ut64 holds the rotation g(x) instead of U_t; P per line
   wf::DevBuf pl64[2], pl32[2];
+  // clover term of the SW operator (wf_load_gauge_clover): half its chiral blocks per parity,
+  // [Nl][2][36][tp]; cleared by wf_load_gauge
+  bool clover = false;
+  double c_s = 0, c_t = 0;
+  wf::DevBuf clov64[2], clov32[2];
   wf::DevBuf tma_err;  // error word of the TMA-fed kernels (bounded waits)
   // index tables of the wide kernels: neighbour lines per parity, traversal order per nrhs
   wf::DevBuf nbr_tab[2];

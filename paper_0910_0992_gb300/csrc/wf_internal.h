@@ -197,4 +197,17 @@ struct ForceArgs {
 };
 void launch_force(const ForceArgs& a, cudaStream_t s);
 
+// Clover term (wf_clover.cu): build H_a, H_b (half the chiral blocks of A, [Nl][2][36][tp] per
+// parity) from the lexicographic FP64 links, rotated by rot[p] (the axial-frame rotation, or
+// null in the caller's gauge); F_scratch holds V x 6 matrices
+void launch_clover_build(const Geom& g, const Cx<double>* U_lex, const Cx<double>* rot[2], double c_s, double c_t,
+                         Cx<double>* F_scratch, Cx<double>* H[2], cudaStream_t s);
+// out = acc + alpha A in on one parity (acc may be null; padding slots get acc or zero)
+template <typename R>
+void launch_clover_apply(const Geom& g, const Cx<R>* H, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc, double alpha,
+                         int nrhs, cudaStream_t s);
+// out = in with the spin halves exchanged, n elements of [..][12][tp] fields
+template <typename R>
+void launch_swap_halves(const Cx<R>* in, Cx<R>* out, size_t n, int tp, cudaStream_t s);
+
 }  // namespace wf
