@@ -150,3 +150,58 @@ def solve(U, Acl, eta, p, tol=1e-10, maxiter=100000):
             break
         inner *= 0.5 * tol / rel
     return psi, total, rel
+
+
+# ---------------------------------------------------------------------------
+# The 4-D Schur (even-odd) clover operator: the paper's comparator for the clover case (§II.B,
+# first display; App. B counts its apply as 2 (C(D) + C(A^-1)) per site pair)
+# ---------------------------------------------------------------------------
+def mu_plus_A(Acl, p):
+    """mu + A(x) per site, (T, L, L, L, 4, 3, 4, 3)."""
+    one = np.einsum("ab,cd->acbd", np.eye(4), np.eye(3))
+    return p.mu * one + Acl
+
+
+def mu_plus_A_inv(Acl, p):
+    """(mu + A(x))^-1 per site (dense 12 x 12 inverse), (T, L, L, L, 4, 3, 4, 3)."""
+    B = mu_plus_A(Acl, p)
+    sh = B.shape
+    return np.linalg.inv(B.reshape(sh[:4] + (12, 12))).reshape(sh)
+
+
+def M_hat4_sw(U, Acl, psi_o, p, par4=None):
+    """(mu + A)^oo - D_w^oe (mu + A)^-1_ee D_w^eo on odd-p_4 sites (D_w = D_t + D_s / gamma_f)."""
+    if par4 is None:
+        par4 = W.parity4(p.L, p.T)
+    ev, od = par4 == 0, par4 == 1
+    x = W.restrict(psi_o, od)
+    he = W.restrict(W.D_w(U, x, p), ev)
+    he = apply_A(mu_plus_A_inv(Acl, p), he)
+    return W.restrict(apply_A(mu_plus_A(Acl, p), x) - W.D_w(U, he, p), od)
+
+
+def M_hat4_sw_dag(U, Acl, psi_o, p, par4=None):
+    return W.spin(W.GAMMA5, M_hat4_sw(U, Acl, W.spin(W.GAMMA5, psi_o), p, par4))
+
+
+def solve_eo4d(U, Acl, eta, p, tol=1e-10, maxiter=100000):
+    """M_SW psi = eta by CGNR on the 4-D Schur operator: b_o = eta_o + D_w^oe (mu + A)^-1_ee eta_e,
+    psi_e = (mu + A)^-1_ee (eta_e + D_w^eo psi_o). Returns (psi, CG iterations, true relative residual)."""
+    par4 = W.parity4(p.L, p.T)
+    ev, od = par4 == 0, par4 == 1
+    Minv = mu_plus_A_inv(Acl, p)
+    eta_e = W.restrict(eta, ev)
+    b = W.restrict(eta, od) + W.restrict(W.D_w(U, apply_A(Minv, eta_e), p), od)
+    A = lambda v: M_hat4_sw(U, Acl, v, p, par4)
+    Ad = lambda v: M_hat4_sw_dag(U, Acl, v, p, par4)
+    inner, y, total, rel, psi = tol, None, 0, np.inf, None
+    for _ in range(8):
+        y, it, _ = SV.cgnr(A, Ad, b, x0=y, tol=inner, maxiter=maxiter - total)
+        total += it
+        psi_o = W.restrict(y, od)
+        psi = apply_A(Minv, W.restrict(eta_e + W.D_w(U, psi_o, p), ev)) + psi_o
+        rel = true_residual(U, Acl, psi, eta, p)
+        if rel <= tol or total >= maxiter:
+            break
+        inner *= 0.5 * tol / rel
+    return psi, total, rel

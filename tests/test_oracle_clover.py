@@ -3,8 +3,8 @@
 ``oracle/clover.py`` is tied to: closed forms of F and A for constant abelian fields in a spatial
 and a temporal plane (derived by hand from the definitions), the reduction to the Wilson 3-D
 Schur operator when A = 0, the product S_L M_SW S_R of dense matrices (Eq. TPrecPartial against
-App. B's sequence), hermiticity, chirality and gauge covariance of A, gamma_5-hermiticity, and a
-dense LU solve.
+App. B's sequence), hermiticity, chirality and gauge covariance of A, gamma_5-hermiticity, dense LU
+solves, and the 4-D Schur clover comparator against the dense Schur complement of M_SW.
 """
 
 import numpy as np
@@ -152,3 +152,35 @@ def test_solve_matches_dense_lu(bc):
     ref = np.linalg.solve(Ms, eta.ravel()).reshape(eta.shape)
     assert rel <= 1e-12 and it > 0
     assert _rel(psi, ref) < 1e-9
+
+
+@pytest.mark.parametrize("bc", [-1, 1])
+def test_clover_4d_schur_is_the_dense_schur_complement(bc):
+    """M-hat_4 of M_SW equals M_oo - M_oe M_ee^-1 M_eo of the dense M_SW in 4-D parity order."""
+    p = _params(2, 4, kappa_s=0.08, xi=3.0, bc=bc)
+    U = S.random_gauge(2, 4, 0.5, 81)
+    Acl = CL.clover_term(U, 1.1, 0.9)
+    par4 = W.parity4(p.L, p.T)
+    ev, od = par4 == 0, par4 == 1
+    blk = lambda a, b: D.matrix(lambda v: CL.M_sw(U, Acl, v, p), p.L, p.T, a, b)
+    ref = blk(od, od) - blk(ev, od) @ np.linalg.solve(blk(ev, ev), blk(od, ev))
+    got = D.matrix(lambda v: CL.M_hat4_sw(U, Acl, v, p, par4), p.L, p.T, od, od)
+    assert _rel(got, ref) < 1e-13
+    zero = np.zeros_like(Acl)
+    psi = S.gaussian_source(p.L, p.T, 82)
+    assert _rel(CL.M_hat4_sw(U, zero, psi, p, par4), W.M_hat4(U, psi, p, par4)) < 1e-14
+
+
+def test_clover_4d_schur_solve(tiny):
+    p, U, Acl = tiny
+    eta = S.gaussian_source(p.L, p.T, 83)
+    psi, it, rel = CL.solve_eo4d(U, Acl, eta, p, tol=1e-12)
+    Ms = D.matrix(lambda v: CL.M_sw(U, Acl, v, p), p.L, p.T)
+    ref = np.linalg.solve(Ms, eta.ravel()).reshape(eta.shape)
+    assert rel <= 1e-12 and it > 0
+    assert _rel(psi, ref) < 1e-9
+    par4 = W.parity4(p.L, p.T)
+    a, b = S.gaussian_source(p.L, p.T, 84), S.gaussian_source(p.L, p.T, 85)
+    lhs = np.vdot(a.ravel(), CL.M_hat4_sw(U, Acl, b, p, par4).ravel())
+    rhs = np.vdot(CL.M_hat4_sw_dag(U, Acl, a, p, par4).ravel(), b.ravel())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
