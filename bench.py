@@ -583,8 +583,8 @@ def run_clover(args):
     """--mode clover: the clover operator with partial temporal preconditioning and 3-D ILU on
     16^3 x 128, xi = 3.5, one Gaussian source, tree-level tadpole coefficients (Eq. ClovCoeffs,
     u_t = 1, gamma_g = gamma_f = xi, u_s from the spatial plaquette): FP64 and FP32 (FP64
-    reliable updates) solves to 1e-10, the Wilson temporal + 3-D Schur solve of the same source
-    beside them, and per-kernel CUDA-event times of one FP32 ILU solve (the clover apply kernel
+    reliable updates) solves to 1e-10, against the 4-D Schur clover solve (the paper's
+    comparator) and the Wilson temporal + 3-D Schur solve of the same source, and per-kernel CUDA-event times of one FP32 ILU solve (the clover apply kernel
     against HBM: half its chiral blocks, 576 B, and the spinor in and out, 192 B, per site in FP32)."""
     import torch
 
@@ -609,10 +609,11 @@ def run_clover(args):
         rows.append({"operator": "wilson", "method": "temporal_schur", "precision": pname, "iterations": it[0],
                      "time_s": t, "true_residual": res[0]})
     w.load_gauge_clover(U, c_s, c_t)
-    for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32")):
-        t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, wf.WF_TEMPORAL_ILU, prec, args.tol)
-        rows.append({"operator": "clover", "method": "temporal_ilu", "precision": pname, "iterations": it[0],
-                     "time_s": t, "true_residual": res[0]})
+    for method in (wf.WF_TEMPORAL_ILU, wf.WF_EO4D):
+        for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32")):
+            t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, method, prec, args.tol)
+            rows.append({"operator": "clover", "method": METHOD_NAMES[method], "precision": pname,
+                         "iterations": it[0], "time_s": t, "true_residual": res[0]})
     wf.wf_profile(w.h, 1)
     wf.wf_solve(w.h, rhs, x, 1, args.tol, wf.WF_TEMPORAL_ILU, wf.WF_FP32, 0)
     prof = wf.wf_profile_get(w.h)

@@ -183,9 +183,12 @@ int wf_apply_schur_noalloc(wf_handle_t* h, const double* in_odd, double* out_odd
  *   plaquette leaves of the mu nu plane at x (orientation of U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag).
  * c_s and c_t are the caller's (Eq. ClovCoeffs gives their tadpole-improved values).
  * wf_load_gauge_clover: wf_load_gauge(h, U), then A built from the same U (FP64, stored with an
- * FP32 copy, 2 x 36 complex per site); a later wf_load_gauge removes it. While a clover term is
- * loaded, wf_solve accepts only WF_TEMPORAL_ILU (which solves M_SW) and wf_force returns WF_EINVAL;
- * the apply entry points above keep applying the Wilson operators.
+ * FP32 copy, 2 x 36 complex per site; for even T also the blocks of mu + A and (mu + A)^-1 in the
+ * 4-D even-odd layout, WF_ESINGULAR if some block has no inverse); a later wf_load_gauge removes
+ * it. While a clover term is loaded, wf_solve accepts WF_TEMPORAL_ILU and WF_EO4D, which then
+ * solve M_SW, WF_EO4D with the 4-D Schur clover operator (mu + A)^oo - D_w^oe (mu + A)^-1_ee D_w^eo
+ * (§II.B, the paper's comparator), which wf_apply_eo4d then applies; wf_force returns WF_EINVAL
+ * and the other apply entry points keep applying the Wilson operators.
  * wf_apply_clover: out = A in on full fields [rhs][V][spin][colour] (FP64).
  * wf_apply_ilu: out = M-tilde_ILU in (dagger: gamma_5 M-tilde_ILU gamma_5) on full fields, with
  *   M-tilde_ILU = S_L M_SW S_R (the Wilson S_L, S_R of §II.B applied to M_SW), applied by the

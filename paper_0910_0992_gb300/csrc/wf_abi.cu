@@ -863,10 +863,59 @@ EoArgs<R> eo_args(wf_handle* h, int par, int nrhs) {
 
 size_t eo_elems(const wf_handle* h) { return (size_t)h->g.L * h->g.L * h->g.L * NSPIN_C * (h->g.T / 2); }
 
-// M-hat_4 = mu - mu^-1 D_w^oe D_w^eo on odd 4-D fields (dagger: S M-hat_4 S), two dslash kernels
+template <typename R>
+const Cx<R>* clover_eo(wf_handle* h, int p, bool inverse);
+template <>
+const Cx<double>* clover_eo<double>(wf_handle* h, int p, bool inverse) {
+  return (inverse ? h->clinv64[p] : h->clmu64[p]).as<Cx<double>>();
+}
+template <>
+const Cx<float>* clover_eo<float>(wf_handle* h, int p, bool inverse) {
+  return (inverse ? h->clinv32[p] : h->clmu32[p]).as<Cx<float>>();
+}
+
+// out = acc + alpha (mu + A)^pp in, or with (mu + A)^-1 (inverse), on 4-D even-odd fields
+template <typename R>
+void clover_eo_on(wf_handle* h, int p, bool inverse, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc, double alpha,
+                  int nrhs) {
+  Prof P(h, pname<R>(inverse ? "clover_inv_eo" : "clover_mu_eo"));
+  launch_clover_apply_eo<R>(h->g, clover_eo<R>(h, p, inverse), in, out, acc, alpha, nrhs, h->stream);
+}
+
+// M-hat_4 = mu - mu^-1 D_w^oe D_w^eo on odd 4-D fields (dagger: S M-hat_4 S), two dslash kernels;
+// with a clover term (mu + A)^oo - D_w^oe (mu + A)^-1_ee D_w^eo (mu + A commutes with gamma_5, so
+// the adjoint exchanges spin halves only around the dslash terms)
 template <typename R>
 void eo4d_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* he, double* norm2) {
   const double mu = h->g.mu;
+  if (h->clover) {
+    const size_t nt = eo_elems(h) * nrhs;
+    Cx<R>* he2 = h->buf<Cx<R>>(pname<R>("op_he2"), nt);
+    Cx<R>* tx = h->buf<Cx<R>>(pname<R>("op_tx"), nt);
+    {
+      EoArgs<R> a = eo_args<R>(h, 0, nrhs);
+      a.in = x;
+      a.swap_in = dagger;
+      a.out = he;
+      Prof P(h, pname<R>("eo4d_dslash_eo"));
+      launch_dslash4<R>(a, h->axial, h->stream);
+    }
+    clover_eo_on<R>(h, 0, true, he, he2, nullptr, 1.0, nrhs);
+    clover_eo_on<R>(h, 1, false, x, tx, nullptr, 1.0, nrhs);
+    EoArgs<R> a = eo_args<R>(h, 1, nrhs);
+    a.in = he2;
+    a.a = R(-1);
+    a.x1 = tx;
+    a.b1 = R(1);
+    a.swap_out = dagger;
+    a.stream_out = 1;
+    a.out = out;
+    a.norm2 = norm2;
+    if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nrhs * sizeof(double), h->stream));
+    Prof P(h, pname<R>("eo4d_dslash_oe_axpy"));
+    launch_dslash4<R>(a, h->axial, h->stream);
+    return;
+  }
   {
     EoArgs<R> a = eo_args<R>(h, 0, nrhs);
     a.in = x;
@@ -930,10 +979,12 @@ int solve_eo4d(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
     Prof P(h, "import_eo_f64");
     launch_import_eo<double>(h->g, eta_lex, eta_e, eta_o, nrhs, frame_rot(h, 0), frame_rot(h, 1), -1, s);
   }
+  const bool cl = h->clover;  // clover: (mu + A)^-1_ee in place of mu^-1, (mu + A) psi in the residual
+  if (cl) clover_eo_on<double>(h, 0, true, eta_e, r_e, nullptr, 1.0, nrhs);  // r_e = (mu + A)^-1 eta_e
   {
     EoArgs<double> a = eo_args<double>(h, 1, nrhs);
-    a.in = eta_e;
-    a.a = 1.0 / mu;
+    a.in = cl ? r_e : eta_e;
+    a.a = cl ? 1.0 : 1.0 / mu;
     a.x1 = eta_o;
     a.b1 = 1.0;
     a.out = b_o;
@@ -962,22 +1013,26 @@ int solve_eo4d(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
     {
       EoArgs<double> a = eo_args<double>(h, 0, nrhs);  // psi_e = mu^-1 (eta_e + D_w^eo psi_o)
       a.in = psi_o;
-      a.a = 1.0 / mu;
+      a.a = cl ? 1.0 : 1.0 / mu;
       a.x1 = eta_e;
-      a.b1 = 1.0 / mu;
-      a.out = psi_e;
+      a.b1 = cl ? 1.0 : 1.0 / mu;
+      a.out = cl ? r_e : psi_e;
       Prof P(h, "eo4d_recon_f64");
       launch_dslash4<double>(a, h->axial, s);
     }
-    for (int p = 0; p < 2; ++p) {  // r = eta - mu psi + D_w psi
+    if (cl) clover_eo_on<double>(h, 0, true, r_e, psi_e, nullptr, 1.0, nrhs);  // psi_e = (mu + A)^-1 (...)
+    for (int p = 0; p < 2; ++p) {  // r = eta - mu psi + D_w psi (clover: eta - (mu + A) psi + D_w psi)
+      Cx<double>* rp = p ? r_o : r_e;
+      const Cx<double>* own = p ? psi_o : psi_e;
+      if (cl) clover_eo_on<double>(h, p, false, own, rp, nullptr, 1.0, nrhs);  // r_p = (mu + A) psi_p
       EoArgs<double> a = eo_args<double>(h, p, nrhs);
       a.in = p ? psi_e : psi_o;
       a.a = 1.0;
       a.x1 = p ? eta_o : eta_e;
       a.b1 = 1.0;
-      a.x2 = p ? psi_o : psi_e;
-      a.b2 = -mu;
-      a.out = p ? r_o : r_e;
+      a.x2 = cl ? rp : own;
+      a.b2 = cl ? -1.0 : -mu;
+      a.out = rp;
       a.df = 0;  // the true residual in FP64 arithmetic
       Prof P(h, "eo4d_residual_f64");
       launch_dslash4<double>(a, h->axial, s);
@@ -1835,6 +1890,29 @@ int wf_load_gauge_clover(wf_handle_t* h, const double* U, double c_s, double c_t
       launch_clover_build(g, dU, h->axial ? rot : nullptr, c_s, c_t, F, H, s);
       for (int p = 0; p < 2; ++p) launch_d2f(H[p], h->clov32[p].as<Cx<float>>(), nh, s);
     }
+    if (g.T % 2 == 0) {  // the 4-D Schur comparator: mu + A and its inverse, 4-D even-odd layout
+      const size_t n4 = (size_t)g.L * g.L * g.L * 72 * (g.T / 2);
+      for (int p = 0; p < 2; ++p) {
+        h->clmu64[p].ensure(n4 * sizeof(Cx<double>), s);
+        h->clinv64[p].ensure(n4 * sizeof(Cx<double>), s);
+        h->clmu32[p].ensure(n4 * sizeof(Cx<float>), s);
+        h->clinv32[p].ensure(n4 * sizeof(Cx<float>), s);
+      }
+      const Cx<double>* Hc[2] = {H[0], H[1]};
+      Cx<double>* M4[2] = {h->clmu64[0].as<Cx<double>>(), h->clmu64[1].as<Cx<double>>()};
+      Cx<double>* Mi4[2] = {h->clinv64[0].as<Cx<double>>(), h->clinv64[1].as<Cx<double>>()};
+      WF_CUDA(cudaMemsetAsync(h->iflag.p, 0, sizeof(int), s));
+      Prof P(h, "clover_eo4_build", 1 + 4);
+      launch_clover_eo4_build(g, Hc, M4, Mi4, h->iflag.as<int>(), s);
+      for (int p = 0; p < 2; ++p) {
+        launch_d2f(M4[p], h->clmu32[p].as<Cx<float>>(), n4, s);
+        launch_d2f(Mi4[p], h->clinv32[p].as<Cx<float>>(), n4, s);
+      }
+      int flag = 0;
+      WF_CUDA(cudaMemcpyAsync(&flag, h->iflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      WF_CUDA(cudaStreamSynchronize(s));
+      if (flag) throw Error(WF_ESINGULAR, "mu + A is singular on some site");
+    }
     WF_CUDA(cudaStreamSynchronize(s));
     h->ws.erase("clover_F");  // V x 6 field-strength matrices: needed only while building
     h->c_s = c_s;
@@ -1914,8 +1992,8 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     bool staged;
     Cx<double>* dx = dev_out(h, x, le, "stage_out", staged);
     if (x0 && staged) WF_CUDA(cudaMemcpyAsync(dx, x, le * sizeof(Cx<double>), cudaMemcpyHostToDevice, h->stream));
-    if (h->clover && method != WF_TEMPORAL_ILU)
-      throw Error(WF_EINVAL, "a clover term is loaded: WF_TEMPORAL_ILU is the method that solves M + A");
+    if (h->clover && method != WF_TEMPORAL_ILU && method != WF_EO4D)
+      throw Error(WF_EINVAL, "a clover term is loaded: WF_TEMPORAL_ILU and WF_EO4D are the methods that solve M + A");
     if (method == WF_TEMPORAL_ILU && x0) throw Error(WF_EINVAL, "WF_TEMPORAL_ILU takes no initial guess");
     int st;
     if (method == WF_TEMPORAL_ILU)

@@ -17,7 +17,8 @@
 // the lexicographic links and rotates it into the axial frame when the handle works there
 // (F -> g F g^dag, g the frame rotation of the site); k_clover_blocks, one thread per entry of
 // H_a, H_b, sums the six planes' F against the chiral blocks of sigma (the host folds the
-// coefficients -c/2 and the 1/2 of H into those 2x2 blocks).
+// coefficients -c/2 and the 1/2 of H into those 2x2 blocks). For the 4-D Schur comparator,
+// k_clover_eo4 stores the blocks of mu + A and of (mu + A)^-1 in the 4-D even-odd layout.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -133,47 +134,115 @@ __global__ void __launch_bounds__(kBlock) k_clover_blocks(const Geom g, const Cl
   H[(((size_t)line_of(g, x, y, z) * 2 + k) * 36 + e) * g.tp + slot_of(g, t)] = acc;
 }
 
-// out = acc + alpha A in (acc may be null: out = alpha A in) on one parity, all right-hand sides
-template <typename R>
+// out = acc + alpha H-blocks in (acc may be null: out = alpha H in) on one parity, all right-hand
+// sides. Line layout (EO = false): fields [rhs][Nl][12][tp], blocks [Nl][2][36][tp], padding slots
+// (t >= T) kept at the accumulator or zero. 4-D even-odd layout (EO = true): fields
+// [rhs][L^3][12][T/2], blocks [L^3][2][36][T/2], no padding.
+template <typename R, bool EO>
 __global__ void __launch_bounds__(kBlock) k_clover_apply(const Geom g, const Cx<R>* __restrict__ H,
                                                          const Cx<R>* __restrict__ in, Cx<R>* out,
                                                          const Cx<R>* acc, R alpha, int nrhs) {
+  const int outer = EO ? g.L * g.L * g.L : g.Nl;
+  const int inner = EO ? g.T / 2 : g.tp;
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)nrhs * g.Nl * g.tp) return;
-  const int sl = (int)(i % g.tp);
-  const int l = (int)((i / g.tp) % g.Nl);
-  const size_t base = (i / g.tp) * NSPIN_C * g.tp + sl;  // ((rhs Nl + l) 12) tp + slot
-  const int t = (sl % g.lpl) * g.n + sl / g.lpl;
-  if (t >= g.T) {  // padding slot: keep it at the accumulator (zero without one)
+  if (i >= (size_t)nrhs * outer * inner) return;
+  const int sl = (int)(i % inner);
+  const int l = (int)((i / inner) % outer);
+  const size_t base = (i / inner) * NSPIN_C * inner + sl;  // ((rhs outer + l) 12) inner + slot
+  if (!EO) {
+    const int t = (sl % g.lpl) * g.n + sl / g.lpl;
+    if (t >= g.T) {  // padding slot: keep it at the accumulator (zero without one)
 #pragma unroll
-    for (int c = 0; c < NSPIN_C; ++c) out[base + (size_t)c * g.tp] = acc ? acc[base + (size_t)c * g.tp] : czero<R>();
-    return;
+      for (int c = 0; c < NSPIN_C; ++c) out[base + (size_t)c * inner] = acc ? acc[base + (size_t)c * inner] : czero<R>();
+      return;
+    }
   }
   Cx<R> sv[6], dv[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    const Cx<R> u = in[base + (size_t)c * g.tp], lo = in[base + (size_t)(c + 6) * g.tp];
+    const Cx<R> u = in[base + (size_t)c * inner], lo = in[base + (size_t)(c + 6) * inner];
     sv[c] = u + lo;
     dv[c] = u - lo;
   }
-  const Cx<R>* Ha = H + ((size_t)l * 2) * 36 * g.tp + sl;
-  const Cx<R>* Hb = Ha + (size_t)36 * g.tp;
+  const Cx<R>* Ha = H + ((size_t)l * 2) * 36 * inner + sl;
+  const Cx<R>* Hb = Ha + (size_t)36 * inner;
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     Cx<R> ya = czero<R>(), yb = czero<R>();
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      ya = cfma(ya, Ha[(size_t)(6 * r + c) * g.tp], sv[c]);
-      yb = cfma(yb, Hb[(size_t)(6 * r + c) * g.tp], dv[c]);
+      ya = cfma(ya, Ha[(size_t)(6 * r + c) * inner], sv[c]);
+      yb = cfma(yb, Hb[(size_t)(6 * r + c) * inner], dv[c]);
     }
     Cx<R> up = alpha * (ya + yb), lo = alpha * (ya - yb);
     if (acc) {
-      up = up + acc[base + (size_t)r * g.tp];
-      lo = lo + acc[base + (size_t)(r + 6) * g.tp];
+      up = up + acc[base + (size_t)r * inner];
+      lo = lo + acc[base + (size_t)(r + 6) * inner];
     }
-    out[base + (size_t)r * g.tp] = up;
-    out[base + (size_t)(r + 6) * g.tp] = lo;
+    out[base + (size_t)r * inner] = up;
+    out[base + (size_t)(r + 6) * inner] = lo;
   }
+}
+
+// The 4-D even-odd blocks of mu + A and of its inverse, from the line-layout blocks H = A_k / 2:
+// one thread per site and chiral block; B = mu 1 + A_k (6x6), B^-1 by Gauss-Jordan elimination
+// with partial pivoting; stored halved like H. Sets *singular when a pivot vanishes.
+__global__ void __launch_bounds__(128) k_clover_eo4(const Geom g, double mu, const Cx<double>* __restrict__ H0,
+                                                    const Cx<double>* __restrict__ H1, Cx<double>* M0, Cx<double>* M1,
+                                                    Cx<double>* Mi0, Cx<double>* Mi1, int* singular) {
+  const size_t V = (size_t)g.L * g.L * g.L * g.T;
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= V * 2) return;
+  const int k = (int)(i % 2);
+  const size_t site = i / 2;
+  int x, y, z, t;
+  site_xyzt(g, site, x, y, z, t);
+  const Cx<double>* H = (((x + y + z) & 1) ? H1 : H0) + (((size_t)line_of(g, x, y, z) * 2 + k) * 36) * g.tp +
+                        slot_of(g, t);
+  const int Th = g.T / 2;
+  const size_t s3 = (size_t)x + g.L * ((size_t)y + g.L * z);
+  const size_t ob = ((s3 * 2 + k) * 36) * Th + t / 2;
+  const bool odd4 = ((x + y + z + t) & 1) != 0;
+  Cx<double>* M = odd4 ? M1 : M0;
+  Cx<double>* Mi = odd4 ? Mi1 : Mi0;
+  Cx<double> a[6][12];  // [B | 1]
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 6; ++c) {
+      const Cx<double> h = H[(size_t)(6 * r + c) * g.tp];
+      a[r][c] = mk<double>(2.0 * h.re + (r == c ? mu : 0.0), 2.0 * h.im);
+      a[r][c + 6] = mk<double>(r == c ? 1.0 : 0.0, 0.0);
+      M[(size_t)(6 * r + c) * Th + ob] = mk<double>(0.5 * a[r][c].re, 0.5 * a[r][c].im);
+    }
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    double best = a[c][c].re * a[c][c].re + a[c][c].im * a[c][c].im;
+    for (int r = c + 1; r < 6; ++r) {
+      const double m = a[r][c].re * a[r][c].re + a[r][c].im * a[r][c].im;
+      if (m > best) {
+        best = m;
+        piv = r;
+      }
+    }
+    if (!(best > 1e-24)) {
+      atomicExch(singular, 1);
+      return;
+    }
+    if (piv != c)
+      for (int j = 0; j < 12; ++j) {
+        const Cx<double> tmp = a[c][j];
+        a[c][j] = a[piv][j];
+        a[piv][j] = tmp;
+      }
+    const Cx<double> inv = mk<double>(a[c][c].re / best, -a[c][c].im / best);
+    for (int j = 0; j < 12; ++j) a[c][j] = cmul(a[c][j], inv);
+    for (int r = 0; r < 6; ++r) {
+      if (r == c) continue;
+      const Cx<double> f = a[r][c];
+      for (int j = 0; j < 12; ++j) a[r][j] = a[r][j] - cmul(f, a[c][j]);
+    }
+  }
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 6; ++c) Mi[(size_t)(6 * r + c) * Th + ob] = mk<double>(0.5 * a[r][c + 6].re, 0.5 * a[r][c + 6].im);
 }
 
 // out = in with the spin halves exchanged (the Dirac-Pauli gamma_5 up to its sign)
@@ -256,13 +325,32 @@ void launch_clover_build(const Geom& g, const Cx<double>* U_lex, const Cx<double
 template <typename R>
 void launch_clover_apply(const Geom& g, const Cx<R>* H, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc, double alpha,
                          int nrhs, cudaStream_t s) {
-  k_clover_apply<R><<<grid_of((size_t)nrhs * g.Nl * g.tp), kBlock, 0, s>>>(g, H, in, out, acc, (R)alpha, nrhs);
+  k_clover_apply<R, false><<<grid_of((size_t)nrhs * g.Nl * g.tp), kBlock, 0, s>>>(g, H, in, out, acc, (R)alpha, nrhs);
   WF_CUDA(cudaGetLastError());
 }
 template void launch_clover_apply<float>(const Geom&, const Cx<float>*, const Cx<float>*, Cx<float>*,
                                          const Cx<float>*, double, int, cudaStream_t);
 template void launch_clover_apply<double>(const Geom&, const Cx<double>*, const Cx<double>*, Cx<double>*,
                                           const Cx<double>*, double, int, cudaStream_t);
+
+template <typename R>
+void launch_clover_apply_eo(const Geom& g, const Cx<R>* H, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc,
+                            double alpha, int nrhs, cudaStream_t s) {
+  const size_t n = (size_t)nrhs * g.L * g.L * g.L * (g.T / 2);
+  k_clover_apply<R, true><<<grid_of(n), kBlock, 0, s>>>(g, H, in, out, acc, (R)alpha, nrhs);
+  WF_CUDA(cudaGetLastError());
+}
+template void launch_clover_apply_eo<float>(const Geom&, const Cx<float>*, const Cx<float>*, Cx<float>*,
+                                            const Cx<float>*, double, int, cudaStream_t);
+template void launch_clover_apply_eo<double>(const Geom&, const Cx<double>*, const Cx<double>*, Cx<double>*,
+                                             const Cx<double>*, double, int, cudaStream_t);
+
+void launch_clover_eo4_build(const Geom& g, const Cx<double>* H[2], Cx<double>* M[2], Cx<double>* Minv[2],
+                             int* singular, cudaStream_t s) {
+  const size_t n = (size_t)g.L * g.L * g.L * g.T * 2;
+  k_clover_eo4<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, g.mu, H[0], H[1], M[0], M[1], Minv[0], Minv[1], singular);
+  WF_CUDA(cudaGetLastError());
+}
 
 template <typename R>
 void launch_swap_halves(const Cx<R>* in, Cx<R>* out, size_t n, int tp, cudaStream_t s) {

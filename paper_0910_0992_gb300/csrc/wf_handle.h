@@ -42,6 +42,9 @@ struct wf_handle {
   bool clover = false;
   double c_s = 0, c_t = 0;
   wf::DevBuf clov64[2], clov32[2];
+  // the same blocks for mu + A and (mu + A)^-1 in the 4-D even-odd layout [L^3][2][36][T/2] per
+  // 4-D parity (even T only): the 4-D Schur clover operator
+  wf::DevBuf clmu64[2], clmu32[2], clinv64[2], clinv32[2];
   wf::DevBuf tma_err;  // error word of the TMA-fed kernels (bounded waits)
   // index tables of the wide kernels: neighbour lines per parity, traversal order per nrhs
   wf::DevBuf nbr_tab[2];

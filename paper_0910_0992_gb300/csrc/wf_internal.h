@@ -206,6 +206,14 @@ void launch_clover_build(const Geom& g, const Cx<double>* U_lex, const Cx<double
 template <typename R>
 void launch_clover_apply(const Geom& g, const Cx<R>* H, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc, double alpha,
                          int nrhs, cudaStream_t s);
+// the same on a 4-D even-odd field [rhs][L^3][12][T/2] with blocks [L^3][2][36][T/2]
+template <typename R>
+void launch_clover_apply_eo(const Geom& g, const Cx<R>* H, const Cx<R>* in, Cx<R>* out, const Cx<R>* acc,
+                            double alpha, int nrhs, cudaStream_t s);
+// blocks of mu + A and of (mu + A)^-1 (halved) in the 4-D even-odd layout, per 4-D parity, from
+// the line-layout blocks H; *singular set where mu + A has no inverse
+void launch_clover_eo4_build(const Geom& g, const Cx<double>* H[2], Cx<double>* M[2], Cx<double>* Minv[2],
+                             int* singular, cudaStream_t s);
 // out = in with the spin halves exchanged, n elements of [..][12][tp] fields
 template <typename R>
 void launch_swap_halves(const Cx<R>* in, Cx<R>* out, size_t n, int tp, cudaStream_t s);

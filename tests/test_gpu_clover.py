@@ -2,9 +2,10 @@
 
 Against ``oracle/clover.py`` on lattices with several warps, padded time lines, both boundary
 conditions and both frames: the clover term A (FP64, 1e-12), M-tilde_ILU and its adjoint
-(FP64 1e-12, FP32 1e-6), the reduction to diag(1, M-hat) without a clover term, solves of
-M_SW to an FP64 true residual <= 1e-10 (checked again with the oracle's M_SW), and the errors of
-the clover state (Wilson-only methods and the force refuse while a clover term is loaded).
+(FP64 1e-12, FP32 1e-6), the reduction to diag(1, M-hat) without a clover term, the 4-D Schur
+clover comparator and its adjoint (same tolerances), solves of M_SW by both methods to an FP64
+true residual <= 1e-10 (checked again with the oracle's M_SW), and the errors of the clover state
+(Wilson-only methods and the force refuse while a clover term is loaded).
 """
 
 import numpy as np
@@ -12,6 +13,7 @@ import pytest
 
 import synthetic as S
 from oracle import clover as CL
+from oracle import solve as SV
 from oracle import wilson as W
 
 pytestmark = pytest.mark.gpu
@@ -77,6 +79,33 @@ def test_ilu_operator(case):
 def test_ilu_solve(case, precision):
     p, U, Acl, eta, w = case
     x, iters, res, status = w.solve(_dev(eta), tol=1e-10, method=wf.WF_TEMPORAL_ILU, precision=precision)
+    assert status == wf.WF_OK
+    assert max(res) <= 1e-10 and min(iters) > 0
+    xh = x.cpu().numpy()
+    for k in range(eta.shape[0]):
+        assert CL.true_residual(U, Acl, xh[k], eta[k], p) <= 2e-10
+
+
+def test_eo4d_clover_operator(case):
+    p, U, Acl, eta, w = case
+    if p.T % 2:
+        pytest.skip("the 4-D even-odd operator needs an even T")
+    par4 = W.parity4(p.L, p.T)
+    od = par4 == 1
+    xo = np.ascontiguousarray(np.stack([SV.compact(eta[k], od) for k in range(eta.shape[0])]))
+    ref = np.stack([SV.compact(CL.M_hat4_sw(U, Acl, SV.expand(xo[k], od), p, par4), od) for k in range(2)])
+    refd = np.stack([SV.compact(CL.M_hat4_sw_dag(U, Acl, SV.expand(xo[k], od), p, par4), od) for k in range(2)])
+    assert _rel(w.apply_eo4d(_dev(xo)).cpu().numpy(), ref) < 1e-12
+    assert _rel(w.apply_eo4d(_dev(xo), dagger=True).cpu().numpy(), refd) < 1e-12
+    assert _rel(w.apply_eo4d(_dev(xo), f32=True).cpu().numpy(), ref) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_eo4d_clover_solve(case, precision):
+    p, U, Acl, eta, w = case
+    if p.T % 2:
+        pytest.skip("the 4-D even-odd method needs an even T")
+    x, iters, res, status = w.solve(_dev(eta), tol=1e-10, method=wf.WF_EO4D, precision=precision)
     assert status == wf.WF_OK
     assert max(res) <= 1e-10 and min(iters) > 0
     xh = x.cpu().numpy()
