@@ -17,7 +17,9 @@ Modules:
   determinant -- log det(mu - D_t) = log|det M| - log|det M-hat| from Polyakov products, and its
              force; the extra Hamiltonian term of the temporal preconditioner in HMC (§IV)
   clover  -- the SW clover term (clover-leaf field strength), M_SW = M + A, partial temporal
-             preconditioning with 3-D ILU (Eq. TPrecPartial, App. B's apply sequence) and its solve
+             preconditioning with 3-D ILU (Eq. TPrecPartial, App. B's apply sequence), the 4-D Schur
+             clover comparator, full SW temporal preconditioning (the line inverse of A + mu - D_t,
+             also by the appendix's Woodbury form) and their solves
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``
 except where its docstring says "parity unpinned".

@@ -205,3 +205,135 @@ def solve_eo4d(U, Acl, eta, p, tol=1e-10, maxiter=100000):
             break
         inner *= 0.5 * tol / rel
     return psi, total, rel
+
+
+# ---------------------------------------------------------------------------
+# Full SW temporal preconditioning (§II.A, the paragraphs on SW fermions; appendix "Full
+# Preconditioning with Clover"): the temporal block Q = A + mu - D_t of each spatial line is
+# inverted whole. Any split C_L^-1 C_R^-1 = Q gives Q-bar = 1 and the form of Eq. TPrecFull; read
+# here with the one-sided split C_L = Q^-1, C_R = 1:
+#   M-hat_full = 1 - gamma_f^-2 (Q^oo)^-1 D_s^oe (Q^ee)^-1 D_s^eo   on odd 3-D sites.
+# ---------------------------------------------------------------------------
+def Q_apply(U, Acl, psi, p):
+    """Q psi = (A + mu - D_t) psi (§II, Eq. for M without its D_s term)."""
+    return apply_A(Acl, psi) + p.mu * psi - W.D_t(U, psi, p.bc)
+
+
+def Q_line_matrix(U, Acl, p, x, y, z, wrap=True):
+    """Dense 12 N_t x 12 N_t matrix of Q on the time line of spatial site (x, y, z), from the
+    definitions: mu + A(t) on the diagonal, -P_- U_0(t) coupling t to t+1, -P_+ U_0(t-1)^dag
+    coupling t to t-1, the wrap couplings carrying the boundary sign s (left out with wrap=False:
+    the open chain T_0 of the appendix)."""
+    T = p.T
+    U0 = U[:, z, y, x, W.MU_T]
+    Qm = np.zeros((12 * T, 12 * T), dtype=np.complex128)
+    for t in range(T):
+        blk = slice(12 * t, 12 * t + 12)
+        Qm[blk, blk] = p.mu * np.eye(12) + Acl[t, z, y, x].reshape(12, 12)
+        tn, tb = (t + 1) % T, (t - 1) % T
+        if wrap or t < T - 1:
+            sf = p.bc if t == T - 1 else 1.0
+            Qm[blk, 12 * tn:12 * tn + 12] -= sf * np.kron(W.P_MINUS, U0[t])
+        if wrap or t > 0:
+            sb = p.bc if t == 0 else 1.0
+            Qm[blk, 12 * tb:12 * tb + 12] -= sb * np.kron(W.P_PLUS, np.conj(U0[tb]).T)
+    return Qm
+
+
+def wrap_factors(U0_last, p):
+    """V (12 N_t x 12) and W^dag (12 x 12 N_t) of the appendix with V W^dag the two wrap couplings:
+    V_0 = -s P_+ U_0(N_t-1)^dag, V_{N_t-1} = -s P_- U_0(N_t-1), W^dag = (P_-, 0, ..., 0, P_+)."""
+    T = p.T
+    V = np.zeros((12 * T, 12), dtype=np.complex128)
+    Wd = np.zeros((12, 12 * T), dtype=np.complex128)
+    V[0:12] = -p.bc * np.kron(W.P_PLUS, np.conj(U0_last).T)
+    V[12 * (T - 1):] = -p.bc * np.kron(W.P_MINUS, U0_last)
+    Wd[:, 0:12] = np.kron(W.P_MINUS, np.eye(3))
+    Wd[:, 12 * (T - 1):] = np.kron(W.P_PLUS, np.eye(3))
+    return V, Wd
+
+
+def Q_inverse(U, Acl, psi, p):
+    """Q^-1 psi, one dense solve per spatial line (the plain definition)."""
+    T, L = p.T, p.L
+    out = np.zeros_like(psi)
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                rhs = psi[..., :, z, y, x, :, :]                      # (..., T, 4, 3)
+                lead = rhs.shape[:-3]
+                b = rhs.reshape(lead + (12 * T,))
+                sol = np.linalg.solve(Q_line_matrix(U, Acl, p, x, y, z), b.reshape(-1, 12 * T).T).T
+                out[..., :, z, y, x, :, :] = sol.reshape(lead + (T, 4, 3))
+    return out
+
+
+def Q_inverse_woodbury(U, Acl, psi, p):
+    """Q^-1 psi by the appendix's single-step Woodbury form, line by line: Q = T_0 + V W^dag with
+    T_0 the open chain (Q without its two wrap couplings) and V, W^dag from ``wrap_factors``;
+    Q^-1 = T_0^-1 - T_0^-1 V (1 + W^dag T_0^-1 V)^-1 W^dag T_0^-1 (T_0 solved densely here; the paper
+    uses an inner CG for it)."""
+    T, L = p.T, p.L
+    out = np.zeros_like(psi)
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                T0 = Q_line_matrix(U, Acl, p, x, y, z, wrap=False)
+                V, Wd = wrap_factors(U[T - 1, z, y, x, W.MU_T], p)
+                rhs = psi[..., :, z, y, x, :, :]
+                lead = rhs.shape[:-3]
+                b = rhs.reshape(lead + (12 * T,)).reshape(-1, 12 * T).T
+                chi = np.linalg.solve(T0, b)
+                T0V = np.linalg.solve(T0, V)
+                lam = np.linalg.inv(np.eye(12) + Wd @ T0V)
+                sol = chi - T0V @ (lam @ (Wd @ chi))
+                out[..., :, z, y, x, :, :] = sol.T.reshape(lead + (T, 4, 3))
+    return out
+
+
+def M_hat_full_sw(U, Acl, psi_o, p, par3=None):
+    """1 - gamma_f^-2 (Q^oo)^-1 D_s^oe (Q^ee)^-1 D_s^eo on odd 3-D sites."""
+    if par3 is None:
+        par3 = W.parity3(p.L, p.T)
+    ev, od = par3 == 0, par3 == 1
+    x = W.restrict(psi_o, od)
+    t = W.restrict(Q_inverse(U, Acl, W.restrict(W.D_s(U, x), ev), p), ev)
+    return x - W.restrict(Q_inverse(U, Acl, W.restrict(W.D_s(U, t), od), p), od) / p.gamma_f ** 2
+
+
+def M_hat_full_sw_dag(U, Acl, psi_o, p, par3=None):
+    """Adjoint of M-hat_full: gamma_5 [Q^oo - gamma_f^-2 D_s^oe (Q^ee)^-1 D_s^eo] (Q^oo)^-1 gamma_5
+    (Q and D_s are gamma_5-hermitian)."""
+    if par3 is None:
+        par3 = W.parity3(p.L, p.T)
+    ev, od = par3 == 0, par3 == 1
+    g = W.restrict(W.spin(W.GAMMA5, psi_o), od)
+    u = W.restrict(Q_inverse(U, Acl, g, p), od)
+    t = W.restrict(Q_inverse(U, Acl, W.restrict(W.D_s(U, u), ev), p), ev)
+    r = W.restrict(Q_apply(U, Acl, u, p), od) - W.restrict(W.D_s(U, t), od) / p.gamma_f ** 2
+    return W.spin(W.GAMMA5, r)
+
+
+def solve_full_sw(U, Acl, eta, p, tol=1e-10, maxiter=100000):
+    """M_SW psi = eta with full SW temporal preconditioning and 3-D Schur: CGNR on
+    M-hat_full psi_o = (Q^oo)^-1 (eta_o + gamma_f^-1 D_s^oe (Q^ee)^-1 eta_e), then
+    psi_e = (Q^ee)^-1 (eta_e + gamma_f^-1 D_s^eo psi_o). Returns (psi, CG iterations, true residual)."""
+    par3 = W.parity3(p.L, p.T)
+    ev, od = par3 == 0, par3 == 1
+    g = p.gamma_f
+    eta_e, eta_o = W.restrict(eta, ev), W.restrict(eta, od)
+    qe = W.restrict(Q_inverse(U, Acl, eta_e, p), ev)
+    b = W.restrict(Q_inverse(U, Acl, eta_o + W.restrict(W.D_s(U, qe), od) / g, p), od)
+    A = lambda v: M_hat_full_sw(U, Acl, v, p, par3)
+    Ad = lambda v: M_hat_full_sw_dag(U, Acl, v, p, par3)
+    inner, y, total, rel, psi = tol, None, 0, np.inf, None
+    for _ in range(8):
+        y, it, _ = SV.cgnr(A, Ad, b, x0=y, tol=inner, maxiter=maxiter - total)
+        total += it
+        psi_o = W.restrict(y, od)
+        psi = W.restrict(Q_inverse(U, Acl, eta_e + W.restrict(W.D_s(U, psi_o), ev) / g, p), ev) + psi_o
+        rel = true_residual(U, Acl, psi, eta, p)
+        if rel <= tol or total >= maxiter:
+            break
+        inner *= 0.5 * tol / rel
+    return psi, total, rel

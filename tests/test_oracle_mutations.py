@@ -212,3 +212,30 @@ def test_wrong_sign_in_ilu_sequence_is_caught(monkeypatch):
     monkeypatch.setattr(CL, "M_ilu", bad)
     with pytest.raises(AssertionError):
         PC.test_ilu_sequence_is_S_L_M_S_R(-1)
+
+
+# --------------------------------------------------------------------------- full SW temporal preconditioning
+def test_swapped_projectors_in_woodbury_are_caught(monkeypatch):
+    import test_oracle_full_sw as PF
+    from oracle import clover as CL
+    orig = CL.wrap_factors
+
+    def bad(U0_last, p):
+        V, Wd = orig(U0_last, p)
+        T = p.T
+        Wd = Wd.copy()
+        Wd[:, 0:12], Wd[:, 12 * (T - 1):] = Wd[:, 12 * (T - 1):].copy(), Wd[:, 0:12].copy()
+        return V, Wd
+
+    monkeypatch.setattr(CL, "wrap_factors", bad)
+    with pytest.raises(AssertionError):
+        PF.test_line_inverse(4, -1)
+
+
+def test_adjoint_in_the_wrong_order_is_caught(monkeypatch):
+    import test_oracle_full_sw as PF
+    from oracle import clover as CL
+    monkeypatch.setattr(CL, "M_hat_full_sw_dag",
+                        lambda U, Acl, v, p, par3=None: W.spin(W.GAMMA5, CL.M_hat_full_sw(U, Acl, W.spin(W.GAMMA5, v), p, par3)))
+    with pytest.raises(AssertionError):
+        PF.test_adjoint_and_solve()
