@@ -104,17 +104,22 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel sources."""
+def traffic_for(kernel, nrhs, config, path=None):
+    """DRAM bytes per launch of `kernel` from a committed ncu record, or None.
+
+    A record counts only for the workload, source count and hop-kernel configuration (the
+    autotuner's kernel family and traversal) it was captured in, and only while the kernel
+    sources are those of the capture (source hash)."""
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        with open(path) as fh:
             t = json.load(fh)
     except Exception:
         return None
     if t.get("source_hash") != source_hash():
         return None
     e = t.get("kernels", {}).get(kernel)
-    if not e or e.get("workload") != WORKLOAD:
+    if not e or e.get("workload") != WORKLOAD or e.get("nrhs") != nrhs or e.get("config") != config:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -302,7 +307,8 @@ def run_ours(args, prm, U, eta):
     bytes_launch = launch_bytes(dom, odd_sites, nsrc)
     achieved = bytes_launch / (ms_l / n_l * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = traffic_for(dom)
+    hop = _hop_config(wf, w, nsrc)
+    traffic = traffic_for(dom, nsrc, hop_config_key(hop))
     schur_ms = sum(cand[k][1] for k in cand)
     total_prof_ms = sum(v[1] for v in prof.values())
 
@@ -382,7 +388,7 @@ def run_ours(args, prm, U, eta):
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
                          "avg_launch_ms": ms_l / n_l},
             "kernels_one_solve": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
-            "hop_kernels_autotuned": _hop_config(wf, w, nsrc),
+            "hop_kernels_autotuned": hop,
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": e2e,
@@ -424,6 +430,13 @@ def run_apply(args, prm, U, eta):
     print(json.dumps({"mode": "apply", "workload": f"{prm['L']}^3x{prm['T']}", "nrhs": nr, "kernels": rows}))
     w.close()
     return 0
+
+
+def hop_config_key(hop):
+    """The hop-kernel configuration as a traffic-record key: "variant=<v>;tile_rows=<r>"."""
+    if not hop:
+        return None
+    return f"variant={hop['variant']};tile_rows={hop['tile_rows']}"
 
 
 def _hop_config(wf, w, nrhs):

@@ -164,13 +164,15 @@ int wf_solve_many(int n, wf_handle_t* const* hs, const double* const* rhs, doubl
  * reserved nearly all device memory, latency-critical loops (cudaFree synchronises the device),
  * processes with a device-memory budget fixed at start-up. The paper has no counterpart; it is
  * a deployment variant of the same operation.
- *   - in_odd and out_odd must be device memory (odd fields as for wf_apply_schur).
+ *   - in_odd and out_odd must be device memory of the handle's GPU (odd fields as for
+ *     wf_apply_schur); host memory or another GPU's memory returns WF_EINVAL.
  *   - Work memory: WF_NOALLOC_SCRATCH_BYTES per device; it holds 4 internal odd fields of
  *     nrhs right-hand sides, so roughly nrhs * L^3 * T <= 43,000 sites (e.g. 8^3 x 64 or
  *     12^3 x 24 for nrhs = 1). Larger requests return WF_EINVAL with the size needed.
  *   - The array exists on every GPU where the library's code is loaded and stays allocated
- *     until the process exits. The first call on a device looks up its device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     until the process exits. Every call looks up its device address in the current context
+ *     (cudaGetSymbolAddress) with the handle's device current.
+ *   - The call returns after its work has finished (it synchronises the handle's stream).
  *   - All calls on a device share the array; each call clears what it uses first. Calls whose
  *     device work overlaps (several streams, handles or host threads) race: order them. */
 #define WF_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -231,11 +233,14 @@ int wf_temporal_logdet(wf_handle_t* h, double* logdet, double* F);
 
 /* Autotuned configuration of the FP32 hop kernels of M-hat (no counterpart in the paper): the
  * first FP32 Schur apply of a handle for a given nrhs times every candidate and keeps the fastest
- * (environment WF_AUTOTUNE=0 at the first apply keeps the built-in choice). variant: 1 one thread
- * per site, 2 n sites per lane; tile_rows: rows of y per traversal tile; ms: the chosen
- * candidate's K-b + K-c time over three runs. Any output pointer may be null. WF_EINVAL if that
- * nrhs has not been tuned (yet). */
+ * (environment WF_AUTOTUNE=0 at the first apply keeps the built-in choice; WF_HOP fixes one, see
+ * the README). variant: 1 one thread per site, 2 n sites per lane, 3 bulk-copy-fed (shared-memory
+ * stages filled by cp.async.bulk); tile_rows: rows of y per traversal tile; ms: the chosen
+ * candidate's K-b + K-c time over three runs (0 if fixed by WF_HOP). wf_hop_pipe_config gives the
+ * bulk-fed kernels' sources per unit (1 or 2) and stages (2 to 4); both are 0 for variants 1 and 2.
+ * Any output pointer may be null. WF_EINVAL if that nrhs has not been tuned (yet). */
 int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float* ms);
+int wf_hop_pipe_config(wf_handle_t* h, int nrhs, int* sources_per_unit, int* stages);
 
 /* Number of kernels this handle has launched since it was created (all entry points). */
 long long wf_launch_count(const wf_handle_t* h);

@@ -50,6 +50,7 @@ _SIGS = {
                            ctypes.POINTER(_ip), ctypes.POINTER(_dp), _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_hop_config": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
+    "wf_hop_pipe_config": (_i, [_vp, _i, _ip, _ip]),
     "wf_profile": (_i, [_vp, _i]),
     "wf_profile_get": (_i, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), _dp, _i]),
 }
@@ -237,6 +238,14 @@ def wf_hop_config(h, nrhs):
     if lib.wf_hop_config(h, int(nrhs), ctypes.byref(v), ctypes.byref(r), ctypes.byref(ms)) != WF_OK:
         return None
     return v.value, r.value, ms.value
+
+
+def wf_hop_pipe_config(h, nrhs):
+    """Sources per unit and stages of the bulk-fed hop kernels for nrhs ((0, 0) for the others), or None."""
+    g, n = ctypes.c_int(), ctypes.c_int()
+    if lib.wf_hop_pipe_config(h, int(nrhs), ctypes.byref(g), ctypes.byref(n)) != WF_OK:
+        return None
+    return g.value, n.value
 
 
 def wf_profile(h, on):

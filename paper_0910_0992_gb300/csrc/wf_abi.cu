@@ -24,16 +24,6 @@ using namespace wf;
 namespace {
 
 
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 int fail(wf_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   return code;
@@ -62,7 +52,7 @@ int guarded(wf_handle* h, F&& f) {
 // device view of an input array (staged to the device if it lives on the host)
 const Cx<double>* dev_in(wf_handle* h, const double* p, size_t elems, const char* name) {
   if (!p) throw Error(WF_EINVAL, "null array argument");
-  if (is_device_ptr(p)) return reinterpret_cast<const Cx<double>*>(p);
+  if (device_resident(p, h->device)) return reinterpret_cast<const Cx<double>*>(p);
   Cx<double>* d = h->buf<Cx<double>>(name, elems);
   WF_CUDA(cudaMemcpyAsync(d, p, elems * sizeof(Cx<double>), cudaMemcpyHostToDevice, h->stream));
   return d;
@@ -70,7 +60,7 @@ const Cx<double>* dev_in(wf_handle* h, const double* p, size_t elems, const char
 // device buffer for an output array; finish_out copies it back if the caller's array is host memory
 Cx<double>* dev_out(wf_handle* h, double* p, size_t elems, const char* name, bool& staged) {
   if (!p) throw Error(WF_EINVAL, "null array argument");
-  staged = !is_device_ptr(p);
+  staged = !device_resident(p, h->device);
   if (!staged) return reinterpret_cast<Cx<double>*>(p);
   return h->buf<Cx<double>>(name, elems);
 }
@@ -247,12 +237,54 @@ void attach_tables(wf_handle* h, LineArgs<float>& a) {
   a.order = ob->as<int2>();
 }
 
+// unit table of the bulk-fed hop kernels: the tiled line order of line_rhs with the sources of a
+// line in groups of gsrc side by side, as (first source, line) pairs (built once per handle, nrhs,
+// tile rows and group size)
+const int2* attach_units(wf_handle* h, const LineArgs<float>& a, int gsrc, int& nunits) {
+  const Geom& g = a.g;
+  const int groups = (a.nrhs + gsrc - 1) / gsrc;
+  nunits = groups * g.Nl;
+  auto& ub = h->unit_tab[(a.nrhs * 64 + g.by) * 4 + gsrc];
+  if (!ub) {
+    std::vector<int2> t((size_t)nunits);
+    for (int pos = 0; pos < g.Nl; ++pos) {
+      int r, l;
+      line_rhs(pos, 1, g, r, l);  // with one source the order is the tiled line order itself
+      for (int k = 0; k < groups; ++k) t[(size_t)pos * groups + k] = make_int2(k * gsrc, l);
+    }
+    ub.reset(new wf::DevBuf());
+    ub->ensure(t.size() * sizeof(int2), h->stream);
+    WF_CUDA(cudaMemcpyAsync(ub->p, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+    WF_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return ub->as<int2>();
+}
+
+// one FP32 axial hop launch (K-b or K-c) in the configuration recorded in a.variant (3: the
+// bulk-fed kernels with a.pipe_g, a.pipe_ns; else the line kernels)
+void launch_hop_config(wf_handle* h, const LineArgs<float>& a0, int kind) {
+  LineArgs<float> a = a0;
+  attach_tables(h, a);
+  if (a.variant == 3) {
+    if (!h->tma_err.p) h->tma_err.ensure(sizeof(int), h->stream);
+    if (const char* e = std::getenv("WF_TEST_DROP_COPY")) a.drop_job = std::atoi(e);  // fault injection (tests)
+    int nunits = 0;
+    const int2* units = attach_units(h, a, a.pipe_g, nunits);
+    launch_hop_pipe(a, kind, a.pipe_g, a.pipe_ns, units, nunits, h->tma_err.as<int>(), h->stream);
+    return;
+  }
+
+  launch_line<float>(a, kind, true, h->stream);
+}
+
 // Autotuner of the FP32 hop kernels K-b and K-c: the first time a handle applies M-hat to a
-// given number of right-hand sides, every candidate (one thread per site or n sites per lane;
-// traversal tiles of each divisor of L from 2 to 12 rows of y) runs K-b and K-c on the call's own
-// buffers, once untimed and three times timed with CUDA events; the fastest is kept for the
-// handle. The timed runs write only the work fields K-b and K-c own (no norms); the call then
-// computes its result as usual.
+// given number of right-hand sides, every candidate -- the register-fed kernels (one thread per
+// site or n sites per lane) and, for 128-slot lines, the bulk-fed kernels with 1 or 2 sources per
+// unit and 2 to 4 stages, each over traversal tiles of every divisor of L from 2 to 12 rows of y --
+// runs K-b and K-c on the call's own buffers, once untimed and three times timed with CUDA
+// events; the fastest is kept for the handle. The timed runs write only the work fields K-b and
+// K-c own (no norms); the call then computes its result as usual. Environment WF_HOP fixes the
+// configuration instead ("wide,<rows>", "lane,<rows>" or "pipe,<sources>,<stages>,<rows>").
 static bool autotune_on(wf_handle* h) {
   if (h->autotune < 0) {
     const char* e = std::getenv("WF_AUTOTUNE");
@@ -261,39 +293,73 @@ static bool autotune_on(wf_handle* h) {
   return h->autotune != 0;
 }
 
+static bool forced_hop(const wf_handle* h, wf_handle::HopTune& t) {
+  const char* e = std::getenv("WF_HOP");
+  if (!e || !*e) return false;
+  int a = 0, b = 0, c = 0;
+  if (std::sscanf(e, "pipe,%d,%d,%d", &a, &b, &c) == 3 && pipe_supported(h->g) && (a == 1 || a == 2) && b >= 2 &&
+      b <= 4 && c >= 1 && h->g.L % c == 0) {
+    t = wf_handle::HopTune{3, c, 0.f, a, b};
+    return true;
+  }
+  if (std::sscanf(e, "wide,%d", &a) == 1 && wide_supported(h->g) && a >= 1 && h->g.L % a == 0) {
+    t = wf_handle::HopTune{1, a, 0.f};
+    return true;
+  }
+  if (std::sscanf(e, "lane,%d", &a) == 1 && a >= 1 && h->g.L % a == 0) {
+    t = wf_handle::HopTune{2, a, 0.f};
+    return true;
+  }
+  throw Error(WF_EINVAL, std::string("WF_HOP: unknown or unsupported configuration ") + e);
+}
+
 static wf_handle::HopTune tune_hops(wf_handle* h, const LineArgs<float>& ab, const LineArgs<float>& ac) {
   wf_handle::HopTune best{0, h->g.by, 0.f};
-  if (!autotune_on(h) || !h->axial) return best;
+  if (!h->axial) return best;
   auto it = h->hop_tune.find(ab.nrhs);
   if (it != h->hop_tune.end()) return it->second;
+  if (forced_hop(h, best)) {
+    h->hop_tune[ab.nrhs] = best;
+    return best;
+  }
+  if (!autotune_on(h)) return best;
   std::vector<int> rows;
   for (int b = 2; b <= 12 && b <= h->g.L; ++b)
     if (h->g.L % b == 0) rows.push_back(b);
   if (rows.empty()) rows.push_back(h->g.by);
+  std::vector<wf_handle::HopTune> cands;
+  for (int by : rows) {
+    if (wide_supported(h->g)) cands.push_back(wf_handle::HopTune{1, by, 0.f});
+    cands.push_back(wf_handle::HopTune{2, by, 0.f});
+    if (pipe_supported(h->g))
+      for (int gs = 1; gs <= 2; ++gs)
+        for (int ns = 2; ns <= 4; ++ns)
+          if (gs == 1 || ns <= 3) cands.push_back(wf_handle::HopTune{3, by, 0.f, gs, ns});
+  }
   cudaEvent_t e0, e1;
   WF_CUDA(cudaEventCreate(&e0));
   WF_CUDA(cudaEventCreate(&e1));
   best.ms = 1e30f;
-  for (int variant = 1; variant <= 2; ++variant) {
-    if (variant == 1 && !wide_supported(h->g)) continue;
-    for (int by : rows) {
-      LineArgs<float> b = ab, c = ac;
-      b.active = c.active = nullptr;
-      b.variant = c.variant = variant;
-      b.g.by = c.g.by = by;
-      c.norm2 = nullptr;
-      attach_tables(h, b);
-      attach_tables(h, c);
-      float ms = 0.f;
-      for (int rep = 0; rep < 4; ++rep) {
-        if (rep == 1) WF_CUDA(cudaEventRecord(e0, h->stream));
-        launch_line<float>(b, LK_SCHUR_B, true, h->stream);
-        launch_line<float>(c, LK_SCHUR_C, true, h->stream);
-      }
-      WF_CUDA(cudaEventRecord(e1, h->stream));
-      WF_CUDA(cudaEventSynchronize(e1));
-      WF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best.ms) best = wf_handle::HopTune{variant, by, ms};
+  for (const auto& cand : cands) {
+    LineArgs<float> b = ab, c = ac;
+    b.active = c.active = nullptr;
+    b.variant = c.variant = cand.variant;
+    b.pipe_g = c.pipe_g = cand.gsrc;
+    b.pipe_ns = c.pipe_ns = cand.ns;
+    b.g.by = c.g.by = cand.by;
+    c.norm2 = nullptr;
+    float ms = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) WF_CUDA(cudaEventRecord(e0, h->stream));
+      launch_hop_config(h, b, LK_SCHUR_B);
+      launch_hop_config(h, c, LK_SCHUR_C);
+    }
+    WF_CUDA(cudaEventRecord(e1, h->stream));
+    WF_CUDA(cudaEventSynchronize(e1));
+    WF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best.ms) {
+      best = cand;
+      best.ms = ms;
     }
   }
   cudaEventDestroy(e0);
@@ -311,12 +377,8 @@ void launch_schur_hop(wf_handle* h, const LineArgs<R>& a, int kind, bool tma) {
       launch_line_tma(b, kind, h->tma_err.as<int>(), h->stream);
       return;
     }
-  }
-  if constexpr (sizeof(R) == 4) {
     if (h->axial) {
-      LineArgs<R> b = a;
-      attach_tables(h, b);
-      launch_line<R>(b, kind, h->axial, h->stream);
+      launch_hop_config(h, a, kind);
       return;
     }
   }
@@ -365,6 +427,8 @@ void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs,
     if (!tma) {
       const wf_handle::HopTune t = tune_hops(h, ab, ac);
       ab.variant = ac.variant = t.variant;
+      ab.pipe_g = ac.pipe_g = t.gsrc;
+      ab.pipe_ns = ac.pipe_ns = t.ns;
       ab.g.by = ac.g.by = t.by;
     }
   }
@@ -1513,7 +1577,7 @@ int force_abi(wf_handle* h, const double* phi_odd, double* F, int precision, dou
   cudaStream_t s = h->stream;
   const Cx<double>* dphi = dev_in(h, phi_odd, ce, "stage_in");
   const bool want_force = F != nullptr;  // null: the action only
-  const bool staged = want_force && !is_device_ptr(F);
+  const bool staged = want_force && !device_resident(F, h->device);
   double* dF = staged ? h->buf<double>("stage_force", V * 32) : F;
   const char* nm[] = {"fo_phi", "fo_X", "fo_Y", "fo_v1", "fo_v2", "fo_v3", "fo_v4", "fo_v5", "fo_v6",
                       "fo_w1", "fo_w2", "fo_w3", "fo_w4", "fo_w5", "fo_w6"};
@@ -2074,6 +2138,17 @@ int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float*
     if (variant) *variant = it->second.variant;
     if (tile_rows) *tile_rows = it->second.by;
     if (ms) *ms = it->second.ms;
+    return WF_OK;
+  });
+}
+
+int wf_hop_pipe_config(wf_handle_t* h, int nrhs, int* sources_per_unit, int* stages) {
+  return guarded(h, [&]() {
+    auto it = h->hop_tune.find(nrhs);
+    if (it == h->hop_tune.end()) throw Error(WF_EINVAL, "no tuned hop configuration for this nrhs yet");
+    const bool pipe = it->second.variant == 3;
+    if (sources_per_unit) *sources_per_unit = pipe ? it->second.gsrc : 0;
+    if (stages) *stages = pipe ? it->second.ns : 0;
     return WF_OK;
   });
 }

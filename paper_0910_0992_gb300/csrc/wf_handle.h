@@ -49,11 +49,17 @@ struct wf_handle {
   // index tables of the wide kernels: neighbour lines per parity, traversal order per nrhs
   wf::DevBuf nbr_tab[2];
   std::map<int, std::unique_ptr<wf::DevBuf>> order_tab;  // key: nrhs * 64 + tile rows
-  // autotuned FP32 hop-kernel configuration per nrhs: kernel family and traversal tile rows
+  // unit tables of the bulk-fed hop kernels: (first source, line) in traversal order
+  std::map<int, std::unique_ptr<wf::DevBuf>> unit_tab;   // key: (nrhs * 64 + tile rows) * 4 + sources per unit
+  // autotuned FP32 hop-kernel configuration per nrhs: kernel family (1 one thread per site, 2 n
+  // sites per lane, 3 bulk-fed), traversal tile rows, and for the bulk-fed kernels the sources per
+  // unit and shared-memory stages
   struct HopTune {
     int variant;
     int by;
     float ms;  // K-b + K-c time of the choice when measured
+    int gsrc = 1;
+    int ns = 3;
   };
   std::map<int, HopTune> hop_tune;
   int autotune = -1;  // -1: not decided yet (environment WF_AUTOTUNE=0 keeps the built-in choice)
@@ -151,6 +157,22 @@ struct Prof {
 template <typename R>
 void schur_apply(wf_handle* h, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* y, Cx<R>* z,
                  double* norm2 = nullptr);
+
+// Whether a caller's array can be used in place on device `dev`: device memory of that GPU or
+// managed memory (true), or host memory, pageable or pinned, which the library stages (false).
+// Device memory of another GPU is rejected with WF_EINVAL: the kernels would reach it through a
+// peer mapping that need not exist.
+inline bool device_resident(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  if (a.device != dev) throw Error(WF_EINVAL, "array lives on another GPU than the handle's");
+  return true;
+}
 
 // colour rotation of parity p for imports/exports (axial frame), or null
 inline const Cx<double>* frame_rot(const wf_handle* h, int p) {

@@ -73,6 +73,13 @@ bool wide_supported(const Geom& g);
 template <typename R>
 void launch_line_wide(const LineArgs<R>& a, int kind, cudaStream_t s);
 
+// bulk-copy-fed FP32 axial hop kernels K-b / K-c for 128-slot lines (wf_pipe.cu): gsrc sources per
+// unit (1 or 2), ns shared-memory stages (2..4); units: [nunits] (first source, line) pairs in
+// traversal order; err: device error word, set when a bounded wait expired
+bool pipe_supported(const Geom& g);
+void launch_hop_pipe(const LineArgs<float>& a, int kind, int gsrc, int ns, const int2* units, int nunits, int* err,
+                     cudaStream_t s);
+
 // TMA-fed FP32 axial variant of the Schur hop kernels (wf_tma.cu); err: device error word
 bool tma_supported(const Geom& g);
 void launch_line_tma(const LineArgs<float>& a, int kind, int* err, cudaStream_t s);

@@ -71,7 +71,9 @@ struct LineArgs {
   // [Nl][6] (neighbour_lines, output parity)
   const int2* order;
   const int* nbr;
-  int variant;  // FP32 axial hop kernels: 0 the built-in choice, 1 one thread per site, 2 n sites per lane
+  int variant;  // FP32 axial hop kernels: 0 the built-in choice, 1 one thread per site, 2 n sites per lane,
+                // 3 bulk-fed (wf_pipe.cu) with pipe_g sources per unit and pipe_ns stages
+  int pipe_g, pipe_ns;
   // if set: [nrhs] flags; right-hand sides whose flag is 0 are skipped (kernels whose CTA or
   // warp holds lines of one right-hand side only; their outputs for those sources are left as is)
   const int* active;

@@ -12,15 +12,17 @@
 // * The work memory is the file-scope array below, WF_NOALLOC_SCRATCH_BYTES = 16 MiB per
 //   device. It exists on every GPU on which this code is loaded and stays there until the
 //   process exits.
-// * The first call on a device looks up the array's device address with
-//   cudaGetSymbolAddress (host code cannot use the array's name as a device pointer); make
-//   that first call before any stream capture.
+// * Host code cannot use the array's name as a device pointer, so every call looks up its
+//   device address with cudaGetSymbolAddress, with the handle's device current. The address
+//   belongs to the current CUDA context; looking it up per call keeps it valid after a
+//   cudaDeviceReset or under another context on the same device.
 // * Every call on a device uses the same array and leaves its contents behind; each call
 //   clears the part it uses before use. Calls whose device work overlaps (other streams,
 //   other handles, other host threads) race on the array: order them.
-// * in_odd and out_odd must be device memory; sizes beyond the array are rejected.
+// * The call returns after its work has finished (it synchronises the handle's stream).
+// * in_odd and out_odd must be device memory of the handle's GPU; sizes beyond the array
+//   are rejected.
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "wf_handle.h"
@@ -33,36 +35,18 @@ namespace {
 constexpr size_t kScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// device address of the array on device `dev` (which must be current), looked up once per device
-void* scratch_address(int dev) {
-  std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (dev < 0 || dev >= kMaxDevices) throw Error(WF_EINVAL, "device ordinal out of range");
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) throw Error(WF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_addr[dev] = p;
-  }
-  return g_addr[dev];
-}
-
-bool on_device(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+// device address of the array in the current context
+void* scratch_address() {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) throw Error(WF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  return p;
 }
 
 int noalloc_apply(wf_handle* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
   if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
   if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
-  if (!in_odd || !out_odd || !on_device(in_odd) || !on_device(out_odd))
+  if (!in_odd || !out_odd || !device_resident(in_odd, h->device) || !device_resident(out_odd, h->device))
     throw Error(WF_EINVAL, "wf_apply_schur_noalloc needs device pointers (host staging would allocate)");
   const size_t nt = h->half_int() * (size_t)nrhs;
   const size_t field_bytes = ((nt * sizeof(Cx<double>) + 255) / 256) * 256;
@@ -70,9 +54,7 @@ int noalloc_apply(wf_handle* h, const double* in_odd, double* out_odd, int dagge
   if (need > kScratchBytes)
     throw Error(WF_EINVAL, "wf_apply_schur_noalloc: this lattice and nrhs need " + std::to_string(need) +
                                " bytes of work memory; the fixed maximum is " + std::to_string(kScratchBytes));
-  int dev = 0;
-  WF_CUDA(cudaGetDevice(&dev));
-  unsigned char* base = static_cast<unsigned char*>(scratch_address(dev));
+  unsigned char* base = static_cast<unsigned char*>(scratch_address());
   auto* x = reinterpret_cast<Cx<double>*>(base);
   auto* o = reinterpret_cast<Cx<double>*>(base + field_bytes);
   auto* y = reinterpret_cast<Cx<double>*>(base + 2 * field_bytes);

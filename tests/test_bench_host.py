@@ -32,17 +32,24 @@ def test_paper_flop_model():
     assert bench.paper_flops_per_apply(24, 128) == (3432 * 128 - 576) * (24 ** 3 // 2)
 
 
-def test_traffic_record_belongs_to_the_kernel_sources(monkeypatch):
-    """The committed DRAM traffic is reported only while the Schur kernels' sources are unchanged."""
-    got = bench.traffic_for("schur_c_hop_tinv_axpy_f32")
-    assert got is not None, "profiles/traffic.json was taken on other kernel sources: recapture it"
-    algorithmic = bench.launch_bytes("schur_c_hop_tinv_axpy_f32", ODD_SITES_24C128, 12)
-    assert 1.0 <= got / algorithmic < 1.6
-    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
-    assert bench.traffic_for("schur_c_hop_tinv_axpy_f32") is None
-    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as fh:
-        assert set(json.load(fh)["kernels"]) == {"schur_a_tdag_f32", "schur_b_hop_tsolve_f32",
-                                                "schur_c_hop_tinv_axpy_f32"}
+def test_traffic_record_binding(tmp_path, monkeypatch):
+    """A DRAM traffic record counts only for its kernel sources, workload, source count and the
+    hop-kernel configuration it was captured in."""
+    cfg = bench.hop_config_key({"variant": "one thread per site", "tile_rows": 6})
+    assert cfg == "variant=one thread per site;tile_rows=6"
+    rec = {"source_hash": bench.source_hash(),
+           "kernels": {"schur_c_hop_tinv_axpy_f32": {"workload": bench.WORKLOAD, "nrhs": 12, "config": cfg,
+                                                     "dram_bytes_per_launch": 3.6e9}}}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
+    k = "schur_c_hop_tinv_axpy_f32"
+    assert bench.traffic_for(k, 12, cfg, str(path)) == 3.6e9
+    assert bench.traffic_for(k, 1, cfg, str(path)) is None                                  # other source count
+    assert bench.traffic_for(k, 12, "variant=one thread per site;tile_rows=8", str(path)) is None  # other traversal
+    assert bench.traffic_for("schur_b_hop_tsolve_f32", 12, cfg, str(path)) is None          # not captured
+    assert bench.traffic_for(k, 12, cfg, str(tmp_path / "absent.json")) is None
+    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)                             # kernels changed
+    assert bench.traffic_for(k, 12, cfg, str(path)) is None
 
 
 class _DoneProc:

@@ -220,7 +220,8 @@ def test_solve_with_double_float_steps(monkeypatch, L, T, method):
 
 @pytest.mark.parametrize("L,T", [(4, 128), (8, 32), (6, 12)])
 def test_autotuned_hop_kernels(monkeypatch, L, T):
-    """The first FP32 Schur apply tunes the hop kernels (family, tile rows); the result of every
+    """The first FP32 Schur apply tunes the hop kernels (family, tile rows, and for the bulk-fed
+    kernels sources per unit and stages); the result of every
     later apply, and of the tuning call itself, matches the oracle. WF_AUTOTUNE=0: no tuning."""
     p = W.Params(L, T, 0.07, xi=3.0, bc=-1)
     U = S.random_gauge(L, T, 0.3, 61)
@@ -237,7 +238,10 @@ def test_autotuned_hop_kernels(monkeypatch, L, T):
             assert _rel(_host(w.apply_schur(_dev(xo), f32=True)), ref) < 1e-6
         cfg = wf.wf_hop_config(w.h, 3)
         if tune == "1":
-            assert cfg is not None and cfg[0] in (1, 2) and L % cfg[1] == 0 and cfg[2] > 0
+            assert cfg is not None and cfg[0] in (1, 2, 3) and L % cfg[1] == 0 and cfg[2] > 0
+            gs, ns = wf.wf_hop_pipe_config(w.h, 3)
+            # bulk-fed kernels only serve 128-slot lines; their group size and stages are reported
+            assert (cfg[0] == 3) == (gs > 0) and (cfg[0] != 3 or (T > 96 and gs in (1, 2) and 2 <= ns <= 4))
         else:
             assert cfg is None
         w.close()

@@ -74,3 +74,29 @@ def test_noalloc_rejects_what_it_cannot_serve():
     wf.wf_apply_schur_noalloc(w.h, x, out, 0, 1)
     assert _rel(out, ref) < 1e-12
     w.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_noalloc_call_allocates_no_device_memory(nrhs):
+    # One call on a separate handle first, so that the kernels' code and the fixed array are
+    # loaded on the device (lazy module loading would otherwise show up as used memory). Then,
+    # on a fresh handle, the device's free memory must be the same before and after the first
+    # call: the call takes nothing from the device beyond what the handle already holds.
+    L, T = 4, 16
+    warm = _handle(L, T, 11)
+    xw = _odd(L, T, nrhs, 12)
+    wf.wf_apply_schur_noalloc(warm.h, xw, torch.empty_like(xw), 0, nrhs)
+    warm.close()
+    w = _handle(L, T, 13)
+    x = _odd(L, T, nrhs, 14)
+    out = torch.empty_like(x)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    wf.wf_apply_schur_noalloc(w.h, x, out, 0, nrhs)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    ref = torch.empty_like(x)
+    wf.wf_apply_schur(w.h, x, ref, 0, nrhs)
+    assert _rel(out, ref) < 1e-12
+    w.close()
