@@ -23,9 +23,11 @@
  *   half    psi[rhs][t][k][spin][colour], k the index of the site among the sites of one
  *           3-D parity p3 = (x + y + z) mod 2 in lexicographic order: k = (x >> 1) + (L/2)(y + L z)
  *           ("odd field" when p3 = 1).
- * Pointers: every array argument may be host or device memory; the library tells them apart
- *   (cudaPointerGetAttributes) and copies host arrays in and out itself. Input and output
- *   must not overlap. The library never keeps a caller pointer after a call returns.
+ * Pointers: every array argument may be host or device memory of the handle's GPU; the library
+ *   tells them apart (cudaPointerGetAttributes) and copies host arrays in and out itself; device
+ *   memory of another GPU returns WF_EINVAL. A call reads every input in full into its own
+ *   buffers before it writes any output, so an output may be the same array as an input (an
+ *   in-place apply). The library never keeps a caller pointer after a call returns.
  * Streams: all device work is ordered on the handle's stream (wf_set_stream); every call
  *   returns only when its results are complete (calls are synchronous for status).
  * Errors: every int-returning call returns WF_OK or one of the codes below and records a
@@ -97,7 +99,10 @@ long long wf_half_elems(const wf_handle_t* h);   /* one parity: 6 L^3 T  */
  * split into U_t and spatial links by 3-D parity) and builds, per spatial site, the SMW
  * wrap-around matrices Lambda = (1 - bc mu^-T P)^-1 of T^-1 and its counterpart for T^-dag
  * (§II.A, step 1: X(0) = -bc mu^-T P with P the Polyakov product, Lambda = (I + W^dag X)^-1).
- * Returns WF_ESINGULAR if some |det(1 - bc mu^-T P)| < 1e-12. */
+ * Returns WF_EINVAL, with nothing loaded, if an entry is NaN or Inf or a link is not SU(3)
+ * within 1e-9 (largest entry of U^dag U - 1 and |det U - 1|: the FP32 storage keeps two rows
+ * of each link and rebuilds the third, which needs det U = 1), and WF_ESINGULAR if some
+ * |det(1 - bc mu^-T P)| < 1e-12. */
 int wf_load_gauge(wf_handle_t* h, const double* U);
 
 /* out = M in (dagger = 0) or M^dag in = gamma_5 M gamma_5 in (dagger = 1); full fields, nrhs of
@@ -142,8 +147,9 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
  * one iteration replayed as a CUDA graph when the handle has a stream of its own (environment
  * WF_GRAPH=0: plain launches). The first FP32 solve or apply for a given nrhs also tunes the
  * Schur operator's kernels (see wf_hop_config).
- * Returns WF_ENOCONV (outputs written) if some right-hand side missed tol within 100000
- * iterations, WF_ENAN if a norm became NaN or Inf. */
+ * Returns WF_ENOCONV (outputs written: the last iterate) if some right-hand side missed tol
+ * within the handle's iteration limit (wf_set_max_iterations), WF_ENAN if a norm became NaN or
+ * Inf (a NaN or Inf in rhs or x0 ends the solve this way). */
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
              int flags, int* iters_out, double* true_resid_out);
 
@@ -241,6 +247,10 @@ int wf_temporal_logdet(wf_handle_t* h, double* logdet, double* F);
  * Any output pointer may be null. WF_EINVAL if that nrhs has not been tuned (yet). */
 int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float* ms);
 int wf_hop_pipe_config(wf_handle_t* h, int nrhs, int* sources_per_unit, int* stages);
+
+/* CG iteration limit of every later solve and force on h (no counterpart in the paper):
+ * maxiter >= 1, or 0 for the default 100000. WF_EINVAL if maxiter < 0. */
+int wf_set_max_iterations(wf_handle_t* h, int maxiter);
 
 /* Number of kernels this handle has launched since it was created (all entry points). */
 long long wf_launch_count(const wf_handle_t* h);

@@ -51,6 +51,7 @@ _SIGS = {
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
     "wf_hop_config": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
     "wf_hop_pipe_config": (_i, [_vp, _i, _ip, _ip]),
+    "wf_set_max_iterations": (_i, [_vp, _i]),
     "wf_profile": (_i, [_vp, _i]),
     "wf_profile_get": (_i, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), _dp, _i]),
 }
@@ -238,6 +239,10 @@ def wf_hop_config(h, nrhs):
     if lib.wf_hop_config(h, int(nrhs), ctypes.byref(v), ctypes.byref(r), ctypes.byref(ms)) != WF_OK:
         return None
     return v.value, r.value, ms.value
+
+
+def wf_set_max_iterations(h, maxiter):
+    return _check(h, lib.wf_set_max_iterations(h, int(maxiter)))
 
 
 def wf_hop_pipe_config(h, nrhs):

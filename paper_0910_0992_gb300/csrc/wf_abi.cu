@@ -853,7 +853,7 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   }
   std::vector<int> iters(nrhs, 0);
   std::vector<double> rel(nrhs, 0.0);
-  const int maxiter = 100000;
+  const int maxiter = h->maxiter;
   int status = WF_OK;
   for (int pass = 0; pass < 6; ++pass) {
     std::vector<int> it = precision == WF_FP32
@@ -1063,7 +1063,7 @@ int solve_eo4d(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
   for (int k = 0; k < nrhs; ++k) target[k] = tol * std::sqrt(eta2[k]);  // |eta - M psi| = |b_o - M-hat_4 psi_o|
   std::vector<int> iters(nrhs, 0);
   std::vector<double> rel(nrhs, 0.0);
-  const int maxiter = 100000;
+  const int maxiter = h->maxiter;
   int status = WF_OK;
   bool have_x0 = x0;
   for (int pass = 0; pass < 6; ++pass) {
@@ -1232,9 +1232,9 @@ int solve_full(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
     for (int pass = 0; pass < 6; ++pass) {
       std::vector<int> it = precision == WF_FP32
                                 ? cgnr<float>(h, full_op<float>(h, temporal), full_op<double>(h, temporal), b, y, 1,
-                                              2 * hn, target, 100000, have_x0)
+                                              2 * hn, target, h->maxiter, have_x0)
                                 : cgnr<double>(h, full_op<double>(h, temporal), full_op<double>(h, temporal), b, y, 1,
-                                               2 * hn, target, 100000, have_x0);
+                                               2 * hn, target, h->maxiter, have_x0);
       its += it[0];
       have_x0 = true;
       if (temporal) {
@@ -1247,7 +1247,7 @@ int solve_full(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int n
       std::vector<double> r2 = eo_norms(h, r, r + hn, hn, 1);
       rel = std::sqrt(r2[0] / (eta2[0] > 0 ? eta2[0] : 1.0));
       if (rel <= tol) break;
-      if (its >= 100000 || pass == 5) {
+      if (its >= h->maxiter || pass == 5) {
         status = WF_ENOCONV;
         break;
       }
@@ -1424,10 +1424,10 @@ int solve_temporal_ilu(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_le
     bool have_x0 = false;
     for (int pass = 0; pass < 6; ++pass) {
       std::vector<int> it = precision == WF_FP32
-                                ? cgnr<float>(h, ilu_op<float>(h), ilu_op<double>(h), b, y, 1, 2 * hn, target, 100000,
+                                ? cgnr<float>(h, ilu_op<float>(h), ilu_op<double>(h), b, y, 1, 2 * hn, target, h->maxiter,
                                               have_x0)
                                 : cgnr<double>(h, ilu_op<double>(h), ilu_op<double>(h), b, y, 1, 2 * hn, target,
-                                               100000, have_x0);
+                                               h->maxiter, have_x0);
       its += it[0];
       have_x0 = true;
       // psi = S_R y: psi_o = C_R^o y_o, psi_e = C_R^e (y_e + g C_L^e D_s^eo C_R^o y_o)
@@ -1445,7 +1445,7 @@ int solve_temporal_ilu(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_le
       std::vector<double> r2 = eo_norms(h, r, r + hn, hn, 1);
       rel = std::sqrt(r2[0] / (eta2[0] > 0 ? eta2[0] : 1.0));
       if (rel <= tol) break;
-      if (its >= 100000 || pass == 5) {
+      if (its >= h->maxiter || pass == 5) {
         status = WF_ENOCONV;
         break;
       }
@@ -1590,8 +1590,8 @@ int force_abi(wf_handle* h, const double* phi_odd, double* F, int precision, dou
     launch_import_compact<double>(g, dphi, phi, 1, 0, frame_rot(h, 1), s);
   }
   // X = (M-hat^dag M-hat)^-1 phi
-  int its = precision == WF_FP32 ? cg_normal<float>(h, schur_op<float>(h, 1), schur_op<double>(h, 1), phi, X, n, tol, 100000)
-                                 : cg_normal<double>(h, schur_op<double>(h, 1), schur_op<double>(h, 1), phi, X, n, tol, 100000);
+  int its = precision == WF_FP32 ? cg_normal<float>(h, schur_op<float>(h, 1), schur_op<double>(h, 1), phi, X, n, tol, h->maxiter)
+                                 : cg_normal<double>(h, schur_op<double>(h, 1), schur_op<double>(h, 1), phi, X, n, tol, h->maxiter);
   if (iters_out) *iters_out = its;
   // Y = M-hat X and S = phi^dag X = |Y|^2
   double* sc = h->buf<double>("fo_scalars", 2);
@@ -1874,6 +1874,17 @@ int wf_load_gauge(wf_handle_t* h, const double* U) {
     const Geom& g = h->g;
     const size_t V = (size_t)g.L * g.L * g.L * g.T;
     const Cx<double>* dU = dev_in(h, U, V * 36, "stage_gauge");
+    {
+      int* chk = h->buf<int>("gauge_check", 1);
+      WF_CUDA(cudaMemsetAsync(chk, 0, sizeof(int), h->stream));
+      launch_check_links(dU, V * 4, 1e-9, chk, h->stream);
+      h->launches += 1;
+      int bad = 0;
+      WF_CUDA(cudaMemcpyAsync(&bad, chk, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      WF_CUDA(cudaStreamSynchronize(h->stream));
+      if (bad & 1) throw Error(WF_EINVAL, "gauge field has a NaN or Inf entry");
+      if (bad & 2) throw Error(WF_EINVAL, "gauge field has a link that is not SU(3) within 1e-9");
+    }
     const size_t nut = (size_t)g.Nl * 9 * g.tp, nus = 3 * nut, nlam = (size_t)g.Nl * 9;
     const size_t nus32 = (size_t)3 * g.Nl * SpatialLinkNC<float>::value * g.tp;
     cudaStream_t s = h->stream;
@@ -2149,6 +2160,14 @@ int wf_hop_pipe_config(wf_handle_t* h, int nrhs, int* sources_per_unit, int* sta
     const bool pipe = it->second.variant == 3;
     if (sources_per_unit) *sources_per_unit = pipe ? it->second.gsrc : 0;
     if (stages) *stages = pipe ? it->second.ns : 0;
+    return WF_OK;
+  });
+}
+
+int wf_set_max_iterations(wf_handle_t* h, int maxiter) {
+  return guarded(h, [&]() {
+    if (maxiter < 0) throw Error(WF_EINVAL, "maxiter must be >= 0");
+    h->maxiter = maxiter ? maxiter : 100000;
     return WF_OK;
   });
 }

@@ -7,7 +7,8 @@
 //     element (rhs, s3, c, h) at ((rhs * L^3 + s3) * 12 + c) * (T/2) + h,   t = 2 h + t0,
 // t0 = (p4 + p3(s3)) mod 2. A spatial neighbour (same t, other p4) sits at the same h; a
 // temporal neighbour sits at h or h +- 1 of the same spatial site. One thread computes one
-// site; consecutive threads take consecutive h, so every load is coalesced.
+// site; consecutive threads take consecutive h, so every load is coalesced. The sources of one
+// spatial site run in consecutive CTAs (they share the site's links).
 // Links are the handle's (same frame as the temporal preconditioner: in the axial frame
 // U_t = 1 except the boundary link P), read through the line layout's index maps.
 #include <cstring>
@@ -38,10 +39,20 @@ __global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   const bool active = i < total;
   const size_t ii = active ? i : 0;
+  // (site position, source, h) with the sources of a site side by side, so that the CTAs of one
+  // site's sources run together and share its links through L2; the site positions follow the
+  // tiled traversal of the line kernels (all x by g.by rows of y, streamed along z), so that a
+  // neighbour's spinor is read again while still in L2
   const int h = (int)(ii % Th);
-  const size_t s3 = (ii / Th) % V3;
-  const int rhs = (int)(ii / (Th * V3));
-  const int x = (int)(s3 % L), y = (int)((s3 / L) % L), z = (int)(s3 / ((size_t)L * L));
+  const size_t sline = ii / Th;
+  const int rhs = (int)(sline % A.nrhs);
+  const int pos = (int)(sline / A.nrhs);
+  const int x = pos % L;
+  int u = pos / L;
+  const int yy = u % g.by;
+  u /= g.by;
+  const int z = u % L, y = (u / L) * g.by + yy;
+  const size_t s3 = (size_t)x + L * ((size_t)y + L * z);
   const int p3 = (x + y + z) & 1;
   const int t0 = eo_t0(A.par, x, y, z);
   const int t = 2 * h + t0;

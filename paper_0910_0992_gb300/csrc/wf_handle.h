@@ -62,6 +62,7 @@ struct wf_handle {
     int ns = 3;
   };
   std::map<int, HopTune> hop_tune;
+  int maxiter = 100000;  // CG iteration limit of every solve (wf_set_max_iterations)
   int autotune = -1;  // -1: not decided yet (environment WF_AUTOTUNE=0 keeps the built-in choice)
   int use_tma = -1;    // -1: not decided yet (environment WF_TMA=1 turns the TMA-fed hop kernels on)
   wf::DevBuf iflag;

@@ -125,6 +125,9 @@ void launch_tline_init(const Geom& g, const Cx<double>* ut, Cx<double>* lamb, Cx
 void launch_axial_frame(const Geom& g, Cx<double>* ut_to_g, Cx<double>* pl, Cx<double>* lamb, Cx<double>* wrap,
                         int* singular, cudaStream_t s);
 void launch_rotate_links(const Geom& g, Cx<double>* us[2], const Cx<double>* gg[2], cudaStream_t s);
+// flag |= 1 if a link of the lexicographic field U ([nlinks][3][3]) is not finite, |= 2 if one is
+// not SU(3) within tol (entries of U^dag U - 1 and det U - 1)
+void launch_check_links(const Cx<double>* U, size_t nlinks, double tol, int* flag, cudaStream_t s);
 void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s);
 // FP32 copy of spatial links in their two-row storage (nlinks = 3 Nl per parity)
 void launch_d2f_links(const Cx<double>* in, Cx<float>* out, size_t nlinks, int tp, cudaStream_t s);

@@ -412,6 +412,51 @@ void launch_d2f_links(const Cx<double>* in, Cx<float>* out, size_t nlinks, int t
   WF_CUDA(cudaGetLastError());
 }
 
+// Gauge-field check at load: every link must be finite and in SU(3) (the FP32 kernels rebuild a
+// link's third row from the first two, which holds only for det U = 1 and U^dag U = 1). One
+// thread per link; flag |= 1 for a non-finite entry, |= 2 for max |(U^dag U - 1)_ij| or
+// |det U - 1| above tol.
+__global__ void k_check_links(const Cx<double>* __restrict__ U, size_t nlinks, double tol, int* flag) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= nlinks) return;
+  Mat3<double> A;
+  bool finite = true;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    A.e[k] = U[i * 9 + k];
+    finite = finite && isfinite(A.e[k].re) && isfinite(A.e[k].im);
+  }
+  if (!finite) {
+    atomicOr(flag, 1);
+    return;
+  }
+  double dev = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Cx<double> s = czero<double>();  // (U^dag U)_ab = sum_c conj(U_ca) U_cb
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s = cfmaconj(s, A.e[3 * c + a], A.e[3 * c + b]);
+      if (a == b) s.re -= 1.0;
+      dev = fmax(dev, fmax(fabs(s.re), fabs(s.im)));
+    }
+  // det U by cofactors along the first row
+  const Cx<double>* e = A.e;
+  const Cx<double> m0 = cmul(e[4], e[8]) - cmul(e[5], e[7]);
+  const Cx<double> m1 = cmul(e[3], e[8]) - cmul(e[5], e[6]);
+  const Cx<double> m2 = cmul(e[3], e[7]) - cmul(e[4], e[6]);
+  const Cx<double> det = cmul(e[0], m0) - cmul(e[1], m1) + cmul(e[2], m2);
+  dev = fmax(dev, fmax(fabs(det.re - 1.0), fabs(det.im)));
+  if (!(dev <= tol)) atomicOr(flag, 2);
+}
+
+void launch_check_links(const Cx<double>* U, size_t nlinks, double tol, int* flag, cudaStream_t s) {
+  const int threads = 256;
+  k_check_links<<<(unsigned)((nlinks + threads - 1) / threads), threads, 0, s>>>(U, nlinks, tol, flag);
+  WF_CUDA(cudaGetLastError());
+}
+
 void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s) {
   k_d2f<<<grid_for(n), kThreads, 0, s>>>(in, out, n);
   WF_CUDA(cudaGetLastError());
