@@ -2,8 +2,9 @@
 
 * FP64 force against the oracle's FP64 adjoint (relative 1e-10), both frames;
   FP32-inner solve against the same (relative 1e-6).
-* The 8^3 x 32, xi = 3 force workload: central finite differences of the library's own
-  action on 20 random links near a point-supported pseudofermion (h = 1e-5), FP64.
+* The force workloads (8^3 x 32 and 16^3 x 64, xi = 3): central finite differences of the
+  library's own action on 20 random links near a point-supported pseudofermion (h = 1e-5), FP64,
+  and FP32-inner against FP64 over the whole lattice.
 * PseudofermionAction: its theta-gradient at theta = 0 equals the force, and a directional
   finite difference of the action through the autograd Function agrees with it.
 """
@@ -59,11 +60,15 @@ def _perturbed(U, mu, site, a, h):
     return OF.perturb(U, mu, site, a, h)
 
 
-def test_force_finite_differences_on_8c32_workload():
-    """20 links near a point-supported pseudofermion: S stays small, so a central difference
-    resolves dS/dU to ~1e-9 (for a field spread over the whole lattice S grows with the volume
-    and the FP64 floor eps * S / h of the difference swamps single-link forces)."""
-    prm, U, _ = S.workload("force_8c32_xi3", with_sources=False)
+@pytest.mark.parametrize("workload", ["force_8c32_xi3", "force_16c64_xi3"])
+def test_force_finite_differences_on_force_workloads(workload):
+    """20 links near a point-supported pseudofermion on each force workload (8^3 x 32 and
+    16^3 x 64, xi = 3): S stays small, so a central difference resolves dS/dU to ~1e-9 (for a
+    field spread over the whole lattice S grows with the volume and the FP64 floor eps * S / h
+    of the difference swamps single-link forces). The difference uses only the library's action
+    (a CG solve), not its force kernels, so it checks them at sizes the oracle cannot reach in a
+    test run; the FP32-inner force must agree with the FP64 one over the whole lattice."""
+    prm, U, _ = S.workload(workload, with_sources=False)
     L, T = prm["L"], prm["T"]
     rng = np.random.default_rng(5)
     src = (7, 3, 2, 4)  # (t, z, y, x): x + y + z = 9, odd
@@ -75,7 +80,10 @@ def test_force_finite_differences_on_8c32_workload():
     w.load_gauge(U)
     F = torch.empty((T, L, L, L, 4, 8), dtype=torch.float64, device="cuda")
     wf.wf_force(w.h, phi_d, F, wf.WF_FP64, 1e-13)
+    F32 = torch.empty_like(F)
+    wf.wf_force(w.h, phi_d, F32, wf.WF_FP32, 1e-12)
     F = F.cpu().numpy()
+    assert _rel(F32.cpu().numpy(), F) < 1e-6
     h = 1e-5
     for _ in range(20):
         mu = int(rng.integers(0, 4))

@@ -3,7 +3,8 @@
 24^3 x 128, xi = 3.5: twelve right-hand sides per launch with the autotuned FP32 hop kernels.
 The oracle computes sampled outputs: one source of a batched M-hat apply against the oracle's
 full-lattice M-hat (FP32 tolerance, 1e-6 relative), and the solve of the twelve point sources
-checked by the oracle's M on two sampled sources (FP64 true residual <= 1e-10, with rounding room);
+checked by the oracle's M on two sampled sources (FP64 true residual <= 1e-10 plus 1e-13 for the
+rounding difference between the two FP64 evaluations of the same residual);
 and log det(mu - D_t) with its force on the whole lattice (1e-13 / 1e-11 relative).
 Each oracle evaluation at this size takes tens of seconds on the host.
 """
@@ -61,7 +62,7 @@ def test_full_size_point_source_solve_sampled(full):
     assert status == wf.WF_OK and max(res) <= 1e-10
     psi = x.cpu().numpy()
     for k in (0, 11):
-        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+        assert SV.true_residual(U, psi[k], eta[k], p) <= 1e-10 + 1e-13
 
 
 def test_full_size_temporal_logdet(full):

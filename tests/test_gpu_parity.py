@@ -31,7 +31,15 @@ CASES = [
     (6, 12, 0.075, 3.5, -1, 0.3, 4),     # L = 6
     (4, 128, 0.074, 3.5, -1, 0.2, 5),    # 4 sites per lane, full warp per line
     (8, 32, 0.07, 3.0, 1, 0.25, 6),      # many warps
+    (4, 48, 0.075, 3.0, -1, 0.25, 7),    # the xi-sweep's 48-slot layout: 3 sites per lane, 16 lanes, 2 lines per warp
+    (4, 96, 0.06, 4.5, 1, 0.25, 8),      # the xi-sweep's 96-slot layout: 3 sites per lane, full warp per line
 ]
+
+# The oracle recomputes ||eta - M psi|| / ||eta|| with its own M for a solution the library
+# accepted at <= 1e-10. The two FP64 evaluations of the same residual differ only by rounding:
+# each site's eta - M psi is formed from O(||eta||)-sized terms with errors of a few eps_64, so
+# the relative difference is ~1e-15; TRUE_RESID allows 1e-13 of it.
+TRUE_RESID = 1e-10 + 1e-13
 
 
 def _rel(a, b):
@@ -120,7 +128,7 @@ def test_solve_temporal_schur(case, precision):
     assert all(i > 0 for i in iters)
     psi = _host(x)
     for k in range(eta.shape[0]):
-        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+        assert SV.true_residual(U, psi[k], eta[k], p) <= TRUE_RESID
 
 
 def test_solve_matches_oracle_solution():
@@ -177,7 +185,7 @@ def test_solve_comparators(case, method, precision):
     assert all(r <= 1e-10 for r in res)
     psi = _host(x)
     for k in range(eta.shape[0]):
-        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+        assert SV.true_residual(U, psi[k], eta[k], p) <= TRUE_RESID
 
 
 def test_fp64_iterations_match_oracle():
@@ -214,7 +222,7 @@ def test_solve_with_double_float_steps(monkeypatch, L, T, method):
     assert status == wf.WF_OK and all(r <= 1e-10 for r in res)
     psi = _host(x)
     for k in range(eta.shape[0]):
-        assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+        assert SV.true_residual(U, psi[k], eta[k], p) <= TRUE_RESID
     w.close()
 
 
@@ -271,7 +279,7 @@ def test_solve_many_ragged_lattices(method):
         assert all(abs(a - b) <= 1 for a, b in zip(its, it1))
         psi = _host(x)
         for k in range(eta.shape[0]):
-            assert SV.true_residual(U, psi[k], eta[k], p) <= 2e-10
+            assert SV.true_residual(U, psi[k], eta[k], p) <= TRUE_RESID
     for w in ws:
         w.close()
 
