@@ -248,7 +248,7 @@ def run_ours(args, prm, U, eta):
         reps.barrier()
         torch.cuda.synchronize()
 
-    prec = wf.WF_FP32 if args.precision == "fp32" else wf.WF_FP64
+    prec = {"fp32": wf.WF_FP32, "fp64": wf.WF_FP64, "fp16mix": wf.WF_FP16MIX}[args.precision]
     stream = torch.cuda.Stream()
     w = wf.Wilson(prm["L"], prm["T"], prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
     w.set_stream(stream.cuda_stream)
@@ -467,7 +467,8 @@ METHOD_NAMES = {0: "unprec", 1: "eo4d", 2: "temporal", 3: "temporal_schur", 4: "
 
 def run_methods(args):
     """--mode methods: 16^3 x 128, xi = 3.5, one Gaussian source; every method in FP64 and in FP32
-    with FP64 reliable updates: iterations, time to solution, FP64 true residual."""
+    with FP64 reliable updates, and the temporal + Schur method with FP16-stored spinors:
+    iterations, time to solution, FP64 true residual."""
     import torch
 
     import paper_0910_0992_gb300 as wf
@@ -486,6 +487,10 @@ def run_methods(args):
             t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, method, prec, args.tol)
             rows.append({"method": METHOD_NAMES[method], "precision": pname, "iterations": it[0],
                          "time_s": t, "true_residual": res[0]})
+    # FP16-stored spinors (FP32 arithmetic, FP32 and FP64 reliable updates): the temporal + Schur method
+    t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, wf.WF_TEMPORAL_SCHUR, wf.WF_FP16MIX, args.tol)
+    rows.append({"method": "temporal_schur", "precision": "fp16mix", "iterations": it[0], "time_s": t,
+                 "true_residual": res[0]})
     w.close()
     print(json.dumps({"mode": "methods", "workload": "wilson_16c128_xi3.5: 16^3x128, xi=3.5, 1 Gaussian source",
                       "tol": args.tol, "results": rows}))
@@ -706,7 +711,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp16mix"], default="fp32")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

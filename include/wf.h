@@ -63,8 +63,12 @@ enum wf_method {
 };
 
 enum wf_precision {
-  WF_FP64 = 0,  /* every operator apply in FP64 */
-  WF_FP32 = 1   /* FP32 operator applies, FP64 reliable updates, S_L / S_R and true residual */
+  WF_FP64 = 0,    /* every operator apply in FP64 */
+  WF_FP32 = 1,    /* FP32 operator applies, FP64 reliable updates, S_L / S_R and true residual */
+  WF_FP16MIX = 2  /* FP16-stored spinors with FP32 arithmetic in the CG (vectors and M-hat's
+                     intermediate fields), FP32 reliable updates of the FP32 increment every 1e-2
+                     drop (environment WF_RELIABLE_DELTA16), FP64 ones every 1e-5 (WF_RELIABLE_DELTA),
+                     FP64 S_L / S_R and true residual; WF_TEMPORAL_SCHUR in the axial frame only */
 };
 
 #define WF_X0 1 /* wf_solve flag: x holds the initial guess on entry */
@@ -135,6 +139,11 @@ int wf_apply_eo4d_f32(wf_handle_t* h, const double* in_odd4, double* out_odd4, i
 int wf_apply_M_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 int wf_apply_Tinv_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+/* M-hat with FP16-stored fields and FP32 arithmetic, the operator of the WF_FP16MIX solve (north-
+ * star precision pattern; the paper fixes no precision): each source is stored divided by its RMS,
+ * so results carry FP16 rounding (about 1e-3 relative) for inputs of any range. Axial frame only;
+ * WF_EINVAL for lattices the one-thread-per-site kernels do not serve. */
+int wf_apply_schur_f16(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
 
 /* Solve M x = rhs for nrhs full-field right-hand sides with CG on the normal equations of the
  * operator `method` selects, FP64 or mixed `precision`. For WF_TEMPORAL_SCHUR the source is

@@ -8,7 +8,7 @@ lib_path = os.path.join(_HERE, "libwf.so")
 
 WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ESINGULAR, WF_ENOCONV, WF_ENAN, WF_ETIMEOUT = range(8)
 WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR, WF_TEMPORAL_ILU = range(5)
-WF_FP64, WF_FP32 = 0, 1
+WF_FP64, WF_FP32, WF_FP16MIX = 0, 1, 2
 WF_X0 = 1
 
 _STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "WF_ESINGULAR",
@@ -36,6 +36,7 @@ _SIGS = {
     "wf_apply_C": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_schur_f16": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_schur_noalloc": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_eo4d": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_eo4d_f32": (_i, [_vp, _vp, _vp, _i, _i]),
@@ -155,6 +156,7 @@ wf_apply_Tinv_f32 = _apply(lib.wf_apply_Tinv_f32)
 wf_apply_C = _apply(lib.wf_apply_C)
 wf_apply_schur = _apply(lib.wf_apply_schur)
 wf_apply_schur_f32 = _apply(lib.wf_apply_schur_f32)
+wf_apply_schur_f16 = _apply(lib.wf_apply_schur_f16)
 wf_apply_schur_noalloc = _apply(lib.wf_apply_schur_noalloc)
 wf_apply_eo4d = _apply(lib.wf_apply_eo4d)
 wf_apply_eo4d_f32 = _apply(lib.wf_apply_eo4d_f32)

@@ -797,6 +797,288 @@ OpFn<R> schur_op(wf_handle* h, int nrhs) {
   return [=](const Cx<R>* x, Cx<R>* y, int dagger, double* norm2) { schur_apply<R>(h, x, y, dagger, nrhs, ty, tz, norm2); };
 }
 
+// M-hat on FP16-stored odd fields, FP32 arithmetic: the kernels of schur_apply<float> (K-a on the
+// line kernel, K-b / K-c on the one-thread-per-site kernels in the tuned traversal) with FP16
+// loads and stores. Element offsets of FP16 fields are taken in Cx16 units before the pointer
+// is carried as Cx<float>*.
+void schur_apply_h16(wf_handle* h, const Cx16* x, Cx16* out, int dagger, int nrhs, Cx16* y, Cx16* z, double* norm2) {
+  const int tp = h->g.tp;
+  auto F = [](const Cx16* q) { return reinterpret_cast<const Cx<float>*>(q); };
+  auto W = [](Cx16* q) { return reinterpret_cast<Cx<float>*>(q); };
+  {
+    LineArgs<float> a = line_args<float>(h, 1, nrhs);
+    a.h16 = 1;
+    a.active = h->op_active;
+    a.src_up = F(dagger ? x + 6 * tp : x);
+    a.src_lo = F(dagger ? x : x + 6 * tp);
+    a.opu = OP_FWD;
+    a.opl = OP_SKIP;
+    a.out = W(y);
+    Prof P(h, "schur_a_tdag_h16");
+    launch_line<float>(a, LK_SCHUR_A, h->axial, h->stream);
+  }
+  auto it = h->hop_tune.find(nrhs);
+  const int by = it != h->hop_tune.end() ? it->second.by : h->g.by;
+  LineArgs<float> ab = line_args<float>(h, 0, nrhs);
+  ab.h16 = 1;
+  ab.active = h->op_active;
+  ab.src_up = F(y);
+  ab.src_lo = F(dagger ? x : x + 6 * tp);
+  ab.opu = OP_FWD;
+  ab.opl = OP_BWD;
+  ab.out = W(z);
+  ab.variant = 1;
+  ab.g.by = by;
+  LineArgs<float> ac = line_args<float>(h, 1, nrhs);
+  ac.h16 = 1;
+  ac.active = h->op_active;
+  ac.src_up = F(z);
+  ac.src_lo = F(z + 6 * tp);
+  ac.opu = OP_COPY;
+  ac.opl = OP_BWD;
+  ac.xpost = F(x);
+  ac.apost = (float)(-1.0 / (h->g.gamma_f * h->g.gamma_f));
+  ac.swap_out = dagger;
+  ac.stream_out = 1;
+  ac.out = W(out);
+  ac.norm2 = norm2;
+  ac.variant = 1;
+  ac.g.by = by;
+  {
+    Prof P(h, "schur_b_hop_tsolve_h16");
+    launch_hop_config(h, ab, LK_SCHUR_B);
+  }
+  {
+    if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nrhs * sizeof(double), h->stream));
+    Prof P(h, "schur_c_hop_tinv_axpy_h16");
+    launch_hop_config(h, ac, LK_SCHUR_C);
+  }
+}
+
+// CGNR with FP16-stored vectors (FP32 arithmetic) and reliable updates on two levels, for
+// the FP16MIX precision. The vectors r, s, p, q of each right-hand side are stored divided by
+// a scale sigma (the RMS of its residual at the last reliable update), so they stay O(1) in
+// FP16. The iterate is accumulated in FP32 (true units) as the increment xi since the last FP64
+// update. A right-hand side asks for a reliable update when its iterated residual fell by
+// delta16 since the last one, or reached its target (then the recomputed residual decides):
+//   * FP32 update: r = r64 - A32 xi, the FP32 residual of the increment against the FP64
+//     residual r64 of the last FP64 update (accurate to ~1e-7 of |r64|, as xi is small);
+//   * FP64 update, when a requesting residual fell below delta64 |r64|: y += xi, xi = 0,
+//     r64 = b - A64 y.
+// Every update refreshes r for all right-hand sides and rescales r, p and gamma by the new
+// sigma; the requesting right-hand sides then finish their iteration (s = A^dag r, p = s + beta
+// p). Iterations run in blocks with device-side checks (k_cg_check) as in cgnr; no CUDA graph.
+std::vector<int> cgnr_h16(wf_handle* h, int nrhs, size_t n, const Cx<double>* b, Cx<double>* y,
+                          const std::vector<double>& target, int maxiter, bool x0) {
+  const size_t nt = n * nrhs;
+  cudaStream_t s = h->stream;
+  const OpFn<float> A32 = schur_op<float>(h, nrhs);
+  const OpFn<double> A64 = schur_op<double>(h, nrhs);
+  Cx16* r = h->buf<Cx16>("h16_r", nt);
+  Cx16* sv = h->buf<Cx16>("h16_s", nt);
+  Cx16* p = h->buf<Cx16>("h16_p", nt);
+  Cx16* q = h->buf<Cx16>("h16_q", nt);
+  Cx16* ty = h->buf<Cx16>("h16_ty", nt);
+  Cx16* tz = h->buf<Cx16>("h16_tz", nt);
+  Cx<float>* xi = h->buf<Cx<float>>("h16_xi", nt);
+  Cx<float>* t32 = h->buf<Cx<float>>("h16_t32", nt);
+  Cx<float>* r32 = h->buf<Cx<float>>("h16_r32", nt);
+  Cx<double>* r64 = h->buf<Cx<double>>("cg_r64", nt);
+  double* sc = h->buf<double>("h16_scalars", 8 * (size_t)nrhs);
+  double *gam = sc, *gnew = sc + nrhs, *qq = sc + 2 * nrhs, *rr = sc + 3 * nrhs, *sig = sc + 4 * nrhs,
+         *fac = sc + 5 * nrhs;
+  int* ist = h->buf<int>("cg_istate", 3 * (size_t)nrhs);
+  int *active = ist, *state = ist + nrhs, *dits = ist + 2 * nrhs;
+  double* lim = h->buf<double>("cg_limits", 2 * (size_t)nrhs);
+  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
+  auto A16 = [&](const Cx16* in, Cx16* out, int dagger, double* norm2) {
+    schur_apply_h16(h, in, out, dagger, nrhs, ty, tz, norm2);
+  };
+  double d16 = 1e-2, d64 = 1e-5;
+  if (const char* e = std::getenv("WF_RELIABLE_DELTA16")) {
+    const double v = std::atof(e);
+    if (v > 0.0 && v < 1.0) d16 = v;
+  }
+  if (const char* e = std::getenv("WF_RELIABLE_DELTA")) {
+    const double v = std::atof(e);
+    if (v > 0.0 && v < 1.0) d64 = v;
+  }
+  std::vector<int> act(nrhs, 1), st(nrhs, 0), cnt(nrhs, 0), iters(nrhs, 0);
+  std::vector<double> sigma(nrhs, 1.0), rmax(nrhs), rlast(nrhs), tgt2(nrhs), ru2(nrhs), f(nrhs, 1.0);
+  auto upload = [&](double* dst, const std::vector<double>& v) {
+    WF_CUDA(cudaMemcpyAsync(dst, v.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  };
+  auto upload_state = [&]() {
+    for (int k = 0; k < nrhs; ++k) {
+      tgt2[k] = (target[k] / sigma[k]) * (target[k] / sigma[k]);
+      ru2[k] = (d16 * rlast[k] / sigma[k]) * (d16 * rlast[k] / sigma[k]);
+    }
+    WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(state, st.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    upload(lim, tgt2);
+    upload(lim + nrhs, ru2);
+    upload(sig, sigma);
+  };
+  // new scales from the residual norms r2 (true units); rescale p and gamma of every rhs by
+  // old / new sigma and store r (true units, in src) scaled into FP16
+  auto rescale = [&](const std::vector<double>& r2, auto* src, bool with_p) {
+    for (int k = 0; k < nrhs; ++k) {
+      const double sn = r2[k] > 0.0 ? std::sqrt(r2[k] / (double)n) : sigma[k];
+      f[k] = sigma[k] / sn;
+      sigma[k] = sn;
+    }
+    std::vector<double> inv(nrhs), f2(nrhs);
+    for (int k = 0; k < nrhs; ++k) {
+      inv[k] = 1.0 / sigma[k];
+      f2[k] = f[k] * f[k];
+    }
+    upload(fac, inv);
+    { Prof P(h, "h16_scale_r"); launch_scale_to_h16(r, src, n, nrhs, fac, s); }
+    if (with_p) {
+      upload(fac, f);
+      { Prof P(h, "h16_scale_p"); launch_scale_to_h16<Cx16>(p, p, n, nrhs, fac, s); }
+      std::vector<double> g = read_scalars(h, gam, nrhs);
+      for (int k = 0; k < nrhs; ++k) g[k] *= f2[k];
+      upload(gam, g);
+    }
+  };
+
+  // r64 = b - A y, or b
+  if (x0) {
+    const int* keep = h->op_active;
+    h->op_active = nullptr;
+    A64(y, r64, 0, nullptr);
+    h->op_active = keep;
+    { Prof P(h, "axpby_f64"); launch_axpby<double>(r64, b, nt, 1.0, -1.0, s); }
+  } else {
+    WF_CUDA(cudaMemsetAsync(y, 0, nt * sizeof(Cx<double>), s));
+    WF_CUDA(cudaMemcpyAsync(r64, b, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  }
+  WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<float>), s));
+  { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
+  std::vector<double> r2 = read_scalars(h, rr, nrhs);
+  for (int k = 0; k < nrhs; ++k) {
+    rmax[k] = rlast[k] = std::sqrt(r2[k]);
+    if (r2[k] <= target[k] * target[k]) {
+      act[k] = 0;
+      st[k] = 1;
+    }
+  }
+  bool done = true;
+  for (int a : act) done = done && !a;
+  if (done) return iters;
+  rescale(r2, r64, false);
+  upload_state();
+  struct ActiveScope {
+    wf_handle* h;
+    ActiveScope(wf_handle* hh, const int* a) : h(hh) { h->op_active = a; }
+    ~ActiveScope() { h->op_active = nullptr; }
+  } active_scope(h, active);
+  A16(r, sv, 1, gam);  // s = A^dag r, gamma = |s|^2
+  WF_CUDA(cudaMemcpyAsync(p, sv, nt * sizeof(Cx16), cudaMemcpyDeviceToDevice, s));
+  WF_CUDA(cudaMemsetAsync(dits, 0, nrhs * sizeof(int), s));
+
+  auto iteration = [&]() {
+    A16(p, q, 0, qq);  // q = A p, |q|^2
+    { Prof P(h, "cg_xr_h16", 2); launch_cg_xr_h16(xi, r, p, q, n, nrhs, gam, qq, sig, active, partial, rr, s); }
+    { Prof P(h, "cg_check"); launch_cg_check(rr, active, state, dits, lim, lim + nrhs, nrhs, s); }
+    A16(r, sv, 1, gnew);  // s = A^dag r, |s|^2
+    { Prof P(h, "cg_p_h16"); launch_cg_p_h16(p, sv, n, nrhs, gnew, gam, active, s); }
+    { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
+  };
+
+  std::vector<double> rrh(nrhs), rr_prev(nrhs, 0.0);
+  int total = 0, nb = 1;
+  while (total < maxiter) {
+    nb = std::min(nb, maxiter - total);
+    for (int i = 0; i < nb; ++i) iteration();
+    total += nb;
+    WF_CUDA(cudaMemcpyAsync(h->host_scalars, rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int* hist = reinterpret_cast<int*>(h->host_scalars + nrhs);
+    WF_CUDA(cudaMemcpyAsync(hist, ist, 3 * nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    check_device_error(h);
+    std::memcpy(rrh.data(), h->host_scalars, nrhs * sizeof(double));
+    bool need = false, need64 = false;
+    for (int k = 0; k < nrhs; ++k) {
+      if (!std::isfinite(rrh[k])) throw Error(WF_ENAN, "NaN or Inf in a solver norm");
+      act[k] = hist[k];
+      const int sk = hist[nrhs + k];
+      cnt[k] = hist[2 * nrhs + k];
+      if (st[k] != 1 && sk != 0) {  // asks for an update (its residual fell by delta16 or met its target)
+        need = true;
+        st[k] = 2;
+        if (sigma[k] * std::sqrt(rrh[k]) < d64 * rmax[k]) need64 = true;
+      }
+    }
+    if (need) {
+      std::vector<double> nr2;
+      if (need64) {
+        { Prof P(h, "add_f_to_d"); launch_add_f_to_d(y, xi, nt, s); }
+        WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<float>), s));
+        const int* keep = h->op_active;
+        h->op_active = nullptr;
+        A64(y, r64, 0, nullptr);
+        h->op_active = keep;
+        { Prof P(h, "axpby_f64"); launch_axpby<double>(r64, b, nt, 1.0, -1.0, s); }  // r64 = b - A y
+        { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
+        nr2 = read_scalars(h, rr, nrhs);
+        rescale(nr2, r64, true);
+        for (int k = 0; k < nrhs; ++k) rmax[k] = rlast[k] = std::sqrt(nr2[k]);
+      } else {
+        const int* keep = h->op_active;
+        h->op_active = nullptr;
+        A32(xi, t32, 0, nullptr);  // A32 xi
+        h->op_active = keep;
+        { Prof P(h, "h16_sub"); launch_sub_d_f(r32, r64, t32, nt, s); }  // r = r64 - A32 xi
+        { Prof P(h, "norm2_f32", 2); launch_norm2<float>(r32, n, nrhs, partial, rr, s); }
+        nr2 = read_scalars(h, rr, nrhs);
+        rescale(nr2, r32, true);
+        for (int k = 0; k < nrhs; ++k) rlast[k] = std::sqrt(nr2[k]);
+      }
+      std::vector<int> resume(nrhs, 0);
+      bool any_resume = false;
+      for (int k = 0; k < nrhs; ++k) {
+        if (st[k] == 1) continue;
+        if (nr2[k] <= target[k] * target[k]) {
+          act[k] = 0;
+          st[k] = 1;
+        } else if (st[k] == 2) {
+          resume[k] = 1;
+          any_resume = true;
+          st[k] = 0;
+          act[k] = 1;
+        }
+      }
+      if (any_resume) {
+        WF_CUDA(cudaMemcpyAsync(active, resume.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+        A16(r, sv, 1, gnew);
+        { Prof P(h, "cg_p_h16"); launch_cg_p_h16(p, sv, n, nrhs, gnew, gam, active, s); }
+        { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
+      }
+      upload_state();
+    }
+    done = true;
+    for (int a : act) done = done && !a;
+    if (done) break;
+    // next block: most of the iterations until the first running source's expected next update
+    // (at least 1, at most 16; 2 right after an update), so that few launches find every source
+    // stopped
+    double need_it = 16.0;
+    for (int k = 0; k < nrhs; ++k) {
+      if (!act[k]) continue;
+      const double rho = rr_prev[k] > 0.0 && !need ? std::pow(rrh[k] / rr_prev[k], 1.0 / nb) : 0.0;
+      if (rho > 0.0 && rho < 1.0)
+        need_it = std::min(need_it, std::log(std::max(ru2[k], tgt2[k]) / rrh[k]) / std::log(rho));
+    }
+    for (int k = 0; k < nrhs; ++k) rr_prev[k] = rrh[k];
+    nb = need ? 2 : (int)std::max(1.0, std::min(16.0, std::floor(0.8 * need_it)));
+  }
+  for (int k = 0; k < nrhs; ++k) iters[k] = cnt[k];
+  { Prof P(h, "add_f_to_d"); launch_add_f_to_d(y, xi, nt, s); }
+  return iters;
+}
+
 // Temporal + 3-D Schur solve (§II.B): prepare with S_L, CGNR on M-hat, reconstruct with S_R,
 // verify with the FP64 true residual of M.
 int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
@@ -856,7 +1138,9 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
   const int maxiter = h->maxiter;
   int status = WF_OK;
   for (int pass = 0; pass < 6; ++pass) {
-    std::vector<int> it = precision == WF_FP32
+    std::vector<int> it = precision == WF_FP16MIX
+                              ? cgnr_h16(h, nrhs, n, b_o, y_o, target, maxiter, have_x0)
+                          : precision == WF_FP32
                               ? cgnr<float>(h, schur_op<float>(h, nrhs), schur_op<double>(h, nrhs), b_o, y_o, nrhs, n,
                                             target, maxiter, have_x0)
                               : cgnr<double>(h, schur_op<double>(h, nrhs), schur_op<double>(h, nrhs), b_o, y_o, nrhs,
@@ -1704,6 +1988,45 @@ int apply_schur_abi(wf_handle* h, const double* in_odd, double* out_odd, int dag
   return WF_OK;
 }
 
+// M-hat with FP16-stored fields (FP32 arithmetic): the operator of the FP16MIX solve. Each
+// source is stored divided by its RMS, so any input range fits FP16.
+int apply_schur_f16_abi(wf_handle* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+  if (!h->axial || !wide_supported(h->g))
+    throw Error(WF_EINVAL, "FP16 storage: the axial frame on lattices the one-thread-per-site kernels serve");
+  const size_t n = h->half_int();
+  const size_t ce = (size_t)nrhs * h->g.T * h->g.Nl * NSPIN_C;
+  const size_t nt = n * nrhs;
+  cudaStream_t s = h->stream;
+  const Cx<double>* din = dev_in(h, in_odd, ce, "stage_in");
+  bool staged;
+  Cx<double>* dout = dev_out(h, out_odd, ce, "stage_out", staged);
+  Cx<float>* x = h->buf<Cx<float>>(pname<float>("ap_x"), nt);
+  Cx<float>* o = h->buf<Cx<float>>(pname<float>("ap_o"), nt);
+  Cx16* x16 = h->buf<Cx16>("ap_x16", nt);
+  Cx16* o16 = h->buf<Cx16>("ap_o16", nt);
+  Cx16* y16 = h->buf<Cx16>("ap_y16", nt);
+  Cx16* z16 = h->buf<Cx16>("ap_z16", nt);
+  double* sc = h->buf<double>("ap_scale", 2 * (size_t)nrhs);
+  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
+  { Prof P(h, "import_compact_f32"); launch_import_compact<float>(h->g, din, x, nrhs, 0, frame_rot(h, 1), s); }
+  { Prof P(h, "norm2_f32", 2); launch_norm2<float>(x, n, nrhs, partial, sc, s); }
+  std::vector<double> x2 = read_scalars(h, sc, nrhs), inv(nrhs), sig(nrhs);
+  for (int k = 0; k < nrhs; ++k) {
+    sig[k] = x2[k] > 0.0 ? std::sqrt(x2[k] / (double)n) : 1.0;
+    inv[k] = 1.0 / sig[k];
+  }
+  WF_CUDA(cudaMemcpyAsync(sc, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(sc + nrhs, sig.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  { Prof P(h, "h16_scale"); launch_scale_to_h16<Cx<float>>(x16, x, n, nrhs, sc, s); }
+  schur_apply_h16(h, x16, o16, dagger, nrhs, y16, z16, nullptr);
+  { Prof P(h, "h16_unscale"); launch_scale_from_h16(o, o16, n, nrhs, sc + nrhs, s); }
+  { Prof P(h, "export_compact_f32"); launch_export_compact<float>(h->g, o, dout, nrhs, 0, frame_rot(h, 1), s); }
+  finish_out(h, out_odd, dout, ce, staged);
+  return WF_OK;
+}
+
 template <typename R>
 int apply_M_abi(wf_handle* h, const double* in, double* out, int dagger, int nrhs) {
   if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
@@ -2039,6 +2362,10 @@ int wf_apply_schur_f32(wf_handle_t* h, const double* in_odd, double* out_odd, in
   return guarded(h, [&]() { return apply_schur_abi<float>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
 }
 
+int wf_apply_schur_f16(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guarded(h, [&]() { return apply_schur_f16_abi(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+
 int wf_force(wf_handle_t* h, const double* phi_odd, double* F, int precision, double tol, double* action,
              int* iters) {
   return guarded(h, [&]() {
@@ -2060,7 +2387,11 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
     if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
     if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
     if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
-    if (precision != WF_FP64 && precision != WF_FP32) throw Error(WF_EINVAL, "unknown precision");
+    if (precision != WF_FP64 && precision != WF_FP32 && precision != WF_FP16MIX)
+      throw Error(WF_EINVAL, "unknown precision");
+    if (precision == WF_FP16MIX && (method != WF_TEMPORAL_SCHUR || !h->axial || !wide_supported(h->g)))
+      throw Error(WF_EINVAL, "WF_FP16MIX: the temporal + Schur method in the axial frame on lattices whose time lines "
+                             "the one-thread-per-site kernels serve");
     const size_t le = h->lex_elems() * nrhs;
     const bool x0 = (flags & WF_X0) != 0;
     const Cx<double>* drhs = dev_in(h, rhs, le, "stage_in");

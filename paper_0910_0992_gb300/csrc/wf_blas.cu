@@ -2,6 +2,7 @@
 // updates. Arrays are [nrhs][n] complex; per-RHS scalars live in device memory, so
 // the CG loop runs without host round trips.
 #include "wf_internal.h"
+#include "wf_line.cuh"
 
 namespace wf {
 
@@ -159,6 +160,151 @@ __global__ void __launch_bounds__(kBT) k_add_f_to_d(Cx<double>* __restrict__ y, 
 }
 void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s) {
   k_add_f_to_d<<<parts_for(n) * 2, kBT, 0, s>>>(y, x, n);
+  WF_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------
+// FP16-stored CG vectors (Cx16, one half2 per complex). Each right-hand side's vectors are
+// stored divided by a scale sigma[rhs] that the solver resets at every reliable update, so that
+// they stay O(1) in FP16; norms are of the stored (scaled) values, in FP32 per thread and FP64
+// across threads.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 h16_ld(const Cx16* p, size_t i) { return __half22float2(p[i].v); }
+__device__ __forceinline__ void h16_st(Cx16* p, size_t i, float re, float im) { p[i].v = __floats2half2_rn(re, im); }
+
+__global__ void __launch_bounds__(kBT) k_norm2_h16(const Cx16* __restrict__ x, size_t n, double* partial) {
+  const int rhs = blockIdx.y;
+  const Cx16* xr = x + (size_t)rhs * n;
+  float part = 0.f;
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const float2 v = h16_ld(xr, i);
+    part = fmaf(v.x, v.x, fmaf(v.y, v.y, part));
+  }
+  double acc = block_sum((double)part);
+  if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = acc;
+}
+void launch_norm2_h16(const Cx16* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s) {
+  const int parts = parts_for(n);
+  k_norm2_h16<<<dim3(parts, nrhs), kBT, 0, s>>>(x, n, partial);
+  k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, out);
+  WF_CUDA(cudaGetLastError());
+}
+
+// alpha = gamma / |q|^2 (scaled units, so alpha is the true step); x += alpha sigma p (x in FP32,
+// true units); r -= alpha q; partial |r|^2 (scaled)
+__global__ void __launch_bounds__(kBT) k_cg_xr_h16(Cx<float>* __restrict__ x, Cx16* __restrict__ r,
+                                                    const Cx16* __restrict__ p, const Cx16* __restrict__ q, size_t n,
+                                                    const double* gamma, const double* qq, const double* sigma,
+                                                    const int* active, double* partial) {
+  const int rhs = blockIdx.y;
+  // a stopped source keeps its vectors and its last partial norms (so the final sum repeats its
+  // last |r|^2)
+  if (!active[rhs]) return;
+  const double qn = qq[rhs];
+  const float alpha = qn > 0.0 ? (float)(gamma[rhs] / qn) : 0.f;
+  const float ax = (float)(qn > 0.0 ? gamma[rhs] / qn * sigma[rhs] : 0.0);
+  const size_t off = (size_t)rhs * n;
+  float part = 0.f;
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const float2 pv = h16_ld(p, off + i), qv = h16_ld(q, off + i);
+    float2 rv = h16_ld(r, off + i);
+    Cx<float> xv = x[off + i];
+    xv.re = fmaf(ax, pv.x, xv.re);
+    xv.im = fmaf(ax, pv.y, xv.im);
+    rv.x = fmaf(-alpha, qv.x, rv.x);
+    rv.y = fmaf(-alpha, qv.y, rv.y);
+    x[off + i] = xv;
+    h16_st(r, off + i, rv.x, rv.y);
+    const float2 rs = h16_ld(r, off + i);  // the norm of what is stored
+    part = fmaf(rs.x, rs.x, fmaf(rs.y, rs.y, part));
+  }
+  double acc = block_sum((double)part);
+  if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = acc;
+}
+void launch_cg_xr_h16(Cx<float>* x, Cx16* r, const Cx16* p, const Cx16* q, size_t n, int nrhs, const double* gamma,
+                      const double* qq, const double* sigma, const int* active, double* partial, double* rr_out,
+                      cudaStream_t s) {
+  const int parts = parts_for(n);
+  k_cg_xr_h16<<<dim3(parts, nrhs), kBT, 0, s>>>(x, r, p, q, n, gamma, qq, sigma, active, partial);
+  k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, rr_out);
+  WF_CUDA(cudaGetLastError());
+}
+
+// beta = gamma_new / gamma_old; p = s + beta p
+__global__ void __launch_bounds__(kBT) k_cg_p_h16(Cx16* __restrict__ p, const Cx16* __restrict__ sv, size_t n,
+                                                   const double* gnew, const double* gold, const int* active) {
+  const int rhs = blockIdx.y;
+  if (!active[rhs]) return;
+  const double go = gold[rhs];
+  const float beta = go > 0.0 ? (float)(gnew[rhs] / go) : 0.f;
+  const size_t off = (size_t)rhs * n;
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const float2 sx = h16_ld(sv, off + i), pv = h16_ld(p, off + i);
+    h16_st(p, off + i, fmaf(beta, pv.x, sx.x), fmaf(beta, pv.y, sx.y));
+  }
+}
+void launch_cg_p_h16(Cx16* p, const Cx16* sv, size_t n, int nrhs, const double* gnew, const double* gold,
+                     const int* active, cudaStream_t s) {
+  k_cg_p_h16<<<dim3(parts_for(n) * 2, nrhs), kBT, 0, s>>>(p, sv, n, gnew, gold, active);
+  WF_CUDA(cudaGetLastError());
+}
+
+// out = in * f[rhs] stored in FP16 (in: FP64, FP32 or FP16)
+template <typename T>
+__device__ __forceinline__ float2 ld_any(const T* p, size_t i) {
+  if constexpr (std::is_same<T, Cx16>::value) {
+    return h16_ld(p, i);
+  } else {
+    return make_float2((float)p[i].re, (float)p[i].im);
+  }
+}
+// (in may be out: each element is read and written by one thread; FP32 arithmetic)
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_scale_to_h16(Cx16* out, const T* in, size_t n, const double* f) {
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n;
+  const float fr = (float)f[rhs];
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const float2 v = ld_any(in, off + i);
+    h16_st(out, off + i, v.x * fr, v.y * fr);
+  }
+}
+template <typename T>
+void launch_scale_to_h16(Cx16* out, const T* in, size_t n, int nrhs, const double* f, cudaStream_t s) {
+  k_scale_to_h16<T><<<dim3(parts_for(n) * 2, nrhs), kBT, 0, s>>>(out, in, n, f);
+  WF_CUDA(cudaGetLastError());
+}
+template void launch_scale_to_h16<Cx<double>>(Cx16*, const Cx<double>*, size_t, int, const double*, cudaStream_t);
+template void launch_scale_to_h16<Cx<float>>(Cx16*, const Cx<float>*, size_t, int, const double*, cudaStream_t);
+template void launch_scale_to_h16<Cx16>(Cx16*, const Cx16*, size_t, int, const double*, cudaStream_t);
+
+// out (FP32) = in (FP16) * f[rhs]
+__global__ void __launch_bounds__(kBT) k_scale_from_h16(Cx<float>* __restrict__ out, const Cx16* __restrict__ in,
+                                                        size_t n, const double* f) {
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n;
+  const float fr = (float)f[rhs];
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const float2 v = h16_ld(in, off + i);
+    out[off + i] = mk<float>(v.x * fr, v.y * fr);
+  }
+}
+void launch_scale_from_h16(Cx<float>* out, const Cx16* in, size_t n, int nrhs, const double* f, cudaStream_t s) {
+  k_scale_from_h16<<<dim3(parts_for(n) * 2, nrhs), kBT, 0, s>>>(out, in, n, f);
+  WF_CUDA(cudaGetLastError());
+}
+
+// out = (float) r64 - a, the residual of an FP32 increment against the last FP64 residual
+__global__ void __launch_bounds__(kBT) k_sub_d_f(Cx<float>* __restrict__ out, const Cx<double>* __restrict__ r64,
+                                                  const Cx<float>* __restrict__ a, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
+    const Cx<double> r = r64[i];
+    const Cx<float> av = a[i];
+    out[i] = mk<float>((float)r.re - av.re, (float)r.im - av.im);
+  }
+}
+void launch_sub_d_f(Cx<float>* out, const Cx<double>* r64, const Cx<float>* a, size_t n, cudaStream_t s) {
+  k_sub_d_f<<<parts_for(n) * 2, kBT, 0, s>>>(out, r64, a, n);
   WF_CUDA(cudaGetLastError());
 }
 

@@ -145,6 +145,18 @@ void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* ga
 template <typename R>
 void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s);      // y += x
+// FP16-stored CG vectors (Cx16, wf_line.cuh), stored divided by a per-rhs scale sigma
+struct Cx16;
+void launch_norm2_h16(const Cx16* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s);
+void launch_cg_xr_h16(Cx<float>* x, Cx16* r, const Cx16* p, const Cx16* q, size_t n, int nrhs, const double* gamma,
+                      const double* qq, const double* sigma, const int* active, double* partial, double* rr_out,
+                      cudaStream_t s);
+void launch_cg_p_h16(Cx16* p, const Cx16* sv, size_t n, int nrhs, const double* gnew, const double* gold,
+                     const int* active, cudaStream_t s);
+template <typename T>  // T = Cx<double>, Cx<float> or Cx16: out = in * f[rhs]
+void launch_scale_to_h16(Cx16* out, const T* in, size_t n, int nrhs, const double* f, cudaStream_t s);
+void launch_sub_d_f(Cx<float>* out, const Cx<double>* r64, const Cx<float>* a, size_t n, cudaStream_t s);  // out = r64 - a
+void launch_scale_from_h16(Cx<float>* out, const Cx16* in, size_t n, int nrhs, const double* f, cudaStream_t s);
 void launch_copy_scalar(double* dst, const double* src, int nrhs, cudaStream_t s, const int* active = nullptr);
 void launch_cg_check(const double* rr, int* active, int* state, int* iters, const double* tgt2, const double* ru2,
                      int nrhs, cudaStream_t s);

@@ -66,8 +66,9 @@ struct LineMinBlocks {
   static constexpr int value = sizeof(R) == 4 ? WF_LINE_MINB : WF_LINE_MINB_F64;
 };
 
-template <typename R, bool AX, int SRC, int OPU, int OPL>
+template <typename R, bool AX, int SRC, int OPU, int OPL, bool H = false>
 __global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(const LineArgs<R> A) {
+  static_assert(!H || SRC == SRC_LOAD, "FP16 storage: the line kernel loads its own site only");
   const Geom& g = A.g;
   const int src = SRC >= 0 ? SRC : A.src;
   const int opu = OPU >= 0 ? OPU : A.opu;
@@ -93,10 +94,10 @@ __global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(
       const int sl = m * g.lpl + jj;
       const bool ok = m < n;
       const bool up = ok && opu != OP_SKIP, lo = ok && opl != OP_SKIP;
-      v[m][0] = up ? ldvec(A.src_up + base, tp, sl) : vzero<R>();
-      v[m][1] = up ? ldvec(A.src_up + base + 3 * tp, tp, sl) : vzero<R>();
-      v[m][2] = lo ? ldvec(A.src_lo + base, tp, sl) : vzero<R>();
-      v[m][3] = lo ? ldvec(A.src_lo + base + 3 * tp, tp, sl) : vzero<R>();
+      v[m][0] = up ? ldv<R, H>(A.src_up, base, tp, sl) : vzero<R>();
+      v[m][1] = up ? ldv<R, H>(A.src_up, base + 3 * tp, tp, sl) : vzero<R>();
+      v[m][2] = lo ? ldv<R, H>(A.src_lo, base, tp, sl) : vzero<R>();
+      v[m][3] = lo ? ldv<R, H>(A.src_lo, base + 3 * tp, tp, sl) : vzero<R>();
     }
   }
   if (A.xpre) {
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(
       if (m >= n) continue;
 #pragma unroll
       for (int s = 0; s < 4; ++s)
-        v[m][s] = vaxpy(A.apre, v[m][s], ldvec(A.xpre + base + 3 * s * tp, tp, m * g.lpl + jj));
+        v[m][s] = vaxpy(A.apre, v[m][s], ldv<R, H>(A.xpre, base + 3 * s * tp, tp, m * g.lpl + jj));
     }
   }
 
@@ -129,8 +130,8 @@ __global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(
         for (int s = 0; s < 2; ++s) {
           const int comp0 = dh * 6 + s * 3;
           Vec3<R> val = valid ? v[m][2 * h + s] : vzero<R>();
-          if (A.xpost) val = vaxpy(A.apost, val, ldvec(A.xpost + base + comp0 * tp, tp, sl));
-          stvec(A.out + base + comp0 * tp, tp, sl, val);
+          if (A.xpost) val = vaxpy(A.apost, val, ldv<R, H>(A.xpost, base + comp0 * tp, tp, sl));
+          stv<R, H>(A.out, base + comp0 * tp, tp, sl, val);
           if (want_norm) nrm += vnorm2(val);
         }
       }
@@ -171,6 +172,21 @@ static bool use_wide(const Geom& g, int kind, bool fp32) {
 
 template <typename R>
 static void launch_line_impl(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
+  if (a.h16) {
+    // FP16 spinor storage (FP32 arithmetic): K-a on this kernel, the hop kernels on the wide one
+    if constexpr (std::is_same<R, float>::value) {
+      if (axial && kind == LK_SCHUR_A && a.g.n >= 1 && a.g.n <= NMAX) {
+        k_line<float, true, SRC_LOAD, OP_FWD, OP_SKIP, true><<<line_blocks(a), kLineThreads, 0, s>>>(a);
+        WF_CUDA(cudaGetLastError());
+        return;
+      }
+      if (axial && (kind == LK_SCHUR_B || kind == LK_SCHUR_C) && wide_supported(a.g)) {
+        launch_line_wide(a, kind, s);
+        return;
+      }
+    }
+    throw Error(1, "line kernel: FP16 storage only for the Schur operator's kernels in the axial frame");
+  }
   if constexpr (sizeof(R) == 4) {
     const bool wide = a.variant == 1 ? wide_supported(a.g) : a.variant == 2 ? false : use_wide(a.g, kind, true);
     if (axial && wide) {

@@ -22,6 +22,10 @@
 //   at the wrap (tline_solve_axial).
 #pragma once
 
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "wf_common.cuh"
 
 namespace wf {
@@ -74,6 +78,8 @@ struct LineArgs {
   int variant;  // FP32 axial hop kernels: 0 the built-in choice, 1 one thread per site, 2 n sites per lane,
                 // 3 bulk-fed (wf_pipe.cu) with pipe_g sources per unit and pipe_ns stages
   int pipe_g, pipe_ns;
+  // FP32 kernels only: the spinor fields (src_up, src_lo, xpre, xpost, out) hold FP16 (Cx16) data
+  int h16;
   // if set: [nrhs] flags; right-hand sides whose flag is 0 are skipped (kernels whose CTA or
   // warp holds lines of one right-hand side only; their outputs for those sources are left as is)
   const int* active;
@@ -187,6 +193,107 @@ template <typename R>
 __device__ __forceinline__ void stvec_stream(Cx<R>* __restrict__ base, int tp, int slot, const Vec3<R>& v) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) st_stream(base + k * tp + slot, v.c[k]);
+}
+
+// ----------------------------------------------------------------------------
+// Spinor storage: FP32 (Cx<float>, 8 B per complex) or FP16 (Cx16, one half2, 4 B per complex),
+// both in the same element layout. FP32 kernels compute in FP32 either way; a kernel compiled
+// for FP16 storage (H = true) converts at every spinor load and store. A field pointer keeps the
+// type Cx<float>* in the argument structures; for FP16 fields it points at Cx16 data, so element
+// offsets are added here, after the cast, never to the Cx<float>* itself.
+// ----------------------------------------------------------------------------
+struct __align__(4) Cx16 {
+  __half2 v;
+};
+
+template <bool H>
+__device__ __forceinline__ Cx<float> ld_sp(const Cx<float>* base, size_t off) {
+  if constexpr (H) {
+    const float2 f = __half22float2(reinterpret_cast<const Cx16*>(base)[off].v);
+    return mk<float>(f.x, f.y);
+  } else {
+    return base[off];
+  }
+}
+template <bool H>
+__device__ __forceinline__ Cx<float> ld_sp_stream(const Cx<float>* base, size_t off) {
+  if constexpr (H) {
+    const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(reinterpret_cast<const Cx16*>(base) + off));
+    __half2 hv;
+    memcpy(&hv, &u, sizeof(u));
+    const float2 f = __half22float2(hv);
+    return mk<float>(f.x, f.y);
+  } else {
+    return ld_stream(base + off);
+  }
+}
+template <bool H>
+__device__ __forceinline__ void st_sp(Cx<float>* base, size_t off, Cx<float> z) {
+  if constexpr (H) {
+    reinterpret_cast<Cx16*>(base)[off].v = __floats2half2_rn(z.re, z.im);
+  } else {
+    base[off] = z;
+  }
+}
+template <bool H>
+__device__ __forceinline__ void st_sp_stream(Cx<float>* base, size_t off, Cx<float> z) {
+  if constexpr (H) {
+    const __half2 hv = __floats2half2_rn(z.re, z.im);
+    unsigned u;
+    memcpy(&u, &hv, sizeof(u));
+    __stcs(reinterpret_cast<unsigned*>(reinterpret_cast<Cx16*>(base) + off), u);
+  } else {
+    st_stream(base + off, z);
+  }
+}
+// three colour components at element offsets off + k tp + slot
+template <bool H>
+__device__ __forceinline__ Vec3<float> ldvec_sp(const Cx<float>* base, size_t off, int tp, int slot) {
+  Vec3<float> v;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = ld_sp<H>(base, off + (size_t)(k * tp + slot));
+  return v;
+}
+template <bool H>
+__device__ __forceinline__ Vec3<float> ldvec_sp_stream(const Cx<float>* base, size_t off, int tp, int slot) {
+  Vec3<float> v;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = ld_sp_stream<H>(base, off + (size_t)(k * tp + slot));
+  return v;
+}
+template <bool H>
+__device__ __forceinline__ void stvec_sp(Cx<float>* base, size_t off, int tp, int slot, const Vec3<float>& v) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) st_sp<H>(base, off + (size_t)(k * tp + slot), v.c[k]);
+}
+template <bool H>
+__device__ __forceinline__ void stvec_sp_stream(Cx<float>* base, size_t off, int tp, int slot, const Vec3<float>& v) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) st_sp_stream<H>(base, off + (size_t)(k * tp + slot), v.c[k]);
+}
+
+// spinor accessors of the line kernels: element offset off from a field's base pointer, in the
+// precision R of the kernel or (H, R = float only) FP16 storage
+template <typename R, bool H>
+__device__ __forceinline__ Vec3<R> ldv(const Cx<R>* base, size_t off, int tp, int slot) {
+  static_assert(!H || std::is_same<R, float>::value, "FP16 storage with FP32 arithmetic only");
+  if constexpr (H) return ldvec_sp<true>(base, off, tp, slot);
+  else return ldvec(base + off, tp, slot);
+}
+template <typename R, bool H>
+__device__ __forceinline__ Vec3<R> ldv_stream(const Cx<R>* base, size_t off, int tp, int slot) {
+  if constexpr (H) return ldvec_sp_stream<true>(base, off, tp, slot);
+  else return ldvec_stream(base + off, tp, slot);
+}
+template <typename R, bool H>
+__device__ __forceinline__ void stv(Cx<R>* base, size_t off, int tp, int slot, const Vec3<R>& v) {
+  if constexpr (H) stvec_sp<true>(base, off, tp, slot, v);
+  else stvec(base + off, tp, slot, v);
+}
+template <typename R, bool H>
+__device__ __forceinline__ void stv_stream(Cx<R>* base, size_t off, int tp, int slot, const Vec3<R>& v) {
+  if constexpr (H) stvec_sp_stream<true>(base, off, tp, slot, v);
+  else stvec_stream(base + off, tp, slot, v);
 }
 
 template <typename R>

@@ -247,7 +247,7 @@ __device__ __forceinline__ void solve_half_wide(Vec3<R>& v0, Vec3<R>& v1, const 
 }
 
 // D_s (the spatial hop of hop_spatial, wf_line.cuh) at one site of line l
-template <typename R, int TPC>
+template <typename R, int TPC, bool H = false>
 __device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, int rhs, int l, int sl) {
   const Geom& g = A.g;
   const int tp = TPC ? TPC : g.tp, Nl = g.Nl;
@@ -261,13 +261,11 @@ __device__ __forceinline__ void hop_site(Vec3<R> (&h)[4], const LineArgs<R>& A, 
     for (int dir = 0; dir < 2; ++dir) {  // 0: forward (x + k), 1: backward (x - k)
       const int ln = nb[2 * k + dir];
       const size_t sb = (size_t)(rhs * Nl + ln) * NSPIN_C * tp;
-      const Cx<R>* up = A.src_up + sb;
-      const Cx<R>* lo = A.src_lo + sb;
       constexpr int LNC = SpatialLinkNC<R>::value;
       const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * LNC * tp
                                  : A.us_nbr + (size_t)(k * Nl + ln) * LNC * tp;
-      const Vec3<R> u0 = ldvec(up, tp, sl), u1 = ldvec(up + 3 * tp, tp, sl);
-      const Vec3<R> d0 = ldvec(lo, tp, sl), d1 = ldvec(lo + 3 * tp, tp, sl);
+      const Vec3<R> u0 = ldv<R, H>(A.src_up, sb, tp, sl), u1 = ldv<R, H>(A.src_up, sb + 3 * tp, tp, sl);
+      const Vec3<R> d0 = ldv<R, H>(A.src_lo, sb, tp, sl), d1 = ldv<R, H>(A.src_lo, sb + 3 * tp, tp, sl);
       const Mat3<R> U = ldlink(lk, tp, sl);
       Vec3<R> s0, s1;
       isigma(k, d0, d1, s0, s1);
@@ -360,7 +358,7 @@ __device__ __forceinline__ void line_norm_whole_warps(double* nrm_s, R nrm, int 
 // SRC, OPU, OPL < 0: taken from the arguments at run time. TPC: the line length tp as a
 // compile-time constant (128: n = 4 sites per group, 32 lanes, so that every load's component
 // offset is an immediate), or 0 to read the layout at run time.
-template <typename R, int SRC, int OPU, int OPL, int TPC>
+template <typename R, int SRC, int OPU, int OPL, int TPC, bool H = false>
 __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
     k_line_wide(const LineArgs<R> A) {
   __shared__ double nrm_s[kWideCta];
@@ -403,20 +401,20 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
       if constexpr (std::is_same<R, df64>::value)
         hop_site_rolled<R, TPC>(v, A, rhs, l, sl);
       else
-        hop_site<R, TPC>(v, A, rhs, l, sl);
+        hop_site<R, TPC, H>(v, A, rhs, l, sl);
     } else {
       if (opu != OP_SKIP) {
-        v[0] = ldvec(A.src_up + base, tp, sl);
-        v[1] = ldvec(A.src_up + base + 3 * tp, tp, sl);
+        v[0] = ldv<R, H>(A.src_up, base, tp, sl);
+        v[1] = ldv<R, H>(A.src_up, base + 3 * tp, tp, sl);
       }
       if (opl != OP_SKIP) {
-        v[2] = ldvec(A.src_lo + base, tp, sl);
-        v[3] = ldvec(A.src_lo + base + 3 * tp, tp, sl);
+        v[2] = ldv<R, H>(A.src_lo, base, tp, sl);
+        v[3] = ldv<R, H>(A.src_lo, base + 3 * tp, tp, sl);
       }
     }
     if (A.xpre) {
 #pragma unroll
-      for (int s = 0; s < 4; ++s) v[s] = vaxpy(A.apre, v[s], ldvec(A.xpre + base + 3 * s * tp, tp, sl));
+      for (int s = 0; s < 4; ++s) v[s] = vaxpy(A.apre, v[s], ldv<R, H>(A.xpre, base + 3 * s * tp, tp, sl));
     }
   }
 
@@ -437,7 +435,7 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
       const bool want_x = A.xpost && line_ok && op != OP_SKIP;
 #pragma unroll
       for (int mm = 0; mm < 4; ++mm)
-        xp[mm] = want_x ? ldvec_stream(A.xpost + base + comp0 * tp, tp, mm * 32 + j) : vzero<R>();
+        xp[mm] = want_x ? ldv_stream<R, H>(A.xpost, base + comp0 * tp, tp, mm * 32 + j) : vzero<R>();
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -462,12 +460,12 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
           if constexpr (kEarlyX)
             val = vaxpy(A.apost, val, xp[mm]);
           else
-            val = vaxpy(A.apost, val, ldvec_stream(A.xpost + base + comp0 * tp, tp, slot));
+            val = vaxpy(A.apost, val, ldv_stream<R, H>(A.xpost, base + comp0 * tp, tp, slot));
         }
         if (A.stream_out)
-          stvec_stream(A.out + base + comp0 * tp, tp, slot, val);
+          stv_stream<R, H>(A.out, base + comp0 * tp, tp, slot, val);
         else
-          stvec(A.out + base + comp0 * tp, tp, slot, val);
+          stv<R, H>(A.out, base + comp0 * tp, tp, slot, val);
         if (A.norm2) nrm += vnorm2(val);
       }
     }
@@ -498,11 +496,11 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
       for (int s = 0; s < 2; ++s) {
         const int comp0 = dh * 6 + s * 3;
         Vec3<R> val = valid ? v[2 * h + s] : vzero<R>();
-        if (A.xpost) val = vaxpy(A.apost, val, ldvec_stream(A.xpost + base + comp0 * tp, tp, sl));
+        if (A.xpost) val = vaxpy(A.apost, val, ldv_stream<R, H>(A.xpost, base + comp0 * tp, tp, sl));
         if (A.stream_out)
-          stvec_stream(A.out + base + comp0 * tp, tp, sl, val);
+          stv_stream<R, H>(A.out, base + comp0 * tp, tp, sl, val);
         else
-          stvec(A.out + base + comp0 * tp, tp, sl, val);
+          stv<R, H>(A.out, base + comp0 * tp, tp, sl, val);
         if (A.norm2) nrm += vnorm2(val);
       }
     }
@@ -545,12 +543,22 @@ void launch_line_wide(const LineArgs<R>& a, int kind, cudaStream_t s) {
   const int lines = a.nrhs * a.g.Nl;
   const int blocks = (lines + LPC - 1) / LPC;
   const bool t128 = a.g.tp == 128 && a.g.n == 4 && a.g.lpl == 32;
-#define WF_KW(SRCV, OPUV, OPLV)                                                         \
-  do {                                                                                  \
-    if (t128)                                                                           \
-      wide::k_line_wide<R, SRCV, OPUV, OPLV, 128><<<blocks, wide::kWideCta, 0, s>>>(a); \
-    else                                                                                \
-      wide::k_line_wide<R, SRCV, OPUV, OPLV, 0><<<blocks, wide::kWideCta, 0, s>>>(a);   \
+  constexpr bool kF32 = std::is_same<R, float>::value;
+  if (a.h16 && !kF32) throw Error(1, "wide line kernel: FP16 storage needs FP32 arithmetic");
+#define WF_KW(SRCV, OPUV, OPLV)                                                                   \
+  do {                                                                                            \
+    constexpr bool kH = kF32 && (SRCV) == SRC_HOP; /* FP16 storage: the hop kernels K-b, K-c */  \
+    if (a.h16) {                                                                                  \
+      if (!kH) throw Error(1, "wide line kernel: FP16 storage only for the hop kernels");         \
+      if (t128)                                                                                   \
+        wide::k_line_wide<R, SRCV, OPUV, OPLV, 128, kH><<<blocks, wide::kWideCta, 0, s>>>(a);     \
+      else                                                                                        \
+        wide::k_line_wide<R, SRCV, OPUV, OPLV, 0, kH><<<blocks, wide::kWideCta, 0, s>>>(a);       \
+    } else if (t128) {                                                                            \
+      wide::k_line_wide<R, SRCV, OPUV, OPLV, 128><<<blocks, wide::kWideCta, 0, s>>>(a);           \
+    } else {                                                                                      \
+      wide::k_line_wide<R, SRCV, OPUV, OPLV, 0><<<blocks, wide::kWideCta, 0, s>>>(a);             \
+    }                                                                                             \
   } while (0)
   switch (kind) {
     case LK_SCHUR_A: WF_KW(SRC_LOAD, OP_FWD, OP_SKIP); break;
