@@ -82,8 +82,8 @@ def paper_flops_per_apply(L, T):
 
 # the sources that compile, launch or lay out the data of the Schur operator's kernels: a change
 # to any of them voids the DRAM traffic recorded in profiles/traffic.json
-HOP_KERNEL_SOURCES = ("wf_abi.cu", "wf_common.cuh", "wf_df64.cuh", "wf_handle.h", "wf_internal.h", "wf_kernels.cu",
-                      "wf_layout.cu", "wf_line.cuh", "wf_wide.cu", "wf_wide.cuh")
+HOP_KERNEL_SOURCES = ("wf_abi.cu", "wf_async.cuh", "wf_common.cuh", "wf_df64.cuh", "wf_handle.h", "wf_internal.h",
+                      "wf_kernels.cu", "wf_layout.cu", "wf_line.cuh", "wf_pipe.cu", "wf_wide.cu", "wf_wide.cuh")
 
 
 def source_hash():
@@ -176,36 +176,62 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)
-def oracle_sample(target_s, prm):
-    """Time the FP64 oracle's M-hat apply on a lattice of the workload's couplings sized for ~target_s.
-
-    Returns (GB/s in the FP64 model bytes, description, threads used, seconds).
-    """
-    import numpy as np
-
+def _oracle_worker(L, T, prm, seed, barrier, out):
+    """One FP64 oracle M-hat apply of its own Gaussian source (a process of oracle_sample)."""
     import synthetic as S
     from oracle import wilson as W
 
-    per_site_s = 37.4 / (24 ** 3 * 128)  # oracle cost measured on an 8-core x86 host, for sizing only
-    L = int(round((target_s / (per_site_s * prm["T"])) ** (1.0 / 3.0)))
-    L = max(4, min(prm["L"], L - (L % 2)))
-    T = prm["T"]
     p = W.Params(L, T, prm["kappa_s"], kappa_t=prm["kappa_t"], bc=prm["bc"])
     U = S.random_gauge(L, T, prm["eps"], prm["seed"])
     par3 = W.parity3(L, T)
-    x = W.restrict(S.gaussian_source(L, T, prm["seed"] + 7), par3 == 1)
-    r0 = resource.getrusage(resource.RUSAGE_SELF)
-    t0 = time.perf_counter()
+    x = W.restrict(S.gaussian_source(L, T, seed), par3 == 1)
+    barrier.wait()  # every process applies at the same time
+    t0 = time.time()
     W.M_hat(U, x, p, par3)
-    dt = time.perf_counter() - t0
-    r1 = resource.getrusage(resource.RUSAGE_SELF)
-    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
-    threads = max(1, int(round(cpu / dt)))
+    out.put((t0, time.time()))
+
+
+def oracle_sample(target_s, prm, procs=None):
+    """Time the FP64 oracle's M-hat apply on the host's cores: one process per core (spawned, so
+    nothing of a CUDA context is inherited), each applying M-hat to its own source on a lattice of
+    the workload's couplings sized for ~target_s, all started together.
+
+    Returns (GB/s in the FP64 model bytes: all processes' bytes over the span from the first start
+    to the last end, description, processes, seconds).
+    """
+    import multiprocessing as mp
+
+    procs = procs or os.cpu_count() or 1
+    per_site_s = 1.4e-5  # one oracle apply per site on one GB300 host core (sizing only)
+    L = int(round((target_s / (per_site_s * prm["T"])) ** (1.0 / 3.0)))
+    L = max(4, min(prm["L"], L - (L % 2)))
+    T = prm["T"]
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"  # one core per process
+    try:
+        ps = [ctx.Process(target=_oracle_worker, args=(L, T, prm, prm["seed"] + 7 + i, barrier, out))
+              for i in range(procs)]
+        for q in ps:
+            q.start()
+        spans = [out.get() for _ in ps]
+        for q in ps:
+            q.join()
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    dt = max(e for _, e in spans) - min(b for b, _ in spans)
     odd_sites = L ** 3 * T // 2
-    gbs = apply_bytes(odd_sites, 1, 2) / dt / 1e9
-    desc = (f"one FP64 oracle M-hat apply on a {L}^3x{T} lattice with the workload's couplings "
-            f"(1 source; the full 24^3x128 x 12-source step is {24 ** 3 / L ** 3 * 12:.0f}x larger)")
-    return gbs, desc, threads, dt
+    gbs = procs * apply_bytes(odd_sites, 1, 2) / dt / 1e9
+    desc = (f"{procs} concurrent FP64 oracle M-hat applies (one process per host core, one Gaussian source "
+            f"each) on a {L}^3x{T} lattice with the workload's couplings; the full 24^3x128 x 12-source step "
+            f"is {24 ** 3 / L ** 3 * 12 / procs:.1f}x that much work")
+    return gbs, desc, procs, dt
 
 
 def run_reference(args, prm):
@@ -357,9 +383,27 @@ def run_ours(args, prm, U, eta):
                        "temporal_schur_iterations": it_ts1[0], "eo4d_iterations": it_eo1[0]},
         }
 
+    # per-kernel rooflines of the operator applies (outside the timed region): the benchmarked
+    # batch and one source (the single-RHS form), for M-hat and for the 4-D even-odd comparator
+    applies = None
+    if not args.no_compare:
+        applies = {f"{op}_{n}src": apply_roofline(wf, torch, w, n, op, odd_sites, peak)
+                   for op in ("schur", "eo4d") for n in (nsrc, 1)}
+        if compare is not None:
+            compare["kernels_batched"] = applies[f"eo4d_{nsrc}src"]
+            compare["kernels_single"] = applies["eo4d_1src"]
+
+    # the same solve with FP16-stored spinors (outside the timed region)
+    fp16 = None
+    if not args.no_compare and prec == wf.WF_FP32:
+        t16, it16, res16 = _timed_solve(wf, torch, w, stream, rhs, x, wf.WF_TEMPORAL_SCHUR, wf.WF_FP16MIX,
+                                        args.tol, reps=2)
+        fp16 = {"precision": "FP16-stored spinors, FP32 arithmetic, FP32 and FP64 reliable updates",
+                "time_to_solve_s": t16, "iterations": it16, "max_true_residual": max(res16)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        gbs, desc, threads, dt = oracle_sample(20.0, prm)
+        gbs, desc, threads, dt = oracle_sample(10.0, prm)
         cpu = {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc,
                "seconds": dt}
 
@@ -386,7 +430,11 @@ def run_ours(args, prm, U, eta):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
-                         "avg_launch_ms": ms_l / n_l},
+                         "avg_launch_ms": ms_l / n_l,
+                         "apply_frac": applies[f"schur_{nsrc}src"]["apply_frac"] if applies else None,
+                         "single_source_apply_frac": applies["schur_1src"]["apply_frac"] if applies else None},
+            "operator_applies": applies,
+            "fp16mix_same_sources": fp16,
             "kernels_one_solve": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
             "hop_kernels_autotuned": hop,
             "clocks": clk,
@@ -433,18 +481,62 @@ def run_apply(args, prm, U, eta):
 
 
 def hop_config_key(hop):
-    """The hop-kernel configuration as a traffic-record key: "variant=<v>;tile_rows=<r>"."""
+    """The hop-kernel configuration as a traffic-record key: "variant=<v>;tile_rows=<r>", and for
+    the bulk-fed kernels ";sources=<g>;stages=<s>"."""
     if not hop:
         return None
-    return f"variant={hop['variant']};tile_rows={hop['tile_rows']}"
+    key = f"variant={hop['variant']};tile_rows={hop['tile_rows']}"
+    if "stages" in hop:
+        key += f";sources={hop['sources_per_unit']};stages={hop['stages']}"
+    return key
+
+
+HOP_VARIANTS = {1: "one thread per site", 2: "sites per lane", 3: "bulk-copy-fed"}
 
 
 def _hop_config(wf, w, nrhs):
     c = wf.wf_hop_config(w.h, nrhs)
     if c is None:
         return None
-    return {"variant": {1: "one thread per site", 2: "sites per lane"}.get(c[0], c[0]), "tile_rows": c[1],
-            "kb_plus_kc_ms_x3": c[2]}
+    r = {"variant": HOP_VARIANTS.get(c[0], c[0]), "tile_rows": c[1], "kb_plus_kc_ms_x3": c[2]}
+    if c[0] == 3:
+        r["sources_per_unit"], r["stages"] = wf.wf_hop_pipe_config(w.h, nrhs)
+    return r
+
+
+def apply_roofline(wf, torch, w, nrhs, op, odd_sites, peak, steps=10):
+    """Per-kernel CUDA-event times of the FP32 operator (op "schur": K-a, K-b, K-c of M-hat; "eo4d":
+    the comparator's two half dslashes) over nrhs sources, with algorithmic bytes, GB/s and the
+    fraction of peak per kernel and for the whole apply (bytes of all its kernels over the sum of
+    their mean launch times). Outside every timed region."""
+    half = w.L ** 3 * w.T // 2 * 12
+    g = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.complex(torch.randn(nrhs * half, generator=g, dtype=torch.float64),
+                      torch.randn(nrhs * half, generator=g, dtype=torch.float64)).cuda()
+    out = torch.empty_like(x)
+    fn = wf.wf_apply_eo4d_f32 if op == "eo4d" else wf.wf_apply_schur_f32
+    model = eo4d_launch_bytes if op == "eo4d" else launch_bytes
+    for _ in range(2):
+        fn(w.h, x, out, 0, nrhs)
+    torch.cuda.synchronize()
+    wf.wf_profile(w.h, 1)
+    for _ in range(steps):
+        fn(w.h, x, out, 0, nrhs)
+    prof = wf.wf_profile_get(w.h)
+    wf.wf_profile(w.h, 0)
+    rows, tot_b, tot_ms = {}, 0.0, 0.0
+    for k, (n, ms) in prof.items():
+        b = model(k, odd_sites, nrhs)
+        if b is None or n == 0:
+            continue
+        avg = ms / n
+        rows[k] = {"avg_launch_ms": avg, "algorithmic_bytes_per_launch": b, "achieved_gbs": b / (avg * 1e-3) / 1e9,
+                   "frac": b / (avg * 1e-3) / 1e9 / peak}
+        tot_b += b
+        tot_ms += avg
+    apply_gbs = tot_b / (tot_ms * 1e-3) / 1e9 if tot_ms else None
+    return {"nrhs": nrhs, "kernels": rows, "apply_ms": tot_ms, "apply_bytes": tot_b, "apply_gbs": apply_gbs,
+            "apply_frac": apply_gbs / peak if apply_gbs else None}
 
 
 def _timed_solve(wf, torch, w, stream, rhs, x, method, prec, tol, reps=1):

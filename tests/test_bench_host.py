@@ -37,6 +37,9 @@ def test_traffic_record_binding(tmp_path, monkeypatch):
     hop-kernel configuration it was captured in."""
     cfg = bench.hop_config_key({"variant": "one thread per site", "tile_rows": 6})
     assert cfg == "variant=one thread per site;tile_rows=6"
+    assert bench.hop_config_key({"variant": "bulk-copy-fed", "tile_rows": 4, "sources_per_unit": 1, "stages": 3}) == \
+        "variant=bulk-copy-fed;tile_rows=4;sources=1;stages=3"
+    assert bench.hop_config_key(None) is None
     rec = {"source_hash": bench.source_hash(),
            "kernels": {"schur_c_hop_tinv_axpy_f32": {"workload": bench.WORKLOAD, "nrhs": 12, "config": cfg,
                                                      "dram_bytes_per_launch": 3.6e9}}}
@@ -96,7 +99,8 @@ def test_spatial_plaquette():
 
 
 def test_oracle_sample_is_small_and_even():
+    """The CPU baseline runs one spawned process per core, all applying at once."""
     prm = dict(S.WORKLOADS["wilson_4c16_xi3"])
-    gbs, desc, threads, dt = bench.oracle_sample(0.01, prm)
-    assert gbs > 0 and threads >= 1 and dt > 0
-    assert "4^3x16" in desc
+    gbs, desc, procs, dt = bench.oracle_sample(0.01, prm, procs=2)
+    assert gbs > 0 and procs == 2 and dt > 0
+    assert "4^3x16" in desc and "2 concurrent" in desc
