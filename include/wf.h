@@ -72,6 +72,7 @@ enum wf_precision {
 };
 
 #define WF_X0 1 /* wf_solve flag: x holds the initial guess on entry */
+#define WF_MAX_SOLVE_RHS 1024 /* right-hand sides of one solve (all lattices of a joint wf_solve_many) */
 
 /* Create a handle for an L^3 x T lattice (§II). kappa_t <= 0 selects kappa_t = xi * kappa_s.
  * bc = +1 or -1. Allocates the gauge storage on the current device. Returns WF_EINVAL for
@@ -151,7 +152,7 @@ int wf_apply_schur_f16(wf_handle_t* h, const double* in_odd, double* out_odd, in
  * when the FP64 true residual ||rhs - M x||_2 / ||rhs||_2 <= tol, computed with the full M.
  * iters_out[k] (CG iterations) and true_resid_out[k] are written for every right-hand side
  * (host arrays of nrhs entries; either may be null). flags: WF_X0 to start from x.
- * WF_FP32: the residual is recomputed in FP64 whenever the FP32 one fell by 1e-5 (environment
+ * 1 <= nrhs <= WF_MAX_SOLVE_RHS (else WF_EINVAL). WF_FP32: the residual is recomputed in FP64 whenever the FP32 one fell by 1e-5 (environment
  * WF_RELIABLE_DELTA); CG iterations run in blocks whose convergence checks happen on the device,
  * one iteration replayed as a CUDA graph when the handle has a stream of its own (environment
  * WF_GRAPH=0: plain launches). The first FP32 solve or apply for a given nrhs also tunes the
@@ -162,13 +163,29 @@ int wf_apply_schur_f16(wf_handle_t* h, const double* in_odd, double* out_odd, in
 int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int method, int precision,
              int flags, int* iters_out, double* true_resid_out);
 
-/* Several independent solves in one call: handle hs[i] (one lattice each, possibly of different
- * sizes; the handles must be distinct) solves nrhs[i] sources rhs[i] into x[i], with the arguments
- * and conventions of wf_solve. Every solve runs on a host thread of its own and on its handle's
- * stream (a temporary stream for handles on the default stream), so the GPU works on all lattices
- * at once: ragged batches such as a sweep over lattice sizes at one anisotropy. No counterpart in the
- * paper (its solves are independent problems). iters_out, resid_out and status_out may be null,
- * or hold n pointers (n statuses); returns WF_OK or the first non-OK status. */
+/* Several solves in one call (ragged batches, such as a sweep over lattice sizes at one
+ * anisotropy): handle hs[i] (one lattice each, possibly of different sizes; the handles must be
+ * distinct) solves nrhs[i] sources rhs[i] into x[i], with the arguments and conventions of wf_solve
+ * (tol, method, precision and flags common to all).
+ *   - Joint path: FP32 temporal + Schur solves (WF_TEMPORAL_SCHUR, WF_FP32) on handles of one
+ *     device, in the axial frame, with one iteration limit, no clover term and at most
+ *     WF_MAX_SOLVE_RHS sources in all are solved as one
+ *     CGNR over the concatenation of all lattices' sources. Each of its kernels (K-a, K-b, K-c, the
+ *     vector updates, norms and convergence checks) runs as one launch over every lattice (eight
+ *     lattices per launch at most); the S_L preparation, the reconstruction, the FP64 reliable
+ *     updates and the FP64 true residual run per lattice, each on its handle's stream, so that
+ *     they overlap. K-b and K-c take each lattice's autotuned configuration (tuned in the call for
+ *     a handle with none for its nrhs): lattices on the one-thread-per-site kernels share one
+ *     launch, the others launch their own. Every source keeps its own CG scalars, stopping test
+ *     and reliable updates, so it takes the iterations of a separate solve (up to the rounding of
+ *     its norms). The call first synchronises every handle's stream; the iterations run on hs[0]'s
+ *     stream; a handle on the default stream, or on a stream another handle uses, works on a
+ *     temporary stream. An error is reported on every handle and as every status.
+ *   - Otherwise (or with environment WF_JOINT=0) every solve runs on a host thread of its own and
+ *     on its handle's stream (a temporary stream for handles on the default stream).
+ * No counterpart in the paper (its solves are independent problems). iters_out, resid_out and
+ * status_out may be null, or hold n pointers (n statuses); returns WF_OK or the first non-OK
+ * status. */
 int wf_solve_many(int n, wf_handle_t* const* hs, const double* const* rhs, double* const* x, const int* nrhs,
                   double tol, int method, int precision, int flags, int* const* iters_out,
                   double* const* resid_out, int* status_out);

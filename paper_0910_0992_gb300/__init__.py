@@ -12,7 +12,7 @@ be torch tensors (CUDA or CPU) or NumPy arrays (host).
 
 from ._lib import (  # noqa: F401
     WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ESINGULAR, WF_ENOCONV, WF_ENAN, WF_ETIMEOUT,
-    WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR, WF_TEMPORAL_ILU, WF_FP64, WF_FP32, WF_FP16MIX, WF_X0,
+    WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR, WF_TEMPORAL_ILU, WF_FP64, WF_FP32, WF_FP16MIX, WF_X0, WF_MAX_SOLVE_RHS,
     WFError, lib, lib_path, exported_symbols,
     wf_create, wf_destroy, wf_set_stream, wf_last_error, wf_set_gauge_frame, wf_field_elems, wf_half_elems,
     wf_load_gauge, wf_load_gauge_clover, wf_apply_clover, wf_apply_ilu, wf_apply_ilu_f32, wf_apply_M, wf_apply_M_f32, wf_apply_Tinv, wf_apply_Tinv_f32, wf_apply_C,

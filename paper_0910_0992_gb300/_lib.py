@@ -10,6 +10,7 @@ WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ESINGULAR, WF_ENOCONV, WF_ENAN, WF_ETI
 WF_UNPREC, WF_EO4D, WF_TEMPORAL, WF_TEMPORAL_SCHUR, WF_TEMPORAL_ILU = range(5)
 WF_FP64, WF_FP32, WF_FP16MIX = 0, 1, 2
 WF_X0 = 1
+WF_MAX_SOLVE_RHS = 1024  # right-hand sides of one solve (all lattices of a joint wf_solve_many)
 
 _STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "WF_ESINGULAR",
            5: "WF_ENOCONV", 6: "WF_ENAN", 7: "WF_ETIMEOUT"}

@@ -543,11 +543,15 @@ using OpFn = std::function<void(const Cx<R>* x, Cx<R>* y, int dagger, double* no
 // CGNR, CG on A^dag A y = A^dag b, with operator applies in precision R (R = double: plain
 // FP64 CG; R = float: FP32 iterations with FP64 reliable updates of the residual, using A64).
 // b and y are FP64 internal vectors of n complex numbers per rhs; stops when |b - A y| <=
-// target[k] for every rhs k. Returns the iterations per rhs.
+// target[k] for every rhs k. Returns the iterations per rhs. reliable = false: no reliable
+// updates (A64 is then called only for an initial guess).
 template <typename R>
 std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, const Cx<double>* b, Cx<double>* y,
-                      int nrhs, size_t n, const std::vector<double>& target, int maxiter, bool x0) {
-  const size_t nt = n * nrhs;
+                      int nrhs, size_t n, const std::vector<double>& target, int maxiter, bool x0,
+                      size_t ntot = 0, const size_t* offs = nullptr, bool reliable = true) {
+  // ragged batches: ntot elements in all, offs the device prefix table of the right-hand sides'
+  // first elements (n then the largest length); otherwise nrhs x n
+  const size_t nt = ntot ? ntot : n * nrhs;
   cudaStream_t s = h->stream;
   double* sc = h->buf<double>("cg_scalars", 16 * (size_t)nrhs);
   double *gam = sc, *gnew = sc + nrhs, *qq = sc + 2 * nrhs, *rr = sc + 3 * nrhs;
@@ -591,7 +595,7 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
   }
   Cx<R>* xacc = mixed ? xi : reinterpret_cast<Cx<R>*>(y);
 
-  { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
+  { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s, offs); }
   std::vector<double> rnorm2 = read_scalars(h, rr, nrhs);
   std::vector<double> rmax(nrhs);
   for (int k = 0; k < nrhs; ++k) {
@@ -628,7 +632,7 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
   std::vector<int> st(nrhs, 0), cnt(nrhs, 0);
   for (int k = 0; k < nrhs; ++k) {
     tgt2[k] = target[k] * target[k];
-    ru2[k] = mixed ? (delta * rmax[k]) * (delta * rmax[k]) : 0.0;
+    ru2[k] = mixed && reliable ? (delta * rmax[k]) * (delta * rmax[k]) : 0.0;
     if (!act[k]) st[k] = 1;
   }
   auto upload_state = [&]() {
@@ -642,10 +646,10 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
 
   auto iteration = [&]() {
     A(p, q, 0, qq);  // q = A p, |q|^2
-    { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s); }
+    { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s, offs); }
     { Prof P(h, "cg_check"); launch_cg_check(rr, active, state, dits, lim, lim + nrhs, nrhs, s); }
     A(r, sv, 1, gnew);  // s = A^dag r, |s|^2
-    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
+    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s, offs); }
     { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
   };
 
@@ -733,7 +737,7 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
       { Prof P(h, "add_f_to_d"); launch_add_f_to_d(y, reinterpret_cast<const Cx<float>*>(xi), nt, s); }
       WF_CUDA(cudaMemsetAsync(xi, 0, nt * sizeof(Cx<R>), s));
       true_schur_residual();
-      { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s); }
+      { Prof P(h, "norm2_f64", 2); launch_norm2<double>(r64, n, nrhs, partial, rr, s, offs); }
       { Prof P(h, "d2f"); launch_d2f(r64, reinterpret_cast<Cx<float>*>(r), nt, s); }
       std::vector<double> r64n = read_scalars(h, rr, nrhs);
       std::vector<int> resume(nrhs, 0);
@@ -756,7 +760,7 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
       if (any_resume) {
         WF_CUDA(cudaMemcpyAsync(active, resume.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
         A(r, sv, 1, gnew);
-        { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s); }
+        { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s, offs); }
         { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
       }
       upload_state();
@@ -1081,8 +1085,15 @@ std::vector<int> cgnr_h16(wf_handle* h, int nrhs, size_t n, const Cx<double>* b,
 
 // Temporal + 3-D Schur solve (§II.B): prepare with S_L, CGNR on M-hat, reconstruct with S_R,
 // verify with the FP64 true residual of M.
+int solve_temporal_schur_dc(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
+                            bool x0, int* iters_out, double* resid_out);
+
 int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
                          int precision, bool x0, int* iters_out, double* resid_out) {
+  if (precision == WF_FP32) {
+    const char* e = std::getenv("WF_DC");
+    if (e && e[0] == '1') return solve_temporal_schur_dc(h, eta_lex, x_lex, nrhs, tol, x0, iters_out, resid_out);
+  }
   const size_t n = h->half_int();
   const size_t nt = n * nrhs;
   cudaStream_t s = h->stream;
@@ -1184,6 +1195,598 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     if (resid_out) resid_out[k] = rel[k];
   }
   return status;
+}
+
+// Temporal + 3-D Schur solve by defect correction, all operator work in FP32: each pass solves
+// M delta = r with the method's own steps in FP32 (S_L, CGNR on M-hat without FP64 reliable
+// updates, S_R) to a relative reduction rho of its Schur residual (at most down to what tol
+// needs), adds delta to the FP64 solution psi and recomputes the true residual r = eta - M psi in
+// FP64; it stops when ||r|| / ||eta|| <= tol for every source. The only FP64 operator apply per
+// pass is the true residual's, which the solve computes anyway. Environment WF_DC_RHO sets rho
+// (default 1e-5).
+int solve_temporal_schur_dc(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
+                            bool x0, int* iters_out, double* resid_out) {
+  const size_t n = h->half_int();
+  const size_t nt = n * nrhs;
+  cudaStream_t s = h->stream;
+  const int tp = h->g.tp;
+  const double igf = 1.0 / h->g.gamma_f;
+  Cx<double>* eta_e = h->buf<Cx<double>>("sv_eta_e", nt);
+  Cx<double>* eta_o = h->buf<Cx<double>>("sv_eta_o", nt);
+  Cx<double>* psi_e = h->buf<Cx<double>>("sv_psi_e", nt);
+  Cx<double>* psi_o = h->buf<Cx<double>>("sv_psi_o", nt);
+  Cx<double>* r_e = h->buf<Cx<double>>("sv_r_e", nt);
+  Cx<double>* r_o = h->buf<Cx<double>>("sv_r_o", nt);
+  Cx<double>* b_o = h->buf<Cx<double>>("sv_b_o", nt);
+  Cx<double>* y_o = h->buf<Cx<double>>("sv_y_o", nt);
+  Cx<float>* r32_e = h->buf<Cx<float>>("dc_r_e", nt);
+  Cx<float>* r32_o = h->buf<Cx<float>>("dc_r_o", nt);
+  Cx<float>* w32_e = h->buf<Cx<float>>("dc_w_e", nt);
+  Cx<float>* w32_o = h->buf<Cx<float>>("dc_w_o", nt);
+  double* sc = h->buf<double>("sv_scalars", 4 * (size_t)nrhs);
+  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
+  double rho = 1e-5;
+  if (const char* e = std::getenv("WF_DC_RHO")) {
+    const double v = std::atof(e);
+    if (v > 0.0 && v < 1.0) rho = v;
+  }
+
+  { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
+  auto norms2 = [&](const Cx<double>* e, const Cx<double>* o) {
+    { Prof P(h, "norm2_f64", 4); launch_norm2<double>(e, n, nrhs, partial, sc, s); launch_norm2<double>(o, n, nrhs, partial, sc + nrhs, s); }
+    std::vector<double> v = read_scalars(h, sc, 2 * nrhs), out(nrhs);
+    for (int k = 0; k < nrhs; ++k) out[k] = v[k] + v[nrhs + k];
+    return out;
+  };
+  const std::vector<double> eta2 = norms2(eta_e, eta_o);
+  if (x0) {
+    { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex, psi_e, psi_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
+    m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
+  } else {
+    WF_CUDA(cudaMemsetAsync(psi_e, 0, nt * sizeof(Cx<double>), s));
+    WF_CUDA(cudaMemsetAsync(psi_o, 0, nt * sizeof(Cx<double>), s));
+    WF_CUDA(cudaMemcpyAsync(r_e, eta_e, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(r_o, eta_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  }
+  std::vector<double> r2 = norms2(r_e, r_o);
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> rel(nrhs);
+  auto relres = [&]() {
+    bool ok = true;
+    for (int k = 0; k < nrhs; ++k) {
+      rel[k] = std::sqrt(r2[k] / (eta2[k] > 0 ? eta2[k] : 1.0));
+      ok = ok && rel[k] <= tol;
+    }
+    return ok;
+  };
+  bool ok = relres();
+  const int maxiter = h->maxiter;
+  int status = WF_OK;
+  const OpFn<float> A = schur_op<float>(h, nrhs);
+  const OpFn<double> A64 = schur_op<double>(h, nrhs);  // not called: no reliable updates, no guess
+  for (int pass = 0; pass < 8 && !ok; ++pass) {
+    // S_L in FP32 on r: w_e = C_R^e C_L^e r_e ; w_o = C_L^o [r_o + gamma_f^-1 D_s^oe w_e]
+    { Prof P(h, "d2f", 2); launch_d2f(r_e, r32_e, nt, s); launch_d2f(r_o, r32_o, nt, s); }
+    line_load<float>(h, 0, r32_e, w32_e, OP_FWD, OP_BWD, nrhs, "prep_tsolve");
+    {
+      LineArgs<float> a = line_args<float>(h, 1, nrhs);
+      a.src_up = w32_e;
+      a.src_lo = w32_e + 6 * tp;
+      a.xpre = r32_o;
+      a.apre = (float)igf;
+      a.opu = OP_COPY;
+      a.opl = OP_BWD;
+      a.src = SRC_HOP;
+      a.out = w32_o;
+      Prof P(h, "prep_hop_f32");
+      launch_line<float>(a, LK_GENERIC, h->axial, s);
+    }
+    WF_CUDA(cudaMemsetAsync(b_o, 0, nt * sizeof(Cx<double>), s));
+    { Prof P(h, "add_f_to_d"); launch_add_f_to_d(b_o, w32_o, nt, s); }
+    // CGNR on M-hat y = w_o to rho ||w_o|| (no further than half of what tol needs; sources
+    // already at tol take no iterations)
+    { Prof P(h, "norm2_f64", 2); launch_norm2<double>(b_o, n, nrhs, partial, sc, s); }
+    const std::vector<double> b2 = read_scalars(h, sc, nrhs);
+    std::vector<double> target(nrhs);
+    for (int k = 0; k < nrhs; ++k)
+      target[k] = rel[k] <= tol ? 2.0 * std::sqrt(b2[k]) + 1.0
+                                : std::max(rho * std::sqrt(b2[k]), 0.5 * tol * std::sqrt(eta2[k]) / (h->g.mu + 1.0));
+    const std::vector<int> it = cgnr<float>(h, A, A64, b_o, y_o, nrhs, n, target, maxiter, false, 0, nullptr, false);
+    for (int k = 0; k < nrhs; ++k) iters[k] += it[k];
+    // S_R in FP32: d_o = C_R^o y_o ; d_e = C_R^e C_L^e [r_e + gamma_f^-1 D_s^eo d_o] ; psi += d
+    { Prof P(h, "d2f"); launch_d2f(y_o, w32_e, nt, s); }  // y_o in FP32 (w_e is free again)
+    line_load<float>(h, 1, w32_e, w32_o, OP_FWD, OP_COPY, nrhs, "recon_tsolve");
+    {
+      LineArgs<float> a = line_args<float>(h, 0, nrhs);
+      a.src_up = w32_o;
+      a.src_lo = w32_o + 6 * tp;
+      a.xpre = r32_e;
+      a.apre = (float)igf;
+      a.opu = OP_FWD;
+      a.opl = OP_BWD;
+      a.src = SRC_HOP;
+      a.out = w32_e;
+      Prof P(h, "recon_hop_f32");
+      launch_line<float>(a, LK_GENERIC, h->axial, s);
+    }
+    { Prof P(h, "add_f_to_d", 2); launch_add_f_to_d(psi_e, w32_e, nt, s); launch_add_f_to_d(psi_o, w32_o, nt, s); }
+    // true residual in FP64
+    m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
+    r2 = norms2(r_e, r_o);
+    ok = relres();
+    bool capped = false;
+    for (int k = 0; k < nrhs; ++k) capped = capped || iters[k] >= maxiter;
+    if (capped) break;
+  }
+  if (!ok) status = WF_ENOCONV;
+  { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters_out) iters_out[k] = iters[k];
+    if (resid_out) resid_out[k] = rel[k];
+  }
+  return status;
+}
+
+// ----------------------------------------------------------------------------
+// Ragged batches: one temporal + Schur solve over several lattices (wf_solve_many)
+// ----------------------------------------------------------------------------
+
+// One lattice of a joint solve: its handle, sources, field length and place in the joint vectors
+struct JointPart {
+  wf_handle* h;
+  int nrhs;
+  size_t n;    // complex numbers per source (odd internal field)
+  size_t off;  // first element of its sources in the joint vectors
+  int r0;      // its first source in the joint numbering
+};
+
+// Events ordering the joint stream (hs[0]'s) and the lattices' own streams: fan_out makes every
+// lattice's stream wait for the joint stream's work so far, fan_in the joint stream for theirs
+struct JointSync {
+  std::vector<cudaEvent_t> ev;
+  explicit JointSync(size_t n) : ev(n + 1, nullptr) {
+    for (auto& e : ev) WF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  ~JointSync() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  void fan_out(const std::vector<JointPart>& parts) const {
+    cudaStream_t s0 = parts[0].h->stream;
+    WF_CUDA(cudaEventRecord(ev[0], s0));
+    for (size_t j = 1; j < parts.size(); ++j) WF_CUDA(cudaStreamWaitEvent(parts[j].h->stream, ev[0], 0));
+  }
+  void fan_in(const std::vector<JointPart>& parts) const {
+    cudaStream_t s0 = parts[0].h->stream;
+    for (size_t j = 1; j < parts.size(); ++j) {
+      WF_CUDA(cudaEventRecord(ev[j], parts[j].h->stream));
+      WF_CUDA(cudaStreamWaitEvent(s0, ev[j], 0));
+    }
+  }
+};
+
+// M-hat of every lattice in FP32, with x, y, the norms and the solver's active flags in the joint
+// numbering, on the joint stream. K-a runs as one launch over all lattices' sources (per
+// kMaxLattices lattices). K-b and K-c take each lattice's autotuned configuration (the tuner runs
+// here, on scratch fields, for a handle that has none for its number of sources): the lattices
+// whose choice is the one-thread-per-site kernels share one launch per kernel, the others (n sites
+// per lane, bulk-fed) launch their own. Tables are attached here, before the solver captures an
+// iteration.
+OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, Cx<float>* tz, Cx<float>* tw,
+                           int nr) {
+  wf_handle* h0 = parts[0].h;
+  struct Own {
+    LineArgs<float> b, c;
+    wf_handle::HopTune t;
+    const int2* units;
+    int nunits;
+    int* err;
+  };
+  std::vector<LineArgs<float>> A, B, C;  // K-a of all; K-b, K-c of the lattices on the shared launch
+  std::vector<int> joined;               // lattice of each B/C entry
+  std::vector<std::pair<int, Own>> own;  // lattices with a launch of their own
+  for (int j = 0; j < (int)parts.size(); ++j) {
+    const JointPart& q = parts[j];
+    wf_handle* h = q.h;
+    const int tp = h->g.tp;
+    LineArgs<float> a = line_args<float>(h, 1, q.nrhs);
+    a.opu = OP_FWD;
+    a.opl = OP_SKIP;
+    a.out = ty + q.off;
+    LineArgs<float> b = line_args<float>(h, 0, q.nrhs);
+    b.src_up = ty + q.off;
+    b.opu = OP_FWD;
+    b.opl = OP_BWD;
+    b.out = tz + q.off;
+    LineArgs<float> c = line_args<float>(h, 1, q.nrhs);
+    c.src_up = tz + q.off;
+    c.src_lo = tz + q.off + 6 * tp;
+    c.opu = OP_COPY;
+    c.opl = OP_BWD;
+    c.apost = (float)(-1.0 / (h->g.gamma_f * h->g.gamma_f));
+    c.stream_out = 1;
+    // the tuner times K-b and K-c on scratch fields of this lattice's size
+    LineArgs<float> bt = b, ct = c;
+    bt.src_lo = ty + q.off;
+    ct.xpost = ty + q.off;
+    ct.out = tw + q.off;
+    const wf_handle::HopTune t = tune_hops(h, bt, ct);
+    b.variant = c.variant = t.variant;
+    b.pipe_g = c.pipe_g = t.gsrc;
+    b.pipe_ns = c.pipe_ns = t.ns;
+    b.g.by = c.g.by = t.by;
+    attach_tables(h, b);
+    attach_tables(h, c);
+    A.push_back(a);
+    if (t.variant <= 1) {
+      B.push_back(b);
+      C.push_back(c);
+      joined.push_back(j);
+    } else {
+      Own o{b, c, t, nullptr, 0, nullptr};
+      if (t.variant == 3) {
+        o.units = attach_units(h, b, t.gsrc, o.nunits);
+        if (!h->tma_err.p) h->tma_err.ensure(sizeof(int), h->stream);
+        o.err = h->tma_err.as<int>();
+      }
+      own.emplace_back(j, o);
+    }
+  }
+  const int nl = (int)parts.size();
+  const int na = (nl + kMaxLattices - 1) / kMaxLattices;
+  const int nb = ((int)B.size() + kMaxLattices - 1) / kMaxLattices + (int)own.size();
+  return [=](const Cx<float>* x, Cx<float>* y, int dagger, double* norm2) mutable {
+    const int* act = h0->op_active;
+    auto set_b = [&](LineArgs<float>& b, const JointPart& q) {
+      const Cx<float>* xu = x + q.off;
+      const Cx<float>* xl = xu + 6 * q.h->g.tp;
+      b.src_lo = dagger ? xu : xl;
+      b.active = act ? act + q.r0 : nullptr;
+    };
+    auto set_c = [&](LineArgs<float>& c, const JointPart& q) {
+      c.xpost = x + q.off;
+      c.swap_out = dagger;
+      c.out = y + q.off;
+      c.norm2 = norm2 ? norm2 + q.r0 : nullptr;
+      c.active = act ? act + q.r0 : nullptr;
+    };
+    for (int j = 0; j < nl; ++j) {
+      const JointPart& q = parts[j];
+      const Cx<float>* xu = x + q.off;
+      const Cx<float>* xl = xu + 6 * q.h->g.tp;
+      A[j].src_up = dagger ? xl : xu;
+      A[j].src_lo = dagger ? xu : xl;
+      A[j].active = act ? act + q.r0 : nullptr;
+    }
+    for (size_t i = 0; i < B.size(); ++i) {
+      set_b(B[i], parts[joined[i]]);
+      set_c(C[i], parts[joined[i]]);
+    }
+    for (auto& o : own) {
+      set_b(o.second.b, parts[o.first]);
+      set_c(o.second.c, parts[o.first]);
+    }
+    cudaStream_t s = h0->stream;
+    auto launch_own = [&](const Own& o, const LineArgs<float>& a, int kind) {
+      if (o.t.variant == 3)
+        launch_hop_pipe(a, kind, o.t.gsrc, o.t.ns, o.units, o.nunits, o.err, s);
+      else
+        launch_line<float>(a, kind, true, s);
+    };
+    { Prof P(h0, "schur_a_tdag_f32", na); launch_line_multi<float>(A, LK_SCHUR_A, s); }
+    {
+      Prof P(h0, "schur_b_hop_tsolve_f32", nb);
+      launch_line_wide_multi<float>(B, LK_SCHUR_B, s);
+      for (const auto& o : own) launch_own(o.second, o.second.b, LK_SCHUR_B);
+    }
+    if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nr * sizeof(double), s));
+    {
+      Prof P(h0, "schur_c_hop_tinv_axpy_f32", nb);
+      launch_line_wide_multi<float>(C, LK_SCHUR_C, s);
+      for (const auto& o : own) launch_own(o.second, o.second.c, LK_SCHUR_C);
+    }
+  };
+}
+
+// M-hat of every lattice in FP64 (the reliable updates): each lattice on its own stream, fenced
+// against the joint stream
+OpFn<double> joint_schur_op64(const std::vector<JointPart>& parts, const JointSync& sync) {
+  std::vector<std::pair<Cx<double>*, Cx<double>*>> work;
+  for (const JointPart& q : parts)
+    work.emplace_back(q.h->buf<Cx<double>>(pname<double>("op_ty"), q.n * q.nrhs),
+                      q.h->buf<Cx<double>>(pname<double>("op_tz"), q.n * q.nrhs));
+  const JointSync* sp = &sync;
+  return [=](const Cx<double>* x, Cx<double>* y, int dagger, double* norm2) {
+    const int* act = parts[0].h->op_active;
+    sp->fan_out(parts);
+    for (size_t j = 0; j < parts.size(); ++j) {
+      const JointPart& q = parts[j];
+      const int* keep = q.h->op_active;
+      q.h->op_active = act ? act + q.r0 : nullptr;
+      schur_apply<double>(q.h, x + q.off, y + q.off, dagger, q.nrhs, work[j].first, work[j].second,
+                          norm2 ? norm2 + q.r0 : nullptr);
+      q.h->op_active = keep;
+    }
+    sp->fan_in(parts);
+  };
+}
+
+// The temporal + Schur solves of several lattices as one CGNR over the concatenation of their
+// odd fields. The FP64 steps -- S_L preparation, reconstruction, true residual, reliable updates
+// and export -- run per lattice, each on its handle's stream so that they overlap; the iterations
+// run on hs[0]'s stream, where every kernel of an iteration covers all lattices' sources. Each
+// source keeps its own CG scalars, stopping test and reliable updates, as in a separate solve. The
+// handles' streams are distinct (the caller sees to it).
+void solve_temporal_schur_joint(int nl, wf_handle* const* hs, const std::vector<const Cx<double>*>& eta_lex,
+                                const std::vector<Cx<double>*>& x_lex, const int* nrhs, double tol, bool x0,
+                                std::vector<std::vector<int>>& iters, std::vector<std::vector<double>>& rel,
+                                std::vector<int>& status) {
+  wf_handle* h0 = hs[0];
+  cudaStream_t s = h0->stream;
+  std::vector<JointPart> parts(nl);
+  size_t ntot = 0, nmax = 0;
+  int nr = 0;
+  for (int j = 0; j < nl; ++j) {
+    parts[j] = {hs[j], nrhs[j], hs[j]->half_int(), ntot, nr};
+    ntot += parts[j].n * nrhs[j];
+    nmax = std::max(nmax, parts[j].n);
+    nr += nrhs[j];
+  }
+  const JointSync sync(parts.size());
+  // the solver's vectors, scratch fields of the operator, the first element of every source
+  Cx<double>* b = h0->buf<Cx<double>>("jv_b", ntot);
+  Cx<double>* y = h0->buf<Cx<double>>("jv_y", ntot);
+  Cx<float>* ty = h0->buf<Cx<float>>("jv_ty_f32", ntot);
+  Cx<float>* tz = h0->buf<Cx<float>>("jv_tz_f32", ntot);
+  Cx<float>* tw = h0->buf<Cx<float>>("jv_tw_f32", ntot);
+  size_t* offs = h0->buf<size_t>("jv_offs", (size_t)nr + 1);
+  {
+    std::vector<size_t> o;
+    for (const JointPart& q : parts)
+      for (int k = 0; k < q.nrhs; ++k) o.push_back(q.off + (size_t)k * q.n);
+    o.push_back(ntot);
+    WF_CUDA(cudaMemcpyAsync(offs, o.data(), o.size() * sizeof(size_t), cudaMemcpyHostToDevice, s));
+    // o is a host temporary; the lattices' streams also write into b and y (zeroed on s)
+    WF_CUDA(cudaStreamSynchronize(s));
+  }
+  // double-float FP64 steps where a handle allows them, as in wf_solve's FP32 solves
+  struct DfAll {
+    std::vector<std::pair<wf_handle*, bool>> old;
+    ~DfAll() {
+      for (auto& p : old) p.first->df_ops = p.second;
+    }
+  } dfall;
+  for (const JointPart& q : parts) {
+    dfall.old.emplace_back(q.h, q.h->df_ops);
+    q.h->df_ops = q.h->df_allowed;
+  }
+
+  struct PerLattice {
+    Cx<double> *eta_e, *eta_o, *a_e, *psi_e, *psi_o, *r_e, *r_o;
+    double* sc;
+    double* partial;
+    std::vector<double> eta2;
+  };
+  std::vector<PerLattice> L(nl);
+  std::vector<double> target(nr);
+  // S_L per lattice on its own stream (all launched before any norm is read back)
+  for (int j = 0; j < nl; ++j) {
+    wf_handle* h = parts[j].h;
+    cudaStream_t sj = h->stream;
+    const int m = parts[j].nrhs;
+    const size_t n = parts[j].n, nt = n * m;
+    PerLattice& P = L[j];
+    P.eta_e = h->buf<Cx<double>>("sv_eta_e", nt);
+    P.eta_o = h->buf<Cx<double>>("sv_eta_o", nt);
+    P.a_e = h->buf<Cx<double>>("sv_a_e", nt);
+    P.psi_e = h->buf<Cx<double>>("sv_psi_e", nt);
+    P.psi_o = h->buf<Cx<double>>("sv_psi_o", nt);
+    P.r_e = h->buf<Cx<double>>("sv_r_e", nt);
+    P.r_o = h->buf<Cx<double>>("sv_r_o", nt);
+    P.sc = h->buf<double>("sv_scalars", 4 * (size_t)m);
+    P.partial = h->buf<double>("cg_partial", 1024 * (size_t)m);
+    Cx<double>* b_o = b + parts[j].off;
+    { Prof Q(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex[j], P.eta_e, P.eta_o, m, 0, frame_rot(h, 0), frame_rot(h, 1), sj); }
+    // a_e = C_R^e C_L^e eta_e ; b_o = C_L^o [eta_o + gamma_f^-1 D_s^oe a_e]
+    line_load<double>(h, 0, P.eta_e, P.a_e, OP_FWD, OP_BWD, m, "prep_tsolve");
+    {
+      LineArgs<double> a = line_args<double>(h, 1, m);
+      a.src_up = P.a_e;
+      a.src_lo = P.a_e + 6 * h->g.tp;
+      a.xpre = P.eta_o;
+      a.apre = 1.0 / h->g.gamma_f;
+      a.opu = OP_COPY;
+      a.opl = OP_BWD;
+      a.src = SRC_HOP;
+      a.out = b_o;
+      Prof Q(h, "prep_hop_f64");
+      launch_line<double>(a, LK_GENERIC, h->axial, sj);
+    }
+    { Prof Q(h, "norm2_f64", 4); launch_norm2<double>(P.eta_e, n, m, P.partial, P.sc, sj); launch_norm2<double>(P.eta_o, n, m, P.partial, P.sc + m, sj); }
+    if (x0) {
+      // the odd part of the guess starts y_o, as in the single solve
+      { Prof Q(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex[j], P.r_e, P.psi_o, m, 0, frame_rot(h, 0), frame_rot(h, 1), sj); }
+      WF_CUDA(cudaMemcpyAsync(y + parts[j].off, P.psi_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, sj));
+    }
+  }
+  for (int j = 0; j < nl; ++j) {
+    const int m = parts[j].nrhs;
+    const std::vector<double> e2 = read_scalars(parts[j].h, L[j].sc, 2 * m);
+    L[j].eta2.resize(m);
+    for (int k = 0; k < m; ++k) {
+      L[j].eta2[k] = e2[k] + e2[m + k];
+      target[parts[j].r0 + k] = tol * std::sqrt(L[j].eta2[k]) / (parts[j].h->g.mu + 1.0);  // as in the single solve
+    }
+  }
+  sync.fan_in(parts);  // b (and y) complete on the joint stream
+
+  const OpFn<float> A = joint_schur_op(parts, ty, tz, tw, nr);
+  const OpFn<double> A64 = joint_schur_op64(parts, sync);
+  const int maxiter = h0->maxiter;
+  std::vector<int> it_all(nr, 0);
+  std::vector<char> ok_l(nl, 0);
+  for (int j = 0; j < nl; ++j) {
+    iters[j].assign(parts[j].nrhs, 0);
+    rel[j].assign(parts[j].nrhs, 0.0);
+    status[j] = WF_OK;
+  }
+  bool have_x0 = x0;
+  for (int pass = 0; pass < 6; ++pass) {
+    const std::vector<int> it = cgnr<float>(h0, A, A64, b, y, nr, nmax, target, maxiter, have_x0, ntot, offs);
+    for (int r = 0; r < nr; ++r) it_all[r] += it[r];
+    have_x0 = true;
+    // S_R and the FP64 true residual per lattice, overlapped on the lattices' streams
+    sync.fan_out(parts);
+    for (int j = 0; j < nl; ++j) {
+      wf_handle* h = parts[j].h;
+      cudaStream_t sj = h->stream;
+      const int m = parts[j].nrhs;
+      const size_t n = parts[j].n;
+      PerLattice& P = L[j];
+      const Cx<double>* y_o = y + parts[j].off;
+      // psi_o = C_R^o y_o ; psi_e = C_R^e C_L^e [eta_e + gamma_f^-1 D_s^eo psi_o]
+      line_load<double>(h, 1, y_o, P.psi_o, OP_FWD, OP_COPY, m, "recon_tsolve");
+      {
+        LineArgs<double> a = line_args<double>(h, 0, m);
+        a.src_up = P.psi_o;
+        a.src_lo = P.psi_o + 6 * h->g.tp;
+        a.xpre = P.eta_e;
+        a.apre = 1.0 / h->g.gamma_f;
+        a.opu = OP_FWD;
+        a.opl = OP_BWD;
+        a.src = SRC_HOP;
+        a.out = P.psi_e;
+        Prof Q(h, "recon_hop_f64");
+        launch_line<double>(a, LK_GENERIC, h->axial, sj);
+      }
+      m_apply<double>(h, P.psi_e, P.psi_o, P.r_e, P.r_o, P.eta_e, P.eta_o, -1.0, m);
+      { Prof Q(h, "norm2_f64", 4); launch_norm2<double>(P.r_e, n, m, P.partial, P.sc, sj); launch_norm2<double>(P.r_o, n, m, P.partial, P.sc + m, sj); }
+    }
+    bool all_ok = true, capped = false;
+    for (int j = 0; j < nl; ++j) {
+      const int m = parts[j].nrhs;
+      const std::vector<double> r2 = read_scalars(parts[j].h, L[j].sc, 2 * m);
+      bool ok = true;
+      for (int k = 0; k < m; ++k) {
+        const int r = parts[j].r0 + k;
+        rel[j][k] = std::sqrt((r2[k] + r2[m + k]) / (L[j].eta2[k] > 0 ? L[j].eta2[k] : 1.0));
+        iters[j][k] = it_all[r];
+        if (rel[j][k] > tol) {
+          ok = false;
+          target[r] *= 0.5 * tol / rel[j][k];
+        }
+        if (it_all[r] >= maxiter) {
+          status[j] = WF_ENOCONV;
+          capped = true;
+        }
+      }
+      ok_l[j] = ok;
+      all_ok = all_ok && ok;
+    }
+    if (all_ok || capped) break;
+    sync.fan_in(parts);  // the next pass's reliable updates read y after this pass's reads
+  }
+  for (int j = 0; j < nl; ++j)
+    if (!ok_l[j]) status[j] = WF_ENOCONV;  // tol not reached within six passes or the iteration limit
+  for (int j = 0; j < nl; ++j) {
+    wf_handle* h = parts[j].h;
+    Prof Q(h, "export_spinor_f64");
+    launch_export_spinor<double>(h->g, L[j].psi_e, L[j].psi_o, x_lex[j], parts[j].nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream);
+  }
+}
+
+// Whether wf_solve_many can solve its lattices jointly: FP32 iterations of the temporal + Schur
+// method in the axial frame, on lattices the one-thread-per-site kernels serve, on one device,
+// with one iteration limit and no clover term (environment WF_JOINT=0: one solve per lattice)
+bool joint_eligible(int n, wf_handle* const* hs, int method, int precision) {
+  if (n < 2 || method != WF_TEMPORAL_SCHUR || precision != WF_FP32) return false;
+  if (const char* e = std::getenv("WF_JOINT"))
+    if (e[0] == '0') return false;
+  if (const char* e = std::getenv("WF_TMA"))
+    if (e[0] == '1') return false;
+  for (int i = 0; i < n; ++i) {
+    const wf_handle* h = hs[i];
+    if (!h->gauge || h->clover || !h->axial || !wide_supported(h->g) || h->use_tma == 1) return false;
+    if (h->device != hs[0]->device || h->maxiter != hs[0]->maxiter) return false;
+  }
+  return true;
+}
+
+// the joint solve holds every lattice's sources in one set of CG scalars
+bool joint_fits(int n, const int* nrhs) {
+  long long nr = 0;
+  for (int i = 0; i < n; ++i) nr += nrhs[i] > 0 ? nrhs[i] : 0;
+  return nr <= WF_MAX_SOLVE_RHS;
+}
+
+// wf_solve_many's joint path: argument checks and host staging per handle as in wf_solve; every
+// handle works on a stream of its own (a temporary one for a handle on the default stream or on
+// another handle's stream), restored after the call
+void solve_many_joint(int n, wf_handle* const* hs, const double* const* rhs, double* const* x, const int* nrhs,
+                      double tol, int flags, int* const* iters_out, double* const* resid_out, std::vector<int>& st) {
+  std::vector<cudaStream_t> old(n), own(n, nullptr);
+  for (int i = 0; i < n; ++i) old[i] = hs[i]->stream;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  auto restore = [&]() {
+    for (int i = 0; i < n; ++i) {
+      if (own[i]) {
+        cudaStreamSynchronize(own[i]);
+        cudaStreamDestroy(own[i]);
+      }
+      hs[i]->stream = old[i];
+    }
+    cudaSetDevice(prev);
+  };
+  try {
+    for (int i = 0; i < n; ++i) hs[i]->err.clear();
+    WF_CUDA(cudaSetDevice(hs[0]->device));
+    if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
+    for (int i = 0; i < n; ++i)
+      if (nrhs[i] < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+    // work the caller queued on the handles' streams comes first
+    for (int i = 0; i < n; ++i) WF_CUDA(cudaStreamSynchronize(old[i]));
+    for (int i = 0; i < n; ++i) {
+      bool shared = old[i] == nullptr;
+      for (int j = 0; j < i && !shared; ++j) shared = old[j] == old[i];
+      if (shared) {
+        WF_CUDA(cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking));
+        hs[i]->stream = own[i];
+      }
+    }
+    const bool x0 = (flags & WF_X0) != 0;
+    std::vector<const Cx<double>*> din(n);
+    std::vector<Cx<double>*> dx(n);
+    std::vector<char> staged(n);
+    std::vector<size_t> le(n);
+    for (int i = 0; i < n; ++i) {
+      le[i] = hs[i]->lex_elems() * nrhs[i];
+      din[i] = dev_in(hs[i], rhs[i], le[i], "stage_in");
+      bool sg = false;
+      dx[i] = dev_out(hs[i], x[i], le[i], "stage_out", sg);
+      staged[i] = sg;
+      if (x0 && sg)
+        WF_CUDA(cudaMemcpyAsync(dx[i], x[i], le[i] * sizeof(Cx<double>), cudaMemcpyHostToDevice, hs[i]->stream));
+    }
+    std::vector<std::vector<int>> it(n);
+    std::vector<std::vector<double>> res(n);
+    solve_temporal_schur_joint(n, hs, din, dx, nrhs, tol, x0, it, res, st);
+    for (int i = 0; i < n; ++i) {
+      finish_out(hs[i], x[i], dx[i], le[i], staged[i]);
+      for (int k = 0; k < nrhs[i]; ++k) {
+        if (iters_out && iters_out[i]) iters_out[i][k] = it[i][k];
+        if (resid_out && resid_out[i]) resid_out[i][k] = res[i][k];
+      }
+      if (st[i] == WF_ENOCONV) hs[i]->err = "solver did not reach tol";
+    }
+  } catch (const Error& e) {
+    for (int i = 0; i < n; ++i) st[i] = fail(hs[i], e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    for (int i = 0; i < n; ++i) st[i] = fail(hs[i], WF_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    for (int i = 0; i < n; ++i) st[i] = fail(hs[i], WF_ECUDA, e.what());
+  }
+  restore();
 }
 
 // ----------------------------------------------------------------------------
@@ -2385,7 +2988,7 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
              int* iters_out, double* true_resid_out) {
   return guarded(h, [&]() {
     if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
-    if (nrhs < 1) throw Error(WF_EINVAL, "nrhs must be >= 1");
+    if (nrhs < 1 || nrhs > WF_MAX_SOLVE_RHS) throw Error(WF_EINVAL, "nrhs must lie in [1, WF_MAX_SOLVE_RHS]");
     if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
     if (precision != WF_FP64 && precision != WF_FP32 && precision != WF_FP16MIX)
       throw Error(WF_EINVAL, "unknown precision");
@@ -2428,6 +3031,15 @@ int wf_solve_many(int n, wf_handle_t* const* hs, const double* const* rhs, doubl
       if (hs[j] == hs[i]) return WF_EINVAL;  // one handle per lattice: a handle is not shared
   }
   std::vector<int> st(n, WF_OK);
+  if (joint_eligible(n, hs, method, precision) && joint_fits(n, nrhs)) {
+    solve_many_joint(n, hs, rhs, x, nrhs, tol, flags, iters_out, resid_out, st);
+    int first = WF_OK;
+    for (int i = 0; i < n; ++i) {
+      if (status_out) status_out[i] = st[i];
+      if (first == WF_OK && st[i] != WF_OK) first = st[i];
+    }
+    return first;
+  }
   std::vector<cudaStream_t> own(n, nullptr);
   try {
     // every solve on a stream of its own (a temporary one for handles on the default stream)

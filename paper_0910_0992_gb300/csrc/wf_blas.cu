@@ -32,10 +32,26 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;  // valid in thread 0
 }
 
+// Ragged batches (several lattices in one CG): offs, if set, is the prefix table [nrhs + 1] of the
+// right-hand sides' first elements in the packed vectors (then n only sizes the grid).
+__device__ __forceinline__ void rhs_range(int rhs, size_t n, const size_t* offs, size_t& off, size_t& len) {
+  if (offs) {
+    off = offs[rhs];
+    len = offs[rhs + 1] - off;
+  } else {
+    off = (size_t)rhs * n;
+    len = n;
+  }
+}
+
 template <typename R>
-__global__ void __launch_bounds__(kBT) k_norm2(const Cx<R>* __restrict__ x, size_t n, double* partial) {
+__global__ void __launch_bounds__(kBT) k_norm2(const Cx<R>* __restrict__ x, size_t n, double* partial,
+                                               const size_t* offs) {
   const int rhs = blockIdx.y;
-  const Cx<R>* xr = x + (size_t)rhs * n;
+  size_t o0, len;
+  rhs_range(rhs, n, offs, o0, len);
+  n = len;
+  const Cx<R>* xr = x + o0;
   R part = R(0);  // per-thread partial sum in the field's precision; FP64 across threads
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
     const Cx<R> v = xr[i];
@@ -54,25 +70,29 @@ __global__ void __launch_bounds__(kBT) k_final_sum(const double* __restrict__ pa
 }
 
 template <typename R>
-void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s) {
+void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s,
+                  const size_t* offs) {
   const int parts = parts_for(n);
-  k_norm2<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, n, partial);
+  k_norm2<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, n, partial, offs);
   k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, out);
   WF_CUDA(cudaGetLastError());
 }
-template void launch_norm2<float>(const Cx<float>*, size_t, int, double*, double*, cudaStream_t);
-template void launch_norm2<double>(const Cx<double>*, size_t, int, double*, double*, cudaStream_t);
+template void launch_norm2<float>(const Cx<float>*, size_t, int, double*, double*, cudaStream_t, const size_t*);
+template void launch_norm2<double>(const Cx<double>*, size_t, int, double*, double*, cudaStream_t, const size_t*);
 
 // alpha = gamma / |q|^2; x += alpha p; r -= alpha q; partial |r|^2
 template <typename R>
 __global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __restrict__ r, const Cx<R>* __restrict__ p,
                                                 const Cx<R>* __restrict__ q, size_t n, const double* gamma,
-                                                const double* qq, const int* active, double* partial) {
+                                                const double* qq, const int* active, double* partial,
+                                                const size_t* offs) {
   const int rhs = blockIdx.y;
   const bool on = active[rhs] != 0;
   const double qn = qq[rhs];
   const R alpha = (on && qn > 0.0) ? (R)(gamma[rhs] / qn) : R(0);
-  const size_t off = (size_t)rhs * n;
+  size_t off, len;
+  rhs_range(rhs, n, offs, off, len);
+  n = len;
   R part = R(0);  // per-thread partial |r|^2 in the field's precision; FP64 across threads
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
     const Cx<R> pv = p[off + i], qv = q[off + i];
@@ -91,26 +111,32 @@ __global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __r
 
 template <typename R>
 void launch_cg_xr(Cx<R>* x, Cx<R>* r, const Cx<R>* p, const Cx<R>* q, size_t n, int nrhs, const double* gamma,
-                  const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s) {
+                  const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s,
+                  const size_t* offs) {
   const int parts = parts_for(n);
-  k_cg_xr<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, r, p, q, n, gamma, qq, active, partial);
+  k_cg_xr<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, r, p, q, n, gamma, qq, active, partial, offs);
   k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, rr_out);
   WF_CUDA(cudaGetLastError());
 }
 template void launch_cg_xr<float>(Cx<float>*, Cx<float>*, const Cx<float>*, const Cx<float>*, size_t, int,
-                                  const double*, const double*, const int*, double*, double*, cudaStream_t);
+                                  const double*, const double*, const int*, double*, double*, cudaStream_t,
+                                  const size_t*);
 template void launch_cg_xr<double>(Cx<double>*, Cx<double>*, const Cx<double>*, const Cx<double>*, size_t, int,
-                                   const double*, const double*, const int*, double*, double*, cudaStream_t);
+                                   const double*, const double*, const int*, double*, double*, cudaStream_t,
+                                   const size_t*);
 
 // beta = gamma_new / gamma_old; p = s + beta p
 template <typename R>
 __global__ void __launch_bounds__(kBT) k_cg_p(Cx<R>* __restrict__ p, const Cx<R>* __restrict__ sv, size_t n,
-                                               const double* gnew, const double* gold, const int* active) {
+                                               const double* gnew, const double* gold, const int* active,
+                                               const size_t* offs) {
   const int rhs = blockIdx.y;
   if (!active[rhs]) return;
   const double go = gold[rhs];
   const R beta = go > 0.0 ? (R)(gnew[rhs] / go) : R(0);
-  const size_t off = (size_t)rhs * n;
+  size_t off, len;
+  rhs_range(rhs, n, offs, off, len);
+  n = len;
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
     const Cx<R> s = sv[off + i];
     Cx<R> pv = p[off + i];
@@ -122,15 +148,15 @@ __global__ void __launch_bounds__(kBT) k_cg_p(Cx<R>* __restrict__ p, const Cx<R>
 
 template <typename R>
 void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* gnew, const double* gold,
-                 const int* active, cudaStream_t s) {
+                 const int* active, cudaStream_t s, const size_t* offs) {
   const int parts = parts_for(n) * 2;
-  k_cg_p<R><<<dim3(parts, nrhs), kBT, 0, s>>>(p, sv, n, gnew, gold, active);
+  k_cg_p<R><<<dim3(parts, nrhs), kBT, 0, s>>>(p, sv, n, gnew, gold, active, offs);
   WF_CUDA(cudaGetLastError());
 }
 template void launch_cg_p<float>(Cx<float>*, const Cx<float>*, size_t, int, const double*, const double*,
-                                 const int*, cudaStream_t);
+                                 const int*, cudaStream_t, const size_t*);
 template void launch_cg_p<double>(Cx<double>*, const Cx<double>*, size_t, int, const double*, const double*,
-                                  const int*, cudaStream_t);
+                                  const int*, cudaStream_t, const size_t*);
 
 template <typename R>
 __global__ void __launch_bounds__(kBT) k_axpby(Cx<R>* __restrict__ y, const Cx<R>* __restrict__ x, size_t n, R a, R b) {

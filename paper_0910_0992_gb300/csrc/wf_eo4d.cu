@@ -162,17 +162,21 @@ __global__ void __launch_bounds__(kEoThreads, WF_EO_MINB) k_dslash4(const EoArgs
     }
   }
   if (A.norm2) {
+    // |out|^2 per right-hand side: a segmented sum over the warp's lanes. A (site, source) pair
+    // holds T/2 consecutive threads, so with T/2 not a multiple of 32 a warp straddles several
+    // pairs; each pair's lanes are contiguous and its last lane adds the pair's sum (one atomic per
+    // pair and warp instead of one per thread)
+    const int lane = threadIdx.x & 31;
+    const int key = active ? (int)sline : -1;
     double dn = (double)nrm;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, off);
-    // a warp may straddle two right-hand sides only if T/2 * L^3 is not a multiple of 32
-    const int rhs0 = __shfl_sync(0xffffffffu, rhs, 0);
-    const bool uniform = __all_sync(0xffffffffu, rhs == rhs0 || !active);
-    if (uniform) {
-      if ((threadIdx.x & 31) == 0 && active) atomicAdd(A.norm2 + rhs0, dn);
-    } else if (active) {
-      atomicAdd(A.norm2 + rhs, (double)nrm);
+    for (int off = 1; off < 32; off <<= 1) {
+      const double v = __shfl_up_sync(0xffffffffu, dn, off);
+      const int kv = __shfl_up_sync(0xffffffffu, key, off);
+      if (lane >= off && kv == key) dn += v;
     }
+    const int knext = __shfl_down_sync(0xffffffffu, key, 1);
+    if (active && (lane == 31 || knext != key)) atomicAdd(A.norm2 + rhs, dn);
   }
 }
 

@@ -68,6 +68,13 @@ enum LineKind { LK_GENERIC = 0, LK_SCHUR_A = 1, LK_SCHUR_B = 2, LK_SCHUR_C = 3 }
 template <typename R>
 void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s);
 
+// one launch (or one per kMaxLattices) over a ragged batch of lattices, each with its own
+// arguments: K-a on the line kernel, K-b / K-c on the one-thread-per-site kernel (tables attached)
+template <typename R>
+void launch_line_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s);
+template <typename R>
+void launch_line_wide_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s);
+
 // axial-frame line kernels with one thread per time site (wf_wide.cu), same arguments
 bool wide_supported(const Geom& g);
 template <typename R>
@@ -133,15 +140,19 @@ void launch_d2f(const Cx<double>* in, Cx<float>* out, size_t n, cudaStream_t s);
 void launch_d2f_links(const Cx<double>* in, Cx<float>* out, size_t nlinks, int tp, cudaStream_t s);
 void launch_f2d(const Cx<float>* in, Cx<double>* out, size_t n, cudaStream_t s);
 
-// BLAS-1 on flat [nrhs][n] arrays; scalars live in device memory
+// BLAS-1 on flat [nrhs][n] arrays; scalars live in device memory. offs (ragged batches of several
+// lattices): device prefix table [nrhs + 1] of each rhs's first element in the packed vectors, n
+// then only sizes the grid (the largest length); null: rhs k occupies [k n, (k + 1) n).
 template <typename R>
-void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s);
+void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s,
+                  const size_t* offs = nullptr);
 template <typename R>
 void launch_cg_xr(Cx<R>* x, Cx<R>* r, const Cx<R>* p, const Cx<R>* q, size_t n, int nrhs, const double* gamma,
-                  const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s);
+                  const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s,
+                  const size_t* offs = nullptr);
 template <typename R>
 void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* gamma_new, const double* gamma_old,
-                 const int* active, cudaStream_t s);
+                 const int* active, cudaStream_t s, const size_t* offs = nullptr);
 template <typename R>
 void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s);      // y += x

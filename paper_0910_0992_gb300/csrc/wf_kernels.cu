@@ -13,7 +13,9 @@
 // them at run time.
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "wf_internal.h"
 #include "wf_line.cuh"
@@ -66,15 +68,16 @@ struct LineMinBlocks {
   static constexpr int value = sizeof(R) == 4 ? WF_LINE_MINB : WF_LINE_MINB_F64;
 };
 
+// The kernel body for block blk of a launch over one lattice (see k_line and k_line_multi).
 template <typename R, bool AX, int SRC, int OPU, int OPL, bool H = false>
-__global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(const LineArgs<R> A) {
+__device__ __forceinline__ void line_body(const LineArgs<R>& A, int blk) {
   static_assert(!H || SRC == SRC_LOAD, "FP16 storage: the line kernel loads its own site only");
   const Geom& g = A.g;
   const int src = SRC >= 0 ? SRC : A.src;
   const int opu = OPU >= 0 ? OPU : A.opu;
   const int opl = OPL >= 0 ? OPL : A.opl;
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = (blk * (int)blockDim.x + (int)threadIdx.x) >> 5;
   const int lg_raw = warp * g.lpw + lane / g.lpl;
   const bool active = lg_raw < A.nrhs * g.Nl;
   const int lg = active ? lg_raw : 0;  // idle lanes still join the warp shuffles
@@ -147,6 +150,19 @@ __global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(
     }
     if (active && jj == 0) atomicAdd(A.norm2 + rhs, dn);
   }
+}
+
+template <typename R, bool AX, int SRC, int OPU, int OPL, bool H = false>
+__global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line(const LineArgs<R> A) {
+  line_body<R, AX, SRC, OPU, OPL, H>(A, blockIdx.x);
+}
+
+// one launch over a ragged batch of lattices (MultiLineArgs, wf_line.cuh)
+template <typename R, bool AX, int SRC, int OPU, int OPL>
+__global__ void __launch_bounds__(kLineThreads, LineMinBlocks<R>::value) k_line_multi(const MultiLineArgs<R> M) {
+  int k = 0;
+  while (k + 1 < M.n && (int)blockIdx.x >= M.blk0[k + 1]) ++k;
+  line_body<R, AX, SRC, OPU, OPL>(M.a[k], (int)blockIdx.x - M.blk0[k]);
 }
 
 template <typename R>
@@ -267,6 +283,31 @@ void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
   }
   launch_line_impl<R>(a, kind, axial, s);
 }
+// K-a (LK_SCHUR_A, axial frame) over a ragged batch of lattices, in launches of up to
+// kMaxLattices lattices
+template <typename R>
+void launch_line_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s) {
+  if (kind != LK_SCHUR_A) throw Error(1, "multi-lattice line kernel: K-a only");
+  for (size_t first = 0; first < as.size(); first += kMaxLattices) {
+    MultiLineArgs<R> M;
+    std::memset(&M, 0, sizeof(M));
+    M.n = (int)std::min<size_t>(kMaxLattices, as.size() - first);
+    int blocks = 0;
+    for (int k = 0; k < M.n; ++k) {
+      const LineArgs<R>& a = as[first + k];
+      if (a.g.n < 1 || a.g.n > NMAX || a.h16) throw Error(1, "multi-lattice line kernel: unsupported layout");
+      M.a[k] = a;
+      M.blk0[k] = blocks;
+      blocks += line_blocks(a);
+    }
+    M.blk0[M.n] = blocks;
+    if (blocks == 0) continue;
+    k_line_multi<R, true, SRC_LOAD, OP_FWD, OP_SKIP><<<blocks, kLineThreads, 0, s>>>(M);
+    WF_CUDA(cudaGetLastError());
+  }
+}
+template void launch_line_multi<float>(const std::vector<LineArgs<float>>&, int, cudaStream_t);
+
 template void launch_line<float>(const LineArgs<float>&, int, bool, cudaStream_t);
 template void launch_line<double>(const LineArgs<double>&, int, bool, cudaStream_t);
 

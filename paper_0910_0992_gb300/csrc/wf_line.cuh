@@ -85,6 +85,16 @@ struct LineArgs {
   const int* active;
 };
 
+// Arguments of one launch over a ragged batch of lattices (kMaxLattices at most per launch): the
+// per-lattice arguments and the first block of each lattice (blk0[n] = total blocks).
+constexpr int kMaxLattices = 8;
+template <typename R>
+struct MultiLineArgs {
+  int n;
+  int blk0[kMaxLattices + 1];
+  LineArgs<R> a[kMaxLattices];
+};
+
 // Order in which the line kernels visit (rhs, line) pairs. Right-hand sides are processed in
 // groups of kRhsGroup; within a group every line is visited for all of the group's
 // right-hand sides side by side, so the line's links are shared through L2 (measured: groups

@@ -9,5 +9,6 @@ bool wide_supported(const Geom& g) {
 }
 
 template void launch_line_wide<float>(const LineArgs<float>&, int, cudaStream_t);
+template void launch_line_wide_multi<float>(const std::vector<LineArgs<float>>&, int, cudaStream_t);
 
 }  // namespace wf

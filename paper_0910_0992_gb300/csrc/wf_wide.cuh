@@ -24,7 +24,10 @@
 // results are those of k_line.
 #pragma once
 
+#include <algorithm>
+#include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "wf_internal.h"
 #include "wf_line.cuh"
@@ -358,9 +361,10 @@ __device__ __forceinline__ void line_norm_whole_warps(double* nrm_s, R nrm, int 
 // SRC, OPU, OPL < 0: taken from the arguments at run time. TPC: the line length tp as a
 // compile-time constant (128: n = 4 sites per group, 32 lanes, so that every load's component
 // offset is an immediate), or 0 to read the layout at run time.
+// The kernel body, for block blk of the launch over one lattice (the single-lattice kernel passes
+// blockIdx.x; the multi-lattice kernel the block's index within its lattice).
 template <typename R, int SRC, int OPU, int OPL, int TPC, bool H = false>
-__global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
-    k_line_wide(const LineArgs<R> A) {
+__device__ __forceinline__ void line_wide_body(const LineArgs<R>& A, int blk) {
   __shared__ double nrm_s[kWideCta];
   const Geom& g = A.g;
   const int src = SRC >= 0 ? SRC : A.src;
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
   const int j = q % lpl;          // = sl % lpl for members (tp and 32 are multiples of lpl)
   const int t = n * j + m;
   const int q0 = li * tp + j;     // the CTA thread holding site 0 of this thread's group
-  const int lg_raw = blockIdx.x * LPC + li;
+  const int lg_raw = blk * LPC + li;
   const bool line_ok = member && lg_raw < A.nrhs * g.Nl;
   int rhs, l;
   if (A.order) {
@@ -532,7 +536,59 @@ __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && O
   }
 }
 
+template <typename R, int SRC, int OPU, int OPL, int TPC, bool H = false>
+__global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
+    k_line_wide(const LineArgs<R> A) {
+  line_wide_body<R, SRC, OPU, OPL, TPC, H>(A, blockIdx.x);
+}
+
+// One launch over several lattices (a ragged batch): block b belongs to the lattice k with
+// M.blk0[k] <= b < M.blk0[k + 1] and runs that lattice's arguments; 128-slot lines take the
+// compiled-length body, the others the run-time one.
+template <typename R, int SRC, int OPU, int OPL>
+__global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
+    k_line_wide_multi(const MultiLineArgs<R> M) {
+  int k = 0;
+  while (k + 1 < M.n && (int)blockIdx.x >= M.blk0[k + 1]) ++k;
+  const LineArgs<R>& A = M.a[k];
+  const int blk = (int)blockIdx.x - M.blk0[k];
+  if (A.g.tp == 128 && A.g.n == 4 && A.g.lpl == 32)
+    line_wide_body<R, SRC, OPU, OPL, 128>(A, blk);
+  else
+    line_wide_body<R, SRC, OPU, OPL, 0>(A, blk);
+}
+
 }  // namespace wide
+
+// K-b or K-c (LK_SCHUR_B / LK_SCHUR_C) over a ragged batch of lattices, each with its own
+// arguments (traversal and neighbour tables attached), in launches of up to kMaxLattices lattices
+template <typename R>
+void launch_line_wide_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s) {
+  for (size_t first = 0; first < as.size(); first += kMaxLattices) {
+    MultiLineArgs<R> M;
+    std::memset(&M, 0, sizeof(M));
+    M.n = (int)std::min<size_t>(kMaxLattices, as.size() - first);
+    int blocks = 0;
+    for (int k = 0; k < M.n; ++k) {
+      const LineArgs<R>& a = as[first + k];
+      if (!wide_supported(a.g) || a.h16 || !a.order || !a.nbr)
+        throw Error(1, "multi-lattice wide kernel: supported layouts, FP32 storage, traversal tables");
+      M.a[k] = a;
+      M.blk0[k] = blocks;
+      const int LPC = wide::kWideCta / a.g.tp;
+      blocks += (a.nrhs * a.g.Nl + LPC - 1) / LPC;
+    }
+    M.blk0[M.n] = blocks;
+    if (blocks == 0) continue;
+    if (kind == LK_SCHUR_B)
+      wide::k_line_wide_multi<R, SRC_HOP, OP_FWD, OP_BWD><<<blocks, wide::kWideCta, 0, s>>>(M);
+    else if (kind == LK_SCHUR_C)
+      wide::k_line_wide_multi<R, SRC_HOP, OP_COPY, OP_BWD><<<blocks, wide::kWideCta, 0, s>>>(M);
+    else
+      throw Error(1, "multi-lattice wide kernel: K-b or K-c only");
+    WF_CUDA(cudaGetLastError());
+  }
+}
 
 // launch of the kernel variant for `kind` (LineKind) over all lines of all right-hand sides;
 // instantiated for float in wf_wide.cu and for double-float in wf_wide_df.cu
