@@ -83,7 +83,8 @@ def paper_flops_per_apply(L, T):
 # the sources that compile, launch or lay out the data of the Schur operator's kernels: a change
 # to any of them voids the DRAM traffic recorded in profiles/traffic.json
 HOP_KERNEL_SOURCES = ("wf_abi.cu", "wf_async.cuh", "wf_common.cuh", "wf_df64.cuh", "wf_handle.h", "wf_internal.h",
-                      "wf_kernels.cu", "wf_layout.cu", "wf_line.cuh", "wf_pipe.cu", "wf_wide.cu", "wf_wide.cuh")
+                      "wf_kernels.cu", "wf_layout.cu", "wf_line.cuh", "wf_pipe.cu", "wf_wide.cu", "wf_wide.cuh",
+                      "wf_wide_body.inc")
 
 
 def source_hash():
@@ -317,10 +318,13 @@ def run_ours(args, prm, U, eta):
     odd_sites = prm["L"] ** 3 * prm["T"] // 2
     launched_f32 = prof.get("schur_c_hop_tinv_axpy_f32", (0, 0))[0]
     applies_f64 = prof.get("schur_c_hop_tinv_axpy_f64", (0, 0))[0]
-    # applies that did work: two per CG iteration, the initial A^dag r, and one completion per
-    # reliable update (= FP64 apply); the rest are block overshoot, whose kernels return at once
-    # because every source had stopped
-    applies_f32 = min(launched_f32, 2 * max(iters) + 1 + applies_f64) if prec == wf.WF_FP32 else launched_f32
+    # applies that did work: two per CG iteration plus the initial A^dag r of every CG run (one per
+    # defect-correction pass, counted by the passes' S_L hops; with reliable updates one run plus a
+    # completion per update, an FP64 apply each); the rest are block overshoot, whose kernels
+    # return at once because every source had stopped
+    passes = prof.get("prep_hop_f32", (0, 0))[0]
+    extra = passes if passes else 1 + applies_f64
+    applies_f32 = min(launched_f32, 2 * max(iters) + extra) if prec == wf.WF_FP32 else launched_f32
     # every M-hat launch sequence works on all nsrc sources at once; per solve
     solve_bytes = applies_f32 * apply_bytes(odd_sites, nsrc) + applies_f64 * apply_bytes(odd_sites, nsrc, 2)
     value = reps.whole_job_rate(args.steps * solve_bytes, ms * 1e-3) / 1e9
@@ -619,25 +623,60 @@ def run_sweep(args):
             r["hop_kernels_autotuned"] = _hop_config(wf, w, eta.shape[0])
             r["iteration_ratio"] = r["eo4d"]["iterations"] / r["temporal_schur"]["iterations"]
             rows.append(r)
-        # the three lattices of this xi in one ragged call (each on its own stream and host thread)
-        hs = [k[0].h for k in keep]
-        rl, xl, nl = [k[1] for k in keep], [k[2] for k in keep], [k[1].shape[0] for k in keep]
+        # the three lattices of this xi in one ragged call
         seq = sum(rr["temporal_schur"]["time_s"] for rr in rows[-3:])
-        wf.wf_solve_many(hs, rl, xl, nl, args.tol, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(3):
-            st, per = wf.wf_solve_many(hs, rl, xl, nl, args.tol, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)
-        torch.cuda.synchronize()
-        t_many = (time.perf_counter() - t0) / 3
-        if st != wf.WF_OK or max(max(q[2]) for q in per) > args.tol:
-            raise RuntimeError(f"ragged solve failed: status {st}")
-        batches.append({"xi": xi, "lattices": [f"{k[0].L}^3x{k[0].T}" for k in keep],
-                        "one_call_s": t_many, "one_at_a_time_s": seq, "speedup": seq / t_many})
+        batches.append(dict(xi=xi, **_ragged_times(wf, torch, keep, args.tol, seq)))
         for k in keep:
             k[0].close()
+
+    # a ragged batch of small lattices (xi = 3.5, two Gaussian sources each), where single
+    # solves do not fill the GPU
+    xi = 3.5
+    ks = 0.9 * S.kappa_critical_free(xi)
+    keep, seq = [], 0.0
+    for i, (L, T) in enumerate(((8, 16), (8, 24), (8, 32), (8, 48), (6, 64), (6, 96), (10, 40), (12, 24))):
+        U = S.random_gauge(L, T, 0.25, 300 + i)
+        eta = S.gaussian_source(L, T, 400 + i, nrhs=2)
+        stream = torch.cuda.Stream()
+        w = wf.Wilson(L, T, ks, kappa_t=xi * ks, bc=-1)
+        w.set_stream(stream.cuda_stream)
+        w.load_gauge(U)
+        rhs = torch.from_numpy(eta).cuda()
+        x = torch.empty_like(rhs)
+        keep.append((w, rhs, x, stream))
+        seq += _timed_solve(wf, torch, w, stream, rhs, x, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32, args.tol, reps=3)[0]
+    batches.append(dict(xi=xi, **_ragged_times(wf, torch, keep, args.tol, seq)))
+    for k in keep:
+        k[0].close()
     print(json.dumps({"mode": "sweep", "tol": args.tol, "results": rows, "ragged_calls": batches}))
     return 0
+
+
+def _ragged_times(wf, torch, keep, tol, seq):
+    """wf_solve_many over the handles in keep: the joint solve (one launch per kernel and iteration
+    across lattices) and the per-lattice path (WF_JOINT=0: a host thread and stream per lattice),
+    each the mean of three calls after a warm-up, against seq, the one-at-a-time total."""
+    hs = [k[0].h for k in keep]
+    rl, xl, nl = [k[1] for k in keep], [k[2] for k in keep], [k[1].shape[0] for k in keep]
+    out = {"lattices": [f"{k[0].L}^3x{k[0].T}" for k in keep], "sources_per_lattice": nl}
+    for key, joint in (("one_call_s", "1"), ("concurrent_streams_s", "0")):
+        os.environ["WF_JOINT"] = joint
+        try:
+            wf.wf_solve_many(hs, rl, xl, nl, tol, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                st, per = wf.wf_solve_many(hs, rl, xl, nl, tol, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)
+            torch.cuda.synchronize()
+        finally:
+            os.environ.pop("WF_JOINT", None)
+        if st != wf.WF_OK or max(max(q[2]) for q in per) > tol:
+            raise RuntimeError(f"ragged solve failed: status {st}")
+        out[key] = (time.perf_counter() - t0) / 3
+    out["one_at_a_time_s"] = seq
+    out["speedup"] = seq / out["one_call_s"]
+    out["speedup_concurrent_streams"] = seq / out["concurrent_streams_s"]
+    return out
 
 
 def run_force(args):

@@ -152,11 +152,17 @@ int wf_apply_schur_f16(wf_handle_t* h, const double* in_odd, double* out_odd, in
  * when the FP64 true residual ||rhs - M x||_2 / ||rhs||_2 <= tol, computed with the full M.
  * iters_out[k] (CG iterations) and true_resid_out[k] are written for every right-hand side
  * (host arrays of nrhs entries; either may be null). flags: WF_X0 to start from x.
- * 1 <= nrhs <= WF_MAX_SOLVE_RHS (else WF_EINVAL). WF_FP32: the residual is recomputed in FP64 whenever the FP32 one fell by 1e-5 (environment
- * WF_RELIABLE_DELTA); CG iterations run in blocks whose convergence checks happen on the device,
- * one iteration replayed as a CUDA graph when the handle has a stream of its own (environment
- * WF_GRAPH=0: plain launches). The first FP32 solve or apply for a given nrhs also tunes the
- * Schur operator's kernels (see wf_hop_config).
+ * 1 <= nrhs <= WF_MAX_SOLVE_RHS (else WF_EINVAL).
+ * WF_FP32 with WF_TEMPORAL_SCHUR: defect correction. Each pass solves M d = r entirely in FP32
+ * (S_L, CGNR on M-hat, S_R) to a 1e-5 reduction of its residual (environment WF_DC_RHO), adds d
+ * to the FP64 solution and recomputes the FP64 true residual r = rhs - M x; two passes reach
+ * 1e-10 on the benchmark lattices. Environment WF_DC=0 selects the scheme of the other methods.
+ * WF_FP32 with the other methods: FP32 CG iterations whose residual is recomputed in FP64
+ * whenever it fell by 1e-5 (reliable updates; environment WF_RELIABLE_DELTA).
+ * CG iterations run in blocks whose convergence checks happen on the device, one iteration
+ * replayed as a CUDA graph when the handle has a stream of its own (environment WF_GRAPH=0: plain
+ * launches). The first FP32 solve or apply for a given nrhs also tunes the Schur operator's
+ * kernels (see wf_hop_config).
  * Returns WF_ENOCONV (outputs written: the last iterate) if some right-hand side missed tol
  * within the handle's iteration limit (wf_set_max_iterations), WF_ENAN if a norm became NaN or
  * Inf (a NaN or Inf in rhs or x0 ends the solve this way). */
@@ -167,18 +173,18 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
  * anisotropy): handle hs[i] (one lattice each, possibly of different sizes; the handles must be
  * distinct) solves nrhs[i] sources rhs[i] into x[i], with the arguments and conventions of wf_solve
  * (tol, method, precision and flags common to all).
- *   - Joint path: FP32 temporal + Schur solves (WF_TEMPORAL_SCHUR, WF_FP32) on handles of one
- *     device, in the axial frame, with one iteration limit, no clover term and at most
- *     WF_MAX_SOLVE_RHS sources in all are solved as one
- *     CGNR over the concatenation of all lattices' sources. Each of its kernels (K-a, K-b, K-c, the
- *     vector updates, norms and convergence checks) runs as one launch over every lattice (eight
- *     lattices per launch at most); the S_L preparation, the reconstruction, the FP64 reliable
- *     updates and the FP64 true residual run per lattice, each on its handle's stream, so that
- *     they overlap. K-b and K-c take each lattice's autotuned configuration (tuned in the call for
- *     a handle with none for its nrhs): lattices on the one-thread-per-site kernels share one
- *     launch, the others launch their own. Every source keeps its own CG scalars, stopping test
- *     and reliable updates, so it takes the iterations of a separate solve (up to the rounding of
- *     its norms). The call first synchronises every handle's stream; the iterations run on hs[0]'s
+ *   - Joint path: FP32 temporal + Schur solves (WF_TEMPORAL_SCHUR, WF_FP32, defect correction)
+ *     on handles of one device, in the axial frame, with one iteration limit, no clover term and
+ *     at most WF_MAX_SOLVE_RHS sources in all are solved as one
+ *     CGNR per defect-correction pass over the concatenation of all lattices' sources. Each of its
+ *     kernels (K-a, K-b, K-c, the vector updates, norms and convergence checks) runs as one launch
+ *     over every lattice (eight lattices per launch at most); the S_L preparation, the
+ *     reconstruction and the FP64 true residual run per lattice, each on its handle's stream, so
+ *     that they overlap. K-b and K-c take each lattice's autotuned configuration (tuned in the
+ *     call for a handle with none for its nrhs): lattices on the one-thread-per-site kernels share
+ *     one launch (128-slot lines and the others apart), the others launch their own. Every source
+ *     keeps its own CG scalars and stopping test, so it takes the iterations of a separate solve
+ *     (up to the rounding of its norms). The call first synchronises every handle's stream; the iterations run on hs[0]'s
  *     stream; a handle on the default stream, or on a stream another handle uses, works on a
  *     temporary stream. An error is reported on every handle and as every status.
  *   - Otherwise (or with environment WF_JOINT=0) every solve runs on a host thread of its own and

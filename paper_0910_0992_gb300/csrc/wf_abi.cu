@@ -1085,14 +1085,31 @@ std::vector<int> cgnr_h16(wf_handle* h, int nrhs, size_t n, const Cx<double>* b,
 
 // Temporal + 3-D Schur solve (§II.B): prepare with S_L, CGNR on M-hat, reconstruct with S_R,
 // verify with the FP64 true residual of M.
-int solve_temporal_schur_dc(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
-                            bool x0, int* iters_out, double* resid_out);
+void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<const Cx<double>*>& eta_lex,
+                             const std::vector<Cx<double>*>& x_lex, const int* nrhs, double tol, bool x0,
+                             std::vector<std::vector<int>>& iters, std::vector<std::vector<double>>& rel,
+                             std::vector<int>& status);
+
+// FP32 temporal + Schur solves take defect correction (solve_temporal_schur_dc) unless the
+// environment sets WF_DC=0, which selects FP32 iterations with FP64 reliable updates
+bool use_defect_correction() {
+  const char* e = std::getenv("WF_DC");
+  return !(e && e[0] == '0');
+}
 
 int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
                          int precision, bool x0, int* iters_out, double* resid_out) {
-  if (precision == WF_FP32) {
-    const char* e = std::getenv("WF_DC");
-    if (e && e[0] == '1') return solve_temporal_schur_dc(h, eta_lex, x_lex, nrhs, tol, x0, iters_out, resid_out);
+  if (precision == WF_FP32 && use_defect_correction()) {
+    std::vector<std::vector<int>> it(1);
+    std::vector<std::vector<double>> res(1);
+    std::vector<int> st(1);
+    wf_handle* const hs[1] = {h};
+    solve_temporal_schur_dc(1, hs, {eta_lex}, {x_lex}, &nrhs, tol, x0, it, res, st);
+    for (int k = 0; k < nrhs; ++k) {
+      if (iters_out) iters_out[k] = it[0][k];
+      if (resid_out) resid_out[k] = res[0][k];
+    }
+    return st[0];
   }
   const size_t n = h->half_int();
   const size_t nt = n * nrhs;
@@ -1189,136 +1206,6 @@ int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_
     if (ok || status == WF_ENOCONV) break;
     if (pass == 5) status = WF_ENOCONV;
   }
-  { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
-  for (int k = 0; k < nrhs; ++k) {
-    if (iters_out) iters_out[k] = iters[k];
-    if (resid_out) resid_out[k] = rel[k];
-  }
-  return status;
-}
-
-// Temporal + 3-D Schur solve by defect correction, all operator work in FP32: each pass solves
-// M delta = r with the method's own steps in FP32 (S_L, CGNR on M-hat without FP64 reliable
-// updates, S_R) to a relative reduction rho of its Schur residual (at most down to what tol
-// needs), adds delta to the FP64 solution psi and recomputes the true residual r = eta - M psi in
-// FP64; it stops when ||r|| / ||eta|| <= tol for every source. The only FP64 operator apply per
-// pass is the true residual's, which the solve computes anyway. Environment WF_DC_RHO sets rho
-// (default 1e-5).
-int solve_temporal_schur_dc(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
-                            bool x0, int* iters_out, double* resid_out) {
-  const size_t n = h->half_int();
-  const size_t nt = n * nrhs;
-  cudaStream_t s = h->stream;
-  const int tp = h->g.tp;
-  const double igf = 1.0 / h->g.gamma_f;
-  Cx<double>* eta_e = h->buf<Cx<double>>("sv_eta_e", nt);
-  Cx<double>* eta_o = h->buf<Cx<double>>("sv_eta_o", nt);
-  Cx<double>* psi_e = h->buf<Cx<double>>("sv_psi_e", nt);
-  Cx<double>* psi_o = h->buf<Cx<double>>("sv_psi_o", nt);
-  Cx<double>* r_e = h->buf<Cx<double>>("sv_r_e", nt);
-  Cx<double>* r_o = h->buf<Cx<double>>("sv_r_o", nt);
-  Cx<double>* b_o = h->buf<Cx<double>>("sv_b_o", nt);
-  Cx<double>* y_o = h->buf<Cx<double>>("sv_y_o", nt);
-  Cx<float>* r32_e = h->buf<Cx<float>>("dc_r_e", nt);
-  Cx<float>* r32_o = h->buf<Cx<float>>("dc_r_o", nt);
-  Cx<float>* w32_e = h->buf<Cx<float>>("dc_w_e", nt);
-  Cx<float>* w32_o = h->buf<Cx<float>>("dc_w_o", nt);
-  double* sc = h->buf<double>("sv_scalars", 4 * (size_t)nrhs);
-  double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
-  double rho = 1e-5;
-  if (const char* e = std::getenv("WF_DC_RHO")) {
-    const double v = std::atof(e);
-    if (v > 0.0 && v < 1.0) rho = v;
-  }
-
-  { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex, eta_e, eta_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
-  auto norms2 = [&](const Cx<double>* e, const Cx<double>* o) {
-    { Prof P(h, "norm2_f64", 4); launch_norm2<double>(e, n, nrhs, partial, sc, s); launch_norm2<double>(o, n, nrhs, partial, sc + nrhs, s); }
-    std::vector<double> v = read_scalars(h, sc, 2 * nrhs), out(nrhs);
-    for (int k = 0; k < nrhs; ++k) out[k] = v[k] + v[nrhs + k];
-    return out;
-  };
-  const std::vector<double> eta2 = norms2(eta_e, eta_o);
-  if (x0) {
-    { Prof P(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex, psi_e, psi_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
-    m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
-  } else {
-    WF_CUDA(cudaMemsetAsync(psi_e, 0, nt * sizeof(Cx<double>), s));
-    WF_CUDA(cudaMemsetAsync(psi_o, 0, nt * sizeof(Cx<double>), s));
-    WF_CUDA(cudaMemcpyAsync(r_e, eta_e, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
-    WF_CUDA(cudaMemcpyAsync(r_o, eta_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
-  }
-  std::vector<double> r2 = norms2(r_e, r_o);
-  std::vector<int> iters(nrhs, 0);
-  std::vector<double> rel(nrhs);
-  auto relres = [&]() {
-    bool ok = true;
-    for (int k = 0; k < nrhs; ++k) {
-      rel[k] = std::sqrt(r2[k] / (eta2[k] > 0 ? eta2[k] : 1.0));
-      ok = ok && rel[k] <= tol;
-    }
-    return ok;
-  };
-  bool ok = relres();
-  const int maxiter = h->maxiter;
-  int status = WF_OK;
-  const OpFn<float> A = schur_op<float>(h, nrhs);
-  const OpFn<double> A64 = schur_op<double>(h, nrhs);  // not called: no reliable updates, no guess
-  for (int pass = 0; pass < 8 && !ok; ++pass) {
-    // S_L in FP32 on r: w_e = C_R^e C_L^e r_e ; w_o = C_L^o [r_o + gamma_f^-1 D_s^oe w_e]
-    { Prof P(h, "d2f", 2); launch_d2f(r_e, r32_e, nt, s); launch_d2f(r_o, r32_o, nt, s); }
-    line_load<float>(h, 0, r32_e, w32_e, OP_FWD, OP_BWD, nrhs, "prep_tsolve");
-    {
-      LineArgs<float> a = line_args<float>(h, 1, nrhs);
-      a.src_up = w32_e;
-      a.src_lo = w32_e + 6 * tp;
-      a.xpre = r32_o;
-      a.apre = (float)igf;
-      a.opu = OP_COPY;
-      a.opl = OP_BWD;
-      a.src = SRC_HOP;
-      a.out = w32_o;
-      Prof P(h, "prep_hop_f32");
-      launch_line<float>(a, LK_GENERIC, h->axial, s);
-    }
-    WF_CUDA(cudaMemsetAsync(b_o, 0, nt * sizeof(Cx<double>), s));
-    { Prof P(h, "add_f_to_d"); launch_add_f_to_d(b_o, w32_o, nt, s); }
-    // CGNR on M-hat y = w_o to rho ||w_o|| (no further than half of what tol needs; sources
-    // already at tol take no iterations)
-    { Prof P(h, "norm2_f64", 2); launch_norm2<double>(b_o, n, nrhs, partial, sc, s); }
-    const std::vector<double> b2 = read_scalars(h, sc, nrhs);
-    std::vector<double> target(nrhs);
-    for (int k = 0; k < nrhs; ++k)
-      target[k] = rel[k] <= tol ? 2.0 * std::sqrt(b2[k]) + 1.0
-                                : std::max(rho * std::sqrt(b2[k]), 0.5 * tol * std::sqrt(eta2[k]) / (h->g.mu + 1.0));
-    const std::vector<int> it = cgnr<float>(h, A, A64, b_o, y_o, nrhs, n, target, maxiter, false, 0, nullptr, false);
-    for (int k = 0; k < nrhs; ++k) iters[k] += it[k];
-    // S_R in FP32: d_o = C_R^o y_o ; d_e = C_R^e C_L^e [r_e + gamma_f^-1 D_s^eo d_o] ; psi += d
-    { Prof P(h, "d2f"); launch_d2f(y_o, w32_e, nt, s); }  // y_o in FP32 (w_e is free again)
-    line_load<float>(h, 1, w32_e, w32_o, OP_FWD, OP_COPY, nrhs, "recon_tsolve");
-    {
-      LineArgs<float> a = line_args<float>(h, 0, nrhs);
-      a.src_up = w32_o;
-      a.src_lo = w32_o + 6 * tp;
-      a.xpre = r32_e;
-      a.apre = (float)igf;
-      a.opu = OP_FWD;
-      a.opl = OP_BWD;
-      a.src = SRC_HOP;
-      a.out = w32_e;
-      Prof P(h, "recon_hop_f32");
-      launch_line<float>(a, LK_GENERIC, h->axial, s);
-    }
-    { Prof P(h, "add_f_to_d", 2); launch_add_f_to_d(psi_e, w32_e, nt, s); launch_add_f_to_d(psi_o, w32_o, nt, s); }
-    // true residual in FP64
-    m_apply<double>(h, psi_e, psi_o, r_e, r_o, eta_e, eta_o, -1.0, nrhs);
-    r2 = norms2(r_e, r_o);
-    ok = relres();
-    bool capped = false;
-    for (int k = 0; k < nrhs; ++k) capped = capped || iters[k] >= maxiter;
-    if (capped) break;
-  }
-  if (!ok) status = WF_ENOCONV;
   { Prof P(h, "export_spinor_f64"); launch_export_spinor<double>(h->g, psi_e, psi_o, x_lex, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s); }
   for (int k = 0; k < nrhs; ++k) {
     if (iters_out) iters_out[k] = iters[k];
@@ -1488,39 +1375,20 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
   };
 }
 
-// M-hat of every lattice in FP64 (the reliable updates): each lattice on its own stream, fenced
-// against the joint stream
-OpFn<double> joint_schur_op64(const std::vector<JointPart>& parts, const JointSync& sync) {
-  std::vector<std::pair<Cx<double>*, Cx<double>*>> work;
-  for (const JointPart& q : parts)
-    work.emplace_back(q.h->buf<Cx<double>>(pname<double>("op_ty"), q.n * q.nrhs),
-                      q.h->buf<Cx<double>>(pname<double>("op_tz"), q.n * q.nrhs));
-  const JointSync* sp = &sync;
-  return [=](const Cx<double>* x, Cx<double>* y, int dagger, double* norm2) {
-    const int* act = parts[0].h->op_active;
-    sp->fan_out(parts);
-    for (size_t j = 0; j < parts.size(); ++j) {
-      const JointPart& q = parts[j];
-      const int* keep = q.h->op_active;
-      q.h->op_active = act ? act + q.r0 : nullptr;
-      schur_apply<double>(q.h, x + q.off, y + q.off, dagger, q.nrhs, work[j].first, work[j].second,
-                          norm2 ? norm2 + q.r0 : nullptr);
-      q.h->op_active = keep;
-    }
-    sp->fan_in(parts);
-  };
-}
-
-// The temporal + Schur solves of several lattices as one CGNR over the concatenation of their
-// odd fields. The FP64 steps -- S_L preparation, reconstruction, true residual, reliable updates
-// and export -- run per lattice, each on its handle's stream so that they overlap; the iterations
-// run on hs[0]'s stream, where every kernel of an iteration covers all lattices' sources. Each
-// source keeps its own CG scalars, stopping test and reliable updates, as in a separate solve. The
-// handles' streams are distinct (the caller sees to it).
-void solve_temporal_schur_joint(int nl, wf_handle* const* hs, const std::vector<const Cx<double>*>& eta_lex,
-                                const std::vector<Cx<double>*>& x_lex, const int* nrhs, double tol, bool x0,
-                                std::vector<std::vector<int>>& iters, std::vector<std::vector<double>>& rel,
-                                std::vector<int>& status) {
+// Temporal + 3-D Schur solve in FP32 by defect correction, for one lattice or jointly for several
+// (wf_solve_many). Each pass solves M delta = r with the method's steps in FP32 -- S_L, CGNR on
+// M-hat without reliable updates, S_R -- to a reduction rho of its Schur residual (no further
+// than what tol needs), adds delta to the FP64 solution psi and recomputes the true residual
+// r = eta - M psi in FP64, the residual the solve reports; it stops when ||r|| / ||eta|| <= tol for
+// every source. The only FP64 operator apply of a pass is that true residual. With several
+// lattices the CGNR runs over the concatenation of their odd fields (joint_schur_op) on hs[0]'s
+// stream, the other steps per lattice on each handle's stream (distinct streams), so that they
+// overlap; every source keeps its own CG scalars and stopping test. Environment WF_DC_RHO sets rho
+// (default 1e-5).
+void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<const Cx<double>*>& eta_lex,
+                             const std::vector<Cx<double>*>& x_lex, const int* nrhs, double tol, bool x0,
+                             std::vector<std::vector<int>>& iters, std::vector<std::vector<double>>& rel,
+                             std::vector<int>& status) {
   wf_handle* h0 = hs[0];
   cudaStream_t s = h0->stream;
   std::vector<JointPart> parts(nl);
@@ -1532,164 +1400,198 @@ void solve_temporal_schur_joint(int nl, wf_handle* const* hs, const std::vector<
     nmax = std::max(nmax, parts[j].n);
     nr += nrhs[j];
   }
+  const bool joint = nl > 1;
   const JointSync sync(parts.size());
-  // the solver's vectors, scratch fields of the operator, the first element of every source
-  Cx<double>* b = h0->buf<Cx<double>>("jv_b", ntot);
-  Cx<double>* y = h0->buf<Cx<double>>("jv_y", ntot);
-  Cx<float>* ty = h0->buf<Cx<float>>("jv_ty_f32", ntot);
-  Cx<float>* tz = h0->buf<Cx<float>>("jv_tz_f32", ntot);
-  Cx<float>* tw = h0->buf<Cx<float>>("jv_tw_f32", ntot);
-  size_t* offs = h0->buf<size_t>("jv_offs", (size_t)nr + 1);
-  {
+  double rho = 1e-5;
+  if (const char* e = std::getenv("WF_DC_RHO")) {
+    const double v = std::atof(e);
+    if (v > 0.0 && v < 1.0) rho = v;
+  }
+  // the solver's vectors (FP64 right-hand side and solution of the Schur system), the operator's
+  // scratch fields and the first element of every source (several lattices)
+  Cx<double>* b = h0->buf<Cx<double>>("sv_b_o", ntot);
+  Cx<double>* y = h0->buf<Cx<double>>("sv_y_o", ntot);
+  Cx<float>* ty = nullptr;
+  Cx<float>* tz = nullptr;
+  Cx<float>* tw = nullptr;
+  size_t* offs = nullptr;
+  if (joint) {
+    ty = h0->buf<Cx<float>>("jv_ty_f32", ntot);
+    tz = h0->buf<Cx<float>>("jv_tz_f32", ntot);
+    tw = h0->buf<Cx<float>>("jv_tw_f32", ntot);
+    offs = h0->buf<size_t>("jv_offs", (size_t)nr + 1);
     std::vector<size_t> o;
     for (const JointPart& q : parts)
       for (int k = 0; k < q.nrhs; ++k) o.push_back(q.off + (size_t)k * q.n);
     o.push_back(ntot);
     WF_CUDA(cudaMemcpyAsync(offs, o.data(), o.size() * sizeof(size_t), cudaMemcpyHostToDevice, s));
-    // o is a host temporary; the lattices' streams also write into b and y (zeroed on s)
-    WF_CUDA(cudaStreamSynchronize(s));
   }
-  // double-float FP64 steps where a handle allows them, as in wf_solve's FP32 solves
-  struct DfAll {
-    std::vector<std::pair<wf_handle*, bool>> old;
-    ~DfAll() {
-      for (auto& p : old) p.first->df_ops = p.second;
-    }
-  } dfall;
-  for (const JointPart& q : parts) {
-    dfall.old.emplace_back(q.h, q.h->df_ops);
-    q.h->df_ops = q.h->df_allowed;
-  }
+  // o is a host temporary, and the lattices' streams write b (zeroed on s when allocated)
+  WF_CUDA(cudaStreamSynchronize(s));
 
   struct PerLattice {
-    Cx<double> *eta_e, *eta_o, *a_e, *psi_e, *psi_o, *r_e, *r_o;
+    Cx<double> *eta_e, *eta_o, *psi_e, *psi_o, *r_e, *r_o;
+    Cx<float> *r32_e, *r32_o, *w32_e, *w32_o;
     double* sc;
     double* partial;
     std::vector<double> eta2;
   };
   std::vector<PerLattice> L(nl);
-  std::vector<double> target(nr);
-  // S_L per lattice on its own stream (all launched before any norm is read back)
+  // per lattice on its stream: |v_e|^2 + |v_o|^2 per source, read back after all are launched
+  auto launch_norms = [&](int j, const Cx<double>* ve, const Cx<double>* vo) {
+    wf_handle* h = parts[j].h;
+    const int m = parts[j].nrhs;
+    Prof Q(h, "norm2_f64", vo ? 4 : 2);
+    launch_norm2<double>(ve, parts[j].n, m, L[j].partial, L[j].sc, h->stream);
+    if (vo) launch_norm2<double>(vo, parts[j].n, m, L[j].partial, L[j].sc + m, h->stream);
+  };
+  auto read_norms = [&](int j, bool two) {
+    const int m = parts[j].nrhs;
+    const std::vector<double> v = read_scalars(parts[j].h, L[j].sc, two ? 2 * m : m);
+    std::vector<double> out(m);
+    for (int k = 0; k < m; ++k) out[k] = two ? v[k] + v[m + k] : v[k];
+    return out;
+  };
   for (int j = 0; j < nl; ++j) {
     wf_handle* h = parts[j].h;
     cudaStream_t sj = h->stream;
-    const int m = parts[j].nrhs;
-    const size_t n = parts[j].n, nt = n * m;
+    const size_t nt = parts[j].n * parts[j].nrhs;
     PerLattice& P = L[j];
     P.eta_e = h->buf<Cx<double>>("sv_eta_e", nt);
     P.eta_o = h->buf<Cx<double>>("sv_eta_o", nt);
-    P.a_e = h->buf<Cx<double>>("sv_a_e", nt);
     P.psi_e = h->buf<Cx<double>>("sv_psi_e", nt);
     P.psi_o = h->buf<Cx<double>>("sv_psi_o", nt);
     P.r_e = h->buf<Cx<double>>("sv_r_e", nt);
     P.r_o = h->buf<Cx<double>>("sv_r_o", nt);
-    P.sc = h->buf<double>("sv_scalars", 4 * (size_t)m);
-    P.partial = h->buf<double>("cg_partial", 1024 * (size_t)m);
-    Cx<double>* b_o = b + parts[j].off;
-    { Prof Q(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex[j], P.eta_e, P.eta_o, m, 0, frame_rot(h, 0), frame_rot(h, 1), sj); }
-    // a_e = C_R^e C_L^e eta_e ; b_o = C_L^o [eta_o + gamma_f^-1 D_s^oe a_e]
-    line_load<double>(h, 0, P.eta_e, P.a_e, OP_FWD, OP_BWD, m, "prep_tsolve");
-    {
-      LineArgs<double> a = line_args<double>(h, 1, m);
-      a.src_up = P.a_e;
-      a.src_lo = P.a_e + 6 * h->g.tp;
-      a.xpre = P.eta_o;
-      a.apre = 1.0 / h->g.gamma_f;
-      a.opu = OP_COPY;
-      a.opl = OP_BWD;
-      a.src = SRC_HOP;
-      a.out = b_o;
-      Prof Q(h, "prep_hop_f64");
-      launch_line<double>(a, LK_GENERIC, h->axial, sj);
-    }
-    { Prof Q(h, "norm2_f64", 4); launch_norm2<double>(P.eta_e, n, m, P.partial, P.sc, sj); launch_norm2<double>(P.eta_o, n, m, P.partial, P.sc + m, sj); }
+    P.r32_e = h->buf<Cx<float>>("dc_r_e", nt);
+    P.r32_o = h->buf<Cx<float>>("dc_r_o", nt);
+    P.w32_e = h->buf<Cx<float>>("dc_w_e", nt);
+    P.w32_o = h->buf<Cx<float>>("dc_w_o", nt);
+    P.sc = h->buf<double>("sv_scalars", 4 * (size_t)parts[j].nrhs);
+    P.partial = h->buf<double>("cg_partial", 1024 * (size_t)parts[j].nrhs);
+    { Prof Q(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, eta_lex[j], P.eta_e, P.eta_o, parts[j].nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), sj); }
+    launch_norms(j, P.eta_e, P.eta_o);
+  }
+  for (int j = 0; j < nl; ++j) L[j].eta2 = read_norms(j, true);
+  for (int j = 0; j < nl; ++j) {
+    wf_handle* h = parts[j].h;
+    cudaStream_t sj = h->stream;
+    const size_t nt = parts[j].n * parts[j].nrhs;
+    PerLattice& P = L[j];
     if (x0) {
-      // the odd part of the guess starts y_o, as in the single solve
-      { Prof Q(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex[j], P.r_e, P.psi_o, m, 0, frame_rot(h, 0), frame_rot(h, 1), sj); }
-      WF_CUDA(cudaMemcpyAsync(y + parts[j].off, P.psi_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, sj));
+      { Prof Q(h, "import_spinor_f64"); launch_import_spinor<double>(h->g, x_lex[j], P.psi_e, P.psi_o, parts[j].nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), sj); }
+      m_apply<double>(h, P.psi_e, P.psi_o, P.r_e, P.r_o, P.eta_e, P.eta_o, -1.0, parts[j].nrhs);
+    } else {
+      WF_CUDA(cudaMemsetAsync(P.psi_e, 0, nt * sizeof(Cx<double>), sj));
+      WF_CUDA(cudaMemsetAsync(P.psi_o, 0, nt * sizeof(Cx<double>), sj));
+      WF_CUDA(cudaMemcpyAsync(P.r_e, P.eta_e, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, sj));
+      WF_CUDA(cudaMemcpyAsync(P.r_o, P.eta_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, sj));
     }
+    launch_norms(j, P.r_e, P.r_o);
   }
+  bool all_ok = true;
   for (int j = 0; j < nl; ++j) {
-    const int m = parts[j].nrhs;
-    const std::vector<double> e2 = read_scalars(parts[j].h, L[j].sc, 2 * m);
-    L[j].eta2.resize(m);
-    for (int k = 0; k < m; ++k) {
-      L[j].eta2[k] = e2[k] + e2[m + k];
-      target[parts[j].r0 + k] = tol * std::sqrt(L[j].eta2[k]) / (parts[j].h->g.mu + 1.0);  // as in the single solve
-    }
-  }
-  sync.fan_in(parts);  // b (and y) complete on the joint stream
-
-  const OpFn<float> A = joint_schur_op(parts, ty, tz, tw, nr);
-  const OpFn<double> A64 = joint_schur_op64(parts, sync);
-  const int maxiter = h0->maxiter;
-  std::vector<int> it_all(nr, 0);
-  std::vector<char> ok_l(nl, 0);
-  for (int j = 0; j < nl; ++j) {
+    const std::vector<double> r2 = read_norms(j, true);
     iters[j].assign(parts[j].nrhs, 0);
-    rel[j].assign(parts[j].nrhs, 0.0);
+    rel[j].resize(parts[j].nrhs);
     status[j] = WF_OK;
+    for (int k = 0; k < parts[j].nrhs; ++k) {
+      rel[j][k] = std::sqrt(r2[k] / (L[j].eta2[k] > 0 ? L[j].eta2[k] : 1.0));
+      all_ok = all_ok && rel[j][k] <= tol;
+    }
   }
-  bool have_x0 = x0;
-  for (int pass = 0; pass < 6; ++pass) {
-    const std::vector<int> it = cgnr<float>(h0, A, A64, b, y, nr, nmax, target, maxiter, have_x0, ntot, offs);
-    for (int r = 0; r < nr; ++r) it_all[r] += it[r];
-    have_x0 = true;
-    // S_R and the FP64 true residual per lattice, overlapped on the lattices' streams
-    sync.fan_out(parts);
+  const OpFn<float> A = joint ? joint_schur_op(parts, ty, tz, tw, nr) : schur_op<float>(h0, nrhs[0]);
+  const OpFn<double> A64 = [](const Cx<double>*, Cx<double>*, int, double*) {
+    throw Error(WF_ECUDA, "defect correction: no FP64 operator apply inside the CG");
+  };
+  const int maxiter = h0->maxiter;
+  std::vector<double> target(nr);
+  bool capped = false;
+  for (int pass = 0; pass < 8 && !all_ok && !capped; ++pass) {
+    // S_L in FP32 on r: w_e = C_R^e C_L^e r_e ; w_o = C_L^o [r_o + gamma_f^-1 D_s^oe w_e] -> b (FP64)
     for (int j = 0; j < nl; ++j) {
       wf_handle* h = parts[j].h;
       cudaStream_t sj = h->stream;
       const int m = parts[j].nrhs;
-      const size_t n = parts[j].n;
+      const size_t nt = parts[j].n * m;
       PerLattice& P = L[j];
-      const Cx<double>* y_o = y + parts[j].off;
-      // psi_o = C_R^o y_o ; psi_e = C_R^e C_L^e [eta_e + gamma_f^-1 D_s^eo psi_o]
-      line_load<double>(h, 1, y_o, P.psi_o, OP_FWD, OP_COPY, m, "recon_tsolve");
+      Cx<double>* b_o = b + parts[j].off;
+      { Prof Q(h, "d2f", 2); launch_d2f(P.r_e, P.r32_e, nt, sj); launch_d2f(P.r_o, P.r32_o, nt, sj); }
+      line_load<float>(h, 0, P.r32_e, P.w32_e, OP_FWD, OP_BWD, m, "prep_tsolve");
       {
-        LineArgs<double> a = line_args<double>(h, 0, m);
-        a.src_up = P.psi_o;
-        a.src_lo = P.psi_o + 6 * h->g.tp;
-        a.xpre = P.eta_e;
-        a.apre = 1.0 / h->g.gamma_f;
+        LineArgs<float> a = line_args<float>(h, 1, m);
+        a.src_up = P.w32_e;
+        a.src_lo = P.w32_e + 6 * h->g.tp;
+        a.xpre = P.r32_o;
+        a.apre = (float)(1.0 / h->g.gamma_f);
+        a.opu = OP_COPY;
+        a.opl = OP_BWD;
+        a.src = SRC_HOP;
+        a.out = P.w32_o;
+        Prof Q(h, "prep_hop_f32");
+        launch_line<float>(a, LK_GENERIC, h->axial, sj);
+      }
+      WF_CUDA(cudaMemsetAsync(b_o, 0, nt * sizeof(Cx<double>), sj));
+      { Prof Q(h, "add_f_to_d"); launch_add_f_to_d(b_o, P.w32_o, nt, sj); }
+      launch_norms(j, b_o, nullptr);
+    }
+    // CGNR to rho ||b|| per source, no further than half of what tol needs (sources already at
+    // tol start converged)
+    for (int j = 0; j < nl; ++j) {
+      const std::vector<double> b2 = read_norms(j, false);
+      const double mu1 = parts[j].h->g.mu + 1.0;
+      for (int k = 0; k < parts[j].nrhs; ++k) {
+        const double bn = std::sqrt(b2[k]);
+        target[parts[j].r0 + k] = rel[j][k] <= tol ? 2.0 * bn + 1.0
+                                                   : std::max(rho * bn, 0.5 * tol * std::sqrt(L[j].eta2[k]) / mu1);
+      }
+    }
+    sync.fan_in(parts);
+    const std::vector<int> it =
+        cgnr<float>(h0, A, A64, b, y, nr, nmax, target, maxiter, false, joint ? ntot : 0, offs, false);
+    sync.fan_out(parts);
+    // S_R in FP32: d_o = C_R^o y_o ; d_e = C_R^e C_L^e [r_e + gamma_f^-1 D_s^eo d_o] ; psi += d ;
+    // r = eta - M psi in FP64
+    for (int j = 0; j < nl; ++j) {
+      wf_handle* h = parts[j].h;
+      cudaStream_t sj = h->stream;
+      const int m = parts[j].nrhs;
+      const size_t nt = parts[j].n * m;
+      PerLattice& P = L[j];
+      { Prof Q(h, "d2f"); launch_d2f(y + parts[j].off, P.w32_e, nt, sj); }  // y_o in FP32 (w_e is free)
+      line_load<float>(h, 1, P.w32_e, P.w32_o, OP_FWD, OP_COPY, m, "recon_tsolve");
+      {
+        LineArgs<float> a = line_args<float>(h, 0, m);
+        a.src_up = P.w32_o;
+        a.src_lo = P.w32_o + 6 * h->g.tp;
+        a.xpre = P.r32_e;
+        a.apre = (float)(1.0 / h->g.gamma_f);
         a.opu = OP_FWD;
         a.opl = OP_BWD;
         a.src = SRC_HOP;
-        a.out = P.psi_e;
-        Prof Q(h, "recon_hop_f64");
-        launch_line<double>(a, LK_GENERIC, h->axial, sj);
+        a.out = P.w32_e;
+        Prof Q(h, "recon_hop_f32");
+        launch_line<float>(a, LK_GENERIC, h->axial, sj);
       }
+      { Prof Q(h, "add_f_to_d", 2); launch_add_f_to_d(P.psi_e, P.w32_e, nt, sj); launch_add_f_to_d(P.psi_o, P.w32_o, nt, sj); }
       m_apply<double>(h, P.psi_e, P.psi_o, P.r_e, P.r_o, P.eta_e, P.eta_o, -1.0, m);
-      { Prof Q(h, "norm2_f64", 4); launch_norm2<double>(P.r_e, n, m, P.partial, P.sc, sj); launch_norm2<double>(P.r_o, n, m, P.partial, P.sc + m, sj); }
+      launch_norms(j, P.r_e, P.r_o);
     }
-    bool all_ok = true, capped = false;
+    all_ok = true;
     for (int j = 0; j < nl; ++j) {
-      const int m = parts[j].nrhs;
-      const std::vector<double> r2 = read_scalars(parts[j].h, L[j].sc, 2 * m);
-      bool ok = true;
-      for (int k = 0; k < m; ++k) {
-        const int r = parts[j].r0 + k;
-        rel[j][k] = std::sqrt((r2[k] + r2[m + k]) / (L[j].eta2[k] > 0 ? L[j].eta2[k] : 1.0));
-        iters[j][k] = it_all[r];
-        if (rel[j][k] > tol) {
-          ok = false;
-          target[r] *= 0.5 * tol / rel[j][k];
-        }
-        if (it_all[r] >= maxiter) {
-          status[j] = WF_ENOCONV;
-          capped = true;
-        }
+      const std::vector<double> r2 = read_norms(j, true);
+      for (int k = 0; k < parts[j].nrhs; ++k) {
+        rel[j][k] = std::sqrt(r2[k] / (L[j].eta2[k] > 0 ? L[j].eta2[k] : 1.0));
+        iters[j][k] += it[parts[j].r0 + k];
+        all_ok = all_ok && rel[j][k] <= tol;
+        capped = capped || iters[j][k] >= maxiter;
       }
-      ok_l[j] = ok;
-      all_ok = all_ok && ok;
     }
-    if (all_ok || capped) break;
-    sync.fan_in(parts);  // the next pass's reliable updates read y after this pass's reads
   }
-  for (int j = 0; j < nl; ++j)
-    if (!ok_l[j]) status[j] = WF_ENOCONV;  // tol not reached within six passes or the iteration limit
   for (int j = 0; j < nl; ++j) {
     wf_handle* h = parts[j].h;
+    for (int k = 0; k < parts[j].nrhs; ++k)
+      if (rel[j][k] > tol) status[j] = WF_ENOCONV;  // within eight passes or the iteration limit
     Prof Q(h, "export_spinor_f64");
     launch_export_spinor<double>(h->g, L[j].psi_e, L[j].psi_o, x_lex[j], parts[j].nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream);
   }
@@ -1699,7 +1601,7 @@ void solve_temporal_schur_joint(int nl, wf_handle* const* hs, const std::vector<
 // method in the axial frame, on lattices the one-thread-per-site kernels serve, on one device,
 // with one iteration limit and no clover term (environment WF_JOINT=0: one solve per lattice)
 bool joint_eligible(int n, wf_handle* const* hs, int method, int precision) {
-  if (n < 2 || method != WF_TEMPORAL_SCHUR || precision != WF_FP32) return false;
+  if (n < 2 || method != WF_TEMPORAL_SCHUR || precision != WF_FP32 || !use_defect_correction()) return false;
   if (const char* e = std::getenv("WF_JOINT"))
     if (e[0] == '0') return false;
   if (const char* e = std::getenv("WF_TMA"))
@@ -1770,7 +1672,7 @@ void solve_many_joint(int n, wf_handle* const* hs, const double* const* rhs, dou
     }
     std::vector<std::vector<int>> it(n);
     std::vector<std::vector<double>> res(n);
-    solve_temporal_schur_joint(n, hs, din, dx, nrhs, tol, x0, it, res, st);
+    solve_temporal_schur_dc(n, hs, din, dx, nrhs, tol, x0, it, res, st);
     for (int i = 0; i < n; ++i) {
       finish_out(hs[i], x[i], dx[i], le[i], staged[i]);
       for (int k = 0; k < nrhs[i]; ++k) {

@@ -361,232 +361,79 @@ __device__ __forceinline__ void line_norm_whole_warps(double* nrm_s, R nrm, int 
 // SRC, OPU, OPL < 0: taken from the arguments at run time. TPC: the line length tp as a
 // compile-time constant (128: n = 4 sites per group, 32 lanes, so that every load's component
 // offset is an immediate), or 0 to read the layout at run time.
-// The kernel body, for block blk of the launch over one lattice (the single-lattice kernel passes
-// blockIdx.x; the multi-lattice kernel the block's index within its lattice).
+// The kernel body (wf_wide_body.inc) as a device function for block blk of one lattice's part of a
+// multi-lattice launch; k_line_wide includes the same body directly.
 template <typename R, int SRC, int OPU, int OPL, int TPC, bool H = false>
 __device__ __forceinline__ void line_wide_body(const LineArgs<R>& A, int blk) {
-  __shared__ double nrm_s[kWideCta];
-  const Geom& g = A.g;
-  const int src = SRC >= 0 ? SRC : A.src;
-  const int opu = OPU >= 0 ? OPU : A.opu;
-  const int opl = OPL >= 0 ? OPL : A.opl;
-  static_assert(TPC == 0 || TPC == 128, "compiled line lengths: run time or 128");
-  const int tp = TPC ? TPC : g.tp, n = TPC ? TPC / 32 : g.n, lpl = TPC ? 32 : g.lpl;
-  const int LPC = kWideCta / tp;  // lines per CTA; threads past LPC * tp idle
-  const int q = threadIdx.x;
-  const int li = q / tp;
-  const bool member = li < LPC;   // the thread belongs to one of the CTA's lines
-  const int sl = member ? q - li * tp : 0;  // its slot
-  const int m = sl / lpl;
-  const int j = q % lpl;          // = sl % lpl for members (tp and 32 are multiples of lpl)
-  const int t = n * j + m;
-  const int q0 = li * tp + j;     // the CTA thread holding site 0 of this thread's group
-  const int lg_raw = blk * LPC + li;
-  const bool line_ok = member && lg_raw < A.nrhs * g.Nl;
-  int rhs, l;
-  if (A.order) {
-    const int2 o = A.order[line_ok ? lg_raw : 0];
-    rhs = o.x;
-    l = o.y;
-  } else {
-    line_rhs(line_ok ? lg_raw : 0, A.nrhs, g, rhs, l);
-  }
-  const bool valid = line_ok && t < g.T;  // owns a site (else padding or idle)
-  const size_t base = ((size_t)rhs * g.Nl + l) * NSPIN_C * tp;
-  if constexpr (TPC == 128) {
-    if (A.active && !A.active[rhs]) return;  // one line per CTA: the whole CTA leaves
-  }
-
-  Vec3<R> v[4];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) v[s] = vzero<R>();
-  if (valid) {
-    if (src == SRC_HOP) {
-      if constexpr (std::is_same<R, df64>::value)
-        hop_site_rolled<R, TPC>(v, A, rhs, l, sl);
-      else
-        hop_site<R, TPC, H>(v, A, rhs, l, sl);
-    } else {
-      if (opu != OP_SKIP) {
-        v[0] = ldv<R, H>(A.src_up, base, tp, sl);
-        v[1] = ldv<R, H>(A.src_up, base + 3 * tp, tp, sl);
-      }
-      if (opl != OP_SKIP) {
-        v[2] = ldv<R, H>(A.src_lo, base, tp, sl);
-        v[3] = ldv<R, H>(A.src_lo, base + 3 * tp, tp, sl);
-      }
-    }
-    if (A.xpre) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) v[s] = vaxpy(A.apre, v[s], ldv<R, H>(A.xpre, base + 3 * s * tp, tp, sl));
-    }
-  }
-
-  if constexpr (TPC == 128) {
-    // transposed solve: thread (m, j) hands site t = 4 j + m to shared memory and takes back spin
-    // m of the four sites of group j (one line per CTA)
-    __shared__ Cx<R> tr[NSPIN_C][4][32];
-    const int sp = m;  // the spin this warp solves and stores
-    const int h = sp >> 1;
-    const int op = h ? opl : opu;
-    const int dh = A.swap_out ? 1 - h : h;
-    const int comp0 = dh * 6 + (sp & 1) * 3;
-    // K-c's post-axpy operand is loaded now, so that its latency overlaps the solve (the other
-    // variants load it at the store)
-    constexpr bool kEarlyX = WF_EARLY_X && SRC == SRC_HOP && OPU == OP_COPY && OPL == OP_BWD;
-    Vec3<R> xp[4];
-    if constexpr (kEarlyX) {
-      const bool want_x = A.xpost && line_ok && op != OP_SKIP;
-#pragma unroll
-      for (int mm = 0; mm < 4; ++mm)
-        xp[mm] = want_x ? ldv_stream<R, H>(A.xpost, base + comp0 * tp, tp, mm * 32 + j) : vzero<R>();
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) tr[3 * s + c][m][j] = v[s].c[c];
-    __syncthreads();
-    Vec3<R> w[4];
-#pragma unroll
-    for (int mm = 0; mm < 4; ++mm)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) w[mm].c[c] = tr[3 * sp + c][mm][j];
-    const Cx<R>* K_line = A.lamf + (size_t)l * 9;
-    if (op == OP_FWD) spin_solve4<R, true>(w, j, g.T, K_line, A.inv_mu, A.bc);
-    if (op == OP_BWD) spin_solve4<R, false>(w, j, g.T, K_line, A.inv_mu, A.bc);
-    R nrm = R(0);
-    if (line_ok && op != OP_SKIP) {
-#pragma unroll
-      for (int mm = 0; mm < 4; ++mm) {
-        const int slot = mm * 32 + j;
-        Vec3<R> val = 4 * j + mm < g.T ? w[mm] : vzero<R>();
-        if (A.xpost) {
-          if constexpr (kEarlyX)
-            val = vaxpy(A.apost, val, xp[mm]);
-          else
-            val = vaxpy(A.apost, val, ldv_stream<R, H>(A.xpost, base + comp0 * tp, tp, slot));
-        }
-        if (A.stream_out)
-          stv_stream<R, H>(A.out, base + comp0 * tp, tp, slot, val);
-        else
-          stv<R, H>(A.out, base + comp0 * tp, tp, slot, val);
-        if (A.norm2) nrm += vnorm2(val);
-      }
-    }
-    if (A.norm2) line_norm_whole_warps(nrm_s, nrm, q, tp, li, sl, line_ok, A.norm2, rhs);
-    return;
-  } else {
-  __shared__ MapStore<R> smap[2];
-  // time-line solves: site maps to shared memory, one barrier, in-group and lane composition
-  const bool solve_u = opu == OP_FWD || opu == OP_BWD;
-  const bool solve_l = opl == OP_FWD || opl == OP_BWD;
-  if (solve_u) put_map(smap[0], q, site_map(v[0], v[1], valid, A.inv_mu));
-  if (solve_l) put_map(smap[1], q, site_map(v[2], v[3], valid, A.inv_mu));
-  if (solve_u || solve_l) __syncthreads();
-  const Cx<R>* K_line = A.lamf + (size_t)l * 9;
-  if (opu == OP_FWD) solve_half_wide<R, true>(v[0], v[1], smap[0], member, q0, m, n, lpl, j, valid, K_line, A.bc);
-  if (opu == OP_BWD) solve_half_wide<R, false>(v[0], v[1], smap[0], member, q0, m, n, lpl, j, valid, K_line, A.bc);
-  if (opl == OP_FWD) solve_half_wide<R, true>(v[2], v[3], smap[1], member, q0, m, n, lpl, j, valid, K_line, A.bc);
-  if (opl == OP_BWD) solve_half_wide<R, false>(v[2], v[3], smap[1], member, q0, m, n, lpl, j, valid, K_line, A.bc);
-
-  R nrm = R(0);
-  if (line_ok) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int op = h ? opl : opu;
-      if (op == OP_SKIP) continue;
-      const int dh = A.swap_out ? 1 - h : h;
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int comp0 = dh * 6 + s * 3;
-        Vec3<R> val = valid ? v[2 * h + s] : vzero<R>();
-        if (A.xpost) val = vaxpy(A.apost, val, ldv_stream<R, H>(A.xpost, base + comp0 * tp, tp, sl));
-        if (A.stream_out)
-          stv_stream<R, H>(A.out, base + comp0 * tp, tp, sl, val);
-        else
-          stv<R, H>(A.out, base + comp0 * tp, tp, sl, val);
-        if (A.norm2) nrm += vnorm2(val);
-      }
-    }
-  }
-  if (A.norm2) {
-    // one atomic per line: warp sums where a line is whole warps, else a per-line loop
-    const int lane = q & 31;
-    double dn = (double)nrm;
-    if (tp % 32 == 0) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(kFull, dn, o);
-      if (lane == 0) nrm_s[q >> 5] = dn;
-      __syncthreads();
-      if (line_ok && sl == 0) {
-        double sum = 0.0;
-        for (int i = 0; i < tp / 32; ++i) sum += nrm_s[(li * tp >> 5) + i];
-        atomicAdd(A.norm2 + rhs, sum);
-      }
-    } else {
-      nrm_s[q] = dn;
-      __syncthreads();
-      if (line_ok && sl == 0) {
-        double sum = 0.0;
-        for (int i = 0; i < tp; ++i) sum += nrm_s[li * tp + i];
-        atomicAdd(A.norm2 + rhs, sum);
-      }
-    }
-  }
-  }
+#define WF_WIDE_BLOCK blk
+#include "wf_wide_body.inc"
+#undef WF_WIDE_BLOCK
 }
 
 template <typename R, int SRC, int OPU, int OPL, int TPC, bool H = false>
 __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
     k_line_wide(const LineArgs<R> A) {
-  line_wide_body<R, SRC, OPU, OPL, TPC, H>(A, blockIdx.x);
+#define WF_WIDE_BLOCK ((int)blockIdx.x)
+#include "wf_wide_body.inc"
+#undef WF_WIDE_BLOCK
 }
 
 // One launch over several lattices (a ragged batch): block b belongs to the lattice k with
-// M.blk0[k] <= b < M.blk0[k + 1] and runs that lattice's arguments; 128-slot lines take the
-// compiled-length body, the others the run-time one.
-template <typename R, int SRC, int OPU, int OPL>
+// M.blk0[k] <= b < M.blk0[k + 1] and runs that lattice's arguments. TPC as for k_line_wide: the
+// lattices of one launch share it (128-slot lines and the others launch apart).
+template <typename R, int SRC, int OPU, int OPL, int TPC>
 __global__ void __launch_bounds__(kWideCta, WideMinBlocks<R, SRC == SRC_HOP && OPU == OP_COPY>::value)
-    k_line_wide_multi(const MultiLineArgs<R> M) {
+    k_line_wide_multi(const __grid_constant__ MultiLineArgs<R> M) {
   int k = 0;
   while (k + 1 < M.n && (int)blockIdx.x >= M.blk0[k + 1]) ++k;
-  const LineArgs<R>& A = M.a[k];
-  const int blk = (int)blockIdx.x - M.blk0[k];
-  if (A.g.tp == 128 && A.g.n == 4 && A.g.lpl == 32)
-    line_wide_body<R, SRC, OPU, OPL, 128>(A, blk);
-  else
-    line_wide_body<R, SRC, OPU, OPL, 0>(A, blk);
+  line_wide_body<R, SRC, OPU, OPL, TPC>(M.a[k], (int)blockIdx.x - M.blk0[k]);
 }
 
 }  // namespace wide
 
 // K-b or K-c (LK_SCHUR_B / LK_SCHUR_C) over a ragged batch of lattices, each with its own
-// arguments (traversal and neighbour tables attached), in launches of up to kMaxLattices lattices
+// arguments (traversal and neighbour tables attached): the lattices with 128-slot lines in
+// launches of up to kMaxLattices, the others likewise
 template <typename R>
 void launch_line_wide_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s) {
-  for (size_t first = 0; first < as.size(); first += kMaxLattices) {
-    MultiLineArgs<R> M;
-    std::memset(&M, 0, sizeof(M));
-    M.n = (int)std::min<size_t>(kMaxLattices, as.size() - first);
-    int blocks = 0;
-    for (int k = 0; k < M.n; ++k) {
-      const LineArgs<R>& a = as[first + k];
+  if (kind != LK_SCHUR_B && kind != LK_SCHUR_C) throw Error(1, "multi-lattice wide kernel: K-b or K-c only");
+  for (int compiled = 1; compiled >= 0; --compiled) {
+    std::vector<const LineArgs<R>*> sel;
+    for (const LineArgs<R>& a : as) {
       if (!wide_supported(a.g) || a.h16 || !a.order || !a.nbr)
         throw Error(1, "multi-lattice wide kernel: supported layouts, FP32 storage, traversal tables");
-      M.a[k] = a;
-      M.blk0[k] = blocks;
-      const int LPC = wide::kWideCta / a.g.tp;
-      blocks += (a.nrhs * a.g.Nl + LPC - 1) / LPC;
+      const bool is128 = a.g.tp == 128 && a.g.n == 4 && a.g.lpl == 32;
+      if (is128 == (compiled == 1)) sel.push_back(&a);
     }
-    M.blk0[M.n] = blocks;
-    if (blocks == 0) continue;
-    if (kind == LK_SCHUR_B)
-      wide::k_line_wide_multi<R, SRC_HOP, OP_FWD, OP_BWD><<<blocks, wide::kWideCta, 0, s>>>(M);
-    else if (kind == LK_SCHUR_C)
-      wide::k_line_wide_multi<R, SRC_HOP, OP_COPY, OP_BWD><<<blocks, wide::kWideCta, 0, s>>>(M);
-    else
-      throw Error(1, "multi-lattice wide kernel: K-b or K-c only");
-    WF_CUDA(cudaGetLastError());
+    for (size_t first = 0; first < sel.size(); first += kMaxLattices) {
+      MultiLineArgs<R> M;
+      std::memset(&M, 0, sizeof(M));
+      M.n = (int)std::min<size_t>(kMaxLattices, sel.size() - first);
+      int blocks = 0;
+      for (int k = 0; k < M.n; ++k) {
+        const LineArgs<R>& a = *sel[first + k];
+        M.a[k] = a;
+        M.blk0[k] = blocks;
+        const int LPC = wide::kWideCta / a.g.tp;
+        blocks += (a.nrhs * a.g.Nl + LPC - 1) / LPC;
+      }
+      M.blk0[M.n] = blocks;
+      if (blocks == 0) continue;
+#define WF_KWM(OPUV, TPCV) wide::k_line_wide_multi<R, SRC_HOP, OPUV, OP_BWD, TPCV><<<blocks, wide::kWideCta, 0, s>>>(M)
+      if (kind == LK_SCHUR_B) {
+        if (compiled)
+          WF_KWM(OP_FWD, 128);
+        else
+          WF_KWM(OP_FWD, 0);
+      } else {
+        if (compiled)
+          WF_KWM(OP_COPY, 128);
+        else
+          WF_KWM(OP_COPY, 0);
+      }
+#undef WF_KWM
+      WF_CUDA(cudaGetLastError());
+    }
   }
 }
 

@@ -83,11 +83,15 @@ def test_hop_variant_apply_parity(monkeypatch, lat, cfg):
         w.close()
 
 
+@pytest.mark.parametrize("scheme", ["dc", "ru"])
 @pytest.mark.parametrize("cfg", ["pipe,1,3", "pipe,2,2"])
-def test_hop_variant_fp32_solve(monkeypatch, cfg):
-    """Three sources through the CG with reliable updates; sources stop at different iterations,
-    so the kernels also run units whose sources are partly stopped."""
+def test_hop_variant_fp32_solve(monkeypatch, cfg, scheme):
+    """Three sources through the FP32 CG (defect correction, or reliable updates with WF_DC=0);
+    sources stop at different iterations, so the kernels also run units whose sources are partly
+    stopped."""
     monkeypatch.setenv("WF_HOP", f"{cfg},2")
+    if scheme == "ru":
+        monkeypatch.setenv("WF_DC", "0")
     L, T, bc, seed = LATTICES[0]
     p, U, eta, xo, par3 = _problem(L, T, bc, seed, 3)
     eta[1] = 0.0

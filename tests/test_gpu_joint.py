@@ -85,7 +85,8 @@ def test_joint_mixed_sizes_against_separate_solves():
         assert nb >= 2 * max(max(it) for it in sep)  # two applies per iteration, one launch each
         for pr in prof[1:]:
             assert pr.get("schur_b_hop_tsolve_f32", (0, 0))[0] == 0
-            assert pr.get("prep_hop_f64", (0, 0))[0] > 0  # FP64 steps stay per lattice
+            assert pr.get("prep_hop_f32", (0, 0))[0] > 0  # S_L and the true residual stay per lattice
+            assert pr.get("apply_M_f64", (0, 0))[0] > 0
     finally:
         for q in lats:
             q[0].close()

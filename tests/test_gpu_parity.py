@@ -119,9 +119,13 @@ def test_host_pointers_match_device(case):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("precision", [wf.WF_FP64, wf.WF_FP32])
-def test_solve_temporal_schur(case, precision):
+@pytest.mark.parametrize("precision", [wf.WF_FP64, wf.WF_FP32, "fp32_reliable_updates"])
+def test_solve_temporal_schur(case, precision, monkeypatch):
+    """FP64 CG; FP32 by defect correction (the default); FP32 with reliable updates (WF_DC=0)."""
     p, U, eta, w = case
+    if precision == "fp32_reliable_updates":
+        monkeypatch.setenv("WF_DC", "0")
+        precision = wf.WF_FP32
     x, iters, res, status = w.solve(_dev(eta), tol=1e-10, precision=precision)
     assert status == wf.WF_OK
     assert all(r <= 1e-10 for r in res)
@@ -208,11 +212,13 @@ def test_fp64_iterations_match_oracle():
 @pytest.mark.parametrize("L,T", [(4, 16), (4, 128), (4, 7)])
 @pytest.mark.parametrize("method", [wf.WF_TEMPORAL_SCHUR, wf.WF_EO4D, wf.WF_TEMPORAL])
 def test_solve_with_double_float_steps(monkeypatch, L, T, method):
-    """WF_DF64=1 at handle creation: the FP64 steps of an FP32 solve (reliable updates, S_L, S_R,
-    the comparators' reconstructions) run in double-float; the FP64 true residual still decides."""
+    """WF_DF64=1 at handle creation: the FP64 steps of an FP32 solve with reliable updates
+    (reliable updates, S_L, S_R, the comparators' reconstructions; WF_DC=0 for the temporal +
+    Schur method) run in double-float; the FP64 true residual still decides."""
     if method == wf.WF_EO4D and T % 2:
         pytest.skip("the 4-D checkerboard needs an even T")
     monkeypatch.setenv("WF_DF64", "1")
+    monkeypatch.setenv("WF_DC", "0")
     p = W.Params(L, T, 0.074, xi=3.5, bc=-1)
     U = S.random_gauge(L, T, 0.25, 41)
     eta = S.gaussian_source(L, T, 42, nrhs=2)
