@@ -64,11 +64,14 @@ enum wf_method {
 
 enum wf_precision {
   WF_FP64 = 0,    /* every operator apply in FP64 */
-  WF_FP32 = 1,    /* FP32 operator applies, FP64 reliable updates, S_L / S_R and true residual */
+  WF_FP32 = 1,    /* FP32 operator applies; FP64 true residual. WF_TEMPORAL_SCHUR: defect
+                     correction (FP32 S_L, CGNR and S_R per pass, see wf_solve); other methods, and
+                     WF_TEMPORAL_SCHUR with environment WF_DC=0: FP64 reliable updates, S_L / S_R */
   WF_FP16MIX = 2  /* FP16-stored spinors with FP32 arithmetic in the CG (vectors and M-hat's
                      intermediate fields), FP32 reliable updates of the FP32 increment every 1e-2
-                     drop (environment WF_RELIABLE_DELTA16), FP64 ones every 1e-5 (WF_RELIABLE_DELTA),
-                     FP64 S_L / S_R and true residual; WF_TEMPORAL_SCHUR in the axial frame only */
+                     drop (environment WF_RELIABLE_DELTA16), inside the defect-correction passes of
+                     WF_FP32; with WF_DC=0 FP64 reliable updates every 1e-5 (WF_RELIABLE_DELTA) and
+                     FP64 S_L / S_R instead; WF_TEMPORAL_SCHUR in the axial frame only */
 };
 
 #define WF_X0 1 /* wf_solve flag: x holds the initial guess on entry */
@@ -173,22 +176,24 @@ int wf_solve(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol,
  * anisotropy): handle hs[i] (one lattice each, possibly of different sizes; the handles must be
  * distinct) solves nrhs[i] sources rhs[i] into x[i], with the arguments and conventions of wf_solve
  * (tol, method, precision and flags common to all).
- *   - Joint path: FP32 temporal + Schur solves (WF_TEMPORAL_SCHUR, WF_FP32, defect correction)
- *     on handles of one device, in the axial frame, with one iteration limit, no clover term and
- *     at most WF_MAX_SOLVE_RHS sources in all are solved as one
- *     CGNR per defect-correction pass over the concatenation of all lattices' sources. Each of its
- *     kernels (K-a, K-b, K-c, the vector updates, norms and convergence checks) runs as one launch
- *     over every lattice (eight lattices per launch at most); the S_L preparation, the
- *     reconstruction and the FP64 true residual run per lattice, each on its handle's stream, so
- *     that they overlap. K-b and K-c take each lattice's autotuned configuration (tuned in the
- *     call for a handle with none for its nrhs): lattices on the one-thread-per-site kernels share
- *     one launch (128-slot lines and the others apart), the others launch their own. Every source
- *     keeps its own CG scalars and stopping test, so it takes the iterations of a separate solve
- *     (up to the rounding of its norms). The call first synchronises every handle's stream; the iterations run on hs[0]'s
- *     stream; a handle on the default stream, or on a stream another handle uses, works on a
- *     temporary stream. An error is reported on every handle and as every status.
- *   - Otherwise (or with environment WF_JOINT=0) every solve runs on a host thread of its own and
- *     on its handle's stream (a temporary stream for handles on the default stream).
+ *   - Default: every solve runs on a host thread of its own and on its handle's stream (a
+ *     temporary stream for handles on the default stream), so that the lattices' solves overlap on
+ *     the GPU, each in its own phase (one lattice's FP64 true residual beside another's FP32
+ *     iterations).
+ *   - Joint path (environment WF_JOINT=1): FP32 temporal + Schur solves (WF_TEMPORAL_SCHUR,
+ *     WF_FP32, defect correction) on handles of one device, in the axial frame, with one iteration
+ *     limit, no clover term and at most WF_MAX_SOLVE_RHS sources in all are solved as one CGNR per
+ *     defect-correction pass over the concatenation of all lattices' sources. Each of its kernels
+ *     (K-a, K-b, K-c, the vector updates, norms and convergence checks) runs as one launch over
+ *     every lattice (eight lattices per launch at most; lattices grouped by kernel family and line
+ *     length, bulk-fed ones on launches of their own) with the lattices' autotuned configurations
+ *     (tuned in the call for a handle with none for its nrhs); S_L, the reconstruction and the FP64
+ *     true residual run per lattice, each on its handle's stream. Every source keeps its own CG
+ *     scalars and stopping test, so it takes the iterations of a separate solve (up to the rounding
+ *     of its norms). The call first synchronises every handle's stream; the iterations run on
+ *     hs[0]'s stream; a handle on the default stream, or on a stream another handle uses, works on
+ *     a temporary stream. An error is reported on every handle and as every status. Measured on
+ *     GB300 it is 10-25 % slower than the default, whose overlapping phases it gives up.
  * No counterpart in the paper (its solves are independent problems). iters_out, resid_out and
  * status_out may be null, or hold n pointers (n statuses); returns WF_OK or the first non-OK
  * status. */

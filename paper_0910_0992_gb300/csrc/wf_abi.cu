@@ -557,8 +557,9 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
   double *gam = sc, *gnew = sc + nrhs, *qq = sc + 2 * nrhs, *rr = sc + 3 * nrhs;
   // device bookkeeping per right-hand side: active, state (0 running, 1 converged, 2 wants a
   // reliable update), iterations; limits: target^2 and the reliable-update threshold^2
-  int* ist = h->buf<int>("cg_istate", 3 * (size_t)nrhs);
+  int* ist = h->buf<int>("cg_istate", 4 * (size_t)nrhs);
   int *active = ist, *state = ist + nrhs, *dits = ist + 2 * nrhs;
+  int* upd = ist + 3 * nrhs;  // sources whose x update of this iteration is still pending
   double* lim = h->buf<double>("cg_limits", 2 * (size_t)nrhs);
   double* partial = h->buf<double>("cg_partial", 1024 * (size_t)nrhs);
   std::vector<int> act(nrhs, 1), iters(nrhs, 0);
@@ -644,12 +645,14 @@ std::vector<int> cgnr(wf_handle* h, const OpFn<R>& A, const OpFn<double>& A64, c
   upload_state();
   WF_CUDA(cudaMemsetAsync(dits, 0, nrhs * sizeof(int), s));
 
+  // x += alpha p is deferred from the r update to the p update, which reads p anyway (one pass
+  // over the vectors less per iteration); a source that stops at the check still takes it there
   auto iteration = [&]() {
     A(p, q, 0, qq);  // q = A p, |q|^2
-    { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(xacc, r, p, q, n, nrhs, gam, qq, active, partial, rr, s, offs); }
+    { Prof P(h, pname<R>("cg_xr"), 2); launch_cg_xr<R>(nullptr, r, p, q, n, nrhs, gam, qq, active, partial, rr, s, offs, upd); }
     { Prof P(h, "cg_check"); launch_cg_check(rr, active, state, dits, lim, lim + nrhs, nrhs, s); }
     A(r, sv, 1, gnew);  // s = A^dag r, |s|^2
-    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s, offs); }
+    { Prof P(h, pname<R>("cg_p")); launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s, offs, xacc, qq, upd); }
     { Prof P(h, "copy_scalar"); launch_copy_scalar(gam, gnew, nrhs, s, active); }
   };
 
@@ -873,7 +876,7 @@ void schur_apply_h16(wf_handle* h, const Cx16* x, Cx16* out, int dagger, int nrh
 // sigma; the requesting right-hand sides then finish their iteration (s = A^dag r, p = s + beta
 // p). Iterations run in blocks with device-side checks (k_cg_check) as in cgnr; no CUDA graph.
 std::vector<int> cgnr_h16(wf_handle* h, int nrhs, size_t n, const Cx<double>* b, Cx<double>* y,
-                          const std::vector<double>& target, int maxiter, bool x0) {
+                          const std::vector<double>& target, int maxiter, bool x0, bool fp64_updates = true) {
   const size_t nt = n * nrhs;
   cudaStream_t s = h->stream;
   const OpFn<float> A32 = schur_op<float>(h, nrhs);
@@ -1012,7 +1015,7 @@ std::vector<int> cgnr_h16(wf_handle* h, int nrhs, size_t n, const Cx<double>* b,
       if (st[k] != 1 && sk != 0) {  // asks for an update (its residual fell by delta16 or met its target)
         need = true;
         st[k] = 2;
-        if (sigma[k] * std::sqrt(rrh[k]) < d64 * rmax[k]) need64 = true;
+        if (fp64_updates && sigma[k] * std::sqrt(rrh[k]) < d64 * rmax[k]) need64 = true;
       }
     }
     if (need) {
@@ -1088,7 +1091,7 @@ std::vector<int> cgnr_h16(wf_handle* h, int nrhs, size_t n, const Cx<double>* b,
 void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<const Cx<double>*>& eta_lex,
                              const std::vector<Cx<double>*>& x_lex, const int* nrhs, double tol, bool x0,
                              std::vector<std::vector<int>>& iters, std::vector<std::vector<double>>& rel,
-                             std::vector<int>& status);
+                             std::vector<int>& status, bool h16 = false);
 
 // FP32 temporal + Schur solves take defect correction (solve_temporal_schur_dc) unless the
 // environment sets WF_DC=0, which selects FP32 iterations with FP64 reliable updates
@@ -1099,12 +1102,12 @@ bool use_defect_correction() {
 
 int solve_temporal_schur(wf_handle* h, const Cx<double>* eta_lex, Cx<double>* x_lex, int nrhs, double tol,
                          int precision, bool x0, int* iters_out, double* resid_out) {
-  if (precision == WF_FP32 && use_defect_correction()) {
+  if ((precision == WF_FP32 || precision == WF_FP16MIX) && use_defect_correction()) {
     std::vector<std::vector<int>> it(1);
     std::vector<std::vector<double>> res(1);
     std::vector<int> st(1);
     wf_handle* const hs[1] = {h};
-    solve_temporal_schur_dc(1, hs, {eta_lex}, {x_lex}, &nrhs, tol, x0, it, res, st);
+    solve_temporal_schur_dc(1, hs, {eta_lex}, {x_lex}, &nrhs, tol, x0, it, res, st, precision == WF_FP16MIX);
     for (int k = 0; k < nrhs; ++k) {
       if (iters_out) iters_out[k] = it[0][k];
       if (resid_out) resid_out[k] = res[0][k];
@@ -1256,9 +1259,9 @@ struct JointSync {
 // numbering, on the joint stream. K-a runs as one launch over all lattices' sources (per
 // kMaxLattices lattices). K-b and K-c take each lattice's autotuned configuration (the tuner runs
 // here, on scratch fields, for a handle that has none for its number of sources): the lattices
-// whose choice is the one-thread-per-site kernels share one launch per kernel, the others (n sites
-// per lane, bulk-fed) launch their own. Tables are attached here, before the solver captures an
-// iteration.
+// whose choice is the one-thread-per-site kernels share one launch per kernel (two: 128-slot lines
+// and the others), so do those on n sites per lane, and the bulk-fed ones launch their own.
+// Tables are attached here, before the solver captures an iteration.
 OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, Cx<float>* tz, Cx<float>* tw,
                            int nr) {
   wf_handle* h0 = parts[0].h;
@@ -1269,9 +1272,10 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
     int nunits;
     int* err;
   };
-  std::vector<LineArgs<float>> A, B, C;  // K-a of all; K-b, K-c of the lattices on the shared launch
-  std::vector<int> joined;               // lattice of each B/C entry
-  std::vector<std::pair<int, Own>> own;  // lattices with a launch of their own
+  std::vector<LineArgs<float>> A, B, C;  // K-a of all; K-b, K-c of the lattices on the shared launches
+  std::vector<LineArgs<float>> B2, C2;   // K-b, K-c of the lattices on n sites per lane
+  std::vector<int> joined, joined2;      // lattice of each B/C and B2/C2 entry
+  std::vector<std::pair<int, Own>> own;  // lattices with a launch of their own (bulk-fed kernels)
   for (int j = 0; j < (int)parts.size(); ++j) {
     const JointPart& q = parts[j];
     wf_handle* h = q.h;
@@ -1309,6 +1313,10 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
       B.push_back(b);
       C.push_back(c);
       joined.push_back(j);
+    } else if (t.variant == 2) {
+      B2.push_back(b);
+      C2.push_back(c);
+      joined2.push_back(j);
     } else {
       Own o{b, c, t, nullptr, 0, nullptr};
       if (t.variant == 3) {
@@ -1321,7 +1329,8 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
   }
   const int nl = (int)parts.size();
   const int na = (nl + kMaxLattices - 1) / kMaxLattices;
-  const int nb = ((int)B.size() + kMaxLattices - 1) / kMaxLattices + (int)own.size();
+  const int nb = ((int)B.size() + kMaxLattices - 1) / kMaxLattices +
+                 ((int)B2.size() + kMaxLattices - 1) / kMaxLattices + (int)own.size();
   return [=](const Cx<float>* x, Cx<float>* y, int dagger, double* norm2) mutable {
     const int* act = h0->op_active;
     auto set_b = [&](LineArgs<float>& b, const JointPart& q) {
@@ -1349,6 +1358,10 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
       set_b(B[i], parts[joined[i]]);
       set_c(C[i], parts[joined[i]]);
     }
+    for (size_t i = 0; i < B2.size(); ++i) {
+      set_b(B2[i], parts[joined2[i]]);
+      set_c(C2[i], parts[joined2[i]]);
+    }
     for (auto& o : own) {
       set_b(o.second.b, parts[o.first]);
       set_c(o.second.c, parts[o.first]);
@@ -1364,12 +1377,14 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
     {
       Prof P(h0, "schur_b_hop_tsolve_f32", nb);
       launch_line_wide_multi<float>(B, LK_SCHUR_B, s);
+      launch_line_multi<float>(B2, LK_SCHUR_B, s);
       for (const auto& o : own) launch_own(o.second, o.second.b, LK_SCHUR_B);
     }
     if (norm2) WF_CUDA(cudaMemsetAsync(norm2, 0, nr * sizeof(double), s));
     {
       Prof P(h0, "schur_c_hop_tinv_axpy_f32", nb);
       launch_line_wide_multi<float>(C, LK_SCHUR_C, s);
+      launch_line_multi<float>(C2, LK_SCHUR_C, s);
       for (const auto& o : own) launch_own(o.second, o.second.c, LK_SCHUR_C);
     }
   };
@@ -1380,7 +1395,9 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
 // M-hat without reliable updates, S_R -- to a reduction rho of its Schur residual (no further
 // than what tol needs), adds delta to the FP64 solution psi and recomputes the true residual
 // r = eta - M psi in FP64, the residual the solve reports; it stops when ||r|| / ||eta|| <= tol for
-// every source. The only FP64 operator apply of a pass is that true residual. With several
+// every source. The only FP64 operator apply of a pass is that true residual. h16 (WF_FP16MIX,
+// one lattice): the pass's CGNR keeps its vectors in FP16 with FP32 recomputations of the
+// residual (cgnr_h16 without its FP64 updates). With several
 // lattices the CGNR runs over the concatenation of their odd fields (joint_schur_op) on hs[0]'s
 // stream, the other steps per lattice on each handle's stream (distinct streams), so that they
 // overlap; every source keeps its own CG scalars and stopping test. Environment WF_DC_RHO sets rho
@@ -1388,7 +1405,7 @@ OpFn<float> joint_schur_op(const std::vector<JointPart>& parts, Cx<float>* ty, C
 void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<const Cx<double>*>& eta_lex,
                              const std::vector<Cx<double>*>& x_lex, const int* nrhs, double tol, bool x0,
                              std::vector<std::vector<int>>& iters, std::vector<std::vector<double>>& rel,
-                             std::vector<int>& status) {
+                             std::vector<int>& status, bool h16) {
   wf_handle* h0 = hs[0];
   cudaStream_t s = h0->stream;
   std::vector<JointPart> parts(nl);
@@ -1401,6 +1418,7 @@ void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<con
     nr += nrhs[j];
   }
   const bool joint = nl > 1;
+  if (joint && h16) throw Error(WF_EINVAL, "FP16 storage: one lattice per solve");
   const JointSync sync(parts.size());
   double rho = 1e-5;
   if (const char* e = std::getenv("WF_DC_RHO")) {
@@ -1548,7 +1566,8 @@ void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<con
     }
     sync.fan_in(parts);
     const std::vector<int> it =
-        cgnr<float>(h0, A, A64, b, y, nr, nmax, target, maxiter, false, joint ? ntot : 0, offs, false);
+        h16 ? cgnr_h16(h0, nr, nmax, b, y, target, maxiter, false, false)
+            : cgnr<float>(h0, A, A64, b, y, nr, nmax, target, maxiter, false, joint ? ntot : 0, offs, false);
     sync.fan_out(parts);
     // S_R in FP32: d_o = C_R^o y_o ; d_e = C_R^e C_L^e [r_e + gamma_f^-1 D_s^eo d_o] ; psi += d ;
     // r = eta - M psi in FP64
@@ -1597,13 +1616,17 @@ void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<con
   }
 }
 
-// Whether wf_solve_many can solve its lattices jointly: FP32 iterations of the temporal + Schur
-// method in the axial frame, on lattices the one-thread-per-site kernels serve, on one device,
-// with one iteration limit and no clover term (environment WF_JOINT=0: one solve per lattice)
+// Whether wf_solve_many solves its lattices jointly: on request (environment WF_JOINT=1), for FP32
+// iterations of the temporal + Schur method in the axial frame, on lattices the one-thread-per-site
+// kernels serve, on one device, with one iteration limit and no clover term. Measured on GB300
+// (the xi sweep's three lattices; eight small lattices) the per-lattice solves on concurrent
+// streams finish 10-25 % sooner: each lattice's FP64 true residuals (bound by the FP64 pipe) then
+// overlap other lattices' FP32 iterations (bound by memory), while the joint passes keep every
+// lattice in the same phase.
 bool joint_eligible(int n, wf_handle* const* hs, int method, int precision) {
   if (n < 2 || method != WF_TEMPORAL_SCHUR || precision != WF_FP32 || !use_defect_correction()) return false;
-  if (const char* e = std::getenv("WF_JOINT"))
-    if (e[0] == '0') return false;
+  const char* e = std::getenv("WF_JOINT");
+  if (!e || e[0] != '1') return false;
   if (const char* e = std::getenv("WF_TMA"))
     if (e[0] == '1') return false;
   for (int i = 0; i < n; ++i) {

@@ -80,28 +80,34 @@ void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* o
 template void launch_norm2<float>(const Cx<float>*, size_t, int, double*, double*, cudaStream_t, const size_t*);
 template void launch_norm2<double>(const Cx<double>*, size_t, int, double*, double*, cudaStream_t, const size_t*);
 
-// alpha = gamma / |q|^2; x += alpha p; r -= alpha q; partial |r|^2
+// alpha = gamma / |q|^2; x += alpha p (x null: left to k_cg_p, see below); r -= alpha q; partial
+// |r|^2; upd (if given) records which right-hand sides took this update
 template <typename R>
 __global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __restrict__ r, const Cx<R>* __restrict__ p,
                                                 const Cx<R>* __restrict__ q, size_t n, const double* gamma,
                                                 const double* qq, const int* active, double* partial,
-                                                const size_t* offs) {
+                                                const size_t* offs, int* upd) {
   const int rhs = blockIdx.y;
   const bool on = active[rhs] != 0;
   const double qn = qq[rhs];
   const R alpha = (on && qn > 0.0) ? (R)(gamma[rhs] / qn) : R(0);
+  if (upd && blockIdx.x == 0 && threadIdx.x == 0) upd[rhs] = on ? 1 : 0;
   size_t off, len;
   rhs_range(rhs, n, offs, off, len);
   n = len;
   R part = R(0);  // per-thread partial |r|^2 in the field's precision; FP64 across threads
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
-    const Cx<R> pv = p[off + i], qv = q[off + i];
-    Cx<R> xv = x[off + i], rv = r[off + i];
-    xv.re = fma(alpha, pv.re, xv.re);
-    xv.im = fma(alpha, pv.im, xv.im);
+    const Cx<R> qv = q[off + i];
+    Cx<R> rv = r[off + i];
+    if (x) {
+      const Cx<R> pv = p[off + i];
+      Cx<R> xv = x[off + i];
+      xv.re = fma(alpha, pv.re, xv.re);
+      xv.im = fma(alpha, pv.im, xv.im);
+      x[off + i] = xv;
+    }
     rv.re = fma(-alpha, qv.re, rv.re);
     rv.im = fma(-alpha, qv.im, rv.im);
-    x[off + i] = xv;
     r[off + i] = rv;
     part = fma(rv.re, rv.re, fma(rv.im, rv.im, part));
   }
@@ -112,51 +118,67 @@ __global__ void __launch_bounds__(kBT) k_cg_xr(Cx<R>* __restrict__ x, Cx<R>* __r
 template <typename R>
 void launch_cg_xr(Cx<R>* x, Cx<R>* r, const Cx<R>* p, const Cx<R>* q, size_t n, int nrhs, const double* gamma,
                   const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s,
-                  const size_t* offs) {
+                  const size_t* offs, int* upd) {
   const int parts = parts_for(n);
-  k_cg_xr<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, r, p, q, n, gamma, qq, active, partial, offs);
+  k_cg_xr<R><<<dim3(parts, nrhs), kBT, 0, s>>>(x, r, p, q, n, gamma, qq, active, partial, offs, upd);
   k_final_sum<<<nrhs, kBT, 0, s>>>(partial, parts, rr_out);
   WF_CUDA(cudaGetLastError());
 }
 template void launch_cg_xr<float>(Cx<float>*, Cx<float>*, const Cx<float>*, const Cx<float>*, size_t, int,
                                   const double*, const double*, const int*, double*, double*, cudaStream_t,
-                                  const size_t*);
+                                  const size_t*, int*);
 template void launch_cg_xr<double>(Cx<double>*, Cx<double>*, const Cx<double>*, const Cx<double>*, size_t, int,
                                    const double*, const double*, const int*, double*, double*, cudaStream_t,
-                                   const size_t*);
+                                   const size_t*, int*);
 
-// beta = gamma_new / gamma_old; p = s + beta p
+// beta = gamma_new / gamma_old; p = s + beta p for the active right-hand sides. With x given, the
+// x update that k_cg_xr left out happens here, before p changes: x += alpha p with alpha =
+// gamma_old / qq for the right-hand sides that took this iteration's r update (upd), also those
+// that stopped at it. One pass over p then serves both updates.
 template <typename R>
 __global__ void __launch_bounds__(kBT) k_cg_p(Cx<R>* __restrict__ p, const Cx<R>* __restrict__ sv, size_t n,
                                                const double* gnew, const double* gold, const int* active,
-                                               const size_t* offs) {
+                                               const size_t* offs, Cx<R>* __restrict__ x, const double* qq,
+                                               const int* upd) {
   const int rhs = blockIdx.y;
-  if (!active[rhs]) return;
+  const bool on = active[rhs] != 0;
+  const bool dox = x && upd[rhs];
+  if (!on && !dox) return;
   const double go = gold[rhs];
   const R beta = go > 0.0 ? (R)(gnew[rhs] / go) : R(0);
+  const double qn = dox ? qq[rhs] : 0.0;
+  const R alpha = qn > 0.0 ? (R)(go / qn) : R(0);
   size_t off, len;
   rhs_range(rhs, n, offs, off, len);
   n = len;
   for (size_t i = blockIdx.x * (size_t)kBT + threadIdx.x; i < n; i += (size_t)gridDim.x * kBT) {
-    const Cx<R> s = sv[off + i];
     Cx<R> pv = p[off + i];
-    pv.re = fma(beta, pv.re, s.re);
-    pv.im = fma(beta, pv.im, s.im);
-    p[off + i] = pv;
+    if (dox) {
+      Cx<R> xv = x[off + i];
+      xv.re = fma(alpha, pv.re, xv.re);
+      xv.im = fma(alpha, pv.im, xv.im);
+      x[off + i] = xv;
+    }
+    if (on) {
+      const Cx<R> s = sv[off + i];
+      pv.re = fma(beta, pv.re, s.re);
+      pv.im = fma(beta, pv.im, s.im);
+      p[off + i] = pv;
+    }
   }
 }
 
 template <typename R>
 void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* gnew, const double* gold,
-                 const int* active, cudaStream_t s, const size_t* offs) {
+                 const int* active, cudaStream_t s, const size_t* offs, Cx<R>* x, const double* qq, const int* upd) {
   const int parts = parts_for(n) * 2;
-  k_cg_p<R><<<dim3(parts, nrhs), kBT, 0, s>>>(p, sv, n, gnew, gold, active, offs);
+  k_cg_p<R><<<dim3(parts, nrhs), kBT, 0, s>>>(p, sv, n, gnew, gold, active, offs, x, qq, upd);
   WF_CUDA(cudaGetLastError());
 }
 template void launch_cg_p<float>(Cx<float>*, const Cx<float>*, size_t, int, const double*, const double*,
-                                 const int*, cudaStream_t, const size_t*);
+                                 const int*, cudaStream_t, const size_t*, Cx<float>*, const double*, const int*);
 template void launch_cg_p<double>(Cx<double>*, const Cx<double>*, size_t, int, const double*, const double*,
-                                  const int*, cudaStream_t, const size_t*);
+                                  const int*, cudaStream_t, const size_t*, Cx<double>*, const double*, const int*);
 
 template <typename R>
 __global__ void __launch_bounds__(kBT) k_axpby(Cx<R>* __restrict__ y, const Cx<R>* __restrict__ x, size_t n, R a, R b) {

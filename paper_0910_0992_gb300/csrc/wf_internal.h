@@ -69,7 +69,8 @@ template <typename R>
 void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s);
 
 // one launch (or one per kMaxLattices) over a ragged batch of lattices, each with its own
-// arguments: K-a on the line kernel, K-b / K-c on the one-thread-per-site kernel (tables attached)
+// arguments: K-a, K-b or K-c on the line kernel (n sites per lane), and K-b / K-c on the
+// one-thread-per-site kernel (tables attached; 128-slot lattices and the others launch apart)
 template <typename R>
 void launch_line_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s);
 template <typename R>
@@ -146,13 +147,18 @@ void launch_f2d(const Cx<float>* in, Cx<double>* out, size_t n, cudaStream_t s);
 template <typename R>
 void launch_norm2(const Cx<R>* x, size_t n, int nrhs, double* partial, double* out, cudaStream_t s,
                   const size_t* offs = nullptr);
+// CG updates: launch_cg_xr does r -= alpha q (alpha = gamma / qq) with |r|^2 into rr_out, and
+// x += alpha p unless x is null; then upd (if given) records the right-hand sides that took the
+// update. launch_cg_p does p = s + beta p (beta = gamma_new / gamma_old) for the active ones and,
+// with x given, first the deferred x += alpha p (alpha = gamma_old / qq) for those flagged in upd.
 template <typename R>
 void launch_cg_xr(Cx<R>* x, Cx<R>* r, const Cx<R>* p, const Cx<R>* q, size_t n, int nrhs, const double* gamma,
                   const double* qq, const int* active, double* partial, double* rr_out, cudaStream_t s,
-                  const size_t* offs = nullptr);
+                  const size_t* offs = nullptr, int* upd = nullptr);
 template <typename R>
 void launch_cg_p(Cx<R>* p, const Cx<R>* sv, size_t n, int nrhs, const double* gamma_new, const double* gamma_old,
-                 const int* active, cudaStream_t s, const size_t* offs = nullptr);
+                 const int* active, cudaStream_t s, const size_t* offs = nullptr, Cx<R>* x = nullptr,
+                 const double* qq = nullptr, const int* upd = nullptr);
 template <typename R>
 void launch_axpby(Cx<R>* y, const Cx<R>* x, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void launch_add_f_to_d(Cx<double>* y, const Cx<float>* x, size_t n, cudaStream_t s);      // y += x

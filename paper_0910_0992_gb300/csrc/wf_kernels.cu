@@ -283,11 +283,12 @@ void launch_line(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s) {
   }
   launch_line_impl<R>(a, kind, axial, s);
 }
-// K-a (LK_SCHUR_A, axial frame) over a ragged batch of lattices, in launches of up to
-// kMaxLattices lattices
+// K-a, K-b or K-c (LK_SCHUR_A/B/C, axial frame) on this kernel over a ragged batch of lattices, in
+// launches of up to kMaxLattices lattices
 template <typename R>
 void launch_line_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_t s) {
-  if (kind != LK_SCHUR_A) throw Error(1, "multi-lattice line kernel: K-a only");
+  if (kind != LK_SCHUR_A && kind != LK_SCHUR_B && kind != LK_SCHUR_C)
+    throw Error(1, "multi-lattice line kernel: K-a, K-b or K-c");
   for (size_t first = 0; first < as.size(); first += kMaxLattices) {
     MultiLineArgs<R> M;
     std::memset(&M, 0, sizeof(M));
@@ -302,7 +303,12 @@ void launch_line_multi(const std::vector<LineArgs<R>>& as, int kind, cudaStream_
     }
     M.blk0[M.n] = blocks;
     if (blocks == 0) continue;
-    k_line_multi<R, true, SRC_LOAD, OP_FWD, OP_SKIP><<<blocks, kLineThreads, 0, s>>>(M);
+    if (kind == LK_SCHUR_A)
+      k_line_multi<R, true, SRC_LOAD, OP_FWD, OP_SKIP><<<blocks, kLineThreads, 0, s>>>(M);
+    else if (kind == LK_SCHUR_B)
+      k_line_multi<R, true, SRC_HOP, OP_FWD, OP_BWD><<<blocks, kLineThreads, 0, s>>>(M);
+    else
+      k_line_multi<R, true, SRC_HOP, OP_COPY, OP_BWD><<<blocks, kLineThreads, 0, s>>>(M);
     WF_CUDA(cudaGetLastError());
   }
 }

@@ -51,6 +51,13 @@ def test_traffic_record_binding(tmp_path, monkeypatch):
     assert bench.traffic_for(k, 12, "variant=one thread per site;tile_rows=8", str(path)) is None  # other traversal
     assert bench.traffic_for("schur_b_hop_tsolve_f32", 12, cfg, str(path)) is None          # not captured
     assert bench.traffic_for(k, 12, cfg, str(tmp_path / "absent.json")) is None
+    # several captured configurations of one kernel
+    cfg8 = "variant=one thread per site;tile_rows=8"
+    rec["kernels"][k] = [rec["kernels"][k], dict(rec["kernels"][k], config=cfg8, dram_bytes_per_launch=3.9e9)]
+    path.write_text(json.dumps(rec))
+    assert bench.traffic_for(k, 12, cfg, str(path)) == 3.6e9
+    assert bench.traffic_for(k, 12, cfg8, str(path)) == 3.9e9
+    assert bench.traffic_for(k, 12, "variant=one thread per site;tile_rows=4", str(path)) is None
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)                             # kernels changed
     assert bench.traffic_for(k, 12, cfg, str(path)) is None
 

@@ -7,7 +7,8 @@ component). The input, K-a's output, K-b's output and the result are each rounde
 operator's norm is O(1), so the relative 2-norm error is about sqrt(4) * 2.8e-4 * O(1) ~ 1e-3;
 the tests allow 3e-3 and also require the error to exceed 1e-6, which FP32 storage would not
 reach (so the FP16 path is the one that ran). Solves must meet the FP64 true residual 1e-10 of
-the full M (checked again with the oracle's M), in at most 1.5 times the FP32 iterations + 5.
+the full M (checked again with the oracle's M), in at most 1.5 times the FP32 iterations + 5, in
+both FP32 schemes (defect correction and, with WF_DC=0, reliable updates).
 """
 
 import numpy as np
@@ -64,8 +65,13 @@ def test_fp16_apply_parity(lat):
         w.close()
 
 
+@pytest.mark.parametrize("scheme", ["dc", "ru"])
 @pytest.mark.parametrize("lat", LATTICES, ids=lambda c: f"L{c[0]}T{c[1]}")
-def test_fp16mix_solve(lat):
+def test_fp16mix_solve(lat, scheme, monkeypatch):
+    """FP16 storage inside defect-correction passes (default), or with FP64 reliable updates and
+    FP64 S_L / S_R (WF_DC=0); the FP32 solve of the same scheme sets the iteration bar."""
+    if scheme == "ru":
+        monkeypatch.setenv("WF_DC", "0")
     L, T, ks, xi, bc, eps, seed = lat
     p = W.Params(L, T, ks, xi=xi, bc=bc)
     U = S.random_gauge(L, T, eps, seed)

@@ -1,6 +1,6 @@
-"""Ragged batches solved jointly (wf_solve_many, FP32 temporal + Schur, axial frame): the CG
-iterations of every lattice run as one solve over the concatenated odd fields, with K-a, K-b and
-K-c launched once per iteration over all lattices' sources.
+"""Ragged batches solved jointly (wf_solve_many with WF_JOINT=1, FP32 temporal + Schur, axial
+frame): the CG iterations of every lattice run as one solve over the concatenated odd fields, with
+K-a, K-b and K-c launched once per iteration over all lattices' sources.
 
 Checks against the FP64 oracle: every solution meets the true residual 1e-10 (recomputed with the
 oracle's M), each source takes the iterations of its separate solve to within one (the joint norms
@@ -34,6 +34,11 @@ MIXED = [(4, 128, 0.074, 3.5, -1, 0.2, 11, 3), (4, 96, 0.06, 4.5, 1, 0.25, 12, 2
 
 def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(autouse=True)
+def _joint(monkeypatch):
+    monkeypatch.setenv("WF_JOINT", "1")  # the joint path is opt-in
 
 
 def _setup(lats):
@@ -163,12 +168,12 @@ def test_joint_iteration_limit():
 
 @pytest.mark.parametrize("how", ["env", "limits"])
 def test_per_lattice_fallback(how, monkeypatch):
-    """WF_JOINT=0, or handles with different iteration limits, take one solve per lattice (each on
-    its own stream and host thread); the results meet the same bar."""
+    """Without WF_JOINT=1 (the default), or with handles of different iteration limits, one solve
+    per lattice (each on its own stream and host thread); the results meet the same bar."""
     lats = _setup(MIXED[1:4])
     try:
         if how == "env":
-            monkeypatch.setenv("WF_JOINT", "0")
+            monkeypatch.delenv("WF_JOINT")
         else:
             wf.wf_set_max_iterations(lats[0][0].h, 5000)
         rhs = [_dev(q[3]) for q in lats]
