@@ -82,6 +82,16 @@ enum wf_precision {
  * odd or too small L, T outside [2, 128], kappa_s <= 0 or bc not +-1. */
 int wf_create(int L, int T, double xi, double kappa_s, double kappa_t, int bc, wf_handle_t** out);
 
+/* Host-only check (no GPU needed) of the index tables the kernels use for an L^3 x T lattice with
+ * nrhs sources and traversal tiles of tile_rows rows of y (0: the default): the neighbour tables
+ * of both parities (every entry a line of the other parity whose opposite neighbour is the entry's
+ * line), the traversal order (every (source, line) pair once) and the bulk-fed kernels' units
+ * (every (source group, line) pair once, for groups of 1 and 2). The library runs the same checks
+ * whenever it builds a table. plant = 1, 2 or 3 corrupts one entry of the neighbour, traversal or
+ * unit table after it is built (a self-test of the checks). Returns WF_OK, WF_EINVAL for invalid
+ * arguments (tile_rows not dividing L), or WF_ECUDA if a check failed. */
+int wf_check_tables(int L, int T, int nrhs, int tile_rows, int plant);
+
 /* Release the handle and all its device memory. Null is accepted. */
 int wf_destroy(wf_handle_t* h);
 

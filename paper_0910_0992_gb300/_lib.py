@@ -51,6 +51,7 @@ _SIGS = {
     "wf_solve_many": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _d, _i, _i, _i,
                            ctypes.POINTER(_ip), ctypes.POINTER(_dp), _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
+    "wf_check_tables": (_i, [_i, _i, _i, _i, _i]),
     "wf_hop_config": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
     "wf_hop_pipe_config": (_i, [_vp, _i, _ip, _ip]),
     "wf_set_max_iterations": (_i, [_vp, _i]),
@@ -234,6 +235,11 @@ def wf_temporal_logdet(h, F=None):
 
 def wf_launch_count(h):
     return lib.wf_launch_count(h)
+
+
+def wf_check_tables(L, T, nrhs, tile_rows=0, plant=0):
+    """Host-only check of the kernels' index tables for a geometry; returns the status code."""
+    return lib.wf_check_tables(int(L), int(T), int(nrhs), int(tile_rows), int(plant))
 
 
 def wf_hop_config(h, nrhs):

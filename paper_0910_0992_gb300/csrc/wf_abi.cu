@@ -213,21 +213,79 @@ bool use_tma_kernels(wf_handle* h) {
   return h->use_tma != 0;
 }
 
+// Host checks of the kernels' index tables (the kernels index fields through them unchecked):
+// every neighbour entry is a line of the other parity whose opposite-direction neighbour is the
+// entry's own line; the traversal order visits every (source, line) pair exactly once; the
+// bulk-fed kernels' units cover every (source group, line) pair exactly once.
+void check_nbr_table(const Geom& g, int p, const std::vector<int>& t) {
+  if (t.size() != (size_t)g.Nl * 6) throw Error(WF_ECUDA, "neighbour table: wrong size");
+  for (int l = 0; l < g.Nl; ++l)
+    for (int d = 0; d < 6; ++d) {
+      const int m = t[(size_t)l * 6 + d];
+      if (m < 0 || m >= g.Nl) throw Error(WF_ECUDA, "neighbour table: line out of range");
+      int back[6];
+      neighbour_lines(g, 1 - p, m, back);
+      if (back[d ^ 1] != l) throw Error(WF_ECUDA, "neighbour table: not symmetric");
+    }
+}
+void check_order_table(const Geom& g, int nrhs, const std::vector<int2>& t) {
+  if (t.size() != (size_t)nrhs * g.Nl) throw Error(WF_ECUDA, "traversal table: wrong size");
+  std::vector<char> seen(t.size(), 0);
+  for (const int2& e : t) {
+    if (e.x < 0 || e.x >= nrhs || e.y < 0 || e.y >= g.Nl) throw Error(WF_ECUDA, "traversal table: entry out of range");
+    char& f = seen[(size_t)e.x * g.Nl + e.y];
+    if (f) throw Error(WF_ECUDA, "traversal table: pair visited twice");
+    f = 1;
+  }
+}
+void check_unit_table(const Geom& g, int nrhs, int gsrc, const std::vector<int2>& t) {
+  const int groups = (nrhs + gsrc - 1) / gsrc;
+  if (t.size() != (size_t)groups * g.Nl) throw Error(WF_ECUDA, "unit table: wrong size");
+  std::vector<char> seen(t.size(), 0);
+  for (const int2& e : t) {
+    if (e.x < 0 || e.x >= nrhs || e.x % gsrc || e.y < 0 || e.y >= g.Nl) throw Error(WF_ECUDA, "unit table: entry out of range");
+    char& f = seen[(size_t)(e.x / gsrc) * g.Nl + e.y];
+    if (f) throw Error(WF_ECUDA, "unit table: unit listed twice");
+    f = 1;
+  }
+}
+std::vector<int> build_nbr_table(const Geom& g, int p) {
+  std::vector<int> t((size_t)g.Nl * 6);
+  for (int l = 0; l < g.Nl; ++l) neighbour_lines(g, p, l, &t[(size_t)l * 6]);
+  check_nbr_table(g, p, t);
+  return t;
+}
+std::vector<int2> build_order_table(const Geom& g, int nrhs) {
+  std::vector<int2> t((size_t)nrhs * g.Nl);
+  for (size_t i = 0; i < t.size(); ++i) line_rhs((int)i, nrhs, g, t[i].x, t[i].y);
+  check_order_table(g, nrhs, t);
+  return t;
+}
+std::vector<int2> build_unit_table(const Geom& g, int nrhs, int gsrc) {
+  const int groups = (nrhs + gsrc - 1) / gsrc;
+  std::vector<int2> t((size_t)groups * g.Nl);
+  for (int pos = 0; pos < g.Nl; ++pos) {
+    int r, l;
+    line_rhs(pos, 1, g, r, l);  // with one source the order is the tiled line order itself
+    for (int k = 0; k < groups; ++k) t[(size_t)pos * groups + k] = make_int2(k * gsrc, l);
+  }
+  check_unit_table(g, nrhs, gsrc, t);
+  return t;
+}
+
 // index tables for the wide kernels (built once per handle and per nrhs, on the handle's stream)
 void attach_tables(wf_handle* h, LineArgs<float>& a) {
   const Geom& g = h->g;
   wf::DevBuf& nb = h->nbr_tab[a.parity];
   if (!nb.p) {
-    std::vector<int> t((size_t)g.Nl * 6);
-    for (int l = 0; l < g.Nl; ++l) neighbour_lines(g, a.parity, l, &t[(size_t)l * 6]);
+    const std::vector<int> t = build_nbr_table(g, a.parity);
     nb.ensure(t.size() * sizeof(int), h->stream);
     WF_CUDA(cudaMemcpyAsync(nb.p, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     WF_CUDA(cudaStreamSynchronize(h->stream));
   }
   auto& ob = h->order_tab[a.nrhs * 64 + a.g.by];
   if (!ob) {
-    std::vector<int2> t((size_t)a.nrhs * g.Nl);
-    for (size_t i = 0; i < t.size(); ++i) line_rhs((int)i, a.nrhs, g, t[i].x, t[i].y);
+    const std::vector<int2> t = build_order_table(a.g, a.nrhs);
     ob.reset(new wf::DevBuf());
     ob->ensure(t.size() * sizeof(int2), h->stream);
     WF_CUDA(cudaMemcpyAsync(ob->p, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
@@ -246,12 +304,7 @@ const int2* attach_units(wf_handle* h, const LineArgs<float>& a, int gsrc, int& 
   nunits = groups * g.Nl;
   auto& ub = h->unit_tab[(a.nrhs * 64 + g.by) * 4 + gsrc];
   if (!ub) {
-    std::vector<int2> t((size_t)nunits);
-    for (int pos = 0; pos < g.Nl; ++pos) {
-      int r, l;
-      line_rhs(pos, 1, g, r, l);  // with one source the order is the tiled line order itself
-      for (int k = 0; k < groups; ++k) t[(size_t)pos * groups + k] = make_int2(k * gsrc, l);
-    }
+    const std::vector<int2> t = build_unit_table(g, a.nrhs, gsrc);
     ub.reset(new wf::DevBuf());
     ub->ensure(t.size() * sizeof(int2), h->stream);
     WF_CUDA(cudaMemcpyAsync(ub->p, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
@@ -513,6 +566,21 @@ void choose_layout(Geom& g) {
   g.by = 1;
   for (int b = 1; b <= g.L && b <= max_rows; ++b)
     if (g.L % b == 0) g.by = b;
+}
+
+// the geometry and line layout of an L^3 x T lattice with the given couplings
+Geom make_geom(int L, int T, double kappa_s, double kappa_t, int bc) {
+  Geom g{};
+  g.L = L;
+  g.T = T;
+  g.Lh = L / 2;
+  g.Nl = L * L * L / 2;
+  g.mu = 1.0 / (2.0 * kappa_t);
+  g.gamma_f = kappa_t / kappa_s;
+  g.bc = (double)bc;
+  check_geometry(L, T);
+  choose_layout(g);
+  return g;
 }
 
 // ----------------------------------------------------------------------------
@@ -2661,16 +2729,7 @@ int wf_create(int L, int T, double xi, double kappa_s, double kappa_t, int bc, w
     h->xi = xi;
     h->kappa_s = kappa_s;
     h->kappa_t = kappa_t;
-    Geom& g = h->g;
-    g.L = L;
-    g.T = T;
-    g.Lh = L / 2;
-    g.Nl = L * L * L / 2;
-    g.mu = 1.0 / (2.0 * kappa_t);
-    g.gamma_f = kappa_t / kappa_s;
-    g.bc = (double)bc;
-    check_geometry(L, T);
-    choose_layout(g);
+    h->g = make_geom(L, T, kappa_s, kappa_t, bc);
     if (const char* e = std::getenv("WF_DF64")) h->df_allowed = e[0] == '1';
     WF_CUDA(cudaGetDevice(&h->device));
     WF_CUDA(cudaMallocHost(&h->host_scalars, 4096 * sizeof(double)));
@@ -3041,6 +3100,41 @@ int wf_set_max_iterations(wf_handle_t* h, int maxiter) {
 }
 
 long long wf_launch_count(const wf_handle_t* h) { return h ? h->launches : 0; }
+
+int wf_check_tables(int L, int T, int nrhs, int tile_rows, int plant) {
+  try {
+    if (nrhs < 1 || nrhs > WF_MAX_SOLVE_RHS || plant < 0 || plant > 3) return WF_EINVAL;
+    Geom g = make_geom(L, T, 0.1, 0.3, -1);
+    if (tile_rows > 0) {
+      if (tile_rows > L || L % tile_rows) return WF_EINVAL;
+      g.by = tile_rows;
+    }
+    for (int p = 0; p < 2; ++p) {
+      std::vector<int> t = build_nbr_table(g, p);
+      if (plant == 1 && p == 1) {
+        std::swap(t[0], t[t.size() - 1]);  // two lines' neighbours exchanged
+        check_nbr_table(g, p, t);
+      }
+    }
+    std::vector<int2> o = build_order_table(g, nrhs);
+    if (plant == 2) {
+      o[o.size() / 2] = o[0];  // one pair visited twice, another never
+      check_order_table(g, nrhs, o);
+    }
+    for (int gs = 1; gs <= 2; ++gs) {
+      std::vector<int2> u = build_unit_table(g, nrhs, gs);
+      if (plant == 3 && gs == 2) {
+        u.back().y = g.Nl;  // a line past the end
+        check_unit_table(g, nrhs, gs, u);
+      }
+    }
+    return WF_OK;
+  } catch (const Error& e) {
+    return e.code;
+  } catch (...) {
+    return WF_ENOMEM;
+  }
+}
 
 int wf_profile(wf_handle_t* h, int on) {
   return guarded(h, [&]() {
