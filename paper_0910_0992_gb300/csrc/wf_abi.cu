@@ -2183,57 +2183,64 @@ void clover_on(wf_handle* h, int p, const Cx<R>* in, Cx<R>* out, const Cx<R>* ac
   launch_clover_apply<R>(h->g, clover_blocks<R>(h, p), in, out, acc, alpha, nrhs, h->stream);
 }
 
-// chi = M-tilde_ILU psi for one right-hand side, by the sequence of App. B:
+// out = xpost + apost C[xpre + apre S(in)] on the lines of `parity` for one right-hand side: S the
+// site's own spinor (SRC_LOAD) or D_s of the other parity (SRC_HOP), C the line operation opu /
+// opl per spin half; xpre / xpost null: no pre- / post-axpy
+template <typename R>
+void line_step(wf_handle* h, int parity, int src, const Cx<R>* in, Cx<R>* out, int opu, int opl, const Cx<R>* xpre,
+               double apre, const Cx<R>* xpost, double apost, const char* name) {
+  LineArgs<R> a = line_args<R>(h, parity, 1);
+  a.src = src;
+  a.src_up = in;
+  a.src_lo = in + 6 * h->g.tp;
+  a.opu = opu;
+  a.opl = opl;
+  a.xpre = xpre;
+  a.apre = (R)apre;
+  a.xpost = xpost;
+  a.apost = (R)apost;
+  a.out = out;
+  // a hop followed by C_L has the compiled variant of the Schur operator's K-c (in FP32 in the
+  // axial frame: the one-thread-per-site kernel)
+  const int kind = src == SRC_HOP && opu == OP_COPY && opl == OP_BWD ? LK_SCHUR_C : LK_GENERIC;
+  Prof P(h, pname<R>(name));
+  launch_line<R>(a, kind, h->axial, h->stream);
+}
+
+// chi = M-tilde_ILU psi for one right-hand side, by the sequence of App. B
 //   t1 = g Dbar^eo psi_o, t2 = Abar^ee (t1 + psi_e), chi_e = psi_e + t2,
 //   chi_o = psi_o + Abar^oo psi_o + g Dbar^oe (t2 - t1)
+// (g = 1 / gamma_f, Dbar = C_L D_s C_R, Abar = C_L A C_R), with each line operation's axpys folded
+// into its kernel: with a = C_R^o psi_o and u = C_L^e D_s^eo a (so t1 = g u),
+//   t2 = C_L^e A^ee C_R^e (psi_e + g u),  chi_e = psi_e + t2,
+//   chi_o = [psi_o + C_L^o A^oo a] + g C_L^o D_s^oe C_R^e (t2 - g u);
+// without a clover term t2 = 0 and chi_o = psi_o - g^2 C_L^o D_s^oe C_R^e u.
 template <typename R>
 void ilu_apply(wf_handle* h, const Cx<R>* pe, const Cx<R>* po, Cx<R>* ce, Cx<R>* co) {
   const size_t hn = h->half_int();
   cudaStream_t s = h->stream;
   const double g = 1.0 / h->g.gamma_f;
-  const bool cl = h->clover;
   Cx<R>* a = h->buf<Cx<R>>(pname<R>("il_a"), hn);
-  Cx<R>* b = h->buf<Cx<R>>(pname<R>("il_b"), hn);
+  Cx<R>* u = h->buf<Cx<R>>(pname<R>("il_u"), hn);
   Cx<R>* c = h->buf<Cx<R>>(pname<R>("il_c"), hn);
   Cx<R>* d = h->buf<Cx<R>>(pname<R>("il_d"), hn);
-  Cx<R>* e = h->buf<Cx<R>>(pname<R>("il_e"), hn);
-  Cx<R>* f = h->buf<Cx<R>>(pname<R>("il_f"), hn);
-  Cx<R>* t1 = h->buf<Cx<R>>(pname<R>("il_t1"), hn);
   Cx<R>* t2 = h->buf<Cx<R>>(pname<R>("il_t2"), hn);
-  auto copy = [&](Cx<R>* dst, const Cx<R>* src) {
-    WF_CUDA(cudaMemcpyAsync(dst, src, hn * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
-  };
-  auto axpby = [&](Cx<R>* y, const Cx<R>* x, double al, double be) {  // y = al x + be y
-    Prof P(h, pname<R>("il_axpby"));
-    launch_axpby<R>(y, x, hn, al, be, s);
-  };
-  line_load<R>(h, 1, po, a, OP_FWD, OP_COPY, 1, "il_c_right");  // a = C_R^o psi_o
-  hop_to<R>(h, 0, a, b, "il_hop");
-  line_load<R>(h, 0, b, t1, OP_COPY, OP_BWD, 1, "il_c_left");
-  axpby(t1, t1, 0.0, g);  // t1 = g Dbar^eo psi_o
-  copy(ce, pe);
-  if (cl) {
-    copy(f, t1);
-    axpby(f, pe, 1.0, 1.0);  // f = t1 + psi_e
-    line_load<R>(h, 0, f, c, OP_FWD, OP_COPY, 1, "il_c_right");
+  Cx<R>* e = h->buf<Cx<R>>(pname<R>("il_e"), hn);
+  line_step<R>(h, 1, SRC_LOAD, po, a, OP_FWD, OP_COPY, nullptr, 0.0, nullptr, 0.0, "il_c_right");  // a = C_R^o psi_o
+  line_step<R>(h, 0, SRC_HOP, a, u, OP_COPY, OP_BWD, nullptr, 0.0, nullptr, 0.0, "il_hop_c_left");  // u = C_L^e D a
+  if (h->clover) {
+    line_step<R>(h, 0, SRC_LOAD, u, c, OP_FWD, OP_COPY, pe, g, nullptr, 0.0, "il_c_right");  // C_R^e (psi_e + g u)
     clover_on<R>(h, 0, c, d, nullptr, 1.0, 1);
-    line_load<R>(h, 0, d, t2, OP_COPY, OP_BWD, 1, "il_c_left");  // t2 = Abar^ee (t1 + psi_e)
-    axpby(ce, t2, 1.0, 1.0);
-    copy(f, t2);
-    axpby(f, t1, -1.0, 1.0);  // f = t2 - t1
+    line_step<R>(h, 0, SRC_LOAD, d, t2, OP_COPY, OP_BWD, nullptr, 0.0, nullptr, 0.0, "il_c_left");  // t2
+    line_step<R>(h, 0, SRC_LOAD, t2, ce, OP_COPY, OP_COPY, pe, 1.0, nullptr, 0.0, "il_axpy");  // chi_e = psi_e + t2
+    line_step<R>(h, 0, SRC_LOAD, u, c, OP_FWD, OP_COPY, t2, -g, nullptr, 0.0, "il_c_right");  // C_R^e (t2 - g u)
+    clover_on<R>(h, 1, a, d, nullptr, 1.0, 1);  // d = A^oo C_R^o psi_o
+    line_step<R>(h, 1, SRC_LOAD, d, e, OP_COPY, OP_BWD, nullptr, 0.0, po, 1.0, "il_c_left");  // psi_o + Abar^oo psi_o
+    line_step<R>(h, 1, SRC_HOP, c, co, OP_COPY, OP_BWD, nullptr, 0.0, e, g, "il_hop_c_left");
   } else {
-    copy(f, t1);
-    axpby(f, f, 0.0, -1.0);  // f = -t1
-  }
-  line_load<R>(h, 0, f, c, OP_FWD, OP_COPY, 1, "il_c_right");
-  hop_to<R>(h, 1, c, d, "il_hop");
-  line_load<R>(h, 1, d, e, OP_COPY, OP_BWD, 1, "il_c_left");  // e = Dbar^oe (t2 - t1)
-  copy(co, po);
-  axpby(co, e, g, 1.0);
-  if (cl) {
-    clover_on<R>(h, 1, a, d, nullptr, 1.0, 1);                  // d = A^oo C_R^o psi_o
-    line_load<R>(h, 1, d, e, OP_COPY, OP_BWD, 1, "il_c_left");  // e = Abar^oo psi_o
-    axpby(co, e, 1.0, 1.0);
+    WF_CUDA(cudaMemcpyAsync(ce, pe, hn * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+    line_step<R>(h, 0, SRC_LOAD, u, c, OP_FWD, OP_COPY, nullptr, 0.0, nullptr, 0.0, "il_c_right");  // C_R^e u
+    line_step<R>(h, 1, SRC_HOP, c, co, OP_COPY, OP_BWD, nullptr, 0.0, po, -g * g, "il_hop_c_left");
   }
 }
 
