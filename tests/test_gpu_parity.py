@@ -299,3 +299,34 @@ def test_solve_many_rejects_a_shared_handle():
     st, _ = wf.wf_solve_many([w.h, w.h], [eta, eta], [x, x], [1, 1], 1e-10, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)
     assert st == wf.WF_EINVAL
     w.close()
+
+
+def test_solve_with_pinned_host_arrays():
+    """Page-locked host arrays for rhs and x (staged by the library): the solution equals the one
+    from device arrays bit for bit, also with an initial guess and for a ragged call."""
+    L, T = 4, 16
+    p = W.Params(L, T, 0.075, xi=3.5, bc=-1)
+    U = S.random_gauge(L, T, 0.25, 51)
+    eta = S.gaussian_source(L, T, 52, nrhs=2)
+    w = wf.Wilson(L, T, 0.075, kappa_t=3.5 * 0.075, bc=-1)
+    try:
+        w.load_gauge(U)
+        xd = torch.empty_like(_dev(eta))
+        st, it_d, _ = wf.wf_solve(w.h, _dev(eta), xd, 2, 1e-10, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32, 0)
+        assert st == wf.WF_OK
+        rh = torch.from_numpy(np.ascontiguousarray(eta)).pin_memory()
+        xh = torch.zeros_like(rh).pin_memory()
+        st, it_h, res = wf.wf_solve(w.h, rh, xh, 2, 1e-10, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32, 0)
+        assert st == wf.WF_OK and it_h == it_d
+        assert np.array_equal(xh.numpy(), _host(xd))
+        for k in range(2):
+            assert SV.true_residual(U, xh.numpy()[k], eta[k], p) <= TRUE_RESID
+        # from the solution as initial guess (read in place) the solve stays at tol
+        st, it0, res0 = wf.wf_solve(w.h, rh, xh, 2, 1e-10, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32, wf.WF_X0)
+        assert st == wf.WF_OK and max(res0) <= 1e-10
+        # a ragged call with pinned arrays
+        xh2 = torch.zeros_like(rh).pin_memory()
+        st, per = wf.wf_solve_many([w.h], [rh], [xh2], [2], 1e-10, wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)
+        assert st == wf.WF_OK and np.array_equal(xh2.numpy(), _host(xd))
+    finally:
+        w.close()
