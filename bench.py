@@ -84,7 +84,7 @@ def paper_flops_per_apply(L, T):
 # to any of them voids the DRAM traffic recorded in profiles/traffic.json
 HOP_KERNEL_SOURCES = ("wf_abi.cu", "wf_async.cuh", "wf_common.cuh", "wf_df64.cuh", "wf_handle.h", "wf_internal.h",
                       "wf_kernels.cu", "wf_layout.cu", "wf_line.cuh", "wf_pipe.cu", "wf_wide.cu", "wf_wide.cuh",
-                      "wf_wide_body.inc")
+                      "wf_wide_body.inc", "wf_line_kernels.cuh")
 
 
 def source_hash():

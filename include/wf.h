@@ -7,7 +7,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Lattice: L^3 x T sites, spatially periodic; time boundary sign bc = +1 (periodic)
- *   or -1 (antiperiodic). L must be even and >= 2; 2 <= T <= 128.
+ *   or -1 (antiperiodic). L must be even and >= 2; 2 <= T <= 256.
  * Operator: the paper's Wilson matrix (§II, Eq. for M with A = 0)
  *       M = mu - D_t - D_s / gamma_f,   mu = 1 / (2 kappa_t),   gamma_f = kappa_t / kappa_s,
  *   i.e. 1/(2 kappa_t) times the hopping-parameter form; D_t and D_s are the temporal
@@ -79,7 +79,10 @@ enum wf_precision {
 
 /* Create a handle for an L^3 x T lattice (§II). kappa_t <= 0 selects kappa_t = xi * kappa_s.
  * bc = +1 or -1. Allocates the gauge storage on the current device. Returns WF_EINVAL for
- * odd or too small L, T outside [2, 128], kappa_s <= 0 or bc not +-1. */
+ * odd or too small L, T outside [2, 256], kappa_s <= 0 or bc not +-1. Time lines longer than 128
+ * sites run on the n-sites-per-lane kernels only (up to 8 sites per lane): FP64 and FP32 solves
+ * and applies; FP16MIX, the one-thread-per-site and bulk-fed hop kernels and joint ragged solves
+ * need T <= 128. */
 int wf_create(int L, int T, double xi, double kappa_s, double kappa_t, int bc, wf_handle_t** out);
 
 /* Host-only check (no GPU needed) of the index tables the kernels use for an L^3 x T lattice with

@@ -533,13 +533,15 @@ void m_apply(wf_handle* h, const Cx<R>* in_e, const Cx<R>* in_o, Cx<R>* out_e, C
 
 void check_geometry(int L, int T) {
   if (L < 2 || (L & 1)) throw Error(WF_EINVAL, "L must be even and >= 2");
-  if (T < 2 || T > 128) throw Error(WF_EINVAL, "T must lie in [2, 128]");
+  if (T < 2 || T > 256) throw Error(WF_EINVAL, "T must lie in [2, 256]");
 }
 
-// choose sites per lane n and lanes per line lpl (power of two <= 32) with minimal padding
+// choose sites per lane n and lanes per line lpl (power of two <= 32) with minimal padding; n <= 4
+// (the layouts of the fast kernels) whenever T <= 128, else up to 8 (the line kernel's long-line
+// variant)
 void choose_layout(Geom& g) {
   int best_tp = 1 << 30, best_n = 0, best_lpl = 0;
-  for (int n = 1; n <= 4; ++n) {
+  for (int n = 1; n <= (g.T <= 32 * NMAX ? NMAX : NMAX_LONG); ++n) {
     int need = (g.T + n - 1) / n;
     int lpl = 1;
     while (lpl < need) lpl <<= 1;
@@ -2724,7 +2726,7 @@ extern "C" {
 int wf_create(int L, int T, double xi, double kappa_s, double kappa_t, int bc, wf_handle_t** out) {
   if (!out) return WF_EINVAL;
   *out = nullptr;
-  if (L < 2 || (L & 1) || T < 2 || T > 128) return WF_EINVAL;
+  if (L < 2 || (L & 1) || T < 2 || T > 256) return WF_EINVAL;
   if (!(kappa_s > 0) || (bc != 1 && bc != -1)) return WF_EINVAL;
   if (!(kappa_t > 0)) {
     if (!(xi > 0)) return WF_EINVAL;

@@ -111,6 +111,11 @@ struct MArgs {
 };
 template <typename R>
 void launch_apply_M(const MArgs<R>& a, bool axial, cudaStream_t s);
+// the long-line variants (lines of 129 to 256 slots; wf_kernels_long_f32.cu, wf_kernels_long_f64.cu)
+template <typename R>
+void launch_line_long(const LineArgs<R>& a, int kind, bool axial, cudaStream_t s);
+template <typename R>
+void launch_apply_M_long(const MArgs<R>& a, bool axial, cudaStream_t s);
 
 // layout conversions
 // g_e / g_o (or gr): per-parity colour rotations of the axial frame, [l][9][tp] FP64, or null

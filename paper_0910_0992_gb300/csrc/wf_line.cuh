@@ -30,7 +30,8 @@
 
 namespace wf {
 
-constexpr int NMAX = 4;  // sites per lane, at most (T <= 32 * NMAX)
+constexpr int NMAX = 4;       // sites per lane of the fast kernels (T <= 32 * NMAX)
+constexpr int NMAX_LONG = 8;  // sites per lane of the n-sites-per-lane kernels' long-line variant (T <= 256)
 
 enum LineOp { OP_COPY = 0, OP_FWD = 1, OP_BWD = 2, OP_SKIP = 3 };
 enum LineSrc { SRC_LOAD = 0, SRC_HOP = 1 };
@@ -383,13 +384,13 @@ __device__ __forceinline__ Vec3<R> vshfl_idx(const Vec3<R>& v, int src, int w) {
 // FWD = false: psi = T^-1 eta. FWD = true: psi = T^-dag eta. v holds eta on entry and
 // psi on exit. ut_line: this line's U_t block ([9][tp]); lam: its Lambda. Warp-collective.
 // ----------------------------------------------------------------------------
-template <typename R, int NS, bool FWD>
-__device__ __forceinline__ void tline_solve_general(Vec3<R> (&v)[NMAX][NS], const Cx<R>* __restrict__ ut_line,
+template <typename R, int NS, bool FWD, int NM>
+__device__ __forceinline__ void tline_solve_general(Vec3<R> (&v)[NM][NS], const Cx<R>* __restrict__ ut_line,
                                                     const Cx<R>* __restrict__ lam, const Geom& g, int jj, R inv_mu,
                                                     R bc) {
   const int T = g.T, tp = g.tp, lpl = g.lpl, n = g.n;
   constexpr bool KEEPU = (sizeof(R) == 4);
-  Mat3<R> Uk[KEEPU ? NMAX : 1];
+  Mat3<R> Uk[KEEPU ? NM : 1];
 
   auto link_slot = [&](int m) {
     int t = jj * n + m;
@@ -404,8 +405,8 @@ __device__ __forceinline__ void tline_solve_general(Vec3<R> (&v)[NMAX][NS], cons
   for (int s = 0; s < NS; ++s) c[s] = vzero<R>();
   bool any = false;
 #pragma unroll
-  for (int q = 0; q < NMAX; ++q) {
-    const int m = FWD ? q : NMAX - 1 - q;
+  for (int q = 0; q < NM; ++q) {
+    const int m = FWD ? q : NM - 1 - q;
     if (!site_valid(m)) continue;
     Mat3<R> U = ldmat(ut_line, tp, link_slot(m));
     if (KEEPU) Uk[KEEPU ? m : 0] = U;
@@ -456,8 +457,8 @@ __device__ __forceinline__ void tline_solve_general(Vec3<R> (&v)[NMAX][NS], cons
   }
 
 #pragma unroll
-  for (int q = 0; q < NMAX; ++q) {
-    const int m = FWD ? q : NMAX - 1 - q;
+  for (int q = 0; q < NM; ++q) {
+    const int m = FWD ? q : NM - 1 - q;
     if (!site_valid(m)) continue;
     Mat3<R> U = KEEPU ? Uk[KEEPU ? m : 0] : ldmat(ut_line, tp, link_slot(m));
 #pragma unroll
@@ -475,8 +476,8 @@ __device__ __forceinline__ void tline_solve_general(Vec3<R> (&v)[NMAX][NS], cons
 // the value entering its bottom is P^dag s psi(N_t-1) (T^-dag). Closure: psi(0) = Lambda C_0,
 // psi(N_t-1) = Lambda^dag C_last, since (1 - s mu^-N_t P^dag)^-1 = Lambda^dag.
 // ----------------------------------------------------------------------------
-template <typename R, int NS, bool FWD>
-__device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NMAX][NS], const Cx<R>* __restrict__ P_line,
+template <typename R, int NS, bool FWD, int NM>
+__device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NM][NS], const Cx<R>* __restrict__ P_line,
                                                   const Cx<R>* __restrict__ lam, const Geom& g, int jj, R inv_mu, R bc) {
   const int T = g.T, lpl = g.lpl, n = g.n;
   auto site_valid = [&](int m) { return m < n && jj * n + m < T; };
@@ -486,8 +487,8 @@ __device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NMAX][NS], const 
 #pragma unroll
   for (int s = 0; s < NS; ++s) c[s] = vzero<R>();
 #pragma unroll
-  for (int q = 0; q < NMAX; ++q) {
-    const int m = FWD ? q : NMAX - 1 - q;
+  for (int q = 0; q < NM; ++q) {
+    const int m = FWD ? q : NM - 1 - q;
     if (!site_valid(m)) continue;
 #pragma unroll
     for (int s = 0; s < NS; ++s) c[s] = vscale(inv_mu, vadd(v[m][s], c[s]));
@@ -532,8 +533,8 @@ __device__ __forceinline__ void tline_solve_axial(Vec3<R> (&v)[NMAX][NS], const 
   }
 
 #pragma unroll
-  for (int q = 0; q < NMAX; ++q) {
-    const int m = FWD ? q : NMAX - 1 - q;
+  for (int q = 0; q < NM; ++q) {
+    const int m = FWD ? q : NM - 1 - q;
     if (!site_valid(m)) continue;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -569,14 +570,14 @@ __device__ __forceinline__ void isigma(int k, const Vec3<R>& a0, const Vec3<R>& 
 //   (1 + gamma_k) psi = (h, +i sigma_k h), h = u - i sigma_k d,
 // so each direction costs two SU(3) matvecs on a half-spinor (App. B: 984 FLOPs/site).
 // ----------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArgs<R>& A, int rhs, int l, int jj) {
+template <typename R, int NM>
+__device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NM][4], const LineArgs<R>& A, int rhs, int l, int jj) {
   const Geom& g = A.g;
   const int tp = g.tp, Nl = g.Nl, T = g.T, n = g.n;
   int nb[6];
   neighbour_lines(g, A.parity, l, nb);
 #pragma unroll
-  for (int m = 0; m < NMAX; ++m)
+  for (int m = 0; m < NM; ++m)
 #pragma unroll
     for (int s = 0; s < 4; ++s) h[m][s] = vzero<R>();
 
@@ -591,7 +592,7 @@ __device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArg
       const Cx<R>* lk = dir == 0 ? A.us_out + (size_t)(k * Nl + l) * LNC * tp
                                  : A.us_nbr + (size_t)(k * Nl + ln) * LNC * tp;
 #pragma unroll
-      for (int m = 0; m < NMAX; ++m) {
+      for (int m = 0; m < NM; ++m) {
         if (m >= n || jj * n + m >= T) continue;
         const int sl = m * g.lpl + jj;
         Vec3<R> u0 = ldvec(up, tp, sl), u1 = ldvec(up + 3 * tp, tp, sl);
@@ -624,7 +625,7 @@ __device__ __forceinline__ void hop_spatial(Vec3<R> (&h)[NMAX][4], const LineArg
     }
   }
 #pragma unroll
-  for (int m = 0; m < NMAX; ++m)
+  for (int m = 0; m < NM; ++m)
 #pragma unroll
     for (int s = 0; s < 4; ++s) h[m][s] = vscale(R(0.5), h[m][s]);
 }

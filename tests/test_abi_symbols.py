@@ -32,5 +32,5 @@ def test_create_rejects_bad_geometry_without_gpu():
     import paper_0910_0992_gb300 as wf
 
     h = ctypes.c_void_p()
-    for L, T, ks, bc in [(3, 8, 0.1, -1), (4, 1, 0.1, -1), (4, 200, 0.1, -1), (4, 8, -0.1, -1), (4, 8, 0.1, 0)]:
+    for L, T, ks, bc in [(3, 8, 0.1, -1), (4, 1, 0.1, -1), (4, 300, 0.1, -1), (4, 8, -0.1, -1), (4, 8, 0.1, 0)]:
         assert wf.lib.wf_create(L, T, 3.0, ks, 0.0, bc, ctypes.byref(h)) == wf.WF_EINVAL

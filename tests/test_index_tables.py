@@ -15,8 +15,8 @@ def _divisors(L):
 
 @pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 16, 24])
 def test_tables_valid_for_every_layout(L):
-    for T in (2, 3, 7, 16, 24, 33, 48, 64, 96, 100, 128):
-        if L >= 16 and T not in (16, 64, 128):
+    for T in (2, 3, 7, 16, 24, 33, 48, 64, 96, 100, 128, 129, 160, 200, 256):
+        if L >= 16 and T not in (16, 64, 128, 256):
             continue  # the large lattices at a few line lengths keep the test quick
         for nrhs in (1, 3, 12):
             for rows in [0] + _divisors(L):
@@ -34,3 +34,4 @@ def test_invalid_arguments():
     assert wf.wf_check_tables(4, 16, 0, 0) == wf.WF_EINVAL   # no sources
     assert wf.wf_check_tables(5, 16, 1, 0) == wf.WF_EINVAL   # odd L
     assert wf.wf_check_tables(4, 16, wf.WF_MAX_SOLVE_RHS + 1, 0) == wf.WF_EINVAL
+    assert wf.wf_check_tables(4, 257, 1, 0) == wf.WF_EINVAL  # longer than 32 lanes x 8 sites
