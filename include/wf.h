@@ -298,8 +298,9 @@ int wf_temporal_logdet(wf_handle_t* h, double* logdet, double* F);
 int wf_hop_config(wf_handle_t* h, int nrhs, int* variant, int* tile_rows, float* ms);
 int wf_hop_pipe_config(wf_handle_t* h, int nrhs, int* sources_per_unit, int* stages);
 
-/* CG iteration limit of every later solve and force on h (no counterpart in the paper):
- * maxiter >= 1, or 0 for the default 100000. WF_EINVAL if maxiter < 0. */
+/* CG iteration limit of every later solve and force on h (no counterpart in the paper; for a
+ * defect-correction solve the iterations of all its passes together): maxiter >= 1, or 0 for the
+ * default 100000. WF_EINVAL if maxiter < 0. */
 int wf_set_max_iterations(wf_handle_t* h, int maxiter);
 
 /* Number of kernels this handle has launched since it was created (all entry points). */

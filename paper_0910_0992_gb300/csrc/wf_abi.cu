@@ -1635,9 +1635,14 @@ void solve_temporal_schur_dc(int nl, wf_handle* const* hs, const std::vector<con
       }
     }
     sync.fan_in(parts);
+    // the iteration limit holds for the passes together
+    int used = 0;
+    for (int j = 0; j < nl; ++j)
+      for (int k = 0; k < parts[j].nrhs; ++k) used = std::max(used, iters[j][k]);
+    const int left = std::max(1, maxiter - used);
     const std::vector<int> it =
-        h16 ? cgnr_h16(h0, nr, nmax, b, y, target, maxiter, false, false)
-            : cgnr<float>(h0, A, A64, b, y, nr, nmax, target, maxiter, false, joint ? ntot : 0, offs, false);
+        h16 ? cgnr_h16(h0, nr, nmax, b, y, target, left, false, false)
+            : cgnr<float>(h0, A, A64, b, y, nr, nmax, target, left, false, joint ? ntot : 0, offs, false);
     sync.fan_out(parts);
     // S_R in FP32: d_o = C_R^o y_o ; d_e = C_R^e C_L^e [r_e + gamma_f^-1 D_s^eo d_o] ; psi += d ;
     // r = eta - M psi in FP64

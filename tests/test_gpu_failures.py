@@ -56,14 +56,19 @@ def test_nan_in_source_reports_enan(precision):
         w.close()
 
 
-@pytest.mark.parametrize("method", [wf.WF_TEMPORAL_SCHUR, wf.WF_EO4D])
-def test_iteration_cap_reports_enoconv_with_outputs_written(method):
+@pytest.mark.parametrize("method,precision", [(wf.WF_TEMPORAL_SCHUR, wf.WF_FP64), (wf.WF_EO4D, wf.WF_FP64),
+                                              (wf.WF_TEMPORAL_SCHUR, wf.WF_FP32)])
+def test_iteration_cap_reports_enoconv_with_outputs_written(method, precision):
+    """The iteration limit ends a solve with WF_ENOCONV and the last iterate written (FP32 temporal +
+    Schur: defect correction, whose passes share the limit)."""
     p, U, eta, w = _setup()
     try:
         wf.wf_set_max_iterations(w.h, 3)
         x0 = torch.full((2, eta[0].size), complex(np.nan, np.nan), dtype=torch.complex128).cuda()
-        st, iters, res = wf.wf_solve(w.h, _dev(eta).reshape(2, -1), x0, 2, 1e-10, method, wf.WF_FP64, 0)
+        st, iters, res = wf.wf_solve(w.h, _dev(eta).reshape(2, -1), x0, 2, 1e-10, method, precision, 0)
         assert st == wf.WF_ENOCONV
+        if precision == wf.WF_FP32:
+            assert all(0 < i <= 3 for i in iters)  # the passes share the limit
         assert all(0 < i <= 3 * 6 for i in iters)  # at most the cap per pass, a few passes
         xs = x0.cpu().numpy().reshape(eta.shape)
         assert np.isfinite(xs).all()
