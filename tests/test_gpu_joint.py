@@ -207,3 +207,25 @@ def test_solve_rejects_too_many_sources():
         assert e.value.code == wf.WF_EINVAL
     finally:
         w.close()
+
+
+@pytest.mark.parametrize("precision", [wf.WF_FP32, wf.WF_FP64])
+def test_solve_at_the_source_limit(precision):
+    """WF_MAX_SOLVE_RHS sources in one solve (a 2^3 x 4 lattice): every source converges, sampled
+    sources meet the oracle's true residual, and the CG bookkeeping of the last source is right."""
+    L, T = 2, 4
+    p = W.Params(L, T, 0.075, xi=3.0, bc=-1)
+    U = S.random_gauge(L, T, 0.3, 97)
+    m = wf.WF_MAX_SOLVE_RHS
+    eta = S.gaussian_source(L, T, 98, nrhs=m)
+    eta[m - 1] *= 1e-3  # the last source at another scale
+    w = wf.Wilson(L, T, 0.075, kappa_t=0.225, bc=-1)
+    try:
+        w.load_gauge(U)
+        x, iters, res, status = w.solve(_dev(eta), tol=1e-10, precision=precision)
+        assert status == wf.WF_OK and len(iters) == m and max(res) <= 1e-10 and min(iters) > 0
+        psi = x.cpu().numpy()
+        for k in (0, 1, m // 2, m - 2, m - 1):
+            assert SV.true_residual(U, psi[k], eta[k], p) <= TRUE_RESID
+    finally:
+        w.close()
