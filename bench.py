@@ -552,13 +552,19 @@ def apply_roofline(wf, torch, w, nrhs, op, odd_sites, peak, steps=10):
 
 
 def _timed_solve(wf, torch, w, stream, rhs, x, method, prec, tol, reps=1):
-    """(seconds per solve, iterations, true residuals) after one warm-up solve."""
+    """(seconds per solve, iterations, true residuals) after one warm-up solve; method "full_sw":
+    wf_solve_full_sw."""
     nr = rhs.shape[0]
-    wf.wf_solve(w.h, rhs, x, nr, tol, method, prec, 0)
+
+    def call():
+        if method == "full_sw":
+            return wf.wf_solve_full_sw(w.h, rhs, x, nr, tol, prec)
+        return wf.wf_solve(w.h, rhs, x, nr, tol, method, prec, 0)
+    call()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        st, it, res = wf.wf_solve(w.h, rhs, x, nr, tol, method, prec, 0)
+        st, it, res = call()
     e1.record(stream)
     torch.cuda.synchronize()
     if st != wf.WF_OK or max(res) > tol:
@@ -767,11 +773,15 @@ def run_clover(args):
         rows.append({"operator": "wilson", "method": "temporal_schur", "precision": pname, "iterations": it[0],
                      "time_s": t, "true_residual": res[0]})
     w.load_gauge_clover(U, c_s, c_t)
-    for method in (wf.WF_TEMPORAL_ILU, wf.WF_EO4D):
+    for method in (wf.WF_TEMPORAL_ILU, wf.WF_EO4D, "full_sw"):
         for prec, pname in ((wf.WF_FP64, "fp64"), (wf.WF_FP32, "fp32")):
             t, it, res = _timed_solve(wf, torch, w, stream, rhs, x, method, prec, args.tol)
-            rows.append({"operator": "clover", "method": METHOD_NAMES[method], "precision": pname,
+            rows.append({"operator": "clover", "method": METHOD_NAMES.get(method, method), "precision": pname,
                          "iterations": it[0], "time_s": t, "true_residual": res[0]})
+    wf.wf_profile(w.h, 1)
+    wf.wf_solve_full_sw(w.h, rhs, x, 1, args.tol, wf.WF_FP32)
+    prof_full = wf.wf_profile_get(w.h)
+    wf.wf_profile(w.h, 0)
     wf.wf_profile(w.h, 1)
     wf.wf_solve(w.h, rhs, x, 1, args.tol, wf.WF_TEMPORAL_ILU, wf.WF_FP32, 0)
     prof = wf.wf_profile_get(w.h)
@@ -785,10 +795,19 @@ def run_clover(args):
     if ca:
         gbs = 768.0 * sites / (ca["avg_ms"] * 1e-3) / 1e9
         ca.update({"gbs": gbs, "hbm_frac": gbs / peak, "hbm_peak": kind})
+    kfull = {}
+    for k, (n, ms) in sorted(prof_full.items(), key=lambda kv: -kv[1][1]):
+        kfull[k] = {"launches": n, "total_ms": ms, "avg_ms": ms / n}
+    qa = kfull.get("qinv_apply_f32")
+    if qa:
+        # one source: per site the 12x12 block Sigma_t^-1 read once (1152 B in FP32; the kernel's
+        # four sweeps read it twice whole and twice half) and the spinor in and out (96 B each)
+        gbs = (1152.0 + 2 * 96.0) * sites / (qa["avg_ms"] * 1e-3) / 1e9
+        qa.update({"gbs": gbs, "hbm_frac": gbs / peak, "hbm_peak": kind})
     w.close()
     print(json.dumps({"mode": "clover", "workload": f"{name}: 16^3x128, xi=3.5, 1 Gaussian source",
                       "c_s": c_s, "c_t": c_t, "u_s": u_s, "tol": args.tol, "results": rows,
-                      "kernels_one_fp32_ilu_solve": kern}))
+                      "kernels_one_fp32_ilu_solve": kern, "kernels_one_fp32_full_sw_solve": kfull}))
     return 0
 
 

@@ -261,6 +261,37 @@ int wf_apply_clover(wf_handle_t* h, const double* in, double* out, int nrhs);
 int wf_apply_ilu(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 int wf_apply_ilu_f32(wf_handle_t* h, const double* in, double* out, int dagger, int nrhs);
 
+/* Full SW temporal preconditioning (§II.A, the paragraphs on SW fermions; appendix "Full
+ * Preconditioning with Clover"): the whole temporal block Q = A + mu - D_t of every spatial line,
+ * clover term included, is inverted, and the 3-D Schur operator on odd sites is
+ *   M-hat_full = 1 - gamma_f^-2 (Q^oo)^-1 D_s^oe (Q^ee)^-1 D_s^eo
+ * (Eq. TPrecFull with C_L = Q^-1, C_R = 1). A is the term of wf_load_gauge_clover, or 0 if none is
+ * loaded (then Q = mu - D_t = C_L^-1 C_R^-1). Q^-1 is the appendix's single Woodbury step
+ * Q = T_0 + V W^dag around the open chain T_0, which the library factors by block LU (FP64, on
+ * every call of these entry points: about 2.3 KB per site of device memory, and half again for the
+ * FP32 entry points) instead of the paper's inner CG.
+ * wf_apply_Qinv: out = Q^-1 in on full fields [rhs][V][spin][colour]; _f32: FP32 applies.
+ * wf_apply_schur_full_sw: out = M-hat_full in (dagger: its adjoint) on odd fields as for
+ *   wf_apply_schur; _f32: FP32 arithmetic.
+ * wf_solve_full_sw: M_SW x = rhs (M_SW = M + A) on full fields by CGNR on M-hat_full with
+ *   b = (Q^oo)^-1 (rhs_o + gamma_f^-1 D_s^oe (Q^ee)^-1 rhs_e) and x_e = (Q^ee)^-1 (rhs_e +
+ *   gamma_f^-1 D_s^eo x_o), in defect-correction passes (at most 8) that each solve for the FP64
+ *   true residual r = rhs - M_SW x in `precision` (WF_FP64, or WF_FP32 with passes to 1e-5) and add
+ *   the correction in FP64, until |r_k| <= tol |rhs_k| for every right-hand side; the handle's
+ *   iteration limit bounds all passes together. iters_out[k] (CG iterations of right-hand side k)
+ *   and true_resid_out[k] (host, may be null) are written for every k.
+ * Arrays may be host or device memory of the handle's GPU (staged if on the host); in and out must
+ * not overlap. Errors: WF_EINVAL (no gauge field, nrhs outside [1, WF_MAX_SOLVE_RHS], tol <= 0,
+ * precision other than WF_FP64 / WF_FP32), WF_ESINGULAR (a block of the factorisation, or the
+ * 12x12 Woodbury matrix of a line, has no inverse), WF_ENAN (a non-finite norm in the solve),
+ * WF_ENOCONV (iteration limit or 8 passes reached; x holds the last iterate). */
+int wf_apply_Qinv(wf_handle_t* h, const double* in, double* out, int nrhs);
+int wf_apply_Qinv_f32(wf_handle_t* h, const double* in, double* out, int nrhs);
+int wf_apply_schur_full_sw(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+int wf_apply_schur_full_sw_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs);
+int wf_solve_full_sw(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int precision,
+                     int* iters_out, double* true_resid_out);
+
 /* Pseudofermion force of the temporally preconditioned operator. For the action
  *   S = phi^dag (M-hat^dag M-hat)^-1 phi,   phi an odd field (as for wf_apply_schur, one source),
  * writes F[t][z][y][x][mu][a] (real, 8 per link, mu = x, y, z, t) = dS/d eps for the perturbation

@@ -16,6 +16,6 @@ from ._lib import (  # noqa: F401
     WFError, lib, lib_path, exported_symbols,
     wf_create, wf_destroy, wf_set_stream, wf_last_error, wf_set_gauge_frame, wf_field_elems, wf_half_elems,
     wf_load_gauge, wf_load_gauge_clover, wf_apply_clover, wf_apply_ilu, wf_apply_ilu_f32, wf_apply_M, wf_apply_M_f32, wf_apply_Tinv, wf_apply_Tinv_f32, wf_apply_C,
-    wf_apply_schur, wf_apply_schur_f32, wf_apply_schur_f16, wf_apply_schur_noalloc, wf_apply_eo4d, wf_apply_eo4d_f32, wf_solve, wf_solve_many, wf_force, wf_temporal_logdet, wf_launch_count, wf_check_tables, wf_hop_config, wf_hop_pipe_config, wf_set_max_iterations, wf_profile, wf_profile_get,
+    wf_apply_schur, wf_apply_schur_f32, wf_apply_schur_f16, wf_apply_schur_noalloc, wf_apply_eo4d, wf_apply_eo4d_f32, wf_apply_Qinv, wf_apply_Qinv_f32, wf_apply_schur_full_sw, wf_apply_schur_full_sw_f32, wf_solve_full_sw, wf_solve, wf_solve_many, wf_force, wf_temporal_logdet, wf_launch_count, wf_check_tables, wf_hop_config, wf_hop_pipe_config, wf_set_max_iterations, wf_profile, wf_profile_get,
     Wilson,
 )

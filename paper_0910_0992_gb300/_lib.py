@@ -48,6 +48,11 @@ _SIGS = {
     "wf_apply_clover": (_i, [_vp, _vp, _vp, _i]),
     "wf_apply_ilu": (_i, [_vp, _vp, _vp, _i, _i]),
     "wf_apply_ilu_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_Qinv": (_i, [_vp, _vp, _vp, _i]),
+    "wf_apply_Qinv_f32": (_i, [_vp, _vp, _vp, _i]),
+    "wf_apply_schur_full_sw": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_apply_schur_full_sw_f32": (_i, [_vp, _vp, _vp, _i, _i]),
+    "wf_solve_full_sw": (_i, [_vp, _vp, _vp, _i, _d, _i, _ip, _dp]),
     "wf_solve_many": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _d, _i, _i, _i,
                            ctypes.POINTER(_ip), ctypes.POINTER(_dp), _ip]),
     "wf_launch_count": (ctypes.c_longlong, [_vp]),
@@ -162,6 +167,26 @@ wf_apply_schur_f16 = _apply(lib.wf_apply_schur_f16)
 wf_apply_schur_noalloc = _apply(lib.wf_apply_schur_noalloc)
 wf_apply_eo4d = _apply(lib.wf_apply_eo4d)
 wf_apply_eo4d_f32 = _apply(lib.wf_apply_eo4d_f32)
+wf_apply_schur_full_sw = _apply(lib.wf_apply_schur_full_sw)
+wf_apply_schur_full_sw_f32 = _apply(lib.wf_apply_schur_full_sw_f32)
+
+
+def wf_apply_Qinv(h, inp, out, nrhs=1):
+    return _check(h, lib.wf_apply_Qinv(h, _ptr(inp), _ptr(out), int(nrhs)))
+
+
+def wf_apply_Qinv_f32(h, inp, out, nrhs=1):
+    return _check(h, lib.wf_apply_Qinv_f32(h, _ptr(inp), _ptr(out), int(nrhs)))
+
+
+def wf_solve_full_sw(h, rhs, x, nrhs, tol, precision=WF_FP64):
+    """Returns (status, iterations[nrhs], true_residual[nrhs]); raises on errors other than WF_ENOCONV."""
+    iters = (ctypes.c_int * nrhs)()
+    res = (ctypes.c_double * nrhs)()
+    code = lib.wf_solve_full_sw(h, _ptr(rhs), _ptr(x), int(nrhs), float(tol), int(precision), iters, res)
+    if code not in (WF_OK, WF_ENOCONV):
+        _check(h, code)
+    return code, list(iters), list(res)
 
 
 def wf_solve(h, rhs, x, nrhs, tol, method, precision, flags=0):
@@ -358,6 +383,23 @@ class Wilson:
         (wf_apply_eo4d_f32 if f32 else wf_apply_eo4d)(self.h, x_odd4, out, dagger,
                                                        self._nrhs(x_odd4, wf_half_elems(self.h)))
         return out
+
+    def apply_Qinv(self, x, f32=False):
+        """(A + mu - D_t)^-1 on full fields (clover term of load_gauge_clover; A = 0 without one)."""
+        out = self._like(x)
+        (wf_apply_Qinv_f32 if f32 else wf_apply_Qinv)(self.h, x, out, self._nrhs(x, wf_field_elems(self.h)))
+        return out
+
+    def apply_schur_full_sw(self, x_odd, dagger=False, f32=False):
+        out = self._like(x_odd)
+        (wf_apply_schur_full_sw_f32 if f32 else wf_apply_schur_full_sw)(self.h, x_odd, out, dagger,
+                                                                         self._nrhs(x_odd, wf_half_elems(self.h)))
+        return out
+
+    def solve_full_sw(self, rhs, tol=1e-10, precision=WF_FP64):
+        x = self._like(rhs)
+        status, iters, res = wf_solve_full_sw(self.h, rhs, x, self._nrhs(rhs, wf_field_elems(self.h)), tol, precision)
+        return x, iters, res, status
 
     def temporal_logdet(self, F=None):
         """log det(mu - D_t) of the loaded gauge field (F, if given, receives its force)."""

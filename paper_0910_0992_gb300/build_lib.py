@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwf.so")
 SOURCES = ["wf_kernels.cu", "wf_layout.cu", "wf_blas.cu", "wf_abi.cu", "wf_noalloc.cu", "wf_eo4d.cu", "wf_force.cu", "wf_tma.cu", "wf_wide.cu", "wf_wide_df.cu", "wf_pipe.cu", "wf_det.cu", "wf_clover.cu",
-           "wf_kernels_long_f32.cu", "wf_kernels_long_f64.cu"]
+           "wf_kernels_long_f32.cu", "wf_kernels_long_f64.cu", "wf_fullsw.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function"]

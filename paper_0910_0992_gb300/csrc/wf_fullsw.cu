@@ -1,0 +1,907 @@
+// Full SW temporal preconditioning (§II.A, the paragraphs on SW fermions; appendix "Full
+// Preconditioning with Clover"): the temporal block Q = A + mu - D_t of every spatial line, the
+// clover term included, is inverted whole, and the 3-D Schur operator on odd sites becomes
+//
+//   M-hat_full = 1 - gamma_f^-2 (Q^oo)^-1 D_s^oe (Q^ee)^-1 D_s^eo,
+//
+// the form of Eq. TPrecFull with the one-sided split C_L = Q^-1, C_R = 1 (any split of Q leaves
+// Q-bar = 1). Its adjoint follows from the gamma_5-hermiticity of Q and D_s:
+//   M-hat_full^dag = 1 - gamma_f^-2 gamma_5 D_s^oe (Q^ee)^-1 D_s^eo (Q^oo)^-1 gamma_5,
+// with gamma_5 = -S (S exchanges the spin halves of the Dirac-Pauli basis), so the two signs cancel.
+//
+// Q on one line is block tridiagonal in time with 12x12 blocks, closed by two wrap couplings. The
+// appendix writes Q = T_0 + V W^dag, T_0 the open chain and V W^dag the wrap (rank 12: the P_+ half
+// of slot 0 couples to slot N_t - 1, the P_- half of slot N_t - 1 to slot 0; V carries -s U_w^dag
+// and -s U_w, U_w the link from N_t - 1 to 0, s the boundary sign; W^dag = (P_-, 0, .., 0, P_+)),
+// and inverts it by one Woodbury step
+//   Q^-1 = T_0^-1 - T_0^-1 V Lambda W^dag T_0^-1,   Lambda = (1 + W^dag T_0^-1 V)^-1.
+// The paper solves T_0 by an inner CG. Here T_0 is factored once per gauge field by block LU
+// (the block Thomas recursion), which its projector couplings make cheap: with W_t the link from
+// t to t + 1 (1 in the axial frame),
+//   Sigma_0 = mu + A(0),
+//   Sigma_t = mu + A(t) - [P_+ (x) W_{t-1}^dag] Sigma_{t-1}^-1 [P_- (x) W_{t-1}]   (t >= 1),
+// so Sigma_t differs from the diagonal block only in its (P_+ rows, P_- columns) corner. One
+// solve T_0 y = b is a forward sweep
+//   z_0 = b_0,   z_t = b_t + [P_+ (x) W_{t-1}^dag] Sigma_{t-1}^-1 z_{t-1}
+// (only the P_+ half of Sigma_{t-1}^-1 z_{t-1} is needed) and a backward sweep
+//   y_{N_t-1} = Sigma_{N_t-1}^-1 z_{N_t-1},   y_t = Sigma_t^-1 (z_t + [P_- (x) W_t] y_{t+1}),
+// and Q^-1 b takes two solves: chi = T_0^-1 b, c = Lambda W^dag chi (W^dag chi: the P_+ half of
+// chi_{N_t-1} and the P_- half of chi_0), then Q^-1 b = T_0^-1 (b - V c).
+//
+// Kernels. k_qinv_setup (FP64, one CTA per line): Sigma_t^-1 for every t by Gauss-Jordan
+// elimination with partial pivoting in shared memory, then the twelve columns of T_0^-1 V by the
+// sweeps (one 16-lane group per column, the forward sweep's z in a global scratch array), then
+// Lambda. k_qinv_apply (FP64 or FP32): one 16-lane group per (line, right-hand side), lane r < 12
+// holding component r (= 3 spin + colour) of the current 12-vector; a sweep step is a 12x12 (6x12
+// in the forward sweep) product whose vector the group exchanges through shared memory. The groups
+// of a CTA hold consecutive right-hand sides of one line, so its blocks come from DRAM once for
+// all of them. Blocks are stored transposed per time slice, [line][t][k][r], so that the twelve
+// lanes of a group read one column k of the block as 12 consecutive elements.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/wf.h"
+#include "wf_handle.h"
+#include "wf_line.cuh"
+
+namespace wf {
+
+namespace {
+
+constexpr int kGrp = 16;                       // lanes per 12-vector group
+constexpr int kApplyThreads = 128;             // 8 groups per CTA
+constexpr int kSetupThreads = 12 * kGrp;       // one group per column of V
+constexpr int kBlk = 144;                      // entries of a 12x12 block
+constexpr size_t kScratchBytes = 256u << 20;   // bound of the setup's sweep scratch per launch
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cconj(Cx<R> a) { return mk<R>(a.re, -a.im); }
+
+// row r of the transposed 12x12 block B (element (r, k) at B[12 k + r]) times the group's vector v
+template <typename R>
+__device__ __forceinline__ Cx<R> row_times(const Cx<R>* __restrict__ B, int r, const Cx<R>* v) {
+  Cx<R> acc = czero<R>();
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc = cfma(acc, B[12 * k + r], v[k]);
+  return acc;
+}
+
+// One solve T_0 y = b on one line by a 16-lane group: lane r < 12 holds component r, lanes 12-15
+// only join the group's barriers (mask). S: the line's Sigma_t^-1 blocks [T][144]; ut: the line's
+// U_t [9][tp] (general frame; unused in the axial frame, where W_t = 1). rhs(t): component r of
+// b_t; zst / zld: store / load component r of the forward sweep's z_t; out(t, y): component r of
+// y_t, produced for t = N_t - 1 down to 0. sh: the group's 16-element exchange vector.
+template <typename R, bool AX, class RhsF, class ZSt, class ZLd, class OutF>
+__device__ __forceinline__ void t0_solve(const Cx<R>* __restrict__ S, const Cx<R>* __restrict__ ut, const Geom& g,
+                                         int r, unsigned mask, Cx<R>* sh, RhsF rhs, ZSt zst, ZLd zld, OutF out) {
+  const int T = g.T;
+  const bool act = r < 12;
+  const int sr = r / 3, cr = r - 3 * (r / 3);  // spin and colour of component r
+  Cx<R> z = act ? rhs(0) : czero<R>();
+  if (act) zst(0, z);
+  for (int t = 1; t < T; ++t) {
+    if (act) sh[r] = z;
+    __syncwarp(mask);
+    const Cx<R> w = r < 6 ? row_times(S + (size_t)(t - 1) * kBlk, r, sh) : czero<R>();
+    __syncwarp(mask);
+    if (r < 6) sh[r] = w;
+    __syncwarp(mask);
+    z = act ? rhs(t) : czero<R>();
+    if (r < 6) {
+      if (AX) {
+        z = z + sh[r];
+      } else {  // + (W_{t-1}^dag w) on spin sr: sum_c conj(W[c][cr]) w[3 sr + c]
+        const int sl = slot_of(g, t - 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z = cfmaconj(z, ut[(size_t)(3 * c + cr) * g.tp + sl], sh[3 * sr + c]);
+      }
+    }
+    __syncwarp(mask);
+    if (act) zst(t, z);
+  }
+  if (act) sh[r] = z;
+  __syncwarp(mask);
+  Cx<R> y = act ? row_times(S + (size_t)(T - 1) * kBlk, r, sh) : czero<R>();
+  if (act) out(T - 1, y);
+  for (int t = T - 2; t >= 0; --t) {
+    __syncwarp(mask);
+    if (act) sh[r] = y;
+    __syncwarp(mask);
+    Cx<R> v = act ? zld(t) : czero<R>();
+    if (act && r >= 6) {
+      if (AX) {
+        v = v + sh[r];
+      } else {  // + (W_t y_{t+1}) on spin sr: sum_c W[cr][c] y[3 sr + c]
+        const int sl = slot_of(g, t);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v = cfma(v, ut[(size_t)(3 * cr + c) * g.tp + sl], sh[3 * sr + c]);
+      }
+    }
+    __syncwarp(mask);
+    if (act) sh[r] = v;
+    __syncwarp(mask);
+    y = act ? row_times(S + (size_t)t * kBlk, r, sh) : czero<R>();
+    if (act) out(t, y);
+  }
+  __syncwarp(mask);
+}
+
+// In-place inverse of the 12x12 left half of a[12][24] (right half: the identity on entry, the
+// inverse on exit) by Gauss-Jordan elimination with partial pivoting; every thread of the CTA
+// calls it. Returns false (the same on all threads) if a pivot is zero or not finite.
+__device__ bool gj_invert(Cx<double> (*a)[24], Cx<double>* fcol, int* piv, int tid, int nthreads) {
+  for (int k = 0; k < 12; ++k) {
+    if (tid == 0) {
+      int p = k;
+      double best = a[k][k].re * a[k][k].re + a[k][k].im * a[k][k].im;
+      for (int i = k + 1; i < 12; ++i) {
+        const double v = a[i][k].re * a[i][k].re + a[i][k].im * a[i][k].im;
+        if (v > best) {
+          best = v;
+          p = i;
+        }
+      }
+      piv[0] = p;
+      piv[1] = (best > 1e-280 && best < 1e280) ? 0 : 1;  // also false for NaN
+    }
+    __syncthreads();
+    if (piv[1]) return false;
+    const int p = piv[0];
+    if (p != k && tid < 24) {
+      const Cx<double> tmp = a[k][tid];
+      a[k][tid] = a[p][tid];
+      a[p][tid] = tmp;
+    }
+    __syncthreads();
+    const Cx<double> pv = a[k][k];
+    __syncthreads();  // every thread has the pivot before row k changes
+    const double d = 1.0 / (pv.re * pv.re + pv.im * pv.im);
+    const Cx<double> ip = mk<double>(pv.re * d, -pv.im * d);
+    if (tid < 24) a[k][tid] = cmul(a[k][tid], ip);
+    if (tid >= 32 && tid < 44) fcol[tid - 32] = a[tid - 32][k];  // rows != k: untouched above
+    __syncthreads();
+    for (int e = tid; e < 12 * 24; e += nthreads) {
+      const int r = e / 24, c = e - 24 * (e / 24);
+      if (r != k) a[r][c] = a[r][c] - cmul(fcol[r], a[k][c]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+struct SetupArgs {
+  Geom g;
+  int line0;               // first line of this launch
+  const Cx<double>* H;     // clover blocks of the parity [Nl][2][36][tp] (H_a, H_b = half the chiral
+                           // blocks of A), or null: A = 0
+  const Cx<double>* ut;    // general frame: U_t of the parity [Nl][9][tp]
+  const Cx<double>* pl;    // axial frame: the boundary link P of every line [Nl][9]
+  double s;                // boundary sign
+  Cx<double>* sinv;        // out: Sigma_t^-1 [Nl][T][144], transposed per block
+  Cx<double>* lam;         // out: Lambda [Nl][144], transposed
+  Cx<double>* scratch;     // [lines of this launch][12][T][12]: forward sweeps of the columns of V
+  int* singular;           // set to 1 if a block has no inverse
+};
+
+template <bool AX>
+__global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs A) {
+  __shared__ Cx<double> aug[12][24];
+  __shared__ Cx<double> prev[kBlk];  // Sigma_{t-1}^-1, transposed
+  __shared__ Cx<double> fcol[12];
+  __shared__ Cx<double> wl[9];       // a link: W_{t-1} while factoring, then U_w
+  __shared__ Cx<double> gsh[12][kGrp];
+  __shared__ int piv[2];
+  const Geom& g = A.g;
+  const int tid = threadIdx.x;
+  const int l = A.line0 + blockIdx.x;
+  const int T = g.T, tp = g.tp;
+  Cx<double>* S = A.sinv + (size_t)l * T * kBlk;
+  const Cx<double>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
+  const Cx<double>* Hl = A.H ? A.H + (size_t)l * 72 * tp : nullptr;
+
+  // block LU of T_0
+  for (int t = 0; t < T; ++t) {
+    const int sl = slot_of(g, t);
+    if (!AX && t > 0 && tid < 9) wl[tid] = ut[(size_t)tid * tp + slot_of(g, t - 1)];
+    __syncthreads();
+    if (tid < kBlk) {
+      const int r = tid / 12, c = tid - 12 * (tid / 12);
+      Cx<double> v = mk<double>(r == c ? g.mu : 0.0, 0.0);
+      if (Hl) {  // A = [[H_a + H_b, H_a - H_b], [H_a - H_b, H_a + H_b]] on the (P_+, P_-) halves
+        const int i = r % 6, j = c % 6;
+        const Cx<double> ha = Hl[(size_t)(6 * i + j) * tp + sl], hb = Hl[(size_t)(36 + 6 * i + j) * tp + sl];
+        v = (r < 6) == (c < 6) ? v + ha + hb : v + ha - hb;
+      }
+      if (t > 0 && r < 6 && c >= 6) {
+        if (AX) {
+          v = v - prev[12 * c + r];
+        } else {  // sum_ab conj(W[a][cr]) Sigma^-1[(sr, a), (sc, b)] W[b][cc]
+          const int sr = r / 3, cr = r % 3, sc = c / 3, cc = c % 3;
+          Cx<double> acc = czero<double>();
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              acc = acc + cmul(cmul(cconj(wl[3 * a + cr]), prev[12 * (3 * sc + b) + 3 * sr + a]), wl[3 * b + cc]);
+          v = v - acc;
+        }
+      }
+      aug[r][c] = v;
+      aug[r][c + 12] = mk<double>(r == c ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    if (!gj_invert(aug, fcol, piv, tid, kSetupThreads)) {
+      if (tid == 0) atomicOr(A.singular, 1);
+      return;
+    }
+    if (tid < kBlk) {
+      const int r = tid / 12, k = tid - 12 * (tid / 12);
+      const Cx<double> v = aug[r][k + 12];
+      prev[12 * k + r] = v;
+      S[(size_t)t * kBlk + 12 * k + r] = v;
+    }
+    __syncthreads();
+  }
+
+  // W^dag T_0^-1 V, one column j of V per group
+  if (tid < 9) wl[tid] = AX ? A.pl[(size_t)l * 9 + tid] : ut[(size_t)tid * tp + slot_of(g, T - 1)];
+  __syncthreads();
+  const int j = tid / kGrp, r = tid % kGrp;
+  const unsigned mask = 0xFFFFu << (tid & 16);
+  Cx<double>* scr = A.scratch + ((size_t)blockIdx.x * 12 + j) * T * 12;
+  const double ms = -A.s;
+  auto rhs = [&](int t) -> Cx<double> {
+    if (j < 6) {  // V_0 = -s P_+ (x) U_w^dag: rows of spin j / 3
+      if (t == 0 && r < 6 && r / 3 == j / 3) return ms * cconj(wl[3 * (j % 3) + r % 3]);
+    } else {      // V_{N_t-1} = -s P_- (x) U_w
+      if (t == T - 1 && r >= 6 && r / 3 == j / 3) return ms * wl[3 * (r % 3) + j % 3];
+    }
+    return czero<double>();
+  };
+  auto zst = [&](int t, Cx<double> v) { scr[(size_t)t * 12 + r] = v; };
+  auto zld = [&](int t) { return scr[(size_t)t * 12 + r]; };
+  Cx<double> y0 = czero<double>(), yT = czero<double>();
+  auto corner = [&](int t, Cx<double> v) {
+    if (t == 0) y0 = v;
+    if (t == T - 1) yT = v;
+  };
+  t0_solve<double, AX>(S, ut, g, r, mask, gsh[j], rhs, zst, zld, corner);
+  __syncthreads();
+  if (r < 12) {  // 1 + W^dag T_0^-1 V, column j
+    aug[r][j] = (r < 6 ? yT : y0) + mk<double>(r == j ? 1.0 : 0.0, 0.0);
+    aug[r][j + 12] = mk<double>(r == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  if (!gj_invert(aug, fcol, piv, tid, kSetupThreads)) {
+    if (tid == 0) atomicOr(A.singular, 1);
+    return;
+  }
+  if (tid < kBlk) {
+    const int rr = tid / 12, k = tid - 12 * (tid / 12);
+    A.lam[(size_t)l * kBlk + 12 * k + rr] = aug[rr][k + 12];
+  }
+}
+
+template <typename R>
+struct QinvArgs {
+  Geom g;
+  int nrhs;
+  const Cx<R>* in;     // [nrhs][Nl][12][tp], one 3-D parity
+  Cx<R>* out;          // out = xpost + apost Q^-1 (S if swap_in) in; out != in
+  const Cx<R>* xpost;  // null: out = Q^-1 in
+  R apost;
+  int swap_in;         // read in with the spin halves exchanged
+  const Cx<R>* sinv;   // [Nl][T][144]
+  const Cx<R>* lam;    // [Nl][144]
+  const Cx<R>* ut;     // general frame: U_t [Nl][9][tp]
+  const Cx<R>* pl;     // axial frame: P [Nl][9]
+  R s;                 // boundary sign
+};
+
+template <typename R, bool AX>
+__global__ void __launch_bounds__(kApplyThreads) k_qinv_apply(const QinvArgs<R> A) {
+  __shared__ Cx<R> gsh[kApplyThreads / kGrp][kGrp];
+  const Geom& g = A.g;
+  const int q = threadIdx.x, r = q % kGrp, gi = q / kGrp;
+  const unsigned mask = 0xFFFFu << (q & 16);
+  const size_t grp = (size_t)blockIdx.x * (kApplyThreads / kGrp) + gi;
+  if (grp >= (size_t)A.nrhs * g.Nl) return;  // the group's 16 lanes leave together
+  const int l = (int)(grp / A.nrhs), k = (int)(grp % A.nrhs);
+  const int T = g.T, tp = g.tp;
+  const bool act = r < 12;
+  const int rc = act ? r : 0;  // lanes 12-15 address component 0 but never load or store
+  const size_t base = ((size_t)k * g.Nl + l) * NSPIN_C * tp;
+  const Cx<R>* in = A.in + base + (size_t)(A.swap_in ? (rc + 6) % 12 : rc) * tp;
+  Cx<R>* out = A.out + base + (size_t)rc * tp;
+  const Cx<R>* xp = A.xpost ? A.xpost + base + (size_t)rc * tp : nullptr;
+  const Cx<R>* S = A.sinv + (size_t)l * T * kBlk;
+  const Cx<R>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
+  Cx<R>* sh = gsh[gi];
+
+  // chi = T_0^-1 b: only its corners chi_0, chi_{N_t-1} are kept; z goes through out
+  auto rhs = [&](int t) { return in[slot_of(g, t)]; };
+  auto zst = [&](int t, Cx<R> v) { out[slot_of(g, t)] = v; };
+  auto zld = [&](int t) { return out[slot_of(g, t)]; };
+  Cx<R> y0 = czero<R>(), yT = czero<R>();
+  auto corner = [&](int t, Cx<R> v) {
+    if (t == 0) y0 = v;
+    if (t == T - 1) yT = v;
+  };
+  t0_solve<R, AX>(S, ut, g, r, mask, sh, rhs, zst, zld, corner);
+
+  // c = Lambda W^dag chi
+  if (act) sh[r] = r < 6 ? yT : y0;
+  __syncwarp(mask);
+  const Cx<R> c = act ? row_times(A.lam + (size_t)l * kBlk, r, sh) : czero<R>();
+  __syncwarp(mask);
+  if (act) sh[r] = c;
+  __syncwarp(mask);
+  // -V c: + s U_w^dag c on the P_+ half of slot 0, + s U_w c on the P_- half of slot N_t - 1
+  Cx<R> v0 = czero<R>(), vT = czero<R>();
+  if (act) {
+    const int sr = r / 3, cr = r % 3;
+    const Cx<R>* uw = AX ? A.pl + (size_t)l * 9 : ut + slot_of(g, T - 1);
+    const size_t st = AX ? 1 : (size_t)tp;
+    if (r < 6) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) v0 = cfmaconj(v0, uw[(3 * cc + cr) * st], sh[3 * sr + cc]);
+      v0 = A.s * v0;
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) vT = cfma(vT, uw[(3 * cr + cc) * st], sh[3 * sr + cc]);
+      vT = A.s * vT;
+    }
+  }
+  __syncwarp(mask);
+  auto rhs2 = [&](int t) {
+    Cx<R> b = in[slot_of(g, t)];
+    if (t == 0) b = b + v0;
+    if (t == T - 1) b = b + vT;
+    return b;
+  };
+  auto fin = [&](int t, Cx<R> y) {
+    const int sl = slot_of(g, t);
+    out[sl] = xp ? xp[sl] + A.apost * y : y;
+  };
+  t0_solve<R, AX>(S, ut, g, r, mask, sh, rhs2, zst, zld, fin);
+  if (act)
+    for (int t = T; t < tp; ++t) out[slot_of(g, t)] = czero<R>();  // padding slots stay zero
+}
+
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
+template <typename R>
+struct QFactors {
+  const Cx<R>* sinv[2];
+  const Cx<R>* lam[2];
+};
+
+const char* const kSinvName[2][2] = {{"fsw_sinv0_f64", "fsw_sinv1_f64"}, {"fsw_sinv0_f32", "fsw_sinv1_f32"}};
+const char* const kLamName[2][2] = {{"fsw_lam0_f64", "fsw_lam1_f64"}, {"fsw_lam0_f32", "fsw_lam1_f32"}};
+
+// Factor T_0 and form Lambda on every line of both parities from the handle's gauge field and
+// clover term (A = 0 without one), in FP64, and with f32 also their FP32 copies.
+void qinv_setup(wf_handle* h, bool f32) {
+  const Geom& g = h->g;
+  cudaStream_t s = h->stream;
+  const size_t nb = (size_t)g.Nl * g.T * kBlk, nl = (size_t)g.Nl * kBlk;
+  const size_t per_line = (size_t)12 * g.T * 12 * sizeof(Cx<double>);
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.Nl, kScratchBytes / per_line));
+  Cx<double>* scratch = h->buf<Cx<double>>("fsw_scratch", (size_t)chunk * 12 * g.T * 12);
+  int* singular = h->buf<int>("fsw_singular", 1);
+  WF_CUDA(cudaMemsetAsync(singular, 0, sizeof(int), s));
+  for (int p = 0; p < 2; ++p) {
+    SetupArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.H = h->clover ? h->clov64[p].as<Cx<double>>() : nullptr;
+    a.ut = h->ut64[p].as<Cx<double>>();
+    a.pl = h->pl64[p].as<Cx<double>>();
+    a.s = g.bc;
+    a.sinv = h->buf<Cx<double>>(kSinvName[0][p], nb);
+    a.lam = h->buf<Cx<double>>(kLamName[0][p], nl);
+    a.scratch = scratch;
+    a.singular = singular;
+    for (int l0 = 0; l0 < g.Nl; l0 += chunk) {
+      a.line0 = l0;
+      const int lines = std::min(chunk, g.Nl - l0);
+      Prof P(h, "qinv_setup_f64");
+      if (h->axial)
+        k_qinv_setup<true><<<lines, kSetupThreads, 0, s>>>(a);
+      else
+        k_qinv_setup<false><<<lines, kSetupThreads, 0, s>>>(a);
+      WF_CUDA(cudaGetLastError());
+    }
+  }
+  int sing = 0;
+  WF_CUDA(cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  if (sing) throw Error(WF_ESINGULAR, "a block of mu + A - D_t on a time line has no inverse");
+  if (f32) {
+    for (int p = 0; p < 2; ++p) {
+      Prof P(h, "qinv_d2f", 2);
+      launch_d2f(h->buf<Cx<double>>(kSinvName[0][p], nb), h->buf<Cx<float>>(kSinvName[1][p], nb), nb, s);
+      launch_d2f(h->buf<Cx<double>>(kLamName[0][p], nl), h->buf<Cx<float>>(kLamName[1][p], nl), nl, s);
+    }
+  }
+}
+
+template <typename R>
+QFactors<R> qfactors(wf_handle* h) {
+  const Geom& g = h->g;
+  const int w = sizeof(R) == 8 ? 0 : 1;
+  QFactors<R> f;
+  for (int p = 0; p < 2; ++p) {
+    f.sinv[p] = h->buf<Cx<R>>(kSinvName[w][p], (size_t)g.Nl * g.T * kBlk);
+    f.lam[p] = h->buf<Cx<R>>(kLamName[w][p], (size_t)g.Nl * kBlk);
+  }
+  return f;
+}
+
+template <typename R>
+const Cx<R>* gauge_ut(wf_handle* h, int p) {
+  if constexpr (sizeof(R) == 8)
+    return h->ut64[p].as<Cx<double>>();
+  else
+    return h->ut32[p].as<Cx<float>>();
+}
+template <typename R>
+const Cx<R>* gauge_pl(wf_handle* h, int p) {
+  if constexpr (sizeof(R) == 8)
+    return h->pl64[p].as<Cx<double>>();
+  else
+    return h->pl32[p].as<Cx<float>>();
+}
+template <typename R>
+const Cx<R>* gauge_us(wf_handle* h, int p) {
+  if constexpr (sizeof(R) == 8)
+    return h->us64[p].as<Cx<double>>();
+  else
+    return h->us32[p].as<Cx<float>>();
+}
+template <typename R>
+const char* tag(const char* f64, const char* f32) {
+  return sizeof(R) == 8 ? f64 : f32;
+}
+
+// out = xpost + apost Q^-1 (S) in on the lines of parity p
+template <typename R>
+void qinv(wf_handle* h, const QFactors<R>& F, int p, const Cx<R>* in, Cx<R>* out, int nrhs, int swap_in = 0,
+          const Cx<R>* xpost = nullptr, double apost = 0.0) {
+  QinvArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = h->g;
+  a.nrhs = nrhs;
+  a.in = in;
+  a.out = out;
+  a.xpost = xpost;
+  a.apost = (R)apost;
+  a.swap_in = swap_in;
+  a.sinv = F.sinv[p];
+  a.lam = F.lam[p];
+  a.ut = gauge_ut<R>(h, p);
+  a.pl = gauge_pl<R>(h, p);
+  a.s = (R)h->g.bc;
+  const size_t groups = (size_t)nrhs * h->g.Nl;
+  const unsigned blocks = (unsigned)((groups + kApplyThreads / kGrp - 1) / (kApplyThreads / kGrp));
+  Prof P(h, tag<R>("qinv_apply_f64", "qinv_apply_f32"));
+  if (h->axial)
+    k_qinv_apply<R, true><<<blocks, kApplyThreads, 0, h->stream>>>(a);
+  else
+    k_qinv_apply<R, false><<<blocks, kApplyThreads, 0, h->stream>>>(a);
+  WF_CUDA(cudaGetLastError());
+}
+
+// out = xpost + apost (S) D_s in on the lines of parity p (in: the other parity)
+template <typename R>
+void hop(wf_handle* h, int p, const Cx<R>* in, Cx<R>* out, int nrhs, const Cx<R>* xpost = nullptr,
+         double apost = 0.0, int swap_out = 0) {
+  LineArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = h->g;
+  a.parity = p;
+  a.nrhs = nrhs;
+  a.src = SRC_HOP;
+  a.opu = OP_COPY;
+  a.opl = OP_COPY;
+  a.src_up = in;
+  a.src_lo = in + 6 * h->g.tp;
+  a.ut = gauge_ut<R>(h, p);
+  a.pl = gauge_pl<R>(h, p);
+  a.us_out = gauge_us<R>(h, p);
+  a.us_nbr = gauge_us<R>(h, 1 - p);
+  a.inv_mu = (R)(1.0 / h->g.mu);
+  a.bc = (R)h->g.bc;
+  a.xpost = xpost;
+  a.apost = (R)apost;
+  a.swap_out = swap_out;
+  a.out = out;
+  a.drop_job = -1;
+  Prof P(h, tag<R>("fsw_hop_f64", "fsw_hop_f32"));
+  launch_line<R>(a, LK_GENERIC, h->axial, h->stream);
+}
+
+// M-hat_full (dagger: its adjoint) on internal odd fields x -> out; e1, e2 (even) and o1 (odd) are
+// work fields of the size of x
+template <typename R>
+void schur_full(wf_handle* h, const QFactors<R>& F, const Cx<R>* x, Cx<R>* out, int dagger, int nrhs, Cx<R>* e1,
+                Cx<R>* e2, Cx<R>* o1) {
+  const double m = -1.0 / (h->g.gamma_f * h->g.gamma_f);
+  if (!dagger) {
+    hop<R>(h, 0, x, e1, nrhs);                          // D_s^eo x
+    qinv<R>(h, F, 0, e1, e2, nrhs);                     // (Q^ee)^-1
+    hop<R>(h, 1, e2, o1, nrhs);                         // D_s^oe
+    qinv<R>(h, F, 1, o1, out, nrhs, 0, x, m);           // x - gamma_f^-2 (Q^oo)^-1 ...
+  } else {
+    qinv<R>(h, F, 1, x, o1, nrhs, 1);                   // (Q^oo)^-1 S x
+    hop<R>(h, 0, o1, e1, nrhs);
+    qinv<R>(h, F, 0, e1, e2, nrhs);
+    hop<R>(h, 1, e2, out, nrhs, x, m, 1);               // x - gamma_f^-2 S D_s^oe ...
+  }
+}
+
+// ----------------------------------------------------------------------------
+// C-ABI bodies
+// ----------------------------------------------------------------------------
+const Cx<double>* stage_in(wf_handle* h, const double* p, size_t elems, const char* name) {
+  if (!p) throw Error(WF_EINVAL, "null array argument");
+  if (device_resident(p, h->device)) return reinterpret_cast<const Cx<double>*>(p);
+  Cx<double>* d = h->buf<Cx<double>>(name, elems);
+  WF_CUDA(cudaMemcpyAsync(d, p, elems * sizeof(Cx<double>), cudaMemcpyHostToDevice, h->stream));
+  return d;
+}
+Cx<double>* stage_out(wf_handle* h, double* p, size_t elems, const char* name, bool& staged) {
+  if (!p) throw Error(WF_EINVAL, "null array argument");
+  staged = !device_resident(p, h->device);
+  return staged ? h->buf<Cx<double>>(name, elems) : reinterpret_cast<Cx<double>*>(p);
+}
+void finish(wf_handle* h, double* p, const Cx<double>* d, size_t elems, bool staged) {
+  if (staged) WF_CUDA(cudaMemcpyAsync(p, d, elems * sizeof(Cx<double>), cudaMemcpyDeviceToHost, h->stream));
+  WF_CUDA(cudaStreamSynchronize(h->stream));
+}
+void check_handle(wf_handle* h, int nrhs) {
+  if (!h->gauge) throw Error(WF_EINVAL, "no gauge field loaded");
+  if (nrhs < 1 || nrhs > WF_MAX_SOLVE_RHS) throw Error(WF_EINVAL, "nrhs must lie in [1, WF_MAX_SOLVE_RHS]");
+}
+
+template <typename R>
+int apply_qinv_abi(wf_handle* h, const double* in, double* out, int nrhs) {
+  check_handle(h, nrhs);
+  const Geom& g = h->g;
+  const size_t le = h->lex_elems() * nrhs, nt = h->half_int() * nrhs;
+  const Cx<double>* din = stage_in(h, in, le, "stage_in");
+  bool staged;
+  Cx<double>* dout = stage_out(h, out, le, "stage_out", staged);
+  Cx<R>* ie = h->buf<Cx<R>>(tag<R>("fsw_ie_f64", "fsw_ie_f32"), nt);
+  Cx<R>* io = h->buf<Cx<R>>(tag<R>("fsw_io_f64", "fsw_io_f32"), nt);
+  Cx<R>* oe = h->buf<Cx<R>>(tag<R>("fsw_oe_f64", "fsw_oe_f32"), nt);
+  Cx<R>* oo = h->buf<Cx<R>>(tag<R>("fsw_oo_f64", "fsw_oo_f32"), nt);
+  qinv_setup(h, sizeof(R) == 4);
+  const QFactors<R> F = qfactors<R>(h);
+  {
+    Prof P(h, tag<R>("import_spinor_f64", "import_spinor_f32"));
+    launch_import_spinor<R>(g, din, ie, io, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream);
+  }
+  qinv<R>(h, F, 0, ie, oe, nrhs);
+  qinv<R>(h, F, 1, io, oo, nrhs);
+  {
+    Prof P(h, tag<R>("export_spinor_f64", "export_spinor_f32"));
+    launch_export_spinor<R>(g, oe, oo, dout, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), h->stream);
+  }
+  finish(h, out, dout, le, staged);
+  return WF_OK;
+}
+
+template <typename R>
+int apply_schur_full_abi(wf_handle* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  check_handle(h, nrhs);
+  const Geom& g = h->g;
+  const size_t ce = (size_t)nrhs * g.T * g.Nl * NSPIN_C, nt = h->half_int() * nrhs;
+  const Cx<double>* din = stage_in(h, in_odd, ce, "stage_in");
+  bool staged;
+  Cx<double>* dout = stage_out(h, out_odd, ce, "stage_out", staged);
+  Cx<R>* x = h->buf<Cx<R>>(tag<R>("fsw_x_f64", "fsw_x_f32"), nt);
+  Cx<R>* o = h->buf<Cx<R>>(tag<R>("fsw_o_f64", "fsw_o_f32"), nt);
+  Cx<R>* e1 = h->buf<Cx<R>>(tag<R>("fsw_e1_f64", "fsw_e1_f32"), nt);
+  Cx<R>* e2 = h->buf<Cx<R>>(tag<R>("fsw_e2_f64", "fsw_e2_f32"), nt);
+  Cx<R>* o1 = h->buf<Cx<R>>(tag<R>("fsw_o1_f64", "fsw_o1_f32"), nt);
+  qinv_setup(h, sizeof(R) == 4);
+  const QFactors<R> F = qfactors<R>(h);
+  {
+    Prof P(h, tag<R>("import_compact_f64", "import_compact_f32"));
+    launch_import_compact<R>(g, din, x, nrhs, 0, frame_rot(h, 1), h->stream);
+  }
+  schur_full<R>(h, F, x, o, dagger, nrhs, e1, e2, o1);
+  {
+    Prof P(h, tag<R>("export_compact_f64", "export_compact_f32"));
+    launch_export_compact<R>(g, o, dout, nrhs, 0, frame_rot(h, 1), h->stream);
+  }
+  finish(h, out_odd, dout, ce, staged);
+  return WF_OK;
+}
+
+// r_p = eta_p - (M + A) psi on parity p, FP64 (the true residual of M_SW)
+void msw_residual(wf_handle* h, int p, const Cx<double>* psi_e, const Cx<double>* psi_o, const Cx<double>* eta,
+                  Cx<double>* r, int nrhs) {
+  MArgs<double> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = h->g;
+  a.parity = p;
+  a.nrhs = nrhs;
+  a.psi_p = p ? psi_o : psi_e;
+  a.psi_q = p ? psi_e : psi_o;
+  a.ut = h->ut64[p].as<Cx<double>>();
+  a.pl = h->pl64[p].as<Cx<double>>();
+  a.us_out = h->us64[p].as<Cx<double>>();
+  a.us_nbr = h->us64[1 - p].as<Cx<double>>();
+  a.x = eta;
+  a.a = -1.0;
+  a.out = r;
+  a.mu = h->g.mu;
+  a.inv_gf = 1.0 / h->g.gamma_f;
+  a.bc = h->g.bc;
+  {
+    Prof P(h, "apply_M_f64");
+    launch_apply_M<double>(a, h->axial, h->stream);
+  }
+  if (h->clover) {
+    Prof P(h, "clover_apply_f64");
+    launch_clover_apply<double>(h->g, h->clov64[p].as<Cx<double>>(), a.psi_p, r, r, -1.0, nrhs, h->stream);
+  }
+}
+
+// Per-rhs |x_e|^2 + |x_o|^2 to the host
+void norms(wf_handle* h, const Cx<double>* xe, const Cx<double>* xo, int nrhs, std::vector<double>& out) {
+  const size_t n = h->half_int();
+  double* partial = h->buf<double>("fsw_partial", 1024 * (size_t)nrhs);
+  double* nn = h->buf<double>("fsw_norms", 2 * (size_t)nrhs);
+  {
+    Prof P(h, "norm2_f64", 4);
+    launch_norm2<double>(xe, n, nrhs, partial, nn, h->stream);
+    launch_norm2<double>(xo, n, nrhs, partial, nn + nrhs, h->stream);
+  }
+  std::vector<double> hn(2 * (size_t)nrhs);
+  WF_CUDA(cudaMemcpyAsync(hn.data(), nn, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  WF_CUDA(cudaStreamSynchronize(h->stream));
+  out.resize(nrhs);
+  for (int k = 0; k < nrhs; ++k) out[k] = hn[k] + hn[nrhs + k];
+}
+
+// CGNR on M-hat_full y = b in precision R, from y = 0, each right-hand side k to
+// |b - M-hat y| <= rho[k] |b| (rho[k] >= 1 or b = 0: no iteration); stops at `left` iterations.
+// its[k] gains the iterations right-hand side k took; returns the iterations of the loop.
+template <typename R>
+int cgnr_full(wf_handle* h, const QFactors<R>& F, const Cx<R>* b, Cx<R>* y, int nrhs, const std::vector<double>& rho,
+              int left, std::vector<int>& its) {
+  cudaStream_t s = h->stream;
+  const size_t n = h->half_int(), nt = n * nrhs;
+  Cx<R>* r = h->buf<Cx<R>>(tag<R>("fsw_cg_r_f64", "fsw_cg_r_f32"), nt);
+  Cx<R>* p = h->buf<Cx<R>>(tag<R>("fsw_cg_p_f64", "fsw_cg_p_f32"), nt);
+  Cx<R>* q = h->buf<Cx<R>>(tag<R>("fsw_cg_q_f64", "fsw_cg_q_f32"), nt);
+  Cx<R>* sv = h->buf<Cx<R>>(tag<R>("fsw_cg_s_f64", "fsw_cg_s_f32"), nt);
+  Cx<R>* e1 = h->buf<Cx<R>>(tag<R>("fsw_e1_f64", "fsw_e1_f32"), nt);
+  Cx<R>* e2 = h->buf<Cx<R>>(tag<R>("fsw_e2_f64", "fsw_e2_f32"), nt);
+  Cx<R>* o1 = h->buf<Cx<R>>(tag<R>("fsw_o1_f64", "fsw_o1_f32"), nt);
+  double* sc = h->buf<double>("fsw_cg_scalars", 5 * (size_t)nrhs);
+  double *gam = sc, *gnew = sc + nrhs, *qq = sc + 2 * nrhs, *rr = sc + 3 * nrhs, *bb = sc + 4 * nrhs;
+  int* active = h->buf<int>("fsw_cg_active", nrhs);
+  double* partial = h->buf<double>("fsw_partial", 1024 * (size_t)nrhs);
+  WF_CUDA(cudaMemsetAsync(y, 0, nt * sizeof(Cx<R>), s));
+  WF_CUDA(cudaMemcpyAsync(r, b, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  schur_full<R>(h, F, r, sv, 1, nrhs, e1, e2, o1);
+  WF_CUDA(cudaMemcpyAsync(p, sv, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+  {
+    Prof P(h, tag<R>("norm2_f64", "norm2_f32"), 4);
+    launch_norm2<R>(sv, n, nrhs, partial, gam, s);
+    launch_norm2<R>(b, n, nrhs, partial, bb, s);
+  }
+  std::vector<double> hb(nrhs), hr(nrhs);
+  std::vector<int> act(nrhs);
+  WF_CUDA(cudaMemcpyAsync(hb.data(), bb, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  int nact = 0;
+  for (int k = 0; k < nrhs; ++k) {
+    if (!std::isfinite(hb[k])) throw Error(WF_ENAN, "NaN or Inf in the preconditioned source");
+    act[k] = hb[k] > 0.0 && rho[k] < 1.0 ? 1 : 0;
+    nact += act[k];
+  }
+  WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  int it = 0;
+  while (nact > 0 && it < left) {
+    schur_full<R>(h, F, p, q, 0, nrhs, e1, e2, o1);
+    {
+      Prof P(h, tag<R>("norm2_f64", "norm2_f32"), 2);
+      launch_norm2<R>(q, n, nrhs, partial, qq, s);
+    }
+    {
+      Prof P(h, tag<R>("cg_xr_f64", "cg_xr_f32"), 2);
+      launch_cg_xr<R>(y, r, p, q, n, nrhs, gam, qq, active, partial, rr, s);
+    }
+    ++it;
+    for (int k = 0; k < nrhs; ++k) its[k] += act[k];
+    WF_CUDA(cudaMemcpyAsync(hr.data(), rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    nact = 0;
+    for (int k = 0; k < nrhs; ++k) {
+      if (!act[k]) continue;
+      if (!std::isfinite(hr[k])) throw Error(WF_ENAN, "NaN or Inf in a CG residual");
+      if (hr[k] <= rho[k] * rho[k] * hb[k]) act[k] = 0;
+      nact += act[k];
+    }
+    WF_CUDA(cudaMemcpyAsync(active, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (nact == 0) break;
+    schur_full<R>(h, F, r, sv, 1, nrhs, e1, e2, o1);
+    {
+      Prof P(h, tag<R>("norm2_f64", "norm2_f32"), 2);
+      launch_norm2<R>(sv, n, nrhs, partial, gnew, s);
+    }
+    {
+      Prof P(h, tag<R>("cg_p_f64", "cg_p_f32"), 2);
+      launch_cg_p<R>(p, sv, n, nrhs, gnew, gam, active, s);
+      launch_copy_scalar(gam, gnew, nrhs, s, active);
+    }
+  }
+  return it;
+}
+
+// M_SW psi = eta with full SW temporal preconditioning and 3-D Schur, by defect correction: every
+// pass solves M_SW delta = r in precision R (source preparation (Q^oo)^-1 (r_o + gamma_f^-1 D_s^oe
+// (Q^ee)^-1 r_e), CGNR on M-hat_full, reconstruction delta_e = (Q^ee)^-1 (r_e + gamma_f^-1 D_s^eo
+// delta_o)), adds delta to psi in FP64 and recomputes the FP64 true residual r = eta - M_SW psi.
+template <typename R>
+int solve_full_abi(wf_handle* h, const double* rhs, double* x, int nrhs, double tol, int* iters_out,
+                   double* resid_out) {
+  check_handle(h, nrhs);
+  if (!(tol > 0)) throw Error(WF_EINVAL, "tol must be > 0");
+  const Geom& g = h->g;
+  cudaStream_t s = h->stream;
+  const size_t le = h->lex_elems() * nrhs, n = h->half_int(), nt = n * nrhs;
+  const Cx<double>* drhs = stage_in(h, rhs, le, "stage_in");
+  bool staged;
+  Cx<double>* dx = stage_out(h, x, le, "stage_out", staged);
+  Cx<double>* eta_e = h->buf<Cx<double>>("fsw_eta_e", nt);
+  Cx<double>* eta_o = h->buf<Cx<double>>("fsw_eta_o", nt);
+  Cx<double>* psi_e = h->buf<Cx<double>>("fsw_psi_e", nt);
+  Cx<double>* psi_o = h->buf<Cx<double>>("fsw_psi_o", nt);
+  Cx<double>* r_e = h->buf<Cx<double>>("fsw_r_e", nt);
+  Cx<double>* r_o = h->buf<Cx<double>>("fsw_r_o", nt);
+  Cx<R>* re = h->buf<Cx<R>>(tag<R>("fsw_re_f64", "fsw_re_f32"), nt);
+  Cx<R>* ro = h->buf<Cx<R>>(tag<R>("fsw_ro_f64", "fsw_ro_f32"), nt);
+  Cx<R>* ue = h->buf<Cx<R>>(tag<R>("fsw_ue_f64", "fsw_ue_f32"), nt);
+  Cx<R>* wo = h->buf<Cx<R>>(tag<R>("fsw_wo_f64", "fsw_wo_f32"), nt);
+  Cx<R>* bo = h->buf<Cx<R>>(tag<R>("fsw_bo_f64", "fsw_bo_f32"), nt);
+  Cx<R>* yo = h->buf<Cx<R>>(tag<R>("fsw_yo_f64", "fsw_yo_f32"), nt);
+  Cx<R>* we = h->buf<Cx<R>>(tag<R>("fsw_we_f64", "fsw_we_f32"), nt);
+  qinv_setup(h, sizeof(R) == 4);
+  const QFactors<R> F = qfactors<R>(h);
+  {
+    Prof P(h, "import_spinor_f64");
+    launch_import_spinor<double>(g, drhs, eta_e, eta_o, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+  }
+  WF_CUDA(cudaMemsetAsync(psi_e, 0, nt * sizeof(Cx<double>), s));
+  WF_CUDA(cudaMemsetAsync(psi_o, 0, nt * sizeof(Cx<double>), s));
+  WF_CUDA(cudaMemcpyAsync(r_e, eta_e, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(r_o, eta_o, nt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  std::vector<double> etan, rn;
+  norms(h, eta_e, eta_o, nrhs, etan);
+  for (int k = 0; k < nrhs; ++k)
+    if (!std::isfinite(etan[k])) throw Error(WF_ENAN, "NaN or Inf in the source");
+  rn = etan;
+  const double gi = 1.0 / g.gamma_f;
+  // each pass aims at half the target; an FP32 pass at no less than 1e-5 of its source
+  const double floor = sizeof(R) == 4 ? 1e-5 : 0.0;
+  std::vector<double> rho(nrhs), rel(nrhs, 1.0);
+  std::vector<int> its(nrhs, 0);
+  int used = 0;
+  bool done = false;
+  for (int pass = 0; pass < 8 && !done; ++pass) {
+    if constexpr (sizeof(R) == 8) {
+      WF_CUDA(cudaMemcpyAsync(re, r_e, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+      WF_CUDA(cudaMemcpyAsync(ro, r_o, nt * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, s));
+    } else {
+      Prof P(h, "d2f", 2);
+      launch_d2f(r_e, re, nt, s);
+      launch_d2f(r_o, ro, nt, s);
+    }
+    for (int k = 0; k < nrhs; ++k) {
+      rel[k] = etan[k] > 0 ? std::sqrt(rn[k] / etan[k]) : 0.0;
+      rho[k] = rel[k] <= tol ? 1.0 : std::max(floor, 0.5 * tol / rel[k]);
+      if (rel[k] <= tol) {  // converged: a zero source keeps its solution as it is
+        WF_CUDA(cudaMemsetAsync(re + k * n, 0, n * sizeof(Cx<R>), s));
+        WF_CUDA(cudaMemsetAsync(ro + k * n, 0, n * sizeof(Cx<R>), s));
+      }
+    }
+    qinv<R>(h, F, 0, re, ue, nrhs);                   // (Q^ee)^-1 r_e
+    hop<R>(h, 1, ue, wo, nrhs, ro, gi);               // r_o + gamma_f^-1 D_s^oe ...
+    qinv<R>(h, F, 1, wo, bo, nrhs);                   // b = (Q^oo)^-1 ...
+    used += cgnr_full<R>(h, F, bo, yo, nrhs, rho, std::max(1, h->maxiter - used), its);
+    hop<R>(h, 0, yo, we, nrhs, re, gi);               // r_e + gamma_f^-1 D_s^eo delta_o
+    qinv<R>(h, F, 0, we, ue, nrhs);                   // delta_e
+    if constexpr (sizeof(R) == 8) {
+      Prof P(h, "axpby_f64", 2);
+      launch_axpby<double>(psi_e, ue, nt, 1.0, 1.0, s);
+      launch_axpby<double>(psi_o, yo, nt, 1.0, 1.0, s);
+    } else {
+      Prof P(h, "add_f_to_d", 2);
+      launch_add_f_to_d(psi_e, ue, nt, s);
+      launch_add_f_to_d(psi_o, yo, nt, s);
+    }
+    msw_residual(h, 0, psi_e, psi_o, eta_e, r_e, nrhs);
+    msw_residual(h, 1, psi_e, psi_o, eta_o, r_o, nrhs);
+    norms(h, r_e, r_o, nrhs, rn);
+    done = true;
+    for (int k = 0; k < nrhs; ++k) {
+      if (!std::isfinite(rn[k])) throw Error(WF_ENAN, "NaN or Inf in a true residual");
+      rel[k] = etan[k] > 0 ? std::sqrt(rn[k] / etan[k]) : 0.0;
+      if (rel[k] > tol) done = false;
+    }
+    if (used >= h->maxiter) break;
+  }
+  {
+    Prof P(h, "export_spinor_f64");
+    launch_export_spinor<double>(g, psi_e, psi_o, dx, nrhs, 0, frame_rot(h, 0), frame_rot(h, 1), s);
+  }
+  finish(h, x, dx, le, staged);
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters_out) iters_out[k] = its[k];
+    if (resid_out) resid_out[k] = rel[k];
+  }
+  return done ? WF_OK : WF_ENOCONV;
+}
+
+template <typename F>
+int guard(wf_handle* h, F&& f) {
+  if (!h) return WF_EINVAL;
+  h->err.clear();
+  try {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) WF_CUDA(cudaSetDevice(h->device));
+    return f();
+  } catch (const Error& e) {
+    h->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return WF_ENOMEM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return WF_ECUDA;
+  } catch (...) {
+    h->err = "unknown error";
+    return WF_ECUDA;
+  }
+}
+
+}  // namespace
+}  // namespace wf
+
+using namespace wf;
+
+extern "C" {
+
+int wf_apply_Qinv(wf_handle_t* h, const double* in, double* out, int nrhs) {
+  return guard(h, [&]() { return apply_qinv_abi<double>(h, in, out, nrhs); });
+}
+int wf_apply_Qinv_f32(wf_handle_t* h, const double* in, double* out, int nrhs) {
+  return guard(h, [&]() { return apply_qinv_abi<float>(h, in, out, nrhs); });
+}
+int wf_apply_schur_full_sw(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guard(h, [&]() { return apply_schur_full_abi<double>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+int wf_apply_schur_full_sw_f32(wf_handle_t* h, const double* in_odd, double* out_odd, int dagger, int nrhs) {
+  return guard(h, [&]() { return apply_schur_full_abi<float>(h, in_odd, out_odd, dagger ? 1 : 0, nrhs); });
+}
+int wf_solve_full_sw(wf_handle_t* h, const double* rhs, double* x, int nrhs, double tol, int precision,
+                     int* iters_out, double* true_resid_out) {
+  return guard(h, [&]() {
+    if (precision == WF_FP64) return solve_full_abi<double>(h, rhs, x, nrhs, tol, iters_out, true_resid_out);
+    if (precision == WF_FP32) return solve_full_abi<float>(h, rhs, x, nrhs, tol, iters_out, true_resid_out);
+    throw Error(WF_EINVAL, "precision must be WF_FP64 or WF_FP32");
+  });
+}
+
+}  // extern "C"
