@@ -267,9 +267,10 @@ int wf_apply_ilu_f32(wf_handle_t* h, const double* in, double* out, int dagger, 
  *   M-hat_full = 1 - gamma_f^-2 (Q^oo)^-1 D_s^oe (Q^ee)^-1 D_s^eo
  * (Eq. TPrecFull with C_L = Q^-1, C_R = 1). A is the term of wf_load_gauge_clover, or 0 if none is
  * loaded (then Q = mu - D_t = C_L^-1 C_R^-1). Q^-1 is the appendix's single Woodbury step
- * Q = T_0 + V W^dag around the open chain T_0, which the library factors by block LU (FP64, on
- * every call of these entry points: about 2.3 KB per site of device memory, and half again for the
- * FP32 entry points) instead of the paper's inner CG.
+ * Q = T_0 + V W^dag around the open chain T_0, which the library factors by block LU (on
+ * every call of these entry points, in the precision of the call: the blocks Sigma_t^-1 and the
+ * Woodbury columns T_0^-1 V, 4.6 KB of device memory per site in FP64, 2.3 KB in FP32) instead of
+ * the paper's inner CG.
  * wf_apply_Qinv: out = Q^-1 in on full fields [rhs][V][spin][colour]; _f32: FP32 applies.
  * wf_apply_schur_full_sw: out = M-hat_full in (dagger: its adjoint) on odd fields as for
  *   wf_apply_schur; _f32: FP32 arithmetic.
@@ -280,8 +281,7 @@ int wf_apply_ilu_f32(wf_handle_t* h, const double* in, double* out, int dagger, 
  *   the correction in FP64, until |r_k| <= tol |rhs_k| for every right-hand side; the handle's
  *   iteration limit bounds all passes together. iters_out[k] (CG iterations of right-hand side k)
  *   and true_resid_out[k] (host, may be null) are written for every k.
- * Arrays may be host or device memory of the handle's GPU (staged if on the host); in and out must
- * not overlap. Errors: WF_EINVAL (no gauge field, nrhs outside [1, WF_MAX_SOLVE_RHS], tol <= 0,
+ * Arrays follow the conventions above (host or device memory; in-place calls allowed). Errors: WF_EINVAL (no gauge field, nrhs outside [1, WF_MAX_SOLVE_RHS], tol <= 0,
  * precision other than WF_FP64 / WF_FP32), WF_ESINGULAR (a block of the factorisation, or the
  * 12x12 Woodbury matrix of a line, has no inverse), WF_ENAN (a non-finite norm in the solve),
  * WF_ENOCONV (iteration limit or 8 passes reached; x holds the last iterate). */

@@ -25,18 +25,24 @@
 //   z_0 = b_0,   z_t = b_t + [P_+ (x) W_{t-1}^dag] Sigma_{t-1}^-1 z_{t-1}
 // (only the P_+ half of Sigma_{t-1}^-1 z_{t-1} is needed) and a backward sweep
 //   y_{N_t-1} = Sigma_{N_t-1}^-1 z_{N_t-1},   y_t = Sigma_t^-1 (z_t + [P_- (x) W_t] y_{t+1}),
-// and Q^-1 b takes two solves: chi = T_0^-1 b, c = Lambda W^dag chi (W^dag chi: the P_+ half of
-// chi_{N_t-1} and the P_- half of chi_0), then Q^-1 b = T_0^-1 (b - V c).
+// and with Z = T_0^-1 V (12 columns, formed once with the factors) Q^-1 b takes one solve:
+// chi = T_0^-1 b, c = Lambda W^dag chi (W^dag chi: the P_+ half of chi_{N_t-1} and the P_- half of
+// chi_0), Q^-1 b = chi - Z c.
 //
-// Kernels. k_qinv_setup (FP64, one CTA per line): Sigma_t^-1 for every t by Gauss-Jordan
-// elimination with partial pivoting in shared memory, then the twelve columns of T_0^-1 V by the
-// sweeps (one 16-lane group per column, the forward sweep's z in a global scratch array), then
-// Lambda. k_qinv_apply (FP64 or FP32): one 16-lane group per (line, right-hand side), lane r < 12
-// holding component r (= 3 spin + colour) of the current 12-vector; a sweep step is a 12x12 (6x12
-// in the forward sweep) product whose vector the group exchanges through shared memory. The groups
-// of a CTA hold consecutive right-hand sides of one line, so its blocks come from DRAM once for
-// all of them. Blocks are stored transposed per time slice, [line][t][k][r], so that the twelve
-// lanes of a group read one column k of the block as 12 consecutive elements.
+// Kernels. k_qinv_setup (one CTA per line, in the precision of the applies that use it: FP64, or
+// FP32 from the FP32 gauge and clover copies, since FP32 solves correct against the FP64 true
+// residual of M_SW and never need FP64 factors): Sigma_t^-1 for every t by Gauss-Jordan elimination
+// with partial pivoting in shared memory, then the twelve columns of T_0^-1 V by the sweeps (one
+// 16-lane group per column, the forward sweep's z in a global scratch array), kept as Z, then
+// Lambda.
+// k_qinv_apply: one 16-lane group per (line, right-hand side), lane r < 12 holding component
+// r (= 3 spin + colour) of the current 12-vector; a sweep step is a 12x12 (6x12 in the forward
+// sweep) product whose vector the group exchanges through shared memory; the correction chi - Z c
+// has no serial chain. Lane r only ever needs
+// row r of a block, so it streams its rows (and b_t) into a per-group ring in shared memory with
+// cp.async several steps ahead of their use: the sweeps' serial chains then wait on shared memory
+// and arithmetic, not on DRAM. Blocks are stored transposed per time slice, [line][t][k][r], so
+// that the twelve lanes of a group copy one column k of a block as 12 consecutive elements.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -51,7 +57,6 @@ namespace wf {
 namespace {
 
 constexpr int kGrp = 16;                       // lanes per 12-vector group
-constexpr int kApplyThreads = 128;             // 8 groups per CTA
 constexpr int kSetupThreads = 12 * kGrp;       // one group per column of V
 constexpr int kBlk = 144;                      // entries of a 12x12 block
 constexpr size_t kScratchBytes = 256u << 20;   // bound of the setup's sweep scratch per launch
@@ -131,34 +136,36 @@ __device__ __forceinline__ void t0_solve(const Cx<R>* __restrict__ S, const Cx<R
 // In-place inverse of the 12x12 left half of a[12][24] (right half: the identity on entry, the
 // inverse on exit) by Gauss-Jordan elimination with partial pivoting; every thread of the CTA
 // calls it. Returns false (the same on all threads) if a pivot is zero or not finite.
-__device__ bool gj_invert(Cx<double> (*a)[24], Cx<double>* fcol, int* piv, int tid, int nthreads) {
+template <typename R>
+__device__ bool gj_invert(Cx<R> (*a)[24], Cx<R>* fcol, int* piv, int tid, int nthreads) {
+  const R lo = sizeof(R) == 8 ? R(1e-280) : R(1e-30), hi = sizeof(R) == 8 ? R(1e280) : R(1e30);
   for (int k = 0; k < 12; ++k) {
     if (tid == 0) {
       int p = k;
-      double best = a[k][k].re * a[k][k].re + a[k][k].im * a[k][k].im;
+      R best = a[k][k].re * a[k][k].re + a[k][k].im * a[k][k].im;
       for (int i = k + 1; i < 12; ++i) {
-        const double v = a[i][k].re * a[i][k].re + a[i][k].im * a[i][k].im;
+        const R v = a[i][k].re * a[i][k].re + a[i][k].im * a[i][k].im;
         if (v > best) {
           best = v;
           p = i;
         }
       }
       piv[0] = p;
-      piv[1] = (best > 1e-280 && best < 1e280) ? 0 : 1;  // also false for NaN
+      piv[1] = (best > lo && best < hi) ? 0 : 1;  // also false for NaN
     }
     __syncthreads();
     if (piv[1]) return false;
     const int p = piv[0];
     if (p != k && tid < 24) {
-      const Cx<double> tmp = a[k][tid];
+      const Cx<R> tmp = a[k][tid];
       a[k][tid] = a[p][tid];
       a[p][tid] = tmp;
     }
     __syncthreads();
-    const Cx<double> pv = a[k][k];
+    const Cx<R> pv = a[k][k];
     __syncthreads();  // every thread has the pivot before row k changes
-    const double d = 1.0 / (pv.re * pv.re + pv.im * pv.im);
-    const Cx<double> ip = mk<double>(pv.re * d, -pv.im * d);
+    const R d = R(1) / (pv.re * pv.re + pv.im * pv.im);
+    const Cx<R> ip = mk<R>(pv.re * d, -pv.im * d);
     if (tid < 24) a[k][tid] = cmul(a[k][tid], ip);
     if (tid >= 32 && tid < 44) fcol[tid - 32] = a[tid - 32][k];  // rows != k: untouched above
     __syncthreads();
@@ -171,35 +178,40 @@ __device__ bool gj_invert(Cx<double> (*a)[24], Cx<double>* fcol, int* piv, int t
   return true;
 }
 
+template <typename R>
 struct SetupArgs {
   Geom g;
-  int line0;               // first line of this launch
-  const Cx<double>* H;     // clover blocks of the parity [Nl][2][36][tp] (H_a, H_b = half the chiral
-                           // blocks of A), or null: A = 0
-  const Cx<double>* ut;    // general frame: U_t of the parity [Nl][9][tp]
-  const Cx<double>* pl;    // axial frame: the boundary link P of every line [Nl][9]
-  double s;                // boundary sign
-  Cx<double>* sinv;        // out: Sigma_t^-1 [Nl][T][144], transposed per block
-  Cx<double>* lam;         // out: Lambda [Nl][144], transposed
-  Cx<double>* scratch;     // [lines of this launch][12][T][12]: forward sweeps of the columns of V
-  int* singular;           // set to 1 if a block has no inverse
+  int line0;            // first line of this launch
+  const Cx<R>* H;       // clover blocks of the parity [Nl][2][36][tp] (H_a, H_b = half the chiral
+                        // blocks of A), or null: A = 0
+  const Cx<R>* ut;      // general frame: U_t of the parity [Nl][9][tp]
+  const Cx<R>* pl;      // axial frame: the boundary link P of every line [Nl][9]
+  R s;                  // boundary sign
+  Cx<R>* sinv;          // out: Sigma_t^-1 [Nl][T][144], transposed per block
+  Cx<R>* lam;           // out: Lambda [Nl][144], transposed
+  Cx<R>* zv;            // out: Z = T_0^-1 V [Nl][T][144], transposed per time slice like sinv
+  Cx<R>* scratch;       // [lines of this launch][12][T][12]: forward sweeps of the columns of V
+  int* singular;        // set to 1 if a block has no inverse
 };
 
-template <bool AX>
-__global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs A) {
-  __shared__ Cx<double> aug[12][24];
-  __shared__ Cx<double> prev[kBlk];  // Sigma_{t-1}^-1, transposed
-  __shared__ Cx<double> fcol[12];
-  __shared__ Cx<double> wl[9];       // a link: W_{t-1} while factoring, then U_w
-  __shared__ Cx<double> gsh[12][kGrp];
+// The factorisation in precision R (FP64 for the FP64 applies and solves; FP32 ones use factors
+// formed in FP32 from the FP32 gauge field and clover term)
+template <typename R, bool AX>
+__global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs<R> A) {
+  __shared__ Cx<R> aug[12][24];
+  __shared__ Cx<R> prev[kBlk];  // Sigma_{t-1}^-1, transposed
+  __shared__ Cx<R> fcol[12];
+  __shared__ Cx<R> wl[9];       // a link: W_{t-1} while factoring, then U_w
+  __shared__ Cx<R> gsh[12][kGrp];
   __shared__ int piv[2];
   const Geom& g = A.g;
   const int tid = threadIdx.x;
   const int l = A.line0 + blockIdx.x;
   const int T = g.T, tp = g.tp;
-  Cx<double>* S = A.sinv + (size_t)l * T * kBlk;
-  const Cx<double>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
-  const Cx<double>* Hl = A.H ? A.H + (size_t)l * 72 * tp : nullptr;
+  Cx<R>* S = A.sinv + (size_t)l * T * kBlk;
+  const Cx<R>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
+  const Cx<R>* Hl = A.H ? A.H + (size_t)l * 72 * tp : nullptr;
+  const R mu = (R)g.mu;
 
   // block LU of T_0
   for (int t = 0; t < T; ++t) {
@@ -208,10 +220,10 @@ __global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs A)
     __syncthreads();
     if (tid < kBlk) {
       const int r = tid / 12, c = tid - 12 * (tid / 12);
-      Cx<double> v = mk<double>(r == c ? g.mu : 0.0, 0.0);
+      Cx<R> v = mk<R>(r == c ? mu : R(0), R(0));
       if (Hl) {  // A = [[H_a + H_b, H_a - H_b], [H_a - H_b, H_a + H_b]] on the (P_+, P_-) halves
         const int i = r % 6, j = c % 6;
-        const Cx<double> ha = Hl[(size_t)(6 * i + j) * tp + sl], hb = Hl[(size_t)(36 + 6 * i + j) * tp + sl];
+        const Cx<R> ha = Hl[(size_t)(6 * i + j) * tp + sl], hb = Hl[(size_t)(36 + 6 * i + j) * tp + sl];
         v = (r < 6) == (c < 6) ? v + ha + hb : v + ha - hb;
       }
       if (t > 0 && r < 6 && c >= 6) {
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs A)
           v = v - prev[12 * c + r];
         } else {  // sum_ab conj(W[a][cr]) Sigma^-1[(sr, a), (sc, b)] W[b][cc]
           const int sr = r / 3, cr = r % 3, sc = c / 3, cc = c % 3;
-          Cx<double> acc = czero<double>();
+          Cx<R> acc = czero<R>();
 #pragma unroll
           for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -229,52 +241,54 @@ __global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs A)
         }
       }
       aug[r][c] = v;
-      aug[r][c + 12] = mk<double>(r == c ? 1.0 : 0.0, 0.0);
+      aug[r][c + 12] = mk<R>(r == c ? R(1) : R(0), R(0));
     }
     __syncthreads();
-    if (!gj_invert(aug, fcol, piv, tid, kSetupThreads)) {
+    if (!gj_invert<R>(aug, fcol, piv, tid, kSetupThreads)) {
       if (tid == 0) atomicOr(A.singular, 1);
       return;
     }
     if (tid < kBlk) {
       const int r = tid / 12, k = tid - 12 * (tid / 12);
-      const Cx<double> v = aug[r][k + 12];
+      const Cx<R> v = aug[r][k + 12];
       prev[12 * k + r] = v;
       S[(size_t)t * kBlk + 12 * k + r] = v;
     }
     __syncthreads();
   }
 
-  // W^dag T_0^-1 V, one column j of V per group
+  // Z = T_0^-1 V and W^dag Z, one column j of V per group
   if (tid < 9) wl[tid] = AX ? A.pl[(size_t)l * 9 + tid] : ut[(size_t)tid * tp + slot_of(g, T - 1)];
   __syncthreads();
   const int j = tid / kGrp, r = tid % kGrp;
   const unsigned mask = 0xFFFFu << (tid & 16);
-  Cx<double>* scr = A.scratch + ((size_t)blockIdx.x * 12 + j) * T * 12;
-  const double ms = -A.s;
-  auto rhs = [&](int t) -> Cx<double> {
+  Cx<R>* scr = A.scratch + ((size_t)blockIdx.x * 12 + j) * T * 12;
+  const R ms = -A.s;
+  auto rhs = [&](int t) -> Cx<R> {
     if (j < 6) {  // V_0 = -s P_+ (x) U_w^dag: rows of spin j / 3
       if (t == 0 && r < 6 && r / 3 == j / 3) return ms * cconj(wl[3 * (j % 3) + r % 3]);
     } else {      // V_{N_t-1} = -s P_- (x) U_w
       if (t == T - 1 && r >= 6 && r / 3 == j / 3) return ms * wl[3 * (r % 3) + j % 3];
     }
-    return czero<double>();
+    return czero<R>();
   };
-  auto zst = [&](int t, Cx<double> v) { scr[(size_t)t * 12 + r] = v; };
+  auto zst = [&](int t, Cx<R> v) { scr[(size_t)t * 12 + r] = v; };
   auto zld = [&](int t) { return scr[(size_t)t * 12 + r]; };
-  Cx<double> y0 = czero<double>(), yT = czero<double>();
-  auto corner = [&](int t, Cx<double> v) {
+  Cx<R> y0 = czero<R>(), yT = czero<R>();
+  Cx<R>* Z = A.zv + (size_t)l * T * kBlk + 12 * j + r;
+  auto column = [&](int t, Cx<R> v) {
+    Z[(size_t)t * kBlk] = v;
     if (t == 0) y0 = v;
     if (t == T - 1) yT = v;
   };
-  t0_solve<double, AX>(S, ut, g, r, mask, gsh[j], rhs, zst, zld, corner);
+  t0_solve<R, AX>(S, ut, g, r, mask, gsh[j], rhs, zst, zld, column);
   __syncthreads();
   if (r < 12) {  // 1 + W^dag T_0^-1 V, column j
-    aug[r][j] = (r < 6 ? yT : y0) + mk<double>(r == j ? 1.0 : 0.0, 0.0);
-    aug[r][j + 12] = mk<double>(r == j ? 1.0 : 0.0, 0.0);
+    aug[r][j] = (r < 6 ? yT : y0) + mk<R>(r == j ? R(1) : R(0), R(0));
+    aug[r][j + 12] = mk<R>(r == j ? R(1) : R(0), R(0));
   }
   __syncthreads();
-  if (!gj_invert(aug, fcol, piv, tid, kSetupThreads)) {
+  if (!gj_invert<R>(aug, fcol, piv, tid, kSetupThreads)) {
     if (tid == 0) atomicOr(A.singular, 1);
     return;
   }
@@ -295,77 +309,208 @@ struct QinvArgs {
   int swap_in;         // read in with the spin halves exchanged
   const Cx<R>* sinv;   // [Nl][T][144]
   const Cx<R>* lam;    // [Nl][144]
+  const Cx<R>* zv;     // Z = T_0^-1 V [Nl][T][144]
   const Cx<R>* ut;     // general frame: U_t [Nl][9][tp]
   const Cx<R>* pl;     // axial frame: P [Nl][9]
   R s;                 // boundary sign
 };
 
+// per-lane asynchronous global -> shared copies (completion tracked per thread in commit groups)
+template <typename R>
+__device__ __forceinline__ void cp_async(Cx<R>* dst, const Cx<R>* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(__cvta_generic_to_global(src)), "n"((int)sizeof(Cx<R>))
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kQGroups = 4;  // 16-lane groups per CTA of k_qinv_apply
+
+// Ring depth of k_qinv_apply: the steps whose operands are in flight (FP32 6, FP64 4)
+template <typename R>
+struct QDepth {
+  static constexpr int value = sizeof(R) == 8 ? 4 : 6;
+};
+
+// Q^-1 per (line, right-hand side), one 16-lane group each: chi = T_0^-1 b by the two sweeps,
+// then Q^-1 b = chi - Z c with c = Lambda W^dag chi, a pass with no serial chain. Every step takes
+// lane r's row of a 12x12 block and one more operand (b_t, or the post-axpy operand) from a
+// per-group ring of D steps in shared memory that the lane fills D - 1 steps ahead with cp.async;
+// a lane reads only what it copied itself, so the ring needs no barrier. z_t and chi_t go through
+// out and come back two steps ahead of their use.
 template <typename R, bool AX>
-__global__ void __launch_bounds__(kApplyThreads) k_qinv_apply(const QinvArgs<R> A) {
-  __shared__ Cx<R> gsh[kApplyThreads / kGrp][kGrp];
+__global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R> A) {
+  constexpr int D = QDepth<R>::value;
+  __shared__ Cx<R> ring[kQGroups][D][13][12];
+  __shared__ Cx<R> gsh[kQGroups][kGrp];
   const Geom& g = A.g;
   const int q = threadIdx.x, r = q % kGrp, gi = q / kGrp;
   const unsigned mask = 0xFFFFu << (q & 16);
-  const size_t grp = (size_t)blockIdx.x * (kApplyThreads / kGrp) + gi;
+  const size_t grp = (size_t)blockIdx.x * kQGroups + gi;
   if (grp >= (size_t)A.nrhs * g.Nl) return;  // the group's 16 lanes leave together
   const int l = (int)(grp / A.nrhs), k = (int)(grp % A.nrhs);
   const int T = g.T, tp = g.tp;
   const bool act = r < 12;
   const int rc = act ? r : 0;  // lanes 12-15 address component 0 but never load or store
+  const int sr = rc / 3, cr = rc - 3 * (rc / 3);
   const size_t base = ((size_t)k * g.Nl + l) * NSPIN_C * tp;
   const Cx<R>* in = A.in + base + (size_t)(A.swap_in ? (rc + 6) % 12 : rc) * tp;
   Cx<R>* out = A.out + base + (size_t)rc * tp;
   const Cx<R>* xp = A.xpost ? A.xpost + base + (size_t)rc * tp : nullptr;
-  const Cx<R>* S = A.sinv + (size_t)l * T * kBlk;
+  const Cx<R>* S = A.sinv + (size_t)l * T * kBlk + rc;  // lane rc's entries: S[t * 144 + 12 k]
+  const Cx<R>* Zl = A.zv + (size_t)l * T * kBlk + rc;
   const Cx<R>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
+  Cx<R>(*rg)[13][12] = ring[gi];
   Cx<R>* sh = gsh[gi];
 
-  // chi = T_0^-1 b: only its corners chi_0, chi_{N_t-1} are kept; z goes through out
-  auto rhs = [&](int t) { return in[slot_of(g, t)]; };
-  auto zst = [&](int t, Cx<R> v) { out[slot_of(g, t)] = v; };
-  auto zld = [&](int t) { return out[slot_of(g, t)]; };
-  Cx<R> y0 = czero<R>(), yT = czero<R>();
-  auto corner = [&](int t, Cx<R> v) {
-    if (t == 0) y0 = v;
-    if (t == T - 1) yT = v;
-  };
-  t0_solve<R, AX>(S, ut, g, r, mask, sh, rhs, zst, zld, corner);
-
-  // c = Lambda W^dag chi
-  if (act) sh[r] = r < 6 ? yT : y0;
-  __syncwarp(mask);
-  const Cx<R> c = act ? row_times(A.lam + (size_t)l * kBlk, r, sh) : czero<R>();
-  __syncwarp(mask);
-  if (act) sh[r] = c;
-  __syncwarp(mask);
-  // -V c: + s U_w^dag c on the P_+ half of slot 0, + s U_w c on the P_- half of slot N_t - 1
-  Cx<R> v0 = czero<R>(), vT = czero<R>();
-  if (act) {
-    const int sr = r / 3, cr = r % 3;
-    const Cx<R>* uw = AX ? A.pl + (size_t)l * 9 : ut + slot_of(g, T - 1);
-    const size_t st = AX ? 1 : (size_t)tp;
-    if (r < 6) {
+  // forward sweep: z_t to out
+  Cx<R> z = czero<R>();
+  {
+    auto issue = [&](int t) {  // step t: b_t, and for lanes 0-5 row rc of Sigma_{t-1}^-1
+      if (t < T && act) {
+        Cx<R>(*d)[12] = rg[t % D];
+        cp_async<R>(&d[12][rc], in + slot_of(g, t));
+        if (t >= 1 && r < 6) {
+          const Cx<R>* src = S + (size_t)(t - 1) * kBlk;
 #pragma unroll
-      for (int cc = 0; cc < 3; ++cc) v0 = cfmaconj(v0, uw[(3 * cc + cr) * st], sh[3 * sr + cc]);
-      v0 = A.s * v0;
-    } else {
+          for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
+        }
+      }
+      cp_commit();
+    };
+    for (int t = 0; t < D - 1; ++t) issue(t);
+    for (int t = 0; t < T; ++t) {
+      issue(t + D - 1);
+      cp_wait<D - 1>();
+      Cx<R>(*d)[12] = rg[t % D];
+      Cx<R> b = act ? d[12][rc] : czero<R>();
+      if (t > 0) {
+        if (act) sh[rc] = z;
+        __syncwarp(mask);
+        Cx<R> w = czero<R>();
+        if (r < 6) {
 #pragma unroll
-      for (int cc = 0; cc < 3; ++cc) vT = cfma(vT, uw[(3 * cr + cc) * st], sh[3 * sr + cc]);
-      vT = A.s * vT;
+          for (int kk = 0; kk < 12; ++kk) w = cfma(w, d[kk][rc], sh[kk]);
+        }
+        __syncwarp(mask);
+        if (r < 6) sh[rc] = w;
+        __syncwarp(mask);
+        if (r < 6) {
+          if (AX) {
+            b = b + sh[rc];
+          } else {  // + (W_{t-1}^dag w) on spin sr
+            const int sl = slot_of(g, t - 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) b = cfmaconj(b, ut[(size_t)(3 * c + cr) * tp + sl], sh[3 * sr + c]);
+          }
+        }
+        __syncwarp(mask);
+      }
+      z = b;
+      if (act) out[slot_of(g, t)] = z;
     }
+    cp_wait<0>();
   }
+
+  // backward sweep: chi_t to out
+  Cx<R> y0 = czero<R>(), yT = czero<R>();
+  {
+    auto issue = [&](int u) {  // step u (t = N_t - 1 - u): row rc of Sigma_t^-1
+      if (u < T && act) {
+        Cx<R>(*d)[12] = rg[u % D];
+        const Cx<R>* src = S + (size_t)(T - 1 - u) * kBlk;
+#pragma unroll
+        for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
+      }
+      cp_commit();
+    };
+    for (int u = 0; u < D - 1; ++u) issue(u);
+    Cx<R> zt = z;
+    Cx<R> znext = act && T >= 2 ? out[slot_of(g, T - 2)] : czero<R>();
+    Cx<R> y = czero<R>();
+    for (int u = 0; u < T; ++u) {
+      const int t = T - 1 - u;
+      issue(u + D - 1);
+      cp_wait<D - 1>();
+      Cx<R>(*d)[12] = rg[u % D];
+      Cx<R> v = zt;
+      zt = znext;
+      if (act && t >= 2) znext = out[slot_of(g, t - 2)];  // used two steps on
+      if (u > 0) {  // + [P_- (x) W_t] y_{t+1}
+        if (act) sh[rc] = y;
+        __syncwarp(mask);
+        if (act && r >= 6) {
+          if (AX) {
+            v = v + sh[rc];
+          } else {
+            const int sl = slot_of(g, t);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v = cfma(v, ut[(size_t)(3 * cr + c) * tp + sl], sh[3 * sr + c]);
+          }
+        }
+        __syncwarp(mask);
+      }
+      if (act) sh[rc] = v;
+      __syncwarp(mask);
+      y = czero<R>();
+      if (act) {
+#pragma unroll
+        for (int kk = 0; kk < 12; ++kk) y = cfma(y, d[kk][rc], sh[kk]);
+      }
+      __syncwarp(mask);
+      if (act) out[slot_of(g, t)] = y;
+      if (t == 0) y0 = y;
+      if (t == T - 1) yT = y;
+    }
+    cp_wait<0>();
+  }
+
+  // c = Lambda W^dag chi (W^dag chi: the P_+ half of chi_{N_t-1}, the P_- half of chi_0)
+  if (act) sh[rc] = r < 6 ? yT : y0;
   __syncwarp(mask);
-  auto rhs2 = [&](int t) {
-    Cx<R> b = in[slot_of(g, t)];
-    if (t == 0) b = b + v0;
-    if (t == T - 1) b = b + vT;
-    return b;
-  };
-  auto fin = [&](int t, Cx<R> y) {
-    const int sl = slot_of(g, t);
-    out[sl] = xp ? xp[sl] + A.apost * y : y;
-  };
-  t0_solve<R, AX>(S, ut, g, r, mask, sh, rhs2, zst, zld, fin);
+  Cx<R> c = czero<R>();
+  if (act) c = row_times(A.lam + (size_t)l * kBlk, rc, sh);
+  __syncwarp(mask);
+  if (act) sh[rc] = c;
+  __syncwarp(mask);
+  Cx<R> cv[12];
+#pragma unroll
+  for (int kk = 0; kk < 12; ++kk) cv[kk] = sh[kk];
+  __syncwarp(mask);
+
+  // out_t = xpost_t + apost (chi_t - Z_t c): independent steps
+  {
+    const bool post = xp != nullptr;
+    auto issue = [&](int t) {  // step t: row rc of Z_t, and xpost_t
+      if (t < T && act) {
+        Cx<R>(*d)[12] = rg[t % D];
+        const Cx<R>* src = Zl + (size_t)t * kBlk;
+#pragma unroll
+        for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
+        if (post) cp_async<R>(&d[12][rc], xp + slot_of(g, t));
+      }
+      cp_commit();
+    };
+    for (int t = 0; t < D - 1; ++t) issue(t);
+    Cx<R> ct = act ? out[slot_of(g, 0)] : czero<R>();
+    Cx<R> cnext = act && T >= 2 ? out[slot_of(g, 1)] : czero<R>();
+    for (int t = 0; t < T; ++t) {
+      issue(t + D - 1);
+      cp_wait<D - 1>();
+      Cx<R>(*d)[12] = rg[t % D];
+      Cx<R> x = ct;
+      ct = cnext;
+      if (act && t + 2 < T) cnext = out[slot_of(g, t + 2)];
+      if (act) {
+#pragma unroll
+        for (int kk = 0; kk < 12; ++kk) x = x - cmul(d[kk][rc], cv[kk]);
+        out[slot_of(g, t)] = post ? d[12][rc] + A.apost * x : x;
+      }
+    }
+    cp_wait<0>();
+  }
   if (act)
     for (int t = T; t < tp; ++t) out[slot_of(g, t)] = czero<R>();  // padding slots stay zero
 }
@@ -377,69 +522,12 @@ template <typename R>
 struct QFactors {
   const Cx<R>* sinv[2];
   const Cx<R>* lam[2];
+  const Cx<R>* zv[2];
 };
 
 const char* const kSinvName[2][2] = {{"fsw_sinv0_f64", "fsw_sinv1_f64"}, {"fsw_sinv0_f32", "fsw_sinv1_f32"}};
 const char* const kLamName[2][2] = {{"fsw_lam0_f64", "fsw_lam1_f64"}, {"fsw_lam0_f32", "fsw_lam1_f32"}};
-
-// Factor T_0 and form Lambda on every line of both parities from the handle's gauge field and
-// clover term (A = 0 without one), in FP64, and with f32 also their FP32 copies.
-void qinv_setup(wf_handle* h, bool f32) {
-  const Geom& g = h->g;
-  cudaStream_t s = h->stream;
-  const size_t nb = (size_t)g.Nl * g.T * kBlk, nl = (size_t)g.Nl * kBlk;
-  const size_t per_line = (size_t)12 * g.T * 12 * sizeof(Cx<double>);
-  const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.Nl, kScratchBytes / per_line));
-  Cx<double>* scratch = h->buf<Cx<double>>("fsw_scratch", (size_t)chunk * 12 * g.T * 12);
-  int* singular = h->buf<int>("fsw_singular", 1);
-  WF_CUDA(cudaMemsetAsync(singular, 0, sizeof(int), s));
-  for (int p = 0; p < 2; ++p) {
-    SetupArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.g = g;
-    a.H = h->clover ? h->clov64[p].as<Cx<double>>() : nullptr;
-    a.ut = h->ut64[p].as<Cx<double>>();
-    a.pl = h->pl64[p].as<Cx<double>>();
-    a.s = g.bc;
-    a.sinv = h->buf<Cx<double>>(kSinvName[0][p], nb);
-    a.lam = h->buf<Cx<double>>(kLamName[0][p], nl);
-    a.scratch = scratch;
-    a.singular = singular;
-    for (int l0 = 0; l0 < g.Nl; l0 += chunk) {
-      a.line0 = l0;
-      const int lines = std::min(chunk, g.Nl - l0);
-      Prof P(h, "qinv_setup_f64");
-      if (h->axial)
-        k_qinv_setup<true><<<lines, kSetupThreads, 0, s>>>(a);
-      else
-        k_qinv_setup<false><<<lines, kSetupThreads, 0, s>>>(a);
-      WF_CUDA(cudaGetLastError());
-    }
-  }
-  int sing = 0;
-  WF_CUDA(cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, s));
-  WF_CUDA(cudaStreamSynchronize(s));
-  if (sing) throw Error(WF_ESINGULAR, "a block of mu + A - D_t on a time line has no inverse");
-  if (f32) {
-    for (int p = 0; p < 2; ++p) {
-      Prof P(h, "qinv_d2f", 2);
-      launch_d2f(h->buf<Cx<double>>(kSinvName[0][p], nb), h->buf<Cx<float>>(kSinvName[1][p], nb), nb, s);
-      launch_d2f(h->buf<Cx<double>>(kLamName[0][p], nl), h->buf<Cx<float>>(kLamName[1][p], nl), nl, s);
-    }
-  }
-}
-
-template <typename R>
-QFactors<R> qfactors(wf_handle* h) {
-  const Geom& g = h->g;
-  const int w = sizeof(R) == 8 ? 0 : 1;
-  QFactors<R> f;
-  for (int p = 0; p < 2; ++p) {
-    f.sinv[p] = h->buf<Cx<R>>(kSinvName[w][p], (size_t)g.Nl * g.T * kBlk);
-    f.lam[p] = h->buf<Cx<R>>(kLamName[w][p], (size_t)g.Nl * kBlk);
-  }
-  return f;
-}
+const char* const kZName[2][2] = {{"fsw_z0_f64", "fsw_z1_f64"}, {"fsw_z0_f32", "fsw_z1_f32"}};
 
 template <typename R>
 const Cx<R>* gauge_ut(wf_handle* h, int p) {
@@ -463,8 +551,73 @@ const Cx<R>* gauge_us(wf_handle* h, int p) {
     return h->us32[p].as<Cx<float>>();
 }
 template <typename R>
+const Cx<R>* clover_of(wf_handle* h, int p) {
+  if constexpr (sizeof(R) == 8)
+    return h->clov64[p].as<Cx<double>>();
+  else
+    return h->clov32[p].as<Cx<float>>();
+}
+template <typename R>
 const char* tag(const char* f64, const char* f32) {
   return sizeof(R) == 8 ? f64 : f32;
+}
+
+
+// Factor T_0 and form Lambda on every line of both parities from the handle's gauge field and
+// clover term (A = 0 without one), in precision R from the gauge and clover copies of that
+// precision.
+template <typename R>
+void qinv_setup(wf_handle* h) {
+  const Geom& g = h->g;
+  cudaStream_t s = h->stream;
+  const int w = sizeof(R) == 8 ? 0 : 1;
+  const size_t nb = (size_t)g.Nl * g.T * kBlk, nl = (size_t)g.Nl * kBlk;
+  const size_t per_line = (size_t)12 * g.T * 12 * sizeof(Cx<R>);
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.Nl, kScratchBytes / per_line));
+  Cx<R>* scratch = h->buf<Cx<R>>(tag<R>("fsw_scratch_f64", "fsw_scratch_f32"), (size_t)chunk * 12 * g.T * 12);
+  int* singular = h->buf<int>("fsw_singular", 1);
+  WF_CUDA(cudaMemsetAsync(singular, 0, sizeof(int), s));
+  for (int p = 0; p < 2; ++p) {
+    SetupArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.H = h->clover ? clover_of<R>(h, p) : nullptr;
+    a.ut = gauge_ut<R>(h, p);
+    a.pl = gauge_pl<R>(h, p);
+    a.s = (R)g.bc;
+    a.sinv = h->buf<Cx<R>>(kSinvName[w][p], nb);
+    a.lam = h->buf<Cx<R>>(kLamName[w][p], nl);
+    a.zv = h->buf<Cx<R>>(kZName[w][p], nb);
+    a.scratch = scratch;
+    a.singular = singular;
+    for (int l0 = 0; l0 < g.Nl; l0 += chunk) {
+      a.line0 = l0;
+      const int lines = std::min(chunk, g.Nl - l0);
+      Prof P(h, tag<R>("qinv_setup_f64", "qinv_setup_f32"));
+      if (h->axial)
+        k_qinv_setup<R, true><<<lines, kSetupThreads, 0, s>>>(a);
+      else
+        k_qinv_setup<R, false><<<lines, kSetupThreads, 0, s>>>(a);
+      WF_CUDA(cudaGetLastError());
+    }
+  }
+  int sing = 0;
+  WF_CUDA(cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  if (sing) throw Error(WF_ESINGULAR, "a block of mu + A - D_t on a time line has no inverse");
+}
+
+template <typename R>
+QFactors<R> qfactors(wf_handle* h) {
+  const Geom& g = h->g;
+  const int w = sizeof(R) == 8 ? 0 : 1;
+  QFactors<R> f;
+  for (int p = 0; p < 2; ++p) {
+    f.sinv[p] = h->buf<Cx<R>>(kSinvName[w][p], (size_t)g.Nl * g.T * kBlk);
+    f.lam[p] = h->buf<Cx<R>>(kLamName[w][p], (size_t)g.Nl * kBlk);
+    f.zv[p] = h->buf<Cx<R>>(kZName[w][p], (size_t)g.Nl * g.T * kBlk);
+  }
+  return f;
 }
 
 // out = xpost + apost Q^-1 (S) in on the lines of parity p
@@ -482,16 +635,17 @@ void qinv(wf_handle* h, const QFactors<R>& F, int p, const Cx<R>* in, Cx<R>* out
   a.swap_in = swap_in;
   a.sinv = F.sinv[p];
   a.lam = F.lam[p];
+  a.zv = F.zv[p];
   a.ut = gauge_ut<R>(h, p);
   a.pl = gauge_pl<R>(h, p);
   a.s = (R)h->g.bc;
   const size_t groups = (size_t)nrhs * h->g.Nl;
-  const unsigned blocks = (unsigned)((groups + kApplyThreads / kGrp - 1) / (kApplyThreads / kGrp));
+  const unsigned blocks = (unsigned)((groups + kQGroups - 1) / kQGroups);
   Prof P(h, tag<R>("qinv_apply_f64", "qinv_apply_f32"));
   if (h->axial)
-    k_qinv_apply<R, true><<<blocks, kApplyThreads, 0, h->stream>>>(a);
+    k_qinv_apply<R, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
   else
-    k_qinv_apply<R, false><<<blocks, kApplyThreads, 0, h->stream>>>(a);
+    k_qinv_apply<R, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
   WF_CUDA(cudaGetLastError());
 }
 
@@ -579,7 +733,7 @@ int apply_qinv_abi(wf_handle* h, const double* in, double* out, int nrhs) {
   Cx<R>* io = h->buf<Cx<R>>(tag<R>("fsw_io_f64", "fsw_io_f32"), nt);
   Cx<R>* oe = h->buf<Cx<R>>(tag<R>("fsw_oe_f64", "fsw_oe_f32"), nt);
   Cx<R>* oo = h->buf<Cx<R>>(tag<R>("fsw_oo_f64", "fsw_oo_f32"), nt);
-  qinv_setup(h, sizeof(R) == 4);
+  qinv_setup<R>(h);
   const QFactors<R> F = qfactors<R>(h);
   {
     Prof P(h, tag<R>("import_spinor_f64", "import_spinor_f32"));
@@ -608,7 +762,7 @@ int apply_schur_full_abi(wf_handle* h, const double* in_odd, double* out_odd, in
   Cx<R>* e1 = h->buf<Cx<R>>(tag<R>("fsw_e1_f64", "fsw_e1_f32"), nt);
   Cx<R>* e2 = h->buf<Cx<R>>(tag<R>("fsw_e2_f64", "fsw_e2_f32"), nt);
   Cx<R>* o1 = h->buf<Cx<R>>(tag<R>("fsw_o1_f64", "fsw_o1_f32"), nt);
-  qinv_setup(h, sizeof(R) == 4);
+  qinv_setup<R>(h);
   const QFactors<R> F = qfactors<R>(h);
   {
     Prof P(h, tag<R>("import_compact_f64", "import_compact_f32"));
@@ -775,7 +929,7 @@ int solve_full_abi(wf_handle* h, const double* rhs, double* x, int nrhs, double 
   Cx<R>* bo = h->buf<Cx<R>>(tag<R>("fsw_bo_f64", "fsw_bo_f32"), nt);
   Cx<R>* yo = h->buf<Cx<R>>(tag<R>("fsw_yo_f64", "fsw_yo_f32"), nt);
   Cx<R>* we = h->buf<Cx<R>>(tag<R>("fsw_we_f64", "fsw_we_f32"), nt);
-  qinv_setup(h, sizeof(R) == 4);
+  qinv_setup<R>(h);
   const QFactors<R> F = qfactors<R>(h);
   {
     Prof P(h, "import_spinor_f64");
