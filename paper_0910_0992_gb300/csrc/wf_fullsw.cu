@@ -328,11 +328,13 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 
 constexpr int kQGroups = 4;  // 16-lane groups per CTA of k_qinv_apply
 
-// Ring depth of k_qinv_apply: the steps whose operands are in flight (FP32 6, FP64 4)
-template <typename R>
+// Ring depth of k_qinv_apply, the steps whose operands are in flight: deep (FP32 6, FP64 4) for
+// few groups per SM, shallow (FP32 3, FP64 2: more CTAs per SM) for four or more sources
+template <typename R, bool DEEP>
 struct QDepth {
-  static constexpr int value = sizeof(R) == 8 ? 4 : 6;
+  static constexpr int value = DEEP ? (sizeof(R) == 8 ? 4 : 6) : (sizeof(R) == 8 ? 2 : 3);
 };
+constexpr int kTMax = 256;  // longest time line
 
 // Q^-1 per (line, right-hand side), one 16-lane group each: chi = T_0^-1 b by the two sweeps,
 // then Q^-1 b = chi - Z c with c = Lambda W^dag chi, a pass with no serial chain. Every step takes
@@ -340,12 +342,15 @@ struct QDepth {
 // per-group ring of D steps in shared memory that the lane fills D - 1 steps ahead with cp.async;
 // a lane reads only what it copied itself, so the ring needs no barrier. z_t and chi_t go through
 // out and come back two steps ahead of their use.
-template <typename R, bool AX>
+template <typename R, bool AX, bool DEEP>
 __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R> A) {
-  constexpr int D = QDepth<R>::value;
+  constexpr int D = QDepth<R, DEEP>::value;
   __shared__ Cx<R> ring[kQGroups][D][13][12];
   __shared__ Cx<R> gsh[kQGroups][kGrp];
+  __shared__ int stab[kTMax];  // slot of every time
   const Geom& g = A.g;
+  for (int i = threadIdx.x; i < g.tp; i += blockDim.x) stab[i] = slot_of(g, i);
+  __syncthreads();
   const int q = threadIdx.x, r = q % kGrp, gi = q / kGrp;
   const unsigned mask = 0xFFFFu << (q & 16);
   const size_t grp = (size_t)blockIdx.x * kQGroups + gi;
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
     auto issue = [&](int t) {  // step t: b_t, and for lanes 0-5 row rc of Sigma_{t-1}^-1
       if (t < T && act) {
         Cx<R>(*d)[12] = rg[t % D];
-        cp_async<R>(&d[12][rc], in + slot_of(g, t));
+        cp_async<R>(&d[12][rc], in + stab[t]);
         if (t >= 1 && r < 6) {
           const Cx<R>* src = S + (size_t)(t - 1) * kBlk;
 #pragma unroll
@@ -391,8 +396,13 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
         __syncwarp(mask);
         Cx<R> w = czero<R>();
         if (r < 6) {
+          Cx<R> w1 = czero<R>();
 #pragma unroll
-          for (int kk = 0; kk < 12; ++kk) w = cfma(w, d[kk][rc], sh[kk]);
+          for (int kk = 0; kk < 12; kk += 2) {
+            w = cfma(w, d[kk][rc], sh[kk]);
+            w1 = cfma(w1, d[kk + 1][rc], sh[kk + 1]);
+          }
+          w = w + w1;
         }
         __syncwarp(mask);
         if (r < 6) sh[rc] = w;
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
           if (AX) {
             b = b + sh[rc];
           } else {  // + (W_{t-1}^dag w) on spin sr
-            const int sl = slot_of(g, t - 1);
+            const int sl = stab[t - 1];
 #pragma unroll
             for (int c = 0; c < 3; ++c) b = cfmaconj(b, ut[(size_t)(3 * c + cr) * tp + sl], sh[3 * sr + c]);
           }
@@ -409,7 +419,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
         __syncwarp(mask);
       }
       z = b;
-      if (act) out[slot_of(g, t)] = z;
+      if (act) out[stab[t]] = z;
     }
     cp_wait<0>();
   }
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
     };
     for (int u = 0; u < D - 1; ++u) issue(u);
     Cx<R> zt = z;
-    Cx<R> znext = act && T >= 2 ? out[slot_of(g, T - 2)] : czero<R>();
+    Cx<R> znext = act && T >= 2 ? out[stab[T - 2]] : czero<R>();
     Cx<R> y = czero<R>();
     for (int u = 0; u < T; ++u) {
       const int t = T - 1 - u;
@@ -437,7 +447,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
       Cx<R>(*d)[12] = rg[u % D];
       Cx<R> v = zt;
       zt = znext;
-      if (act && t >= 2) znext = out[slot_of(g, t - 2)];  // used two steps on
+      if (act && t >= 2) znext = out[stab[t - 2]];  // used two steps on
       if (u > 0) {  // + [P_- (x) W_t] y_{t+1}
         if (act) sh[rc] = y;
         __syncwarp(mask);
@@ -445,7 +455,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
           if (AX) {
             v = v + sh[rc];
           } else {
-            const int sl = slot_of(g, t);
+            const int sl = stab[t];
 #pragma unroll
             for (int c = 0; c < 3; ++c) v = cfma(v, ut[(size_t)(3 * cr + c) * tp + sl], sh[3 * sr + c]);
           }
@@ -456,11 +466,16 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
       __syncwarp(mask);
       y = czero<R>();
       if (act) {
+        Cx<R> y1 = czero<R>();
 #pragma unroll
-        for (int kk = 0; kk < 12; ++kk) y = cfma(y, d[kk][rc], sh[kk]);
+        for (int kk = 0; kk < 12; kk += 2) {
+          y = cfma(y, d[kk][rc], sh[kk]);
+          y1 = cfma(y1, d[kk + 1][rc], sh[kk + 1]);
+        }
+        y = y + y1;
       }
       __syncwarp(mask);
-      if (act) out[slot_of(g, t)] = y;
+      if (act) out[stab[t]] = y;
       if (t == 0) y0 = y;
       if (t == T - 1) yT = y;
     }
@@ -489,30 +504,30 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
         const Cx<R>* src = Zl + (size_t)t * kBlk;
 #pragma unroll
         for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
-        if (post) cp_async<R>(&d[12][rc], xp + slot_of(g, t));
+        if (post) cp_async<R>(&d[12][rc], xp + stab[t]);
       }
       cp_commit();
     };
     for (int t = 0; t < D - 1; ++t) issue(t);
-    Cx<R> ct = act ? out[slot_of(g, 0)] : czero<R>();
-    Cx<R> cnext = act && T >= 2 ? out[slot_of(g, 1)] : czero<R>();
+    Cx<R> ct = act ? out[stab[0]] : czero<R>();
+    Cx<R> cnext = act && T >= 2 ? out[stab[1]] : czero<R>();
     for (int t = 0; t < T; ++t) {
       issue(t + D - 1);
       cp_wait<D - 1>();
       Cx<R>(*d)[12] = rg[t % D];
       Cx<R> x = ct;
       ct = cnext;
-      if (act && t + 2 < T) cnext = out[slot_of(g, t + 2)];
+      if (act && t + 2 < T) cnext = out[stab[t + 2]];
       if (act) {
 #pragma unroll
         for (int kk = 0; kk < 12; ++kk) x = x - cmul(d[kk][rc], cv[kk]);
-        out[slot_of(g, t)] = post ? d[12][rc] + A.apost * x : x;
+        out[stab[t]] = post ? d[12][rc] + A.apost * x : x;
       }
     }
     cp_wait<0>();
   }
   if (act)
-    for (int t = T; t < tp; ++t) out[slot_of(g, t)] = czero<R>();  // padding slots stay zero
+    for (int t = T; t < tp; ++t) out[stab[t]] = czero<R>();  // padding slots stay zero
 }
 
 // ----------------------------------------------------------------------------
@@ -639,13 +654,22 @@ void qinv(wf_handle* h, const QFactors<R>& F, int p, const Cx<R>* in, Cx<R>* out
   a.ut = gauge_ut<R>(h, p);
   a.pl = gauge_pl<R>(h, p);
   a.s = (R)h->g.bc;
+  if (h->g.tp > kTMax) throw Error(WF_EINVAL, "Q^-1 kernel: padded time line longer than 256 slots");
   const size_t groups = (size_t)nrhs * h->g.Nl;
   const unsigned blocks = (unsigned)((groups + kQGroups - 1) / kQGroups);
   Prof P(h, tag<R>("qinv_apply_f64", "qinv_apply_f32"));
-  if (h->axial)
-    k_qinv_apply<R, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
-  else
-    k_qinv_apply<R, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+  const bool deep = nrhs < 4;
+  if (h->axial) {
+    if (deep)
+      k_qinv_apply<R, true, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+    else
+      k_qinv_apply<R, true, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+  } else {
+    if (deep)
+      k_qinv_apply<R, false, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+    else
+      k_qinv_apply<R, false, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+  }
   WF_CUDA(cudaGetLastError());
 }
 

@@ -3,7 +3,7 @@ Preconditioning with Clover") against ``oracle/clover.py``.
 
 Q^-1 = (A + mu - D_t)^-1 (FP64 1e-12, FP32 1e-5) and M-hat_full with its adjoint (same
 tolerances) on lattices with several warps, padded and odd time lines, a 160-site line (five
-sites per lane), both boundary conditions and both frames; without a clover term Q^-1 equals the
+sites per lane), both boundary conditions and both frames, with two and five sources; without a clover term Q^-1 equals the
 Wilson C_R C_L; solves of M_SW in FP64 and by FP32 defect correction to the oracle-checked 1e-10
 true residual, in the oracle's iteration count (FP64); host arrays; and the errors (precision,
 arguments, iteration limit, NaN source).
@@ -73,6 +73,22 @@ def test_qinv(case):
     x = _dev(eta)
     assert _rel(w.apply_Qinv(x).cpu().numpy(), ref) < 1e-12
     assert _rel(w.apply_Qinv(x, f32=True).cpu().numpy(), ref) < 1e-5
+
+
+def test_qinv_many_sources(case):
+    """Five sources: the launch configuration for four or more sources (a shallower operand ring)."""
+    key, p, U, Acl, eta, w = case
+    if key not in ((4, 12), (2, 160)):
+        pytest.skip("two layouts suffice")
+    eta5 = S.gaussian_source(p.L, p.T, 149, nrhs=5)
+    ref = _oracle(key + ("Qinv5",), lambda: CL.Q_inverse(U, Acl, eta5, p))
+    x = _dev(eta5)
+    assert _rel(w.apply_Qinv(x).cpu().numpy(), ref) < 1e-12
+    assert _rel(w.apply_Qinv(x, f32=True).cpu().numpy(), ref) < 1e-5
+    x5, iters, res, status = w.solve_full_sw(x, tol=1e-10, precision=wf.WF_FP32)
+    assert status == wf.WF_OK and max(res) <= 1e-10
+    psi = x5.cpu().numpy()
+    assert max(CL.true_residual(U, Acl, psi[k], eta5[k], p) for k in range(5)) <= TRUE_RESID
 
 
 def test_schur_full(case):
