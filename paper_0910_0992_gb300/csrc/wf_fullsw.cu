@@ -41,8 +41,8 @@
 // has no serial chain. Lane r only ever needs
 // row r of a block, so it streams its rows (and b_t) into a per-group ring in shared memory with
 // cp.async several steps ahead of their use: the sweeps' serial chains then wait on shared memory
-// and arithmetic, not on DRAM. Blocks are stored transposed per time slice, [line][t][k][r], so
-// that the twelve lanes of a group copy one column k of a block as 12 consecutive elements.
+// and arithmetic, not on DRAM. Blocks are stored row-major per time slice, [line][t][r][k], so that
+// a lane copies its row as 16-byte pieces.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -64,12 +64,12 @@ constexpr size_t kScratchBytes = 256u << 20;   // bound of the setup's sweep scr
 template <typename R>
 __device__ __forceinline__ Cx<R> cconj(Cx<R> a) { return mk<R>(a.re, -a.im); }
 
-// row r of the transposed 12x12 block B (element (r, k) at B[12 k + r]) times the group's vector v
+// row r of the 12x12 block B (element (r, k) at B[12 r + k]) times the group's vector v
 template <typename R>
 __device__ __forceinline__ Cx<R> row_times(const Cx<R>* __restrict__ B, int r, const Cx<R>* v) {
   Cx<R> acc = czero<R>();
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc = cfma(acc, B[12 * k + r], v[k]);
+  for (int k = 0; k < 12; ++k) acc = cfma(acc, B[12 * r + k], v[k]);
   return acc;
 }
 
@@ -187,9 +187,9 @@ struct SetupArgs {
   const Cx<R>* ut;      // general frame: U_t of the parity [Nl][9][tp]
   const Cx<R>* pl;      // axial frame: the boundary link P of every line [Nl][9]
   R s;                  // boundary sign
-  Cx<R>* sinv;          // out: Sigma_t^-1 [Nl][T][144], transposed per block
-  Cx<R>* lam;           // out: Lambda [Nl][144], transposed
-  Cx<R>* zv;            // out: Z = T_0^-1 V [Nl][T][144], transposed per time slice like sinv
+  Cx<R>* sinv;          // out: Sigma_t^-1 [Nl][T][144], row-major per block
+  Cx<R>* lam;           // out: Lambda [Nl][144], row-major
+  Cx<R>* zv;            // out: Z = T_0^-1 V [Nl][T][144], row-major per time slice
   Cx<R>* scratch;       // [lines of this launch][12][T][12]: forward sweeps of the columns of V
   int* singular;        // set to 1 if a block has no inverse
 };
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs<R>
       const int r = tid / 12, k = tid - 12 * (tid / 12);
       const Cx<R> v = aug[r][k + 12];
       prev[12 * k + r] = v;
-      S[(size_t)t * kBlk + 12 * k + r] = v;
+      S[(size_t)t * kBlk + 12 * r + k] = v;
     }
     __syncthreads();
   }
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs<R>
   auto zst = [&](int t, Cx<R> v) { scr[(size_t)t * 12 + r] = v; };
   auto zld = [&](int t) { return scr[(size_t)t * 12 + r]; };
   Cx<R> y0 = czero<R>(), yT = czero<R>();
-  Cx<R>* Z = A.zv + (size_t)l * T * kBlk + 12 * j + r;
+  Cx<R>* Z = A.zv + (size_t)l * T * kBlk + 12 * r + j;
   auto column = [&](int t, Cx<R> v) {
     Z[(size_t)t * kBlk] = v;
     if (t == 0) y0 = v;
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_qinv_setup(const SetupArgs<R>
   }
   if (tid < kBlk) {
     const int rr = tid / 12, k = tid - 12 * (tid / 12);
-    A.lam[(size_t)l * kBlk + 12 * k + rr] = aug[rr][k + 12];
+    A.lam[(size_t)l * kBlk + 12 * rr + k] = aug[rr][k + 12];
   }
 }
 
@@ -322,17 +322,69 @@ __device__ __forceinline__ void cp_async(Cx<R>* dst, const Cx<R>* src) {
                "l"(__cvta_generic_to_global(src)), "n"((int)sizeof(Cx<R>))
                : "memory");
 }
+// 16 bytes: two FP32 or one FP64 complex element (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+// elements k and k + 1 of a 16-byte aligned row in shared memory
+__device__ __forceinline__ void ld_pair(const Cx<float>* p, Cx<float>& a, Cx<float>& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = mk<float>(v.x, v.y);
+  b = mk<float>(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const Cx<double>* p, Cx<double>& a, Cx<double>& b) {
+  a = p[0];
+  b = p[1];
+}
+// lane row of 12 block elements from global src (16-byte aligned) to shared dst
+template <typename R>
+__device__ __forceinline__ void cp_row(Cx<R>* dst, const Cx<R>* src) {
+  constexpr int per = 16 / (int)sizeof(Cx<R>);
+#pragma unroll
+  for (int i = 0; i < 12; i += per) cp_async16(dst + i, src + i);
+}
+// row . v over 12 elements, two accumulators
+template <typename R>
+__device__ __forceinline__ Cx<R> row_dot(const Cx<R>* row, const Cx<R>* v) {
+  Cx<R> a0 = czero<R>(), a1 = czero<R>();
+#pragma unroll
+  for (int k = 0; k < 12; k += 2) {
+    Cx<R> m0, m1, v0, v1;
+    ld_pair(row + k, m0, m1);
+    ld_pair(v + k, v0, v1);
+    a0 = cfma(a0, m0, v0);
+    a1 = cfma(a1, m1, v1);
+  }
+  return a0 + a1;
+}
+// row . v with v in registers
+template <typename R>
+__device__ __forceinline__ Cx<R> row_dot_reg(const Cx<R>* row, const Cx<R> (&v)[12]) {
+  Cx<R> a0 = czero<R>(), a1 = czero<R>();
+#pragma unroll
+  for (int k = 0; k < 12; k += 2) {
+    Cx<R> m0, m1;
+    ld_pair(row + k, m0, m1);
+    a0 = cfma(a0, m0, v[k]);
+    a1 = cfma(a1, m1, v[k + 1]);
+  }
+  return a0 + a1;
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int kQGroups = 4;  // 16-lane groups per CTA of k_qinv_apply
 
-// Ring depth of k_qinv_apply, the steps whose operands are in flight: deep (FP32 6, FP64 4) for
-// few groups per SM, shallow (FP32 3, FP64 2: more CTAs per SM) for four or more sources
-template <typename R, bool DEEP>
-struct QDepth {
-  static constexpr int value = DEEP ? (sizeof(R) == 8 ? 4 : 6) : (sizeof(R) == 8 ? 2 : 3);
+// Ring of k_qinv_apply: depth (the steps whose operands are in flight; a shallower ring with more
+// CTAs per SM measured slower) and elements per lane row (12 of a block, the step's other operand,
+// and padding that keeps rows 16-byte aligned and 16-byte row reads free of bank conflicts)
+template <typename R>
+struct QRing {
+  static constexpr int depth = sizeof(R) == 8 ? 4 : 6;
+  static constexpr int row = sizeof(R) == 8 ? 13 : 14;
 };
 constexpr int kTMax = 256;  // longest time line
 
@@ -342,11 +394,11 @@ constexpr int kTMax = 256;  // longest time line
 // per-group ring of D steps in shared memory that the lane fills D - 1 steps ahead with cp.async;
 // a lane reads only what it copied itself, so the ring needs no barrier. z_t and chi_t go through
 // out and come back two steps ahead of their use.
-template <typename R, bool AX, bool DEEP>
+template <typename R, bool AX>
 __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R> A) {
-  constexpr int D = QDepth<R, DEEP>::value;
-  __shared__ Cx<R> ring[kQGroups][D][13][12];
-  __shared__ Cx<R> gsh[kQGroups][kGrp];
+  constexpr int D = QRing<R>::depth, RW = QRing<R>::row;
+  __shared__ __align__(16) Cx<R> ring[kQGroups][D][12][RW];
+  __shared__ __align__(16) Cx<R> gsh[kQGroups][kGrp];
   __shared__ int stab[kTMax];  // slot of every time
   const Geom& g = A.g;
   for (int i = threadIdx.x; i < g.tp; i += blockDim.x) stab[i] = slot_of(g, i);
@@ -364,10 +416,10 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
   const Cx<R>* in = A.in + base + (size_t)(A.swap_in ? (rc + 6) % 12 : rc) * tp;
   Cx<R>* out = A.out + base + (size_t)rc * tp;
   const Cx<R>* xp = A.xpost ? A.xpost + base + (size_t)rc * tp : nullptr;
-  const Cx<R>* S = A.sinv + (size_t)l * T * kBlk + rc;  // lane rc's entries: S[t * 144 + 12 k]
-  const Cx<R>* Zl = A.zv + (size_t)l * T * kBlk + rc;
+  const Cx<R>* S = A.sinv + (size_t)l * T * kBlk + 12 * rc;  // lane rc's row: S[t * 144 + k]
+  const Cx<R>* Zl = A.zv + (size_t)l * T * kBlk + 12 * rc;
   const Cx<R>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
-  Cx<R>(*rg)[13][12] = ring[gi];
+  Cx<R>(*rg)[12][RW] = ring[gi];
   Cx<R>* sh = gsh[gi];
 
   // forward sweep: z_t to out
@@ -375,13 +427,9 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
   {
     auto issue = [&](int t) {  // step t: b_t, and for lanes 0-5 row rc of Sigma_{t-1}^-1
       if (t < T && act) {
-        Cx<R>(*d)[12] = rg[t % D];
-        cp_async<R>(&d[12][rc], in + stab[t]);
-        if (t >= 1 && r < 6) {
-          const Cx<R>* src = S + (size_t)(t - 1) * kBlk;
-#pragma unroll
-          for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
-        }
+        Cx<R>* d = rg[t % D][rc];
+        cp_async<R>(d + 12, in + stab[t]);
+        if (t >= 1 && r < 6) cp_row<R>(d, S + (size_t)(t - 1) * kBlk);
       }
       cp_commit();
     };
@@ -389,21 +437,12 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
     for (int t = 0; t < T; ++t) {
       issue(t + D - 1);
       cp_wait<D - 1>();
-      Cx<R>(*d)[12] = rg[t % D];
-      Cx<R> b = act ? d[12][rc] : czero<R>();
+      const Cx<R>* d = rg[t % D][rc];
+      Cx<R> b = act ? d[12] : czero<R>();
       if (t > 0) {
         if (act) sh[rc] = z;
         __syncwarp(mask);
-        Cx<R> w = czero<R>();
-        if (r < 6) {
-          Cx<R> w1 = czero<R>();
-#pragma unroll
-          for (int kk = 0; kk < 12; kk += 2) {
-            w = cfma(w, d[kk][rc], sh[kk]);
-            w1 = cfma(w1, d[kk + 1][rc], sh[kk + 1]);
-          }
-          w = w + w1;
-        }
+        const Cx<R> w = r < 6 ? row_dot(d, sh) : czero<R>();
         __syncwarp(mask);
         if (r < 6) sh[rc] = w;
         __syncwarp(mask);
@@ -429,10 +468,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
   {
     auto issue = [&](int u) {  // step u (t = N_t - 1 - u): row rc of Sigma_t^-1
       if (u < T && act) {
-        Cx<R>(*d)[12] = rg[u % D];
-        const Cx<R>* src = S + (size_t)(T - 1 - u) * kBlk;
-#pragma unroll
-        for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
+        cp_row<R>(rg[u % D][rc], S + (size_t)(T - 1 - u) * kBlk);
       }
       cp_commit();
     };
@@ -444,7 +480,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
       const int t = T - 1 - u;
       issue(u + D - 1);
       cp_wait<D - 1>();
-      Cx<R>(*d)[12] = rg[u % D];
+      const Cx<R>* d = rg[u % D][rc];
       Cx<R> v = zt;
       zt = znext;
       if (act && t >= 2) znext = out[stab[t - 2]];  // used two steps on
@@ -464,16 +500,7 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
       }
       if (act) sh[rc] = v;
       __syncwarp(mask);
-      y = czero<R>();
-      if (act) {
-        Cx<R> y1 = czero<R>();
-#pragma unroll
-        for (int kk = 0; kk < 12; kk += 2) {
-          y = cfma(y, d[kk][rc], sh[kk]);
-          y1 = cfma(y1, d[kk + 1][rc], sh[kk + 1]);
-        }
-        y = y + y1;
-      }
+      y = act ? row_dot(d, sh) : czero<R>();
       __syncwarp(mask);
       if (act) out[stab[t]] = y;
       if (t == 0) y0 = y;
@@ -500,11 +527,9 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
     const bool post = xp != nullptr;
     auto issue = [&](int t) {  // step t: row rc of Z_t, and xpost_t
       if (t < T && act) {
-        Cx<R>(*d)[12] = rg[t % D];
-        const Cx<R>* src = Zl + (size_t)t * kBlk;
-#pragma unroll
-        for (int kk = 0; kk < 12; ++kk) cp_async<R>(&d[kk][rc], src + 12 * kk);
-        if (post) cp_async<R>(&d[12][rc], xp + stab[t]);
+        Cx<R>* d = rg[t % D][rc];
+        cp_row<R>(d, Zl + (size_t)t * kBlk);
+        if (post) cp_async<R>(d + 12, xp + stab[t]);
       }
       cp_commit();
     };
@@ -514,14 +539,13 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
     for (int t = 0; t < T; ++t) {
       issue(t + D - 1);
       cp_wait<D - 1>();
-      Cx<R>(*d)[12] = rg[t % D];
+      const Cx<R>* d = rg[t % D][rc];
       Cx<R> x = ct;
       ct = cnext;
       if (act && t + 2 < T) cnext = out[stab[t + 2]];
       if (act) {
-#pragma unroll
-        for (int kk = 0; kk < 12; ++kk) x = x - cmul(d[kk][rc], cv[kk]);
-        out[stab[t]] = post ? d[12][rc] + A.apost * x : x;
+        x = x - row_dot_reg(d, cv);
+        out[stab[t]] = post ? d[12] + A.apost * x : x;
       }
     }
     cp_wait<0>();
@@ -658,18 +682,10 @@ void qinv(wf_handle* h, const QFactors<R>& F, int p, const Cx<R>* in, Cx<R>* out
   const size_t groups = (size_t)nrhs * h->g.Nl;
   const unsigned blocks = (unsigned)((groups + kQGroups - 1) / kQGroups);
   Prof P(h, tag<R>("qinv_apply_f64", "qinv_apply_f32"));
-  const bool deep = nrhs < 4;
-  if (h->axial) {
-    if (deep)
-      k_qinv_apply<R, true, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
-    else
-      k_qinv_apply<R, true, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
-  } else {
-    if (deep)
-      k_qinv_apply<R, false, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
-    else
-      k_qinv_apply<R, false, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
-  }
+  if (h->axial)
+    k_qinv_apply<R, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+  else
+    k_qinv_apply<R, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
   WF_CUDA(cudaGetLastError());
 }
 

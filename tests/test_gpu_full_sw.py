@@ -4,9 +4,9 @@ Preconditioning with Clover") against ``oracle/clover.py``.
 Q^-1 = (A + mu - D_t)^-1 (FP64 1e-12, FP32 1e-5) and M-hat_full with its adjoint (same
 tolerances) on lattices with several warps, padded and odd time lines, a 160-site line (five
 sites per lane), both boundary conditions and both frames, with two and five sources; without a
-clover term Q^-1 equals the Wilson C_R C_L; solves of M_SW in FP64 and by FP32 defect correction to the oracle-checked 1e-10
-true residual, in the oracle's iteration count (FP64); host arrays; and the errors (precision,
-arguments, iteration limit, NaN source).
+clover term Q^-1 equals the Wilson C_R C_L; solves of M_SW in FP64 and by FP32 defect correction
+to the oracle-checked 1e-10 true residual, in the oracle's iteration count (FP64); host arrays;
+and the errors (precision, arguments, iteration limit, NaN source).
 """
 
 import numpy as np
@@ -76,7 +76,7 @@ def test_qinv(case):
 
 
 def test_qinv_many_sources(case):
-    """Five sources: the launch configuration for four or more sources (a shallower operand ring)."""
+    """Five sources: groups of one CTA on different lines and sources; their FP32 solve."""
     key, p, U, Acl, eta, w = case
     if key not in ((4, 12), (2, 160)):
         pytest.skip("two layouts suffice")
