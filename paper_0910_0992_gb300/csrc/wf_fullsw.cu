@@ -322,9 +322,10 @@ __device__ __forceinline__ void cp_async(Cx<R>* dst, const Cx<R>* src) {
                "l"(__cvta_generic_to_global(src)), "n"((int)sizeof(Cx<R>))
                : "memory");
 }
-// 16 bytes: two FP32 or one FP64 complex element (both addresses 16-byte aligned)
+// 16 bytes: two FP32 or one FP64 complex element (both addresses 16-byte aligned), cached in L1
+// so that the sources of one line on an SM share the rows
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
                "l"(__cvta_generic_to_global(src))
                : "memory");
 }
