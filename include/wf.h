@@ -267,10 +267,11 @@ int wf_apply_ilu_f32(wf_handle_t* h, const double* in, double* out, int dagger, 
  *   M-hat_full = 1 - gamma_f^-2 (Q^oo)^-1 D_s^oe (Q^ee)^-1 D_s^eo
  * (Eq. TPrecFull with C_L = Q^-1, C_R = 1). A is the term of wf_load_gauge_clover, or 0 if none is
  * loaded (then Q = mu - D_t = C_L^-1 C_R^-1). Q^-1 is the appendix's single Woodbury step
- * Q = T_0 + V W^dag around the open chain T_0, which the library factors by block LU (on
- * every call of these entry points, in the precision of the call: the blocks Sigma_t^-1 and the
- * Woodbury columns T_0^-1 V, 4.6 KB of device memory per site in FP64, 2.3 KB in FP32) instead of
- * the paper's inner CG.
+ * Q = T_0 + V W^dag around the open chain T_0, which the library factors by block LU instead of
+ * the paper's inner CG, in the precision of the call: the blocks Sigma_t^-1 and the Woodbury
+ * columns T_0^-1 V, 4.6 KB of device memory per site in FP64, 2.3 KB in FP32. The factors are kept
+ * for later calls; every call first compares a 64-bit fingerprint of the arrays they were formed
+ * from (clover term, U_t or P, frame) with the current ones and factors again on a change.
  * wf_apply_Qinv: out = Q^-1 in on full fields [rhs][V][spin][colour]; _f32: FP32 applies.
  * wf_apply_schur_full_sw: out = M-hat_full in (dagger: its adjoint) on odd fields as for
  *   wf_apply_schur; _f32: FP32 arithmetic.

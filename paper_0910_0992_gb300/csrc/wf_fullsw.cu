@@ -603,11 +603,76 @@ const char* tag(const char* f64, const char* f32) {
 }
 
 
+// The finalizer of Steele, Lea and Flood's SplitMix64 generator, a 64-bit mixing function
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+// *out += sum over words i of mix64(w_i + (i + 1) golden + salt) (mod 2^64): a fingerprint of the
+// n words that does not depend on the order in which threads add their parts
+__global__ void __launch_bounds__(256) k_fingerprint(const unsigned long long* __restrict__ w, size_t n,
+                                                     unsigned long long salt, unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc += mix64(w[i] + (i + 1) * 0x9e3779b97f4a7c15ull + salt);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// Whether the factors of precision R on the handle were formed from the gauge field and clover
+// term it holds now. The factors depend on the frame, the presence of a clover term and the
+// arrays the setup reads (clover blocks, U_t or P of both parities); a 64-bit fingerprint of those
+// is kept beside the factors, and *key receives the current one.
+template <typename R>
+bool qinv_current(wf_handle* h, unsigned long long* key) {
+  const Geom& g = h->g;
+  cudaStream_t s = h->stream;
+  unsigned long long* kb = h->buf<unsigned long long>(tag<R>("fsw_key_f64", "fsw_key_f32"), 3);
+  WF_CUDA(cudaMemsetAsync(kb, 0, sizeof(unsigned long long), s));
+  auto add = [&](const void* p, size_t bytes, unsigned long long salt) {
+    const size_t n = bytes / sizeof(unsigned long long);
+    const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8));
+    Prof P(h, "fsw_fingerprint");
+    k_fingerprint<<<blocks, 256, 0, s>>>(static_cast<const unsigned long long*>(p), n, salt, kb);
+    WF_CUDA(cudaGetLastError());
+  };
+  for (int p = 0; p < 2; ++p) {
+    if (h->clover) add(clover_of<R>(h, p), (size_t)g.Nl * 72 * g.tp * sizeof(Cx<R>), 0x1000ull + p);
+    if (h->axial)
+      add(gauge_pl<R>(h, p), (size_t)g.Nl * 9 * sizeof(Cx<R>), 0x2000ull + p);
+    else
+      add(gauge_ut<R>(h, p), (size_t)g.Nl * 9 * g.tp * sizeof(Cx<R>), 0x3000ull + p);
+  }
+  unsigned long long hk[3];
+  WF_CUDA(cudaMemcpyAsync(hk, kb, sizeof(hk), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  *key = hk[0] ^ (h->axial ? 0x5bd1e995ull : 0ull) ^ (h->clover ? 0xc2b2ae35ull << 32 : 0ull);
+  return hk[2] == 1 && hk[1] == *key;
+}
+
+// Record (valid = 1) or withdraw (valid = 0) the fingerprint of the factors of precision R
+template <typename R>
+void qinv_mark(wf_handle* h, unsigned long long key, unsigned long long valid) {
+  unsigned long long* kb = h->buf<unsigned long long>(tag<R>("fsw_key_f64", "fsw_key_f32"), 3);
+  const unsigned long long v[2] = {key, valid};
+  WF_CUDA(cudaMemcpyAsync(kb + 1, v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+  WF_CUDA(cudaStreamSynchronize(h->stream));
+}
+
 // Factor T_0 and form Lambda on every line of both parities from the handle's gauge field and
 // clover term (A = 0 without one), in precision R from the gauge and clover copies of that
-// precision.
+// precision; kept until the gauge field, the clover term or the frame changes.
 template <typename R>
 void qinv_setup(wf_handle* h) {
+  unsigned long long key = 0;
+  if (qinv_current<R>(h, &key)) return;
+  qinv_mark<R>(h, key, 0);  // a factorisation that fails part-way leaves no valid mark
   const Geom& g = h->g;
   cudaStream_t s = h->stream;
   const int w = sizeof(R) == 8 ? 0 : 1;
@@ -645,6 +710,7 @@ void qinv_setup(wf_handle* h) {
   WF_CUDA(cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, s));
   WF_CUDA(cudaStreamSynchronize(s));
   if (sing) throw Error(WF_ESINGULAR, "a block of mu + A - D_t on a time line has no inverse");
+  qinv_mark<R>(h, key, 1);
 }
 
 template <typename R>

@@ -4,7 +4,7 @@ Preconditioning with Clover") against ``oracle/clover.py``.
 Q^-1 = (A + mu - D_t)^-1 (FP64 1e-12, FP32 1e-5) and M-hat_full with its adjoint (same
 tolerances) on lattices with several warps, padded and odd time lines, a 160-site line (five
 sites per lane), both boundary conditions and both frames, with two and five sources; without a
-clover term Q^-1 equals the Wilson C_R C_L; solves of M_SW in FP64 and by FP32 defect correction
+clover term Q^-1 equals the Wilson C_R C_L; the kept factors follow every reload of the field; solves of M_SW in FP64 and by FP32 defect correction
 to the oracle-checked 1e-10 true residual, in the oracle's iteration count (FP64); host arrays;
 and the errors (precision, arguments, iteration limit, NaN source).
 """
@@ -152,6 +152,33 @@ def test_without_clover_term_q_is_the_wilson_block(axial):
         zero = np.zeros(U.shape[:4] + (4, 3, 4, 3), dtype=np.complex128)
         assert _rel(got, CL.Q_inverse(U, zero, eta, p)) < 1e-12
         assert _rel(got, w.apply_C(w.apply_C(x, 0), 1).cpu().numpy()) < 1e-12
+    finally:
+        w.close()
+
+
+@pytest.mark.parametrize("axial", [True, False], ids=["axial", "general"])
+def test_factors_follow_the_loaded_field(axial):
+    """The factors are reused while the field is unchanged and formed again after every reload:
+    another gauge field, other clover coefficients, no clover term, and the first field again."""
+    L, T, ks, xi, bc = 4, 12, 0.07, 3.5, -1
+    p = W.Params(L, T, ks, xi=xi, bc=bc)
+    U1, U2 = S.random_gauge(L, T, 0.3, 50), S.random_gauge(L, T, 0.3, 51)
+    eta = S.gaussian_source(L, T, 150, nrhs=1)
+    zero = np.zeros(U1.shape[:4] + (4, 3, 4, 3), dtype=np.complex128)
+    w = wf.Wilson(L, T, ks, kappa_t=xi * ks, bc=bc, axial=axial)
+    try:
+        x = _dev(eta)
+        for U, cs, ct in ((U1, 1.0, 0.9), (U1, 1.0, 0.9), (U2, 1.0, 0.9), (U2, 0.6, 1.2), (U2, None, None),
+                          (U1, 1.0, 0.9)):
+            if cs is None:
+                w.load_gauge(U)
+                Acl = zero
+            else:
+                w.load_gauge_clover(U, cs, ct)
+                Acl = CL.clover_term(U, cs, ct)
+            ref = CL.Q_inverse(U, Acl, eta, p)
+            for f32, tol in ((False, 1e-12), (True, 1e-5), (False, 1e-12)):
+                assert _rel(w.apply_Qinv(x, f32=f32).cpu().numpy(), ref) < tol
     finally:
         w.close()
 
