@@ -73,8 +73,9 @@ __device__ __forceinline__ Cx<R> row_times(const Cx<R>* __restrict__ B, int r, c
   return acc;
 }
 
-// One solve T_0 y = b on one line by a 16-lane group: lane r < 12 holds component r, lanes 12-15
-// only join the group's barriers (mask). S: the line's Sigma_t^-1 blocks [T][144]; ut: the line's
+// One solve T_0 y = b on one line by a 16-lane group, as the setup runs it for the columns of V
+// (the apply kernel has its own sweeps, fed ahead through shared memory): lane r < 12 holds
+// component r, lanes 12-15 only join the group's barriers (mask). S: the line's Sigma_t^-1 blocks [T][144]; ut: the line's
 // U_t [9][tp] (general frame; unused in the axial frame, where W_t = 1). rhs(t): component r of
 // b_t; zst / zld: store / load component r of the forward sweep's z_t; out(t, y): component r of
 // y_t, produced for t = N_t - 1 down to 0. sh: the group's 16-element exchange vector.
