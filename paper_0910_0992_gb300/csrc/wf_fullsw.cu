@@ -556,6 +556,172 @@ __global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply(const QinvArgs<R
     for (int t = T; t < tp; ++t) out[stab[t]] = czero<R>();  // padding slots stay zero
 }
 
+// The same Q^-1 for four or more sources: a CTA holds kQGroups consecutive sources of one line,
+// which read the same block rows, so one ring serves all its groups. The first group's lanes fill
+// it D - 1 steps ahead; a CTA barrier per step publishes a slot to every group and also tells the
+// filling lanes that the slot they refill next has been read. Each group's own operands (b_t,
+// z_t, chi_t and the post-axpy operand) come from global memory two steps ahead in registers.
+// Groups past the last source compute on zeros and store nothing, but join every barrier.
+template <typename R, bool AX>
+__global__ void __launch_bounds__(kQGroups * kGrp) k_qinv_apply_shared(const QinvArgs<R> A) {
+  constexpr int D = QRing<R>::depth, RW = QRing<R>::row;
+  __shared__ __align__(16) Cx<R> ring[D][12][RW];
+  __shared__ __align__(16) Cx<R> gsh[kQGroups][kGrp];
+  __shared__ int stab[kTMax];  // slot of every time
+  const Geom& g = A.g;
+  for (int i = threadIdx.x; i < g.tp; i += blockDim.x) stab[i] = slot_of(g, i);
+  __syncthreads();
+  const int q = threadIdx.x, r = q % kGrp, gi = q / kGrp;
+  const unsigned mask = 0xFFFFu << (q & 16);
+  const int nq = (A.nrhs + kQGroups - 1) / kQGroups;
+  const int l = (int)(blockIdx.x / nq), k = (int)(blockIdx.x % nq) * kQGroups + gi;
+  const int T = g.T, tp = g.tp;
+  const bool act = r < 12;
+  const bool io = act && k < A.nrhs;   // lanes that load and store this group's source
+  const bool fill = act && gi == 0;    // lanes that fill the ring
+  const int rc = act ? r : 0;
+  const int sr = rc / 3, cr = rc - 3 * (rc / 3);
+  const size_t base = ((size_t)(k < A.nrhs ? k : 0) * g.Nl + l) * NSPIN_C * tp;
+  const Cx<R>* in = A.in + base + (size_t)(A.swap_in ? (rc + 6) % 12 : rc) * tp;
+  Cx<R>* out = A.out + base + (size_t)rc * tp;
+  const Cx<R>* xp = A.xpost ? A.xpost + base + (size_t)rc * tp : nullptr;
+  const Cx<R>* S = A.sinv + (size_t)l * T * kBlk + 12 * rc;
+  const Cx<R>* Zl = A.zv + (size_t)l * T * kBlk + 12 * rc;
+  const Cx<R>* ut = AX ? nullptr : A.ut + (size_t)l * 9 * tp;
+  Cx<R>* sh = gsh[gi];
+  auto ld = [&](const Cx<R>* p, int t) { return io && t < T ? p[stab[t]] : czero<R>(); };
+
+  // forward sweep: z_t to out
+  Cx<R> z = czero<R>();
+  {
+    auto issue = [&](int t) {  // step t: rows 0-5 of Sigma_{t-1}^-1
+      if (fill && r < 6 && t >= 1 && t < T) cp_row<R>(ring[t % D][rc], S + (size_t)(t - 1) * kBlk);
+      if (gi == 0) cp_commit();
+    };
+    for (int t = 0; t < D - 1; ++t) issue(t);
+    Cx<R> bt = ld(in, 0), bn = ld(in, 1);
+    for (int t = 0; t < T; ++t) {
+      if (gi == 0) cp_wait<D - 2>();
+      __syncthreads();
+      issue(t + D - 1);
+      const Cx<R>* d = ring[t % D][rc];
+      Cx<R> b = bt;
+      bt = bn;
+      bn = ld(in, t + 2);
+      if (t > 0) {
+        if (act) sh[rc] = z;
+        __syncwarp(mask);
+        const Cx<R> w = r < 6 ? row_dot(d, sh) : czero<R>();
+        __syncwarp(mask);
+        if (r < 6) sh[rc] = w;
+        __syncwarp(mask);
+        if (r < 6) {
+          if (AX) {
+            b = b + sh[rc];
+          } else {
+            const int sl = stab[t - 1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) b = cfmaconj(b, ut[(size_t)(3 * c + cr) * tp + sl], sh[3 * sr + c]);
+          }
+        }
+        __syncwarp(mask);
+      }
+      z = b;
+      if (io) out[stab[t]] = z;
+    }
+    if (gi == 0) cp_wait<0>();
+    __syncthreads();
+  }
+
+  // backward sweep: chi_t to out
+  Cx<R> y0 = czero<R>(), yT = czero<R>();
+  {
+    auto issue = [&](int u) {  // step u (t = N_t - 1 - u): row rc of Sigma_t^-1
+      if (fill && u < T) cp_row<R>(ring[u % D][rc], S + (size_t)(T - 1 - u) * kBlk);
+      if (gi == 0) cp_commit();
+    };
+    for (int u = 0; u < D - 1; ++u) issue(u);
+    Cx<R> zt = z;
+    Cx<R> zn = ld(out, T - 2);
+    Cx<R> y = czero<R>();
+    for (int u = 0; u < T; ++u) {
+      const int t = T - 1 - u;
+      if (gi == 0) cp_wait<D - 2>();
+      __syncthreads();
+      issue(u + D - 1);
+      const Cx<R>* d = ring[u % D][rc];
+      Cx<R> v = zt;
+      zt = zn;
+      zn = t >= 2 ? ld(out, t - 2) : czero<R>();
+      if (u > 0) {
+        if (act) sh[rc] = y;
+        __syncwarp(mask);
+        if (act && r >= 6) {
+          if (AX) {
+            v = v + sh[rc];
+          } else {
+            const int sl = stab[t];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v = cfma(v, ut[(size_t)(3 * cr + c) * tp + sl], sh[3 * sr + c]);
+          }
+        }
+        __syncwarp(mask);
+      }
+      if (act) sh[rc] = v;
+      __syncwarp(mask);
+      y = act ? row_dot(d, sh) : czero<R>();
+      __syncwarp(mask);
+      if (io) out[stab[t]] = y;
+      if (t == 0) y0 = y;
+      if (t == T - 1) yT = y;
+    }
+    if (gi == 0) cp_wait<0>();
+    __syncthreads();
+  }
+
+  // c = Lambda W^dag chi
+  if (act) sh[rc] = r < 6 ? yT : y0;
+  __syncwarp(mask);
+  Cx<R> c = czero<R>();
+  if (act) c = row_times(A.lam + (size_t)l * kBlk, rc, sh);
+  __syncwarp(mask);
+  if (act) sh[rc] = c;
+  __syncwarp(mask);
+  Cx<R> cv[12];
+#pragma unroll
+  for (int kk = 0; kk < 12; ++kk) cv[kk] = sh[kk];
+  __syncwarp(mask);
+
+  // out_t = xpost_t + apost (chi_t - Z_t c)
+  {
+    auto issue = [&](int t) {  // step t: row rc of Z_t
+      if (fill && t < T) cp_row<R>(ring[t % D][rc], Zl + (size_t)t * kBlk);
+      if (gi == 0) cp_commit();
+    };
+    for (int t = 0; t < D - 1; ++t) issue(t);
+    Cx<R> ct = ld(out, 0), cn = ld(out, 1);
+    Cx<R> xt = xp ? ld(xp, 0) : czero<R>(), xn = xp ? ld(xp, 1) : czero<R>();
+    for (int t = 0; t < T; ++t) {
+      if (gi == 0) cp_wait<D - 2>();
+      __syncthreads();
+      issue(t + D - 1);
+      const Cx<R>* d = ring[t % D][rc];
+      Cx<R> x = ct, xv = xt;
+      ct = cn;
+      cn = ld(out, t + 2);
+      if (xp) {
+        xt = xn;
+        xn = ld(xp, t + 2);
+      }
+      x = x - row_dot_reg(d, cv);
+      if (io) out[stab[t]] = xp ? xv + A.apost * x : x;
+    }
+    if (gi == 0) cp_wait<0>();
+  }
+  if (io)
+    for (int t = T; t < tp; ++t) out[stab[t]] = czero<R>();  // padding slots stay zero
+}
+
 // ----------------------------------------------------------------------------
 // Host side
 // ----------------------------------------------------------------------------
@@ -750,10 +916,17 @@ void qinv(wf_handle* h, const QFactors<R>& F, int p, const Cx<R>* in, Cx<R>* out
   const size_t groups = (size_t)nrhs * h->g.Nl;
   const unsigned blocks = (unsigned)((groups + kQGroups - 1) / kQGroups);
   Prof P(h, tag<R>("qinv_apply_f64", "qinv_apply_f32"));
-  if (h->axial)
+  if (nrhs >= kQGroups) {  // one ring per CTA of kQGroups sources of one line
+    const unsigned sblocks = (unsigned)((size_t)h->g.Nl * ((nrhs + kQGroups - 1) / kQGroups));
+    if (h->axial)
+      k_qinv_apply_shared<R, true><<<sblocks, kQGroups * kGrp, 0, h->stream>>>(a);
+    else
+      k_qinv_apply_shared<R, false><<<sblocks, kQGroups * kGrp, 0, h->stream>>>(a);
+  } else if (h->axial) {
     k_qinv_apply<R, true><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
-  else
+  } else {
     k_qinv_apply<R, false><<<blocks, kQGroups * kGrp, 0, h->stream>>>(a);
+  }
   WF_CUDA(cudaGetLastError());
 }
 
