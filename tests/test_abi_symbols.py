@@ -34,3 +34,17 @@ def test_create_rejects_bad_geometry_without_gpu():
     h = ctypes.c_void_p()
     for L, T, ks, bc in [(3, 8, 0.1, -1), (4, 1, 0.1, -1), (4, 300, 0.1, -1), (4, 8, -0.1, -1), (4, 8, 0.1, 0)]:
         assert wf.lib.wf_create(L, T, 3.0, ks, 0.0, bc, ctypes.byref(h)) == wf.WF_EINVAL
+
+
+def test_full_sw_entry_points_reject_a_null_handle_without_gpu():
+    """The full SW entry points check their handle before any device work."""
+    import paper_0910_0992_gb300 as wf
+
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    assert wf.lib.wf_apply_Qinv(None, None, None, 1) == wf.WF_EINVAL
+    assert wf.lib.wf_apply_Qinv_f32(None, None, None, 1) == wf.WF_EINVAL
+    assert wf.lib.wf_apply_schur_full_sw(None, None, None, 0, 1) == wf.WF_EINVAL
+    assert wf.lib.wf_apply_schur_full_sw_f32(None, None, None, 1, 1) == wf.WF_EINVAL
+    assert wf.lib.wf_solve_full_sw(None, None, None, 1, 1e-10, wf.WF_FP32, ctypes.byref(it),
+                                   ctypes.byref(res)) == wf.WF_EINVAL
